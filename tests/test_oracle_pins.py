@@ -1,0 +1,254 @@
+"""Pins of the CPU oracle against what the paper and the mathematics fix.
+
+Each test checks the oracle against something other than itself: values printed
+in the paper (Tables I, II-IV), closed forms (two-site energy, free fermions,
+atomic limit, the nnz formula of Sec. IV.A), invariants (Hermiticity, the
+half-filling complement of Sec. IX, Euler's theorem for the gradients) and an
+independent dense Hamiltonian built from Jordan-Wigner operator products.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from conftest import golden
+from oracle import hub_oracle as O
+from paper_1307_7542_gb300 import workloads as W
+
+
+def _random_model(M, seed, long_range=True, U_scale=4.0):
+    """Random graph on M sites (a ring plus, optionally, long-range bonds) with random
+    t, U, eps -- long bonds exercise Jordan-Wigner strings over many sites."""
+    bonds = [tuple(b) for b in W.ring_bonds(M).tolist()]
+    if long_range and M >= 4:
+        r = W.uniform(seed + 99, 2 * M)
+        for k in range(M):
+            i, j = int(r[2 * k] * M), int(r[2 * k + 1] * M)
+            if i != j and (i, j) not in bonds and (j, i) not in bonds:
+                bonds.append((i, j))
+    nb = len(bonds)
+    t = W.uniform(seed, nb, 0.3, 1.3) * np.where(W.uniform(seed + 1, nb) < 0.3, -1.0, 1.0)
+    U = W.uniform(seed + 2, M, 0.0, U_scale)
+    eps = W.uniform(seed + 3, M, -0.7, 0.7)
+    return O.Model(M, bonds, t, U, eps)
+
+
+# ---------------------------------------------------------------------------------- Table I
+
+def test_table1_basis_and_index():
+    """Table I (Sec. II): M = 3, (2, 1): the nine states in the order of Eq. count2."""
+    rows = golden("table1_M3_up2_dn1.txt")
+    B = O.basis(3, 2, 1)
+    assert B.shape == (9,)
+    for r in rows:
+        up, bu, iu, dn, bd, idn, idx = r[0], int(r[1]), int(r[2]), r[3], int(r[4]), int(r[5]), int(r[6])
+        assert int(up, 2) == bu and int(dn, 2) == bd              # strings: site 1 rightmost
+        assert idx == (idn - 1) * 3 + iu                             # Eq. count2
+        assert int(B[idx - 1]) == bu + (bd << 3)                     # Eq. 6: I = I_up + 2^M I_dn
+    # worked example: |110>|010> has index (2-1)*3 + 3 = 6
+    assert int(np.searchsorted(B, np.uint64(6 + (2 << 3)))) + 1 == 6
+
+
+@pytest.mark.parametrize("M,nu,nd,dim", [(int(r[0]), int(r[1]), int(r[2]), int(r[3])) for r in golden("dims.txt")[:4]])
+def test_printed_dimensions(M, nu, nd, dim):
+    """Hilbert-space dimensions printed in Tables II-IV; count_up*count_dn (Eq. count3)."""
+    assert O._load().hubo_basis(M, nu, nd, None) == dim
+    assert math.comb(M, nu) * math.comb(M, nd) == dim
+
+
+# ----------------------------------------------------------------------- closed forms
+
+@pytest.mark.parametrize("U", [0.0, 1.0, 4.0, 8.0])
+def test_two_site_closed_form(U):
+    """Two sites, one electron per spin: E0 = (U - sqrt(U^2 + 16 t^2)) / 2."""
+    t = 1.0
+    m = O.Model(2, W.ring_bonds(2), t, U)
+    B = O.basis(2, 1, 1)
+    H = np.column_stack([O.apply(m, B, e) for e in np.eye(B.shape[0])])
+    E0 = np.linalg.eigvalsh(H)[0]
+    assert abs(E0 - (U - math.sqrt(U * U + 16 * t * t)) / 2) < 1e-14
+
+
+@pytest.mark.parametrize("case", ["ring8", "ring10", "torus4x2", "star", "random_open"])
+def test_free_fermions(case):
+    """U = 0: E0 is the sum of the lowest N_up and N_dn one-body levels.  A wrong
+    Jordan-Wigner sign (e.g. on the periodic wrap bond) changes the spectrum."""
+    if case == "ring8":
+        m, nu, nd = O.Model(8, W.ring_bonds(8), 1.0, 0.0), 4, 4
+        ref = -9.65685424949                      # -2 sum cos(2 pi k/8) over the 4+4 lowest levels
+        assert abs(O.free_fermion_E0(m, 4, 4) - ref) < 1e-10
+    elif case == "ring10":
+        m, nu, nd = O.Model(10, W.ring_bonds(10), 1.0, 0.0), 5, 5
+        lv = np.sort(-2 * np.cos(2 * np.pi * np.arange(10) / 10))
+        assert abs(O.free_fermion_E0(m, 5, 5) - 2 * lv[:5].sum()) < 1e-12
+    elif case == "torus4x2":
+        m, nu, nd = O.Model(8, W.square_bonds(4, 2, True), 1.0, 0.0), 3, 4
+    elif case == "star":
+        p = W.aim_star(3)
+        m, nu, nd = O.Model(p["M"], p["bonds"], p["t"], 0.0, p["eps"]), 4, 3
+    else:
+        rm = _random_model(7, 11)
+        m, nu, nd = O.Model(7, rm.bonds, rm.t, 0.0, rm.eps), 3, 2
+    B = O.basis(m.M, nu, nd)
+    res = O.lanczos(m, B, W.normal(5, B.shape[0]), maxit=400, tol=1e-13)
+    assert abs(res["E0"] - O.free_fermion_E0(m, nu, nd)) < 1e-9
+
+
+@pytest.mark.parametrize("M,nu,nd", [(6, 3, 3), (6, 4, 5), (5, 5, 2), (4, 4, 4)])
+def test_atomic_limit(M, nu, nd):
+    """t = 0: H is diagonal, E0 = U * max(0, N_up + N_dn - M) (uniform U), and H x = diag x."""
+    U = 3.5
+    m = O.Model(M, W.ring_bonds(M), 0.0, U)
+    B = O.basis(M, nu, nd)
+    x = W.normal(1, B.shape[0])
+    d = O.apply(m, B, np.ones(B.shape[0]))
+    assert abs(d.min() - U * max(0, nu + nd - M)) < 1e-14
+    np.testing.assert_allclose(O.apply(m, B, x), d * x, rtol=0, atol=1e-14)
+
+
+def test_diagonal_when_one_spin_is_full():
+    """Sec. III.B: when N_up or N_dn equals M every diagonal element is U*min(N_up, N_dn)."""
+    U = 2.5
+    for M, nu, nd in [(5, 5, 2), (6, 3, 6)]:
+        m = O.Model(M, W.ring_bonds(M), 1.0, U)
+        B = O.basis(M, nu, nd)
+        assert np.all(np.abs(O.diagonal(m, B) - U * min(nu, nd)) < 1e-14)
+
+
+@pytest.mark.parametrize("lat", ["ring8", "torus4x2", "open3x3", "star8"])
+def test_nnz_formula(lat):
+    """Sec. IV.A: nnz(H_sigma) = F*C(M-2, N_sigma-1) with F = 2*(number of bonds), and the
+    off-diagonal nonzeros of H are nnz(H_up)*count_dn + nnz(H_dn)*count_up."""
+    bonds = {"ring8": W.ring_bonds(8), "torus4x2": W.square_bonds(4, 2, True),
+             "open3x3": W.square_bonds(3, 3, False), "star8": W.star_bonds(7)}[lat]
+    M = int(bonds.max()) + 1
+    nu, nd = 4, 3
+    m = O.Model(M, bonds, 1.0, 4.0)
+    B = O.basis(M, nu, nd)
+    total = sum(O.row(m, B, n)[0].size for n in range(B.shape[0]))
+    nnz_u, nnz_d = O.nnz_spin(M, nu, len(bonds)), O.nnz_spin(M, nd, len(bonds))
+    assert total == nnz_u * math.comb(M, nd) + nnz_d * math.comb(M, nu)
+    for spin, nz in (("up", nnz_u), ("dn", nnz_d)):
+        _, rp, _, _ = O.spin_csr(m, nu, nd, spin, B)
+        assert rp[-1] == nz
+
+
+# ------------------------------------------------------------------------- invariants
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_hermitian(seed):
+    """<a, H b> = <H a, b> for random vectors (a hop and its reverse carry the same sign)."""
+    m = _random_model(8, seed)
+    B = O.basis(8, 3, 5)
+    a, b = W.normal(seed + 10, B.shape[0]), W.normal(seed + 20, B.shape[0])
+    lhs, rhs = a @ O.apply(m, B, b), O.apply(m, B, a) @ b
+    assert abs(lhs - rhs) <= 1e-12 * (abs(lhs) + 1.0)
+
+
+def test_half_filling_complement():
+    """Sec. IX: the spin basis with M - N electrons is the bit complement (masked to M bits)
+    of the N-electron basis, in reverse order."""
+    M = 8
+    for N in range(0, M + 1):
+        a = O.spin_parts(M, O.basis(M, N, 0))[0]
+        b = O.spin_parts(M, O.basis(M, M - N, 0))[0]
+        assert np.array_equal(b, (~a[::-1]) & np.uint64((1 << M) - 1))
+
+
+def test_equal_spin_matrices_identical():
+    """Sec. X: for N_up = N_dn the one-spin hopping matrices are identical."""
+    m = _random_model(7, 4)
+    up = O.spin_csr(m, 3, 3, "up")
+    dn = O.spin_csr(m, 3, 3, "dn")
+    for a, b in zip(up, dn):
+        assert np.array_equal(a, b)
+
+
+# ----------------------------------------------------------- independent dense Hamiltonian
+
+@pytest.mark.parametrize("M,nu,nd,seed", [(3, 2, 1, 0), (4, 2, 2, 1), (5, 3, 2, 2), (6, 3, 3, 3),
+                                          (6, 2, 5, 4), (6, 6, 1, 5), (5, 0, 3, 6)])
+def test_apply_matches_dense_fock(M, nu, nd, seed):
+    """The oracle's hop/sign/binary-search apply equals the dense Hamiltonian built from
+    Jordan-Wigner operator products (Eq. 1 with the ordering of Eq. 7), entry by entry."""
+    m = _random_model(M, seed)
+    B = O.basis(M, nu, nd)
+    Hd = O.dense_fock(m, nu, nd)
+    assert np.allclose(Hd, Hd.T, atol=0, rtol=0)
+    x = W.normal(seed, B.shape[0])
+    y = O.apply(m, B, x)
+    bound = np.abs(Hd) @ np.abs(x)
+    assert np.all(np.abs(y - Hd @ x) <= 1e-13 * bound + 1e-300)
+    # the columns too: H e_k reproduces every matrix element
+    for k in range(0, B.shape[0], max(1, B.shape[0] // 7)):
+        e = np.zeros(B.shape[0])
+        e[k] = 1.0
+        col = O.apply(m, B, e)
+        off = np.arange(B.shape[0]) != k
+        assert np.array_equal(col[off], Hd[off, k])                # off-diagonal: exact
+        assert abs(col[k] - Hd[k, k]) <= 1e-14 * (abs(Hd[k, k]) + 1.0)  # diagonal: summation order
+
+
+@pytest.mark.parametrize("M,nu,nd,seed", [(5, 2, 3, 7), (6, 3, 3, 8), (6, 2, 2, 9)])
+def test_lanczos_matches_dense(M, nu, nd, seed):
+    """Plain Lanczos reaches the lowest eigenvalue of the dense matrix, and psi is its
+    eigenvector (up to sign)."""
+    m = _random_model(M, seed)
+    B = O.basis(M, nu, nd)
+    w, V = np.linalg.eigh(O.dense_fock(m, nu, nd))
+    res = O.lanczos(m, B, W.normal(seed, B.shape[0]), maxit=500, tol=1e-13, want_psi=True)
+    assert abs(res["E0"] - w[0]) < 1e-10 * max(1.0, abs(w[0]))
+    if w[1] - w[0] > 1e-6:
+        assert 1.0 - abs(res["psi"] @ V[:, 0]) < 1e-9
+
+
+# ------------------------------------------------------------------------- gradients
+
+@pytest.mark.parametrize("M,nu,nd,seed", [(5, 2, 2, 12), (6, 3, 2, 13)])
+def test_gradient_vs_finite_differences(M, nu, nd, seed):
+    """Hellmann-Feynman expectations equal central finite differences of the dense lowest
+    eigenvalue, and satisfy Euler's relation sum_theta theta dE/dtheta = E0 (H is
+    homogeneous of degree one in (t, U, eps))."""
+    m = _random_model(M, seed)
+    B = O.basis(M, nu, nd)
+    w, V = np.linalg.eigh(O.dense_fock(m, nu, nd))
+    assert w[1] - w[0] > 1e-4
+    dt, dU, de = O.expectations(m, B, V[:, 0])
+    h = 1e-5
+
+    def E(t=None, U=None, eps=None):
+        mm = O.Model(M, m.bonds, m.t if t is None else t, m.U if U is None else U,
+                     m.eps if eps is None else eps)
+        return np.linalg.eigvalsh(O.dense_fock(mm, nu, nd))[0]
+
+    for b in range(m.n_bonds):
+        tp, tm = m.t.copy(), m.t.copy()
+        tp[b] += h
+        tm[b] -= h
+        assert abs((E(t=tp) - E(t=tm)) / (2 * h) - dt[b]) < 1e-7
+    for i in range(M):
+        Up, Um = m.U.copy(), m.U.copy()
+        Up[i] += h
+        Um[i] -= h
+        assert abs((E(U=Up) - E(U=Um)) / (2 * h) - dU[i]) < 1e-7
+        ep, em = m.eps.copy(), m.eps.copy()
+        ep[i] += h
+        em[i] -= h
+        assert abs((E(eps=ep) - E(eps=em)) / (2 * h) - de[i]) < 1e-7
+    assert abs(m.t @ dt + m.U @ dU + m.eps @ de - w[0]) < 1e-11
+    assert abs(de.sum() - (nu + nd)) < 1e-11                    # particle number
+
+
+# ---------------------------------------------------------------------------- Table IV
+
+@pytest.mark.slow
+def test_table4_ring14():
+    """Table IV (Sec. V): 1D ring M = 14, U = 4, t = 1, half filling, E0 = -8.0883491038.
+    The paper's plain Lanczos gives a variational (upper) estimate printed to 10
+    decimals; the converged oracle must lie within 2e-10 of it."""
+    ref = {int(r[0]): float(r[2]) for r in golden("table4_E0.txt")}[14]
+    m = O.Model(14, W.ring_bonds(14), 1.0, 4.0)
+    B = O.basis(14, 7, 7)
+    res = O.lanczos(m, B, W.normal(0, B.shape[0]), maxit=300, tol=1e-12)
+    assert res["converged"]
+    assert abs(res["E0"] - ref) < 2e-10
