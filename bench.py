@@ -1,0 +1,316 @@
+#!/usr/bin/env python
+"""Benchmark: H.x applies/s inside plain Lanczos on the 4x4 periodic Hubbard lattice.
+
+Workload: 4x4 periodic square lattice, half filling (N_up = N_dn = 8), t = 1, U = 4,
+D = 12870^2 = 165,636,900 (FP64 vectors of 1.33 GB, larger than L2), start vector
+SplitMix64/Box-Muller normal with seed 0.  One step = one Lanczos iteration of the hot
+path: the matrix-free apply w = H q plus the recurrence (two FP64 dot products, two
+axpys, a normalisation and the alpha/beta read-back).  The spin bases and hopping
+matrices are built once, before timing.
+
+Prints ONE JSON line (rank 0).  --impl reference times the CPU oracle (two-spin basis,
+binary search) on a bounded sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+MEASURED = os.path.join(ROOT, "MEASURED_PEAKS.json")
+FALLBACK_HBM_GBS = 6800.0
+# FP64 issue rate of the GB300: the nominal 1.25 TFLOP/s dense FP64 counts an FMA as two
+# flops, i.e. 152 SMs x 2 FP64 instructions/clock x 2.07 GHz = 0.629e12 instructions/s.
+FP64_INSTR_PEAK = 152 * 2 * 2.07e9
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=100)
+    p.add_argument("--warmup", type=int, default=5)
+    p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    p.add_argument("--U", type=float, default=4.0)
+    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--lanczos-iters", type=int, default=200, help="iterations of the E0 wall-time run")
+    p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
+    p.add_argument("--no-cpu-baseline", action="store_true")
+    return p.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", 0)), int(os.environ.get("LOCAL_RANK", 0)),
+            int(os.environ.get("WORLD_SIZE", 1)))
+
+
+def peaks():
+    try:
+        with open(MEASURED) as f:
+            m = json.load(f)
+        return float(m["hbm_gbs"]), "measured"
+    except Exception:
+        return FALLBACK_HBM_GBS, "fallback"
+
+
+class Clocks:
+    """nvidia-smi samples of SM clock and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile(mode="w+", suffix=".csv", delete=False)
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "100"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.p = None
+        time.sleep(0.3)
+
+    def stop(self):
+        if self.p is None:
+            return None
+        time.sleep(0.15)
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except Exception:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.count(",") >= 8]
+        os.unlink(self.f.name)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        mx = max(float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit())
+        reasons = set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            for k, n in enumerate(names):
+                if r[5 + k].strip().lower().startswith("active"):
+                    reasons.add(n)
+        sm_sorted = sorted(sm)
+        med = sm_sorted[len(sm_sorted) // 2] if sm_sorted else None
+        return {"sm_mhz": med, "sm_max_mhz": mx, "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def smi_index(local_rank):
+    vis = os.environ.get("CUDA_VISIBLE_DEVICES", "")
+    ids = [v for v in vis.split(",") if v.strip()]
+    if ids and ids[min(local_rank, len(ids) - 1)].strip().isdigit():
+        return int(ids[min(local_rank, len(ids) - 1)])
+    return local_rank
+
+
+def workload(U):
+    from paper_1307_7542_gb300 import workloads as W
+    return W.square4x4(U)
+
+
+def config_json(w, D, n_gpus):
+    return {"workload": f"4x4 periodic square lattice, half filling (8,8), t=1, U={w['U'][0]:g}",
+            "M": 16, "n_up": 8, "n_dn": 8, "dim": D, "step": "one Lanczos iteration (apply + recurrence)",
+            "vector_bytes": 8 * D, "l2": "inputs larger than L2 (1.33 GB per FP64 vector); no flush needed",
+            "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}
+
+
+# ----------------------------------------------------------------------------- CPU oracle
+
+def oracle_sample(w, x, seconds, min_rows=2000):
+    """Time the oracle's apply on the first R rows of the workload, R sized to take about
+    `seconds`; returns (applies per second, rows, elapsed, threads)."""
+    from oracle import hub_oracle as O
+    om = O.Model(w["M"], w["bonds"], w["t"], w["U"], w["eps"])
+    B = O.basis(w["M"], w["n_up"], w["n_dn"])
+    D = B.shape[0]
+    r = min_rows
+    t0 = time.perf_counter()
+    O.apply(om, B, x, rows=(0, r))
+    dt = time.perf_counter() - t0
+    R = int(min(D, max(r, r * seconds / max(dt, 1e-6))))
+    t0 = time.perf_counter()
+    O.apply(om, B, x, rows=(D // 3, min(D, D // 3 + R)))
+    el = time.perf_counter() - t0
+    return (R / D) / el, R, el, O.threads(), B, om
+
+
+def run_reference(a):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return 0
+    import numpy as np
+    from oracle import hub_oracle as O
+    from paper_1307_7542_gb300 import workloads as W
+    w = workload(a.U)
+    D = math.comb(16, 8) ** 2
+    x = W.normal(0, D)
+    om = O.Model(w["M"], w["bonds"], w["t"], w["U"], w["eps"])
+    B = O.basis(16, 8, 8)
+    # size one step (a bounded sample of rows) to about 2 s of CPU
+    r = 2000
+    t0 = time.perf_counter()
+    O.apply(om, B, x, rows=(0, r))
+    R = int(max(r, r * 2.0 / max(time.perf_counter() - t0, 1e-6)))
+    for k in range(a.warmup):
+        O.apply(om, B, x, rows=(0, R))
+    t0 = time.perf_counter()
+    for k in range(a.steps):
+        r0 = (k * 7919 * R) % (D - R)
+        O.apply(om, B, x, rows=(r0, r0 + R))
+    el = time.perf_counter() - t0
+    value = a.steps * (R / D) / el
+    sample = f"{R} of {D} output rows per step ({R / D:.2e} of one apply), {O.threads()} threads"
+    line = {"impl": "reference", "metric": "H.x applies/s (4x4 PBC half filling, U=4)",
+            "value": value, "unit": "applies/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": 1000 * el / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_json(w, D, 1),
+            "cpu_baseline": {"value": value, "unit": "applies/s", "cores": O.threads(), "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "applies/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+    return 0
+
+
+# ----------------------------------------------------------------------------- GPU arm
+
+def run_gpu(a):
+    import numpy as np
+    import torch
+    import torch.distributed as dist
+
+    rank, local, world = dist_env()
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    import __graft_entry__
+    if rank == 0 or world == 1:
+        __graft_entry__.build()
+    if world > 1:
+        dist.barrier()
+    from paper_1307_7542_gb300 import hub
+    from paper_1307_7542_gb300 import workloads as W
+
+    w = workload(a.U)
+    t_setup = time.perf_counter()
+    m = hub.Hubbard(w["M"], w["n_up"], w["n_dn"], w["bonds"], w["t"], w["U"], w["eps"])
+    setup_s = time.perf_counter() - t_setup
+    D = m.D
+    x_host = W.normal(0, D)
+    x0 = torch.from_numpy(x_host).cuda()
+    stream = torch.cuda.current_stream()
+
+    # warm-up steps
+    m.ground(x0, maxit=max(a.warmup, 1), tol=0.0)
+    torch.cuda.synchronize()
+
+    clocks = Clocks(smi_index(local)) if rank == 0 else None
+    if clocks:
+        clocks.start()
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    hub.hub_profile(m.h, True)
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    r = m.ground(x0, maxit=a.steps, tol=0.0)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
+    elapsed_ms = e0.elapsed_time(e1)
+    apply_ms, n_apply, n_kern = hub.hub_profile_read(m.h)
+    hub.hub_profile(m.h, False)
+    clk = clocks.stop() if clocks else None
+    assert r["iters"] == a.steps, r
+
+    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
+    if world > 1:
+        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
+    elapsed_ms = float(t_max.item())
+    value = world * a.steps / (elapsed_ms / 1000.0)
+
+    # apply roofline (dominant kernel)
+    apply_avg_ms = apply_ms / max(n_apply, 1)
+    nnz_u, _ = hub.hub_csr_info(m.h, 0)
+    nnz_d, _ = hub.hub_csr_info(m.h, 1)
+    nnz_H = nnz_u * m.count_dn + nnz_d * m.count_up + D           # Sec. IV.A nnz formula
+    alg_bytes = 16 * D                                             # read x, write y
+    hbm_gbs, peak_kind = peaks()
+    gbs = alg_bytes / (apply_avg_ms / 1000.0) / 1e9
+    fp64_rate = nnz_H / (apply_avg_ms / 1000.0)
+    roofline = {"bound": "alu", "kernel": "k_apply_f64", "achieved": fp64_rate / 1e12,
+                "peak": FP64_INSTR_PEAK / 1e12, "unit": "T FP64 instr/s",
+                "frac": fp64_rate / FP64_INSTR_PEAK, "traffic": None,
+                "peak_source": "derived: 152 SMs x 2 FP64 instr/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                "work_per_launch": f"nnz(H) = {nnz_H} multiply-adds",
+                "hbm": {"achieved_gbs": gbs, "peak_gbs": hbm_gbs, "frac": gbs / hbm_gbs,
+                        "peak_source": f"{peak_kind} (MEASURED_PEAKS.json hbm_gbs)" if peak_kind == "measured"
+                        else "fallback 6.8 TB/s", "algorithmic_bytes": alg_bytes},
+                "apply_ms": apply_avg_ms, "apply_launches": n_apply}
+
+    # Lanczos E0 wall time: a full run of a.lanczos_iters iterations, energy only
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    rl = m.ground(x0, maxit=a.lanczos_iters, tol=0.0)
+    torch.cuda.synchronize()
+    lanczos = {"E0": rl["E0"], "iterations": rl["iters"], "wall_s": time.perf_counter() - t0}
+
+    # end-to-end: the host-buffer apply through the C ABI (H2D + apply + D2H each step)
+    xh = torch.from_numpy(x_host).pin_memory()
+    yh = torch.empty(D, dtype=torch.float64).pin_memory()
+    hub.hub_apply_host(m.h, xh, yh)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(a.e2e_steps):
+        hub.hub_apply_host(m.h, xh, yh)
+    e2e_s = time.perf_counter() - t0
+    e2e = {"value": world * a.e2e_steps / e2e_s, "unit": "applies/s",
+           "h2d_bytes_per_step": 8 * D, "d2h_bytes_per_step": 8 * D,
+           "call": "hub_apply_host (pinned host x in, host y out)"}
+    del xh, yh
+
+    line = {"metric": "H.x applies/s (4x4 PBC half filling, U=4); Lanczos E0 wall time",
+            "value": value, "unit": "applies/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
+            "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": config_json(w, D, world), "roofline": roofline, "lanczos_e0": lanczos,
+            "setup_s": setup_s, "e2e": e2e, "gpu_launches": n_kern, "clocks": clk}
+
+    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+        aps, R, el, thr, _, _ = oracle_sample(w, x_host, a.cpu_seconds)
+        line["cpu_baseline"] = {"value": aps, "unit": "applies/s", "cores": thr, "kind": "oracle",
+                                "sample": f"oracle apply of {R} of {D} output rows ({el:.1f} s), scaled to "
+                                          f"whole applies"}
+    m.close()
+    if rank == 0:
+        print(json.dumps(line))
+    if world > 1:
+        dist.destroy_process_group()
+    return 0
+
+
+def main():
+    a = parse()
+    if a.impl == "reference":
+        return run_reference(a)
+    return run_gpu(a)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,165 @@
+/*
+ * hub.h -- C ABI of the GB300 library for matrix-free Hubbard exact diagonalisation in
+ * the one-spin-configuration basis (Sharma & Ahsan, "Organization of the Hilbert Space
+ * for Exact Diagonalization of Hubbard Model").
+ *
+ * Model (Sec. I, Eq. 1, with per-bond hopping, per-site interaction and site energy):
+ *     H = - sum_b t_b sum_sigma (c+_{i_b sigma} c_{j_b sigma} + h.c.)
+ *         + sum_i U_i n_{i up} n_{i dn} + sum_i eps_i (n_{i up} + n_{i dn}).
+ *
+ * State layout (Sec. II, Eq. count2; Sec. IV.A, the vecold reshape): a vector of the
+ * sector (N_up, N_dn) is the count_dn x count_up row-major matrix X, element
+ * (d, u) at flat index n = d * count_up + u, where u and d are the 0-based ranks of the
+ * spin strings I_up and I_dn in the ascending list of M-bit strings with N_up (N_dn)
+ * bits set.  Site i (0-based) is bit i of a spin string.  With this layout
+ *     H x = I_dn (x) H_up  +  H_dn (x) I_up  +  H_U            (Sec. IV.A, Eq. 11)
+ * i.e. Y = X H_up^T + H_dn X + diag o X.
+ *
+ * Conventions for every entry point:
+ *   - Return HUB_OK (0) on success, a negative HUB_ERR_* code on failure, or a positive
+ *     informational code.  Nothing throws across the ABI.  hub_last_error() gives a
+ *     message for the calling thread's last failure.
+ *   - Pointers named *_dev are device pointers owned by the caller, pointers named
+ *     *_host are host pointers owned by the caller.  Vectors are FP64, dense, of length
+ *     D = count_up * count_dn, 8-byte aligned.
+ *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
+ *     Calls that take a stream enqueue work on it and may return before it finishes,
+ *     except where stated.  Set-up calls (hub_basis, hub_hopping, hub_set_U) run on
+ *     the legacy default stream and return after their work is complete.
+ *   - The library allocates device memory only for what a handle owns: the spin bases,
+ *     the hopping matrices, per-state diagonal tables and the Lanczos workspace.  All of
+ *     it is released by hub_free.
+ *   - A handle is not thread-safe; calls on one handle must not overlap.
+ */
+#ifndef HUB_H
+#define HUB_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define HUB_OK 0
+#define HUB_CONVERGED_BREAKDOWN 1 /* Lanczos met an invariant subspace: E0 is exact there */
+#define HUB_ERR_ARG (-1)          /* invalid argument (sizes, sites, bonds, NULL pointers)  */
+#define HUB_ERR_OOM (-2)          /* device or host allocation failed                       */
+#define HUB_ERR_CUDA (-3)         /* a CUDA runtime call failed                             */
+#define HUB_ERR_NOCONV (-4)       /* Lanczos hit maxit before |dE0| < tol (E0 still set)    */
+#define HUB_ERR_STATE (-5)        /* call order: e.g. hub_apply before hub_hopping           */
+#define HUB_ERR_TIMEOUT (-6)      /* a device-side bounded wait gave up (batched solver)    */
+
+#define HUB_SPIN_UP 0
+#define HUB_SPIN_DN 1
+
+typedef struct hub_ctx *hub_t;
+
+/* Message for the calling thread's most recent failure ("" if none). */
+const char *hub_last_error(void);
+
+/*
+ * Sector set-up: counts and one-spin bases (Sec. II, Eqs. count2-count3, Appendix A).
+ * M sites (1 <= M <= 30), n_up, n_dn electrons (0 <= n <= M).  Builds on the GPU the
+ * ascending lists of M-bit strings with n_up and n_dn bits set (Algorithm I's order),
+ * by combinadic unranking; when n_up == n_dn the two spins share one list (Sec. X).
+ * On success *out owns the handle; release it with hub_free.
+ */
+int hub_basis(int M, int n_up, int n_dn, hub_t *out);
+
+/* count_up = C(M, n_up) and count_dn = C(M, n_dn) (Eq. count3); either pointer may be NULL. */
+int hub_dims(hub_t h, int64_t *n_up, int64_t *n_dn);
+
+/* Copy the spin basis (uint32 strings, ascending) of spin 0 (up) or 1 (down) to host. */
+int hub_get_basis(hub_t h, int spin, uint32_t *basis_host);
+
+/*
+ * One-spin hopping matrices H_up and H_dn (Sec. III.A, Eq. 8; Sec. IV.A, Eqs. 9-10),
+ * built on the GPU in CSR form.  bonds_host[2b], bonds_host[2b+1] are the 0-based sites
+ * of undirected bond b (b < n_bonds <= 256), i != j, no bond listed twice; t_host[b] its
+ * hopping.  eps_host[M] are site energies or NULL for zero.  For a spin string s and a
+ * bond (i, j) with exactly one end occupied the row of s holds the column
+ * rank(s ^ (1<<i) ^ (1<<j)) with value -t_b * (-1)^(popcount of s strictly between i
+ * and j); columns are ascending within a row.  May be called again to change t / eps.
+ */
+int hub_hopping(hub_t h, int n_bonds, const int32_t *bonds_host, const double *t_host,
+                const double *eps_host);
+
+/* On-site interaction: n_U == 1 for a uniform U, or n_U == M for per-site U_i. */
+int hub_set_U(hub_t h, int n_U, const double *U_host);
+
+/* Shape of a spin's CSR: number of nonzeros and longest row.  Either pointer may be NULL. */
+int hub_csr_info(hub_t h, int spin, int64_t *nnz, int32_t *max_row);
+
+/* Copy a spin's CSR to host: rowptr[count+1], cols[nnz] (int32), vals[nnz] (FP64). */
+int hub_get_csr(hub_t h, int spin, int32_t *rowptr_host, int32_t *cols_host, double *vals_host);
+
+/*
+ * y = H x (Sec. IV.A, Eq. 11, applied matrix-free as X H_up^T + H_dn X + diag o X;
+ * Sec. III.B for the diagonal, evaluated from popcount(I_up & I_dn) on the fly).
+ * x_dev and y_dev must not overlap.  Requires hub_hopping and hub_set_U.
+ */
+int hub_apply(hub_t h, const double *x_dev, double *y_dev, void *stream);
+
+/*
+ * The same product on host buffers: copies x_host to the device, applies H, copies the
+ * result to y_host, and returns when y_host is complete.  Uses two device vectors the
+ * handle allocates on first use.
+ */
+int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream);
+
+/*
+ * Ground state by plain Lanczos without re-orthogonalisation (Sec. IV; Sec. V).
+ * q_1 = x0/|x0| (x0_dev == NULL: a uniform [-1, 1) vector from SplitMix64, seed 0).
+ * Each iteration: w = H q_j - beta_{j-1} q_{j-1}; alpha_j = <q_j, w>; w -= alpha_j q_j;
+ * beta_j = |w|; E0_j = lowest eigenvalue of the tridiagonal T_j.  Stops when
+ * |E0_j - E0_{j-1}| < tol (tol <= 0: run exactly maxit iterations), on breakdown
+ * (beta_j <= 1e-14 |alpha_j|, returns HUB_CONVERGED_BREAKDOWN) or at maxit (returns
+ * HUB_ERR_NOCONV, *E0 still set).  If psi_dev != NULL the recurrence is run a second
+ * time to form the normalised ground-state vector.  Blocks until done; *E0 and *iters
+ * are host pointers (iters may be NULL).  Workspace: three device vectors.
+ */
+int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, double *E0,
+                       double *psi_dev, int *iters, void *stream);
+
+/* The alpha_j, beta_j of the last hub_lanczos_ground (host arrays of length >= cap). */
+int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host, int cap, int *n);
+
+/*
+ * Hellmann-Feynman gradients of E0 = <psi|H|psi> for a normalised eigenvector psi:
+ *   dE_dt[b]   = <psi| -sum_sigma (c+_i c_j + h.c.) |psi>     (dH/dt_b, per bond)
+ *   dE_dU[i]   = <psi| n_{i up} n_{i dn} |psi>                (double occupancy, per site)
+ *   dE_deps[i] = <psi| n_{i up} + n_{i dn} |psi>              (density, per site)
+ * Host outputs (n_bonds, M, M doubles); any may be NULL.  Blocks until done.
+ * For an unnormalised psi the results are the quadratic forms psi^T (dH/dtheta) psi.
+ */
+int hub_grad(hub_t h, const double *psi_dev, double *dE_dt_host, double *dE_dU_host,
+             double *dE_deps_host, void *stream);
+
+/*
+ * Vector-Jacobian product of y = H(theta) x for a cotangent ybar:
+ *   xbar_dev = H ybar (H is symmetric), and the parameter cotangents
+ *   tbar[b] = ybar^T (dH/dt_b) x, Ubar[i] = ybar^T (dH/dU_i) x, epsbar[i] = ybar^T (dH/deps_i) x
+ * (host outputs; any of the four outputs may be NULL).  Blocks until done.
+ */
+int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_dev, double *xbar_dev,
+                  double *tbar_host, double *Ubar_host, double *epsbar_host, void *stream);
+
+/*
+ * Measurement hooks (no counterpart in the paper).  hub_profile(h, 1) resets the counters
+ * and starts recording a CUDA event pair on the launching stream around every apply
+ * launch (up to 65536 launches are timed; later ones are only counted); hub_profile(h, 0)
+ * stops.  hub_profile_read waits for the recorded events and returns the summed apply
+ * time in milliseconds, the number of apply launches and the number of kernels the
+ * handle launched since profiling started.  Any output pointer may be NULL.
+ */
+int hub_profile(hub_t h, int enable);
+int hub_profile_read(hub_t h, double *apply_ms, int64_t *apply_launches, int64_t *kernel_launches);
+
+/* Release a handle and everything it owns.  NULL is ignored. */
+void hub_free(hub_t h);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* HUB_H */

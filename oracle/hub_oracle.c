@@ -24,6 +24,7 @@
  */
 #include <stdint.h>
 #include <stddef.h>
+#include <math.h>
 #ifdef _OPENMP
 #include <omp.h>
 #endif
@@ -112,20 +113,21 @@ static int hop(uint64_t I, int off, int i, int j, uint64_t *J, int *sign)
 
 /*
  * y[n - r0] = (H x)_n for rows n in [r0, r1) (the matrix-free product of Sec. IV,
- * one output row at a time).  bonds[2b], bonds[2b+1] are 0-based site ids.
- * U[M], eps[M] are per-site.  Returns 0, or HUBO_ERR_MISSING if a hopped state is
+ * one output row at a time).  With absolute != 0 every matrix element and every x_m is
+ * replaced by its absolute value, giving (|H| |x|)_n, the scale of per-entry tolerances.
+ * bonds[2b], bonds[2b+1] are 0-based site ids.  U[M], eps[M] are per-site.  Returns 0, or HUBO_ERR_MISSING if a hopped state is
  * not in the list (which would mean the list is not a closed sector).
  */
 int hubo_apply(int M, int n_bonds, const int32_t *bonds, const double *t, const double *U,
                const double *eps, const uint64_t *basis, int64_t D, const double *x, double *y,
-               int64_t r0, int64_t r1)
+               int64_t r0, int64_t r1, int absolute)
 {
     if (r0 < 0 || r1 > D || r0 > r1) return HUBO_ERR_ARG;
     int err = 0;
 #pragma omp parallel for schedule(dynamic, 4096) reduction(| : err)
     for (int64_t n = r0; n < r1; n++) {
         uint64_t I = basis[n];
-        double acc = diag_element(M, I, U, eps) * x[n];
+        double acc = absolute ? fabs(diag_element(M, I, U, eps) * x[n]) : diag_element(M, I, U, eps) * x[n];
         for (int b = 0; b < n_bonds; b++) {
             for (int s = 0; s < 2; s++) {
                 uint64_t J;
@@ -133,7 +135,7 @@ int hubo_apply(int M, int n_bonds, const int32_t *bonds, const double *t, const 
                 if (!hop(I, s * M, bonds[2 * b], bonds[2 * b + 1], &J, &sign)) continue;
                 int64_t m = find_state(basis, D, J);
                 if (m < 0) { err = 1; continue; }
-                acc += -t[b] * (double)sign * x[m];
+                acc += absolute ? fabs(t[b] * x[m]) : -t[b] * (double)sign * x[m];
             }
         }
         y[n - r0] = acc;

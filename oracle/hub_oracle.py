@@ -62,7 +62,7 @@ def _load():
         lib.hubo_basis.restype = i64
         lib.hubo_basis.argtypes = [i32, i32, i32, dp]
         lib.hubo_apply.restype = i32
-        lib.hubo_apply.argtypes = [i32, i32, dp, dp, dp, dp, dp, i64, dp, dp, i64, i64]
+        lib.hubo_apply.argtypes = [i32, i32, dp, dp, dp, dp, dp, i64, dp, dp, i64, i64, i32]
         lib.hubo_row.restype = i32
         lib.hubo_row.argtypes = [i32, i32, dp, dp, dp, i64, i64, dp, dp, i32]
         lib.hubo_expect.restype = i32
@@ -119,8 +119,9 @@ def spin_parts(M: int, I: np.ndarray):
     return I & mask, I >> np.uint64(M)
 
 
-def apply(model: Model, B: np.ndarray, x: np.ndarray, rows=None) -> np.ndarray:
-    """(H x)_n for n in rows = (r0, r1) (default: all), matrix-free (Sec. IV, Sec. V)."""
+def apply(model: Model, B: np.ndarray, x: np.ndarray, rows=None, absolute: bool = False) -> np.ndarray:
+    """(H x)_n for n in rows = (r0, r1) (default: all), matrix-free (Sec. IV, Sec. V).
+    With absolute=True: (|H| |x|)_n, every matrix element and x entry by absolute value."""
     lib = _load()
     D = B.shape[0]
     r0, r1 = (0, D) if rows is None else rows
@@ -128,7 +129,7 @@ def apply(model: Model, B: np.ndarray, x: np.ndarray, rows=None) -> np.ndarray:
     assert x.shape == (D,)
     y = np.empty(r1 - r0, dtype=np.float64)
     rc = lib.hubo_apply(model.M, model.n_bonds, _p(model.bonds), _p(model.t), _p(model.U),
-                        _p(model.eps), _p(B), D, _p(x), _p(y), r0, r1)
+                        _p(model.eps), _p(B), D, _p(x), _p(y), r0, r1, 1 if absolute else 0)
     if rc != 0:
         raise RuntimeError(f"hubo_apply failed ({rc})")
     return y
@@ -260,6 +261,27 @@ def lanczos(model: Model, B: np.ndarray, x0: np.ndarray, maxit: int = 300, tol: 
             psi += v[j + 1] * q
         out["psi"] = psi / np.linalg.norm(psi)
     return out
+
+
+def quadratic_forms(model: Model, B: np.ndarray, v: np.ndarray):
+    """Raw quadratic forms v^T (dH/dtheta) v for every bond and site (no normalisation)."""
+    lib = _load()
+    v = np.ascontiguousarray(v, dtype=np.float64)
+    dt = np.empty(model.n_bonds)
+    dU = np.empty(model.M)
+    de = np.empty(model.M)
+    rc = lib.hubo_expect(model.M, model.n_bonds, _p(model.bonds), _p(B), B.shape[0], _p(v),
+                         _p(dt), _p(dU), _p(de))
+    if rc != 0:
+        raise RuntimeError("hubo_expect failed")
+    return dt, dU, de
+
+
+def bilinear_forms(model: Model, B: np.ndarray, a: np.ndarray, b: np.ndarray):
+    """a^T (dH/dtheta) b by polarisation of the symmetric forms: (q(a+b) - q(a-b)) / 4."""
+    p = quadratic_forms(model, B, a + b)
+    m = quadratic_forms(model, B, a - b)
+    return tuple((x - y) / 4.0 for x, y in zip(p, m))
 
 
 def expectations(model: Model, B: np.ndarray, psi: np.ndarray):

@@ -1,0 +1,174 @@
+// hub_apply.cu -- the matrix-free Hamiltonian product (K3).
+//
+// Sec. IV.A, Eq. 11: H = I_dn (x) H_up + H_dn (x) I_up + H_U.  With the state stored as
+// the count_dn x count_up row-major matrix X (Eq. count2; the vecold reshape of Sec.
+// IV.A), the spin-up term is X H_up^T -- a gather inside one row of X -- and the
+// spin-down term is H_dn X -- a combination of whole rows of X (Sec. IV.A: "vecnew =
+// H_up x vecold" and "vecnew = vecold x H_dn^T", transposed to this row-major layout).
+// The diagonal (Sec. III.B) is sum_i U_i bit_i(I_up & I_dn) + eps(I_up) + eps(I_dn),
+// computed on the fly from popcount instead of Algorithm II's index_U tables.
+//
+// Kernel shape (FP64 path): one CTA per row d of X (grid-stride).  The CTA stages row d
+// in shared memory when it fits; each thread owns columns u and sums the H_up row of u
+// (gather from shared memory) and the H_dn row of d (coalesced loads of the neighbour
+// rows X[d'][u], served from L2).
+#include "hub_internal.cuh"
+
+namespace hub {
+
+__device__ __forceinline__ double diag_of(const Ham &H, uint32_t Iu, uint32_t Id, int64_t u, int64_t d) {
+  double v;
+  if (H.uniform_U) {
+    v = H.U0 * (double)__popc(Iu & Id);
+  } else {
+    v = 0.0;
+    for (uint32_t m = Iu & Id; m; m &= m - 1) v += H.U[__ffs(m) - 1];
+  }
+  if (H.has_eps) v += H.eps_up[u] + H.eps_dn[d];
+  return v;
+}
+
+template <bool kStage>
+__global__ void __launch_bounds__(512) k_apply_f64(const Ham H, const double *__restrict__ x,
+                                                   double *__restrict__ y) {
+  extern __shared__ double xs[];
+  const int64_t nu = H.n_up, nd = H.n_dn;
+  for (int64_t d = blockIdx.x; d < nd; d += gridDim.x) {
+    const double *__restrict__ xrow = x + d * nu;
+    if (kStage) {
+      for (int64_t u = threadIdx.x; u < nu; u += blockDim.x) xs[u] = xrow[u];
+      __syncthreads();
+    }
+    const uint32_t Id = H.basis_dn[d];
+    const int32_t k0 = H.rp_dn[d], k1 = H.rp_dn[d + 1];
+    for (int64_t u = threadIdx.x; u < nu; u += blockDim.x) {
+      const double xv = kStage ? xs[u] : xrow[u];
+      double acc = diag_of(H, H.basis_up[u], Id, u, d) * xv;
+      const int32_t j0 = H.rp_up[u], j1 = H.rp_up[u + 1];
+      for (int32_t k = j0; k < j1; ++k) {
+        const int32_t c = H.col_up[k];
+        acc = fma(H.val_up[k], kStage ? xs[c] : xrow[c], acc);
+      }
+      for (int32_t k = k0; k < k1; ++k) acc = fma(H.val_dn[k], x[(int64_t)H.col_dn[k] * nu + u], acc);
+      y[d * nu + u] = acc;
+    }
+    if (kStage) __syncthreads();
+  }
+}
+
+static size_t stage_bytes(const Ham &H) { return sizeof(double) * (size_t)H.n_up; }
+
+static int apply_kernels(const hub_ctx *h, const double *x, double *y, cudaStream_t s);
+
+constexpr int64_t kMaxTimed = 65536;
+
+int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
+  if (!h->prof) return apply_kernels(h, x, y, s);
+  cudaEvent_t e0 = nullptr, e1 = nullptr;
+  if (h->n_timed < kMaxTimed) {
+    if ((int64_t)h->ev_start.size() <= h->n_timed) {
+      HUB_CUDA(cudaEventCreate(&e0));
+      HUB_CUDA(cudaEventCreate(&e1));
+      h->ev_start.push_back(e0);
+      h->ev_end.push_back(e1);
+    }
+    e0 = h->ev_start[h->n_timed];
+    e1 = h->ev_end[h->n_timed];
+    HUB_CUDA(cudaEventRecord(e0, s));
+  }
+  int rc = apply_kernels(h, x, y, s);
+  if (rc) return rc;
+  if (e1) {
+    HUB_CUDA(cudaEventRecord(e1, s));
+    ++h->n_timed;
+  }
+  ++h->n_apply;
+  ++h->n_kernels;
+  return HUB_OK;
+}
+
+static int apply_kernels(const hub_ctx *h, const double *x, double *y, cudaStream_t s) {
+  const Ham H = h->view();
+  if (H.n_up == 0 || H.n_dn == 0) return HUB_OK;
+  const size_t smem = stage_bytes(H);
+  const int threads = H.n_up >= 512 ? 512 : (H.n_up >= 128 ? 256 : 64);
+  int64_t grid = H.n_dn;
+  const int64_t cap = (int64_t)num_sms() * 8;
+  if (grid > cap) grid = cap;
+  if (smem <= 200 * 1024) {
+    HUB_CUDA(cudaFuncSetAttribute(k_apply_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_apply_f64<true><<<(int)grid, threads, smem, s>>>(H, x, y);
+  } else {
+    k_apply_f64<false><<<(int)grid, threads, 0, s>>>(H, x, y);
+  }
+  HUB_LAUNCH_CHECK();
+  return HUB_OK;
+}
+
+static int check_ready(const hub_ctx *h, const char *who) {
+  if (!h) return fail(HUB_ERR_ARG, std::string(who) + ": NULL handle");
+  if (!h->have_hop) return fail(HUB_ERR_STATE, std::string(who) + ": call hub_hopping first");
+  if (!h->have_U) return fail(HUB_ERR_STATE, std::string(who) + ": call hub_set_U first");
+  return HUB_OK;
+}
+
+int ready(const hub_ctx *h, const char *who) { return check_ready(h, who); }
+
+}  // namespace hub
+
+using namespace hub;
+
+extern "C" int hub_apply(hub_t h, const double *x_dev, double *y_dev, void *stream) {
+  int rc = check_ready(h, "hub_apply");
+  if (rc) return rc;
+  if (!x_dev || !y_dev) return fail(HUB_ERR_ARG, "hub_apply: NULL vector");
+  const int64_t D = h->count[0] * h->count[1];
+  if (x_dev < y_dev + D && y_dev < x_dev + D) return fail(HUB_ERR_ARG, "hub_apply: x and y overlap");
+  return apply_launch(h, x_dev, y_dev, (cudaStream_t)stream);
+}
+
+extern "C" int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream) {
+  int rc = check_ready(h, "hub_apply_host");
+  if (rc) return rc;
+  if (!x_host || !y_host) return fail(HUB_ERR_ARG, "hub_apply_host: NULL vector");
+  const int64_t D = h->count[0] * h->count[1];
+  if (!h->hx) {
+    if (!dev_alloc((void **)&h->hx, sizeof(double) * D, "host-apply input") ||
+        !dev_alloc((void **)&h->hy, sizeof(double) * D, "host-apply output")) {
+      dev_free(h->hx);
+      h->hx = nullptr;
+      return HUB_ERR_OOM;
+    }
+  }
+  cudaStream_t s = (cudaStream_t)stream;
+  HUB_CUDA(cudaMemcpyAsync(h->hx, x_host, sizeof(double) * D, cudaMemcpyHostToDevice, s));
+  rc = apply_launch(h, h->hx, h->hy, s);
+  if (rc) return rc;
+  HUB_CUDA(cudaMemcpyAsync(y_host, h->hy, sizeof(double) * D, cudaMemcpyDeviceToHost, s));
+  HUB_CUDA(cudaStreamSynchronize(s));
+  return HUB_OK;
+}
+
+extern "C" int hub_profile(hub_t h, int enable) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_profile: NULL handle");
+  h->prof = enable != 0;
+  if (h->prof) {
+    h->n_apply = h->n_timed = h->n_kernels = 0;
+  }
+  return HUB_OK;
+}
+
+extern "C" int hub_profile_read(hub_t h, double *apply_ms, int64_t *apply_launches, int64_t *kernel_launches) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_profile_read: NULL handle");
+  double total = 0.0;
+  for (int64_t k = 0; k < h->n_timed; ++k) {
+    HUB_CUDA(cudaEventSynchronize(h->ev_end[k]));
+    float ms = 0.f;
+    HUB_CUDA(cudaEventElapsedTime(&ms, h->ev_start[k], h->ev_end[k]));
+    total += ms;
+  }
+  if (apply_ms) *apply_ms = h->n_timed ? total * (double)h->n_apply / (double)h->n_timed : 0.0;
+  if (apply_launches) *apply_launches = h->n_apply;
+  if (kernel_launches) *kernel_launches = h->n_kernels;
+  return HUB_OK;
+}

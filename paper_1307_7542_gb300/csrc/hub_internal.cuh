@@ -1,0 +1,144 @@
+// hub_internal.cuh -- handle layout, error plumbing and device helpers shared by the
+// library's translation units.  Not part of the public ABI (see include/hub.h).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/hub.h"
+
+namespace hub {
+
+constexpr int kMaxSites = 30;   // spin strings fit in uint32, two-spin index fits in int64
+constexpr int kMaxBonds = 256;
+
+// ---------------------------------------------------------------------------------------
+// Errors: every entry point returns a code; the message goes to a thread-local string.
+// ---------------------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what, const char *file, int line);
+
+#define HUB_CUDA(call)                                                        \
+  do {                                                                        \
+    cudaError_t e_ = (call);                                                  \
+    if (e_ != cudaSuccess) return ::hub::cuda_fail(e_, #call, __FILE__, __LINE__); \
+  } while (0)
+
+#define HUB_LAUNCH_CHECK() HUB_CUDA(cudaGetLastError())
+
+// ---------------------------------------------------------------------------------------
+// One-spin hopping matrix in CSR form (Sec. IV.A, Eqs. 9-10).
+// ---------------------------------------------------------------------------------------
+struct SpinCSR {
+  int32_t *rowptr = nullptr;   // [count + 1]
+  int32_t *col = nullptr;      // [nnz], ascending within a row
+  double *val = nullptr;       // [nnz], -t_b * (-1)^(electrons strictly between the sites)
+  uint32_t *scol = nullptr;    // [nnz], col | (sign bit << 31): -t_b = -t * sign for uniform t
+  uint8_t *bond = nullptr;     // [nnz], bond id of the entry (gradients)
+  int64_t nnz = 0;
+  int32_t max_row = 0;
+};
+
+struct hub_ctx_impl;
+
+// Read-only view of everything a kernel needs, passed by value.
+struct Ham {
+  int M;
+  int64_t n_up, n_dn;                 // count_up, count_dn
+  const uint32_t *basis_up, *basis_dn;
+  const int32_t *rp_up, *rp_dn;       // CSR row pointers
+  const int32_t *col_up, *col_dn;
+  const double *val_up, *val_dn;
+  const uint32_t *scol_up, *scol_dn;  // signed columns (uniform-t kernels)
+  const double *eps_up, *eps_dn;      // per-state site-energy sums (nullptr when eps == 0)
+  int uniform_U;                      // 1: U_i = U0 for all i
+  double U0;
+  double U[kMaxSites];                // per-site U_i
+  int uniform_t;                      // 1: all t_b equal to t0
+  double t0;
+  int has_eps;
+};
+
+}  // namespace hub
+
+// The handle behind the opaque hub_t.
+struct hub_ctx {
+  int device = 0;
+  int M = 0;
+  int N[2] = {0, 0};
+  int64_t count[2] = {0, 0};
+  bool shared = false;                 // N_up == N_dn: one basis and one CSR for both spins
+  uint32_t *basis[2] = {nullptr, nullptr};
+  uint64_t *binom = nullptr;           // device Pascal triangle, (kMaxSites+1)^2
+
+  bool have_hop = false;
+  int n_bonds = 0;
+  std::vector<int32_t> bonds;
+  std::vector<double> t, eps;
+  hub::SpinCSR csr[2];
+  double *eps_state[2] = {nullptr, nullptr};
+  bool has_eps = false;
+
+  bool have_U = false;
+  bool uniform_U = true;
+  double U0 = 0.0;
+  std::vector<double> U;
+
+  // Lanczos workspace (3 vectors), scalars, partial sums and the last run's coefficients.
+  double *work[3] = {nullptr, nullptr, nullptr};
+  double *psi_tmp = nullptr;
+  double *d_scal = nullptr;            // [8] device scalars
+  double *h_scal = nullptr;            // [8] pinned host mirror
+  double *partials = nullptr;          // reduction partials
+  int64_t partials_n = 0;
+  std::vector<double> alpha, beta;
+
+  // host-buffer apply
+  double *hx = nullptr, *hy = nullptr;
+
+  // measurement: event pairs around apply launches, launch counters
+  bool prof = false;
+  std::vector<cudaEvent_t> ev_start, ev_end;
+  int64_t n_apply = 0;                 // apply launches since hub_profile(h, 1)
+  int64_t n_timed = 0;                 // of which timed with an event pair
+  int64_t n_kernels = 0;               // all kernels launched since hub_profile(h, 1)
+
+  hub::Ham view() const;
+};
+
+namespace hub {
+
+// Allocation helpers: on failure they set the message and return false.
+bool dev_alloc(void **p, size_t bytes, const char *what);
+void dev_free(void *p);
+int ensure_partials(hub_ctx *h, int64_t n);
+
+// Launch helpers.
+int num_sms();
+constexpr int kReduceThreads = 256;
+
+// Deterministic FP64 reduction of partials[0..n) into *out (device), one block.
+int reduce_partials(const double *partials, int n, double *out, int mode, cudaStream_t s);
+
+// Apply entry used by Lanczos and the VJP (no argument checks).
+int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s);
+
+// Count kernel launches for the measurement hooks.
+inline void count_launch(hub_ctx *h, int n = 1) {
+  if (h->prof) h->n_kernels += n;
+}
+
+// Device helpers ------------------------------------------------------------------------
+__host__ __device__ inline int popc32(uint32_t v) {
+#ifdef __CUDA_ARCH__
+  return __popc(v);
+#else
+  return __builtin_popcount(v);
+#endif
+}
+
+}  // namespace hub

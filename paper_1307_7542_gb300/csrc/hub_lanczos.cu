@@ -1,0 +1,360 @@
+// hub_lanczos.cu -- plain Lanczos ground state (K4) on top of the matrix-free apply.
+//
+// Sec. IV: only the product H q is needed to span the Krylov space K_j(H, q); Sec. V: the
+// simplest Lanczos without re-orthogonalisation gives the ground state of Table IV.  Each
+// iteration here:  w = H q_j;  w -= beta_{j-1} q_{j-1};  alpha_j = <q_j, w>;
+// w -= alpha_j q_j;  beta_j = |w|;  q_{j+1} = w / beta_j.  The FP64 dot products are
+// reduced per block with warp shuffles, then across blocks in a fixed order, so results
+// do not depend on scheduling.  E0_j, the lowest eigenvalue of the tridiagonal T_j, is
+// found on the host by Sturm-sequence bisection; the ground-state vector comes from a
+// second pass with the eigenvector of T (inverse iteration).
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "hub_internal.cuh"
+
+namespace hub {
+
+int ready(const hub_ctx *h, const char *who);
+
+constexpr int kVecThreads = 256;
+
+static int vec_grid() { return num_sms() * 4; }
+
+__device__ __forceinline__ double warp_sum(double v) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+// Block sum into partials[blockIdx.x] (fixed order within the block).
+__device__ __forceinline__ void block_partial(double v, double *partials) {
+  __shared__ double ws[32];
+  v = warp_sum(v);
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  if (wid == 0) {
+    double s = lane < (int)(blockDim.x >> 5) ? ws[lane] : 0.0;
+    s = warp_sum(s);
+    if (lane == 0) partials[blockIdx.x] = s;
+  }
+}
+
+// partials <- sum_k a_k b_k
+__global__ void k_dot(int64_t n, const double *__restrict__ a, const double *__restrict__ b,
+                      double *__restrict__ partials) {
+  double v = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    v = fma(a[k], b[k], v);
+  block_partial(v, partials);
+}
+
+// w -= (*beta_prev) q_prev;  partials <- <q, w>
+__global__ void k_sub_dot(int64_t n, double *__restrict__ w, const double *__restrict__ q_prev,
+                          const double *__restrict__ q, const double *__restrict__ beta_prev,
+                          double *__restrict__ partials) {
+  const double bp = *beta_prev;
+  double v = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double wk = fma(-bp, q_prev[k], w[k]);
+    w[k] = wk;
+    v = fma(q[k], wk, v);
+  }
+  block_partial(v, partials);
+}
+
+// w -= (*alpha) q;  partials <- |w|^2
+__global__ void k_sub_norm(int64_t n, double *__restrict__ w, const double *__restrict__ q,
+                           const double *__restrict__ alpha, double *__restrict__ partials) {
+  const double a = *alpha;
+  double v = 0.0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    double wk = fma(-a, q[k], w[k]);
+    w[k] = wk;
+    v = fma(wk, wk, v);
+  }
+  block_partial(v, partials);
+}
+
+// w /= *beta; the first thread also records beta as the next beta_prev.
+__global__ void k_scale_inv(int64_t n, double *__restrict__ w, double *__restrict__ scal) {
+  const double inv = 1.0 / scal[1];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    w[k] *= inv;
+  if (blockIdx.x == 0 && threadIdx.x == 0) scal[2] = scal[1];
+}
+
+// dst = src / *nrm
+__global__ void k_copy_scaled(int64_t n, double *__restrict__ dst, const double *__restrict__ src,
+                              const double *__restrict__ nrm) {
+  const double inv = 1.0 / *nrm;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    dst[k] = src[k] * inv;
+}
+
+// v /= *nrm (in place)
+__global__ void k_scale_by(int64_t n, double *__restrict__ v, const double *__restrict__ nrm) {
+  const double inv = 1.0 / *nrm;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    v[k] *= inv;
+}
+
+// y += a x
+__global__ void k_axpy(int64_t n, double a, const double *__restrict__ x, double *__restrict__ y) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    y[k] = fma(a, x[k], y[k]);
+}
+
+// w = H q already in w:  w -= a q + b q_prev;  then w /= c  (second pass, known coefficients)
+__global__ void k_recur(int64_t n, double *__restrict__ w, const double *__restrict__ q,
+                        const double *__restrict__ q_prev, double a, double b, double inv_c) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    w[k] = (w[k] - a * q[k] - b * q_prev[k]) * inv_c;
+}
+
+// Start vector for x0 == NULL: uniform [-1, 1) from SplitMix64 (seed 0, counter k).
+__global__ void k_splitmix_uniform(int64_t n, double *__restrict__ out) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    uint64_t z = (uint64_t)(k + 1) * 0x9E3779B97F4A7C15ull;
+    z = (z ^ (z >> 30)) * 0xBF58476D1CE4E5B9ull;
+    z = (z ^ (z >> 27)) * 0x94D049BB133111EBull;
+    z ^= z >> 31;
+    out[k] = (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host: symmetric tridiagonal T (diag a[0..k), off-diagonal b[0..k-1)).
+// ---------------------------------------------------------------------------------------
+
+// Number of eigenvalues of T smaller than x (Sturm sequence of the LDL^T pivots).
+static int sturm_count(const double *a, const double *b, int k, double x) {
+  int cnt = 0;
+  double d = 1.0;
+  for (int i = 0; i < k; ++i) {
+    double bb = i ? b[i - 1] * b[i - 1] : 0.0;
+    d = (a[i] - x) - (i ? bb / d : 0.0);
+    if (d == 0.0) d = -1e-300;
+    if (d < 0.0) ++cnt;
+  }
+  return cnt;
+}
+
+double tridiag_lowest(const double *a, const double *b, int k) {
+  if (k == 1) return a[0];
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = 0; i < k; ++i) {
+    double r = (i ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+    lo = fmin(lo, a[i] - r);
+    hi = fmax(hi, a[i] + r);
+  }
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(a, b, k, mid) >= 1) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
+// Eigenvector of T for eigenvalue lam by inverse iteration (tridiagonal LU with partial
+// pivoting), normalised, first nonzero component positive.
+std::vector<double> tridiag_vector(const double *a, const double *b, int k, double lam) {
+  std::vector<double> v(k, 1.0);
+  if (k == 1) return v;
+  const double scale = fabs(lam) + 1.0;
+  const double shift = lam - 1e-13 * scale;   // keep T - shift*I nonsingular
+  // U has three diagonals u0, u1, u2; L multipliers m and pivot flags
+  std::vector<double> u0(k), u1(k), u2(k), m(k), dl(k), dd(k), du(k);
+  std::vector<char> piv(k, 0);
+  for (int i = 0; i < k; ++i) {
+    dd[i] = a[i] - shift;
+    du[i] = i < k - 1 ? b[i] : 0.0;
+    dl[i] = i < k - 1 ? b[i] : 0.0;   // sub-diagonal entry (i+1, i)
+  }
+  // Gaussian elimination on rows i, i+1 with partial pivoting
+  double c0 = dd[0], c1 = du[0], c2 = 0.0;   // current row i: (c0 at col i, c1 at i+1, c2 at i+2)
+  for (int i = 0; i < k - 1; ++i) {
+    double r0 = dl[i], r1 = dd[i + 1], r2 = i + 1 < k - 1 ? du[i + 1] : 0.0;   // row i+1 at cols i, i+1, i+2
+    if (fabs(r0) > fabs(c0)) {   // swap rows
+      piv[i] = 1;
+      std::swap(c0, r0);
+      std::swap(c1, r1);
+      std::swap(c2, r2);
+    }
+    if (c0 == 0.0) c0 = 1e-300;
+    m[i] = r0 / c0;
+    u0[i] = c0;
+    u1[i] = c1;
+    u2[i] = c2;
+    c0 = r1 - m[i] * c1;
+    c1 = r2 - m[i] * c2;
+    c2 = 0.0;
+  }
+  u0[k - 1] = c0 == 0.0 ? 1e-300 : c0;
+  u1[k - 1] = 0.0;
+  u2[k - 1] = 0.0;
+  for (int rep = 0; rep < 3; ++rep) {
+    // forward: apply L^-1 with the recorded swaps
+    for (int i = 0; i < k - 1; ++i) {
+      if (piv[i]) std::swap(v[i], v[i + 1]);
+      v[i + 1] -= m[i] * v[i];
+    }
+    // backward: U x = v
+    for (int i = k - 1; i >= 0; --i) {
+      double s = v[i];
+      if (i + 1 < k) s -= u1[i] * v[i + 1];
+      if (i + 2 < k) s -= u2[i] * v[i + 2];
+      v[i] = s / u0[i];
+    }
+    double nrm = 0.0;
+    for (double x : v) nrm += x * x;
+    nrm = sqrt(nrm);
+    for (double &x : v) x /= nrm;
+  }
+  for (int i = 0; i < k; ++i)
+    if (v[i] != 0.0) {
+      if (v[i] < 0) for (double &x : v) x = -x;
+      break;
+    }
+  return v;
+}
+
+static int ensure_workspace(hub_ctx *h, int64_t D) {
+  for (int k = 0; k < 3; ++k)
+    if (!h->work[k] && !dev_alloc((void **)&h->work[k], sizeof(double) * D, "Lanczos vector")) return HUB_ERR_OOM;
+  if (!h->d_scal && !dev_alloc((void **)&h->d_scal, sizeof(double) * 8, "Lanczos scalars")) return HUB_ERR_OOM;
+  if (!h->h_scal) HUB_CUDA(cudaMallocHost((void **)&h->h_scal, sizeof(double) * 8));
+  return ensure_partials(h, vec_grid());
+}
+
+}  // namespace hub
+
+using namespace hub;
+
+extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, double *E0,
+                                  double *psi_dev, int *iters, void *stream) {
+  int rc = ready(h, "hub_lanczos_ground");
+  if (rc) return rc;
+  if (!E0) return fail(HUB_ERR_ARG, "hub_lanczos_ground: E0 is NULL");
+  if (maxit < 1) return fail(HUB_ERR_ARG, "hub_lanczos_ground: maxit < 1");
+  const int64_t D = h->count[0] * h->count[1];
+  if (D == 0) return fail(HUB_ERR_ARG, "hub_lanczos_ground: empty sector");
+  rc = ensure_workspace(h, D);
+  if (rc) return rc;
+  cudaStream_t s = (cudaStream_t)stream;
+  const int G = vec_grid(), T = kVecThreads;
+  double *qp = h->work[0], *q = h->work[1], *w = h->work[2];
+  double *scal = h->d_scal, *P = h->partials;
+
+  // q_1 = x0 / |x0|
+  const double *x0 = x0_dev;
+  if (!x0) {
+    k_splitmix_uniform<<<G, T, 0, s>>>(D, w);
+    HUB_LAUNCH_CHECK();
+    x0 = w;
+  }
+  count_launch(h, x0_dev ? 3 : 4);   // [splitmix], dot, reduce, copy_scaled
+  k_dot<<<G, T, 0, s>>>(D, x0, x0, P);
+  HUB_LAUNCH_CHECK();
+  if ((rc = reduce_partials(P, G, scal + 3, 1, s))) return rc;
+  k_copy_scaled<<<G, T, 0, s>>>(D, q, x0, scal + 3);
+  HUB_CUDA(cudaMemsetAsync(qp, 0, sizeof(double) * D, s));
+  HUB_CUDA(cudaMemsetAsync(scal + 2, 0, sizeof(double), s));
+  HUB_CUDA(cudaMemcpyAsync(h->h_scal + 3, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HUB_CUDA(cudaStreamSynchronize(s));
+  if (!(h->h_scal[3] > 0.0) || !std::isfinite(h->h_scal[3]))
+    return fail(HUB_ERR_ARG, "hub_lanczos_ground: start vector is zero or not finite");
+
+  h->alpha.clear();
+  h->beta.clear();
+  double E = 0.0, E_prev = 0.0;
+  int status = HUB_ERR_NOCONV;
+  for (int j = 0; j < maxit; ++j) {
+    if ((rc = apply_launch(h, q, w, s))) return rc;
+    count_launch(h, 5);   // sub_dot, reduce, sub_norm, reduce, scale_inv
+    k_sub_dot<<<G, T, 0, s>>>(D, w, qp, q, scal + 2, P);
+    HUB_LAUNCH_CHECK();
+    if ((rc = reduce_partials(P, G, scal + 0, 0, s))) return rc;
+    k_sub_norm<<<G, T, 0, s>>>(D, w, q, scal + 0, P);
+    HUB_LAUNCH_CHECK();
+    if ((rc = reduce_partials(P, G, scal + 1, 1, s))) return rc;
+    HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 2 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    const double a = h->h_scal[0], b = h->h_scal[1];
+    if (!std::isfinite(a) || !std::isfinite(b)) return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha/beta");
+    h->alpha.push_back(a);
+    h->beta.push_back(b);
+    E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
+    if (tol > 0 && j > 0 && fabs(E - E_prev) < tol) {
+      status = HUB_OK;
+      break;
+    }
+    E_prev = E;
+    if (b <= 1e-14 * fmax(1.0, fabs(a))) {
+      status = HUB_CONVERGED_BREAKDOWN;
+      break;
+    }
+    if (j + 1 < maxit) {
+      k_scale_inv<<<G, T, 0, s>>>(D, w, scal);
+      HUB_LAUNCH_CHECK();
+      double *t0 = qp;
+      qp = q;
+      q = w;
+      w = t0;
+    }
+  }
+  if (tol <= 0 && status == HUB_ERR_NOCONV) status = HUB_OK;
+  *E0 = E;
+  const int k = (int)h->alpha.size();
+  if (iters) *iters = k;
+
+  if (psi_dev) {
+    // second pass: psi = sum_j v_j q_j with v the lowest eigenvector of T_k
+    std::vector<double> v = tridiag_vector(h->alpha.data(), h->beta.data(), k, E);
+    qp = h->work[0];
+    q = h->work[1];
+    w = h->work[2];
+    const double *xs = x0_dev;
+    if (!xs) {
+      k_splitmix_uniform<<<G, T, 0, s>>>(D, w);
+      HUB_LAUNCH_CHECK();
+      xs = w;
+    }
+    k_copy_scaled<<<G, T, 0, s>>>(D, q, xs, scal + 3);
+    HUB_CUDA(cudaMemsetAsync(qp, 0, sizeof(double) * D, s));
+    HUB_CUDA(cudaMemsetAsync(psi_dev, 0, sizeof(double) * D, s));
+    for (int j = 0; j < k; ++j) {
+      k_axpy<<<G, T, 0, s>>>(D, v[j], q, psi_dev);
+      HUB_LAUNCH_CHECK();
+      if (j + 1 == k) break;
+      if ((rc = apply_launch(h, q, w, s))) return rc;
+      k_recur<<<G, T, 0, s>>>(D, w, q, qp, h->alpha[j], j ? h->beta[j - 1] : 0.0, 1.0 / h->beta[j]);
+      HUB_LAUNCH_CHECK();
+      double *t0 = qp;
+      qp = q;
+      q = w;
+      w = t0;
+    }
+    // normalise psi
+    k_dot<<<G, T, 0, s>>>(D, psi_dev, psi_dev, P);
+    HUB_LAUNCH_CHECK();
+    if ((rc = reduce_partials(P, G, scal + 4, 1, s))) return rc;
+    k_scale_by<<<G, T, 0, s>>>(D, psi_dev, scal + 4);
+    HUB_LAUNCH_CHECK();
+    HUB_CUDA(cudaStreamSynchronize(s));
+  }
+  if (status == HUB_ERR_NOCONV) set_error("hub_lanczos_ground: maxit reached before |dE0| < tol");
+  return status;
+}
+
+extern "C" int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host, int cap, int *n) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_lanczos_coeffs: NULL handle");
+  int k = (int)h->alpha.size();
+  if (n) *n = k;
+  for (int i = 0; i < k && i < cap; ++i) {
+    if (alpha_host) alpha_host[i] = h->alpha[i];
+    if (beta_host) beta_host[i] = h->beta[i];
+  }
+  return HUB_OK;
+}

@@ -1,0 +1,326 @@
+"""Thin Python binding of the C ABI in ``include/hub.h`` (argument marshalling only).
+
+Every function named ``hub_*`` here calls the C entry point of the same name in
+``_build/libhub.so``; all arithmetic runs in the CUDA kernels of that library.  There
+is no CPU fallback: if the library cannot be loaded, every call raises.
+
+``Hubbard`` wraps one handle (a sector of a lattice model) and takes torch tensors on
+the GPU for vectors.  ``ApplyFn`` and ``GroundEnergyFn`` are torch.autograd.Functions
+whose backward passes are the library's adjoint kernels (``hub_apply_vjp``, ``hub_grad``).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "_build", "libhub.so")
+
+HUB_OK = 0
+HUB_CONVERGED_BREAKDOWN = 1
+HUB_ERR_ARG = -1
+HUB_ERR_OOM = -2
+HUB_ERR_CUDA = -3
+HUB_ERR_NOCONV = -4
+HUB_ERR_STATE = -5
+HUB_ERR_TIMEOUT = -6
+
+# (name, restype, argtypes) of every exported entry point.
+_i, _i64, _d, _p = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
+SIGNATURES = {
+    "hub_last_error": (ctypes.c_char_p, []),
+    "hub_basis": (_i, [_i, _i, _i, ctypes.POINTER(_p)]),
+    "hub_dims": (_i, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "hub_get_basis": (_i, [_p, _i, _p]),
+    "hub_hopping": (_i, [_p, _i, _p, _p, _p]),
+    "hub_set_U": (_i, [_p, _i, _p]),
+    "hub_csr_info": (_i, [_p, _i, ctypes.POINTER(_i64), ctypes.POINTER(ctypes.c_int32)]),
+    "hub_get_csr": (_i, [_p, _i, _p, _p, _p]),
+    "hub_apply": (_i, [_p, _p, _p, _p]),
+    "hub_apply_host": (_i, [_p, _p, _p, _p]),
+    "hub_lanczos_ground": (_i, [_p, _p, _i, _d, ctypes.POINTER(_d), _p, ctypes.POINTER(_i), _p]),
+    "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
+    "hub_grad": (_i, [_p, _p, _p, _p, _p, _p]),
+    "hub_apply_vjp": (_i, [_p, _p, _p, _p, _p, _p, _p, _p]),
+    "hub_profile": (_i, [_p, _i]),
+    "hub_profile_read": (_i, [_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "hub_free": (None, [_p]),
+}
+
+_lib = None
+
+
+class HubError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"[{code}] {msg}")
+        self.code = code
+
+
+def lib():
+    """The loaded CUDA library; raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run __graft_entry__.build() or python -m paper_1307_7542_gb300.build)")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+def _check(rc, ok=(HUB_OK,)):
+    if rc not in ok:
+        raise HubError(rc, lib().hub_last_error().decode())
+    return rc
+
+
+def _ptr(t):
+    """Device or host address of a contiguous torch tensor / numpy array (None -> NULL)."""
+    if t is None:
+        return None
+    if isinstance(t, np.ndarray):
+        assert t.flags["C_CONTIGUOUS"]
+        return ctypes.c_void_p(t.ctypes.data)
+    assert t.is_contiguous()
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    import torch
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+# ------------------------------------------------------------------------ raw C ABI calls
+
+def hub_basis(M, n_up, n_dn):
+    h = ctypes.c_void_p()
+    _check(lib().hub_basis(M, n_up, n_dn, ctypes.byref(h)))
+    return h
+
+
+def hub_dims(h):
+    a, b = _i64(), _i64()
+    _check(lib().hub_dims(h, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def hub_get_basis(h, spin, n):
+    out = np.empty(n, dtype=np.uint32)
+    _check(lib().hub_get_basis(h, spin, _ptr(out)))
+    return out
+
+
+def hub_hopping(h, bonds, t, eps=None):
+    bonds = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1))
+    e = None if eps is None else np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(-1))
+    _check(lib().hub_hopping(h, bonds.shape[0], _ptr(bonds), _ptr(t), _ptr(e)))
+
+
+def hub_set_U(h, U):
+    U = np.ascontiguousarray(np.atleast_1d(np.asarray(U, dtype=np.float64)))
+    _check(lib().hub_set_U(h, U.shape[0], _ptr(U)))
+
+
+def hub_csr_info(h, spin):
+    nnz, mx = _i64(), ctypes.c_int32()
+    _check(lib().hub_csr_info(h, spin, ctypes.byref(nnz), ctypes.byref(mx)))
+    return nnz.value, mx.value
+
+
+def hub_get_csr(h, spin, n_rows):
+    nnz, _ = hub_csr_info(h, spin)
+    rp = np.empty(n_rows + 1, dtype=np.int32)
+    cols = np.empty(max(nnz, 1), dtype=np.int32)
+    vals = np.empty(max(nnz, 1), dtype=np.float64)
+    _check(lib().hub_get_csr(h, spin, _ptr(rp), _ptr(cols), _ptr(vals)))
+    return rp, cols[:nnz], vals[:nnz]
+
+
+def hub_apply(h, x, y, stream=None):
+    _check(lib().hub_apply(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def hub_apply_host(h, x, y, stream=None):
+    _check(lib().hub_apply_host(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def hub_lanczos_ground(h, x0, maxit, tol, psi=None, stream=None):
+    E0, it = _d(), _i()
+    rc = lib().hub_lanczos_ground(h, _ptr(x0), maxit, tol, ctypes.byref(E0), _ptr(psi),
+                                  ctypes.byref(it), _stream(stream))
+    _check(rc, ok=(HUB_OK, HUB_CONVERGED_BREAKDOWN, HUB_ERR_NOCONV))
+    return E0.value, it.value, rc
+
+
+def hub_lanczos_coeffs(h, cap=100000):
+    a, b = np.empty(cap), np.empty(cap)
+    n = _i()
+    _check(lib().hub_lanczos_coeffs(h, _ptr(a), _ptr(b), cap, ctypes.byref(n)))
+    return a[: n.value], b[: n.value]
+
+
+def hub_grad(h, psi, n_bonds, M, stream=None):
+    dt, dU, de = np.empty(n_bonds), np.empty(M), np.empty(M)
+    _check(lib().hub_grad(h, _ptr(psi), _ptr(dt), _ptr(dU), _ptr(de), _stream(stream)))
+    return dt, dU, de
+
+
+def hub_apply_vjp(h, ybar, x, xbar, n_bonds, M, want_params=True, stream=None):
+    dt = np.empty(n_bonds) if want_params else None
+    dU = np.empty(M) if want_params else None
+    de = np.empty(M) if want_params else None
+    _check(lib().hub_apply_vjp(h, _ptr(ybar), _ptr(x), _ptr(xbar), _ptr(dt), _ptr(dU), _ptr(de),
+                               _stream(stream)))
+    return dt, dU, de
+
+
+def hub_profile(h, enable):
+    _check(lib().hub_profile(h, 1 if enable else 0))
+
+
+def hub_profile_read(h):
+    """(summed apply milliseconds, apply launches, all kernel launches) since hub_profile(h, 1)."""
+    ms, na, nk = _d(), _i64(), _i64()
+    _check(lib().hub_profile_read(h, ctypes.byref(ms), ctypes.byref(na), ctypes.byref(nk)))
+    return ms.value, na.value, nk.value
+
+
+def hub_free(h):
+    if h:
+        lib().hub_free(h)
+
+
+# ------------------------------------------------------------------------- object wrapper
+
+class Hubbard:
+    """One sector (N_up, N_dn) of a lattice model on the GPU.
+
+    Parameters follow Eq. 1: bonds (pairs of 0-based sites), per-bond t, per-site (or
+    uniform) U, optional per-site eps.
+    """
+
+    def __init__(self, M, n_up, n_dn, bonds, t, U, eps=None):
+        self.M, self.n_up, self.n_dn = int(M), int(n_up), int(n_dn)
+        self.bonds = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+        self.h = hub_basis(self.M, self.n_up, self.n_dn)
+        self.count_up, self.count_dn = hub_dims(self.h)
+        self.D = self.count_up * self.count_dn
+        self.set_params(t, U, eps)
+
+    def set_params(self, t, U, eps=None):
+        nb = self.bonds.shape[0]
+        t = np.asarray(t, dtype=np.float64)
+        self.t = np.full(nb, float(t)) if t.ndim == 0 else t.reshape(nb).copy()
+        U = np.asarray(U, dtype=np.float64)
+        self.U = np.full(self.M, float(U)) if U.ndim == 0 else U.reshape(self.M).copy()
+        self.eps = np.zeros(self.M) if eps is None else np.asarray(eps, dtype=np.float64).reshape(self.M).copy()
+        hub_hopping(self.h, self.bonds, self.t, self.eps if np.any(self.eps) else None)
+        hub_set_U(self.h, self.U if np.any(self.U != self.U[0]) else self.U[:1])
+
+    @property
+    def n_bonds(self):
+        return self.bonds.shape[0]
+
+    def basis(self, spin):
+        return hub_get_basis(self.h, spin, self.count_up if spin == 0 else self.count_dn)
+
+    def csr(self, spin):
+        return hub_get_csr(self.h, spin, self.count_up if spin == 0 else self.count_dn)
+
+    def apply(self, x, y=None, stream=None):
+        import torch
+        if y is None:
+            y = torch.empty_like(x)
+        hub_apply(self.h, x, y, stream)
+        return y
+
+    def ground(self, x0=None, maxit=300, tol=1e-12, want_psi=False, stream=None):
+        import torch
+        psi = torch.empty(self.D, dtype=torch.float64, device="cuda") if want_psi else None
+        E0, iters, rc = hub_lanczos_ground(self.h, x0, maxit, tol, psi, stream)
+        return dict(E0=E0, iters=iters, status=rc, psi=psi)
+
+    def grad(self, psi, stream=None):
+        return hub_grad(self.h, psi, self.n_bonds, self.M, stream)
+
+    def vjp(self, ybar, x, want_params=True, stream=None):
+        import torch
+        xbar = torch.empty_like(ybar)
+        dt, dU, de = hub_apply_vjp(self.h, ybar, x, xbar, self.n_bonds, self.M, want_params, stream)
+        return xbar, dt, dU, de
+
+    def close(self):
+        if self.h:
+            hub_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+# ------------------------------------------------------------------------- autograd
+
+def _autograd():
+    import torch
+
+    class ApplyFn(torch.autograd.Function):
+        """y = H(t, U, eps) x.  Backward: xbar = H ybar (H symmetric); parameter
+        cotangents ybar^T (dH/dtheta) x from the library's bilinear-form kernel."""
+
+        @staticmethod
+        def forward(ctx, model, x, t, U, eps):
+            model.set_params(t.detach().cpu().numpy(), U.detach().cpu().numpy(), eps.detach().cpu().numpy())
+            y = model.apply(x.detach().contiguous())
+            ctx.model = model
+            ctx.save_for_backward(x)
+            return y
+
+        @staticmethod
+        def backward(ctx, ybar):
+            (x,) = ctx.saved_tensors
+            m = ctx.model
+            xbar, dt, dU, de = m.vjp(ybar.contiguous(), x.contiguous(), want_params=any(ctx.needs_input_grad[2:]))
+            dev = ybar.device
+            cvt = (lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64, device=dev))
+            return None, xbar, cvt(dt), cvt(dU), cvt(de)
+
+    class GroundEnergyFn(torch.autograd.Function):
+        """E0(t, U, eps) by Lanczos; backward by Hellmann-Feynman (hub_grad on psi)."""
+
+        @staticmethod
+        def forward(ctx, model, t, U, eps, x0, maxit, tol):
+            model.set_params(t.detach().cpu().numpy(), U.detach().cpu().numpy(), eps.detach().cpu().numpy())
+            r = model.ground(x0, maxit=maxit, tol=tol, want_psi=True)
+            ctx.model = model
+            ctx.psi = r["psi"]
+            return torch.tensor(r["E0"], dtype=torch.float64)
+
+        @staticmethod
+        def backward(ctx, gE):
+            dt, dU, de = ctx.model.grad(ctx.psi)
+            g = float(gE)
+            cvt = (lambda a: torch.as_tensor(a * g, dtype=torch.float64))
+            return None, cvt(dt), cvt(dU), cvt(de), None, None, None
+
+    return ApplyFn, GroundEnergyFn
+
+
+def apply_fn(model, x, t, U, eps):
+    """Differentiable y = H x (see ApplyFn)."""
+    return _autograd()[0].apply(model, x, t, U, eps)
+
+
+def ground_energy(model, t, U, eps, x0=None, maxit=300, tol=1e-12):
+    """Differentiable ground-state energy (see GroundEnergyFn)."""
+    return _autograd()[1].apply(model, t, U, eps, x0, maxit, tol)
