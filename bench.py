@@ -131,7 +131,7 @@ def config_json(w, D, n_gpus):
 
 # ----------------------------------------------------------------------------- CPU oracle
 
-def oracle_sample(w, x, seconds, min_rows=2000):
+def oracle_sample(w, x, seconds, min_rows=20000):
     """Time the oracle's apply on the first R rows of the workload, R sized to take about
     `seconds`; returns (applies per second, rows, elapsed, threads)."""
     from oracle import hub_oracle as O
@@ -139,9 +139,13 @@ def oracle_sample(w, x, seconds, min_rows=2000):
     B = O.basis(w["M"], w["n_up"], w["n_dn"])
     D = B.shape[0]
     r = min_rows
-    t0 = time.perf_counter()
-    O.apply(om, B, x, rows=(0, r))
-    dt = time.perf_counter() - t0
+    while True:                                   # grow the sample until it takes >= 1 s
+        t0 = time.perf_counter()
+        O.apply(om, B, x, rows=(0, r))
+        dt = time.perf_counter() - t0
+        if dt >= 1.0 or r >= D:
+            break
+        r = min(D, r * 4)
     R = int(min(D, max(r, r * seconds / max(dt, 1e-6))))
     t0 = time.perf_counter()
     O.apply(om, B, x, rows=(D // 3, min(D, D // 3 + R)))
@@ -162,10 +166,15 @@ def run_reference(a):
     om = O.Model(w["M"], w["bonds"], w["t"], w["U"], w["eps"])
     B = O.basis(16, 8, 8)
     # size one step (a bounded sample of rows) to about 2 s of CPU
-    r = 2000
-    t0 = time.perf_counter()
-    O.apply(om, B, x, rows=(0, r))
-    R = int(max(r, r * 2.0 / max(time.perf_counter() - t0, 1e-6)))
+    r = 20000
+    while True:
+        t0 = time.perf_counter()
+        O.apply(om, B, x, rows=(0, r))
+        dt = time.perf_counter() - t0
+        if dt >= 0.5 or r >= D:
+            break
+        r = min(D, r * 4)
+    R = int(min(D - 1, max(r, r * 2.0 / max(dt, 1e-6))))
     for k in range(a.warmup):
         O.apply(om, B, x, rows=(0, R))
     t0 = time.perf_counter()

@@ -283,6 +283,7 @@ def _autograd():
             model.set_params(t.detach().cpu().numpy(), U.detach().cpu().numpy(), eps.detach().cpu().numpy())
             y = model.apply(x.detach().contiguous())
             ctx.model = model
+            ctx.param_devices = (t.device, U.device, eps.device)
             ctx.save_for_backward(x)
             return y
 
@@ -291,9 +292,9 @@ def _autograd():
             (x,) = ctx.saved_tensors
             m = ctx.model
             xbar, dt, dU, de = m.vjp(ybar.contiguous(), x.contiguous(), want_params=any(ctx.needs_input_grad[2:]))
-            dev = ybar.device
-            cvt = (lambda a: None if a is None else torch.as_tensor(a, dtype=torch.float64, device=dev))
-            return None, xbar, cvt(dt), cvt(dU), cvt(de)
+            devs = ctx.param_devices
+            cvt = (lambda a, dev: None if a is None else torch.as_tensor(a, dtype=torch.float64, device=dev))
+            return None, xbar, cvt(dt, devs[0]), cvt(dU, devs[1]), cvt(de, devs[2])
 
     class GroundEnergyFn(torch.autograd.Function):
         """E0(t, U, eps) by Lanczos; backward by Hellmann-Feynman (hub_grad on psi)."""
