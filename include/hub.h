@@ -52,6 +52,13 @@ extern "C" {
 #define HUB_SPIN_UP 0
 #define HUB_SPIN_DN 1
 
+#define HUB_MODE_AUTO 0   /* fast double-float path when t and U are uniform, else FP64 */
+#define HUB_MODE_FP64 1   /* always the native FP64 kernels                              */
+
+#define HUB_PROF_APPLY 0  /* a whole product H x (both passes on the fast path)       */
+#define HUB_PROF_UP 1     /* fast path pass 1: spin-up hops + diagonal                 */
+#define HUB_PROF_DN 2     /* fast path pass 2: spin-down hops + epilogue               */
+
 typedef struct hub_ctx *hub_t;
 
 /* Message for the calling thread's most recent failure ("" if none). */
@@ -145,15 +152,32 @@ int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_dev, double *
                   double *tbar_host, double *Ubar_host, double *epsbar_host, void *stream);
 
 /*
+ * Arithmetic path (no counterpart in the paper).  HUB_MODE_AUTO (default) runs products
+ * with uniform t and U on the fast path: vectors held as pairs of FP32 numbers (about 48
+ * significant bits), sums by error-free transformations on the FP32 pipe, because the
+ * FP64 unit of this GPU issues about 1/70 of the FP32 rate.  Inputs and outputs of every
+ * entry point stay FP64.  HUB_MODE_FP64 forces the native FP64 kernels.
+ */
+int hub_set_mode(hub_t h, int mode);
+
+/*
+ * Waits for the handle's queued work and reports a device-side failure: HUB_ERR_TIMEOUT
+ * if a bounded wait inside a kernel gave up since the last check (the flag is cleared),
+ * HUB_ERR_CUDA on a CUDA error, else HUB_OK.  hub_lanczos_ground checks this itself.
+ */
+int hub_check(hub_t h);
+
+/*
  * Measurement hooks (no counterpart in the paper).  hub_profile(h, 1) resets the counters
- * and starts recording a CUDA event pair on the launching stream around every apply
- * launch (up to 65536 launches are timed; later ones are only counted); hub_profile(h, 0)
- * stops.  hub_profile_read waits for the recorded events and returns the summed apply
- * time in milliseconds, the number of apply launches and the number of kernels the
- * handle launched since profiling started.  Any output pointer may be NULL.
+ * and starts recording a CUDA event pair on the launching stream around every product
+ * (HUB_PROF_APPLY) and every fast-path pass (HUB_PROF_UP, HUB_PROF_DN); up to 65536
+ * launches per kind are timed, later ones only counted.  hub_profile(h, 0) stops.
+ * hub_profile_read waits for the events and returns, for one kind, the summed time in
+ * milliseconds and the number of launches, plus the number of kernels the handle launched
+ * since profiling started.  Any output pointer may be NULL.
  */
 int hub_profile(hub_t h, int enable);
-int hub_profile_read(hub_t h, double *apply_ms, int64_t *apply_launches, int64_t *kernel_launches);
+int hub_profile_read(hub_t h, int kind, double *ms, int64_t *launches, int64_t *kernel_launches);
 
 /* Release a handle and everything it owns.  NULL is ignored. */
 void hub_free(hub_t h);

@@ -58,38 +58,44 @@ __global__ void __launch_bounds__(512) k_apply_f64(const Ham H, const double *__
 
 static size_t stage_bytes(const Ham &H) { return sizeof(double) * (size_t)H.n_up; }
 
-static int apply_kernels(const hub_ctx *h, const double *x, double *y, cudaStream_t s);
+static int apply_kernels(hub_ctx *h, const double *x, double *y, cudaStream_t s);
 
 constexpr int64_t kMaxTimed = 65536;
 
-int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
-  if (!h->prof) return apply_kernels(h, x, y, s);
-  cudaEvent_t e0 = nullptr, e1 = nullptr;
-  if (h->n_timed < kMaxTimed) {
-    if ((int64_t)h->ev_start.size() <= h->n_timed) {
+int prof_mark(hub_ctx *h, int kind, bool begin, cudaStream_t s) {
+  if (!h->prof) return HUB_OK;
+  int64_t &nt = h->n_timed[kind];
+  if (begin) {
+    if (nt >= kMaxTimed) return HUB_OK;
+    if ((int64_t)h->ev_start[kind].size() <= nt) {
+      cudaEvent_t e0, e1;
       HUB_CUDA(cudaEventCreate(&e0));
       HUB_CUDA(cudaEventCreate(&e1));
-      h->ev_start.push_back(e0);
-      h->ev_end.push_back(e1);
+      h->ev_start[kind].push_back(e0);
+      h->ev_end[kind].push_back(e1);
     }
-    e0 = h->ev_start[h->n_timed];
-    e1 = h->ev_end[h->n_timed];
-    HUB_CUDA(cudaEventRecord(e0, s));
+    HUB_CUDA(cudaEventRecord(h->ev_start[kind][nt], s));
+  } else {
+    ++h->n_launch[kind];
+    if (nt >= kMaxTimed) return HUB_OK;
+    HUB_CUDA(cudaEventRecord(h->ev_end[kind][nt], s));
+    ++nt;
   }
-  int rc = apply_kernels(h, x, y, s);
-  if (rc) return rc;
-  if (e1) {
-    HUB_CUDA(cudaEventRecord(e1, s));
-    ++h->n_timed;
-  }
-  ++h->n_apply;
-  ++h->n_kernels;
   return HUB_OK;
 }
 
-static int apply_kernels(const hub_ctx *h, const double *x, double *y, cudaStream_t s) {
+int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
+  int rc = prof_mark(h, HUB_PROF_APPLY, true, s);
+  if (rc) return rc;
+  if ((rc = apply_kernels(h, x, y, s))) return rc;
+  return prof_mark(h, HUB_PROF_APPLY, false, s);
+}
+
+static int apply_kernels(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   const Ham H = h->view();
   if (H.n_up == 0 || H.n_dn == 0) return HUB_OK;
+  if (use_fast(h)) return fast_apply_f64(h, x, y, s);
+  count_launch(h);
   const size_t smem = stage_bytes(H);
   const int threads = H.n_up >= 512 ? 512 : (H.n_up >= 128 ? 256 : 64);
   int64_t grid = H.n_dn;
@@ -153,22 +159,36 @@ extern "C" int hub_profile(hub_t h, int enable) {
   if (!h) return fail(HUB_ERR_ARG, "hub_profile: NULL handle");
   h->prof = enable != 0;
   if (h->prof) {
-    h->n_apply = h->n_timed = h->n_kernels = 0;
+    for (int k = 0; k < 3; ++k) h->n_launch[k] = h->n_timed[k] = 0;
+    h->n_kernels = 0;
   }
   return HUB_OK;
 }
 
-extern "C" int hub_profile_read(hub_t h, double *apply_ms, int64_t *apply_launches, int64_t *kernel_launches) {
-  if (!h) return fail(HUB_ERR_ARG, "hub_profile_read: NULL handle");
+extern "C" int hub_profile_read(hub_t h, int kind, double *ms, int64_t *launches, int64_t *kernel_launches) {
+  if (!h || kind < 0 || kind > 2) return fail(HUB_ERR_ARG, "hub_profile_read: bad argument");
   double total = 0.0;
-  for (int64_t k = 0; k < h->n_timed; ++k) {
-    HUB_CUDA(cudaEventSynchronize(h->ev_end[k]));
-    float ms = 0.f;
-    HUB_CUDA(cudaEventElapsedTime(&ms, h->ev_start[k], h->ev_end[k]));
-    total += ms;
+  for (int64_t k = 0; k < h->n_timed[kind]; ++k) {
+    HUB_CUDA(cudaEventSynchronize(h->ev_end[kind][k]));
+    float t = 0.f;
+    HUB_CUDA(cudaEventElapsedTime(&t, h->ev_start[kind][k], h->ev_end[kind][k]));
+    total += t;
   }
-  if (apply_ms) *apply_ms = h->n_timed ? total * (double)h->n_apply / (double)h->n_timed : 0.0;
-  if (apply_launches) *apply_launches = h->n_apply;
+  const int64_t nt = h->n_timed[kind], nl = h->n_launch[kind];
+  if (ms) *ms = nt ? total * (double)nl / (double)nt : 0.0;
+  if (launches) *launches = nl;
   if (kernel_launches) *kernel_launches = h->n_kernels;
   return HUB_OK;
+}
+
+extern "C" int hub_set_mode(hub_t h, int mode) {
+  if (!h || (mode != HUB_MODE_AUTO && mode != HUB_MODE_FP64)) return fail(HUB_ERR_ARG, "hub_set_mode: bad argument");
+  h->mode = mode;
+  return HUB_OK;
+}
+
+extern "C" int hub_check(hub_t h) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_check: NULL handle");
+  HUB_CUDA(cudaDeviceSynchronize());
+  return fast_check_error(h);
 }

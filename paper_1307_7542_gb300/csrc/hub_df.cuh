@@ -1,0 +1,138 @@
+// hub_df.cuh -- double-float arithmetic on the FP32 pipe, and FP64 <-> double-float
+// conversions done with integer instructions.
+//
+// On this GPU the FP64 unit issues about 0.5e12 instructions/s (conversions between
+// FP32 and FP64 run there too), against about 36e12/s for FP32 and integer work.  The
+// fast apply therefore keeps vectors as pairs (hi, lo) of FP32 numbers with
+// x ~= hi + lo (about 48 significant bits) and sums with the error-free transformation
+// TwoSum (Knuth, TAOCP vol. 2, 4.2.2; Moller 1965): s = a + b, e = (a - (s - bb)) +
+// (b - bb) with bb = s - a gives a + b = s + e exactly.  Products use the FMA-based
+// TwoProd (p = a*b, e = fma(a, b, -p) is exact).  Nothing here uses an FP64 instruction
+// except the single add in df_to_f64.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace hub {
+
+// (s, e) with s + e == a + b exactly (round-to-nearest FP32, no overflow).
+__device__ __forceinline__ void two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+
+// (s, e) with s + e == a + b exactly, valid when |a| >= |b| (or a == 0).
+__device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &e) {
+  s = __fadd_rn(a, b);
+  e = __fsub_rn(b, __fsub_rn(s, a));
+}
+
+// Accumulator: the exact sum of the high parts is kept as H plus the rounding errors,
+// which go to L together with the low parts.
+struct DfAcc {
+  float H, L;
+};
+
+__device__ __forceinline__ void acc_add(DfAcc &a, float2 v) {
+  float s, e;
+  two_sum(a.H, v.x, s, e);
+  a.H = s;
+  a.L = __fadd_rn(__fadd_rn(a.L, v.y), e);
+}
+
+__device__ __forceinline__ void acc_sub(DfAcc &a, float2 v) {
+  float s, e;
+  two_sum(a.H, -v.x, s, e);
+  a.H = s;
+  a.L = __fadd_rn(__fsub_rn(a.L, v.y), e);
+}
+
+// Normalised double-float value of an accumulator.
+__device__ __forceinline__ float2 acc_value(const DfAcc &a) {
+  float s, e;
+  two_sum(a.H, a.L, s, e);
+  return make_float2(s, e);
+}
+
+// a + b for normalised double-floats (sloppy addition: TwoSum of the high parts).
+__device__ __forceinline__ float2 df_add(float2 a, float2 b) {
+  float s, e;
+  two_sum(a.x, b.x, s, e);
+  e = __fadd_rn(e, __fadd_rn(a.y, b.y));
+  float r, f;
+  fast_two_sum(s, e, r, f);
+  return make_float2(r, f);
+}
+
+// a * b for double-floats (TwoProd of the high parts plus the cross terms).
+__device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
+  float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  float r, f;
+  fast_two_sum(p, e, r, f);
+  return make_float2(r, f);
+}
+
+// a * b + c for double-floats.
+__device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) { return df_add(df_mul(a, b), c); }
+
+// 2^k as a float for -126 <= k <= 127.
+__device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
+
+// FP64 -> double-float with a power-of-two scale 2^-shift applied exactly, using integer
+// instructions only: hi takes the leading 24 significant bits (truncated), lo the next 29
+// bits rounded to FP32 (error <= 2^-48 |x|).  Zero and FP64 subnormals map to 0; results
+// below the FP32 normal range keep FP32 gradual underflow.  Requires |x| 2^-shift < 2^127.
+__device__ __forceinline__ float2 f64_to_df(double x, int shift) {
+  const uint64_t b = (uint64_t)__double_as_longlong(x);
+  const uint32_t hi32 = (uint32_t)(b >> 32), lo32 = (uint32_t)b;
+  const int e = (int)((hi32 >> 20) & 0x7ffu);
+  if (e == 0) return make_float2(0.f, 0.f);
+  const int E = e - 1023 - shift;                       // x 2^-shift = 1.f * 2^E
+  const uint32_t sign = hi32 & 0x80000000u;
+  const uint32_t m23 = ((hi32 & 0xfffffu) << 3) | (lo32 >> 29);
+  const float one_m = __uint_as_float(0x3f800000u | m23);   // 1.m23 in [1, 2)
+  const uint32_t rem = lo32 & 0x1fffffffu;                   // next 29 bits: rem * 2^-52
+  float h, l;
+  // scale in two exact steps so that every intermediate power of two is a normal float
+  const int k1 = E > 0 ? (E > 126 ? 126 : E) : (E < -126 ? -126 : E);
+  const int k2 = E - k1;
+  h = __fmul_rn(__fmul_rn(one_m, pow2f(k1)), pow2f(k2 < -126 ? -126 : k2));
+  l = __fmul_rn(__fmul_rn(__uint2float_rn(rem), pow2f(-52)), pow2f(k1));
+  l = __fmul_rn(l, pow2f(k2 < -126 ? -126 : k2));
+  if (sign) {
+    h = -h;
+    l = -l;
+  }
+  return make_float2(h, l);
+}
+
+// Exact FP32 -> FP64 bit pattern conversion with integer instructions (normal and
+// subnormal floats), scaled by 2^shift.
+__device__ __forceinline__ double f32_to_f64_scaled(float f, int shift) {
+  uint32_t u = __float_as_uint(f);
+  const uint32_t sign = u & 0x80000000u;
+  uint32_t mag = u & 0x7fffffffu;
+  if (mag == 0) return __longlong_as_double((long long)((uint64_t)sign << 32));
+  int e = (int)(mag >> 23);
+  uint32_t m = mag & 0x7fffffu;
+  if (e == 0) {                 // subnormal: normalise
+    int lz = __clz(m) - 8;      // leading zeros within the 23-bit field
+    m = (m << (lz + 1)) & 0x7fffffu;
+    e = 1 - (lz + 1);
+  }
+  const uint64_t E = (uint64_t)(e - 127 + 1023 + shift);
+  const uint64_t bits = ((uint64_t)sign << 32) | (E << 52) | ((uint64_t)m << 29);
+  return __longlong_as_double((long long)bits);
+}
+
+// Double-float -> FP64 (scaled by 2^shift): two exact conversions and one FP64 add.
+__device__ __forceinline__ double df_to_f64(float2 v, int shift) {
+  return f32_to_f64_scaled(v.x, shift) + f32_to_f64_scaled(v.y, shift);
+}
+
+}  // namespace hub

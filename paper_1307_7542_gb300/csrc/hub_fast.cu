@@ -1,0 +1,772 @@
+// hub_fast.cu -- the fast apply for uniform hopping (K3 fast path) and the double-float
+// Lanczos built on it.
+//
+// The product is Eq. 11 of Sec. IV.A on the count_dn x count_up state matrix X (Eq.
+// count2):  Y = X H_up^T + H_dn X + diag o X, with every hopping element -t * esign
+// (Eq. 8) and diag = U popcount(I_up & I_dn) + eps(I_up) + eps(I_dn) (Sec. III.B).  The
+// two hopping terms want different memory orders, so they run as two passes:
+//
+//   pass 1 (k_up): one CTA per row d.  Row d of X is copied whole into shared memory by
+//     one bulk asynchronous copy (cp.async.bulk, completion on an mbarrier), then each
+//     thread sums the H_up row of its columns u from shared memory (in-row gather) and
+//     adds the diagonal: Z[d][u] = t S_up + diag X[d][u].
+//   pass 2 (k_dn): tiles of 32 rows x 64 columns, launched strip-major (all tiles of one
+//     column strip are adjacent in the grid), so the strip of X that the H_dn rows
+//     combine -- count_dn x 64 values -- stays in L2 while the whole strip is processed
+//     and X is read from HBM about once.  Each warp adds t S_dn to Z for its rows with
+//     128-bit loads of whole rows of the strip.
+//
+// Vectors are double-float (hub_df.cuh) with rows padded to an even length so that every
+// row starts on a 16-byte boundary (bulk copies and 16-byte loads).  The hopping rows are
+// reordered by sign (entries adding x first, then entries subtracting x), so no per-term
+// sign handling is needed, and columns are stored as uint16 when count <= 65536.
+#include <algorithm>
+#include <cmath>
+#include <new>
+#include <vector>
+
+#include "hub_df.cuh"
+#include "hub_internal.cuh"
+
+namespace hub {
+
+int ready(const hub_ctx *h, const char *who);
+double tridiag_lowest(const double *a, const double *b, int k);
+std::vector<double> tridiag_vector(const double *a, const double *b, int k, double lam);
+
+// ---------------------------------------------------------------------------------------
+// Small PTX wrappers: mbarrier and bulk copy (sm_90+).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t *bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t *bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ void bulk_g2s(void *dst, const void *src, uint32_t bytes, uint64_t *bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t *bar, uint32_t phase) {
+  uint32_t ok;
+  asm volatile(
+      "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n selp.u32 %0, 1, 0, p;\n}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(phase)
+      : "memory");
+  return ok != 0;
+}
+// Bounded wait: gives up after ~2^24 polls (each poll may suspend the thread briefly).
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase) {
+  for (uint32_t it = 0; it < (1u << 24); ++it)
+    if (mbar_try_wait(bar, phase)) return true;
+  return false;
+}
+
+// ---------------------------------------------------------------------------------------
+// Fast-path view (passed by value).
+// ---------------------------------------------------------------------------------------
+struct FastView {
+  int64_t n_up, n_dn, ld;            // ld: padded row length (even)
+  const uint32_t *basis_up, *basis_dn;
+  const int32_t *rp_up, *sp_up;      // row start and sign split of H_up
+  const int32_t *rp_dn, *sp_dn;
+  const void *col_up, *col_dn;       // uint16 or uint32 columns
+  const float2 *eps_up, *eps_dn;     // per-state site energies (double-float) or null
+  float2 t;                          // uniform hopping t (double-float)
+  int t_is_one;
+  float2 Utab[32];                   // U * k for k = popcount(I_up & I_dn)
+  int *err;                          // device error flag (bounded waits)
+};
+
+template <typename Col>
+__device__ __forceinline__ int64_t colat(const void *c, int64_t k) {
+  return (int64_t)((const Col *)c)[k];
+}
+
+// ---------------------------------------------------------------------------------------
+// Sign-split CSR: per row, entries with esign = -1 (element +t: add x) first, then the
+// entries with esign = +1 (element -t: subtract x); columns ascending inside each group.
+// ---------------------------------------------------------------------------------------
+template <typename Col>
+__global__ void k_split_csr(int64_t n, const int32_t *__restrict__ rp, const uint32_t *__restrict__ scol,
+                            int32_t *__restrict__ sp, Col *__restrict__ col) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int32_t a = rp[r], b = rp[r + 1];
+    int32_t w = a;
+    for (int32_t k = a; k < b; ++k)
+      if (scol[k] >> 31) col[w++] = (Col)(scol[k] & 0x7fffffffu);
+    sp[r] = w;
+    for (int32_t k = a; k < b; ++k)
+      if (!(scol[k] >> 31)) col[w++] = (Col)(scol[k] & 0x7fffffffu);
+  }
+}
+
+__global__ void k_eps_df(int64_t n, const double *__restrict__ e, float2 *__restrict__ out) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
+    out[r] = f64_to_df(e[r], 0);
+}
+
+// ---------------------------------------------------------------------------------------
+// Conversions between the ABI's FP64 layout (row length n_up) and the padded double-float
+// layout (row length ld), with a power-of-two scale.
+// ---------------------------------------------------------------------------------------
+// partials[block] = max biased FP64 exponent of |x| over the block's elements
+__global__ void k_max_exp(int64_t D, const double *__restrict__ x, int *__restrict__ partials) {
+  int m = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < D; k += (int64_t)gridDim.x * blockDim.x) {
+    const uint32_t hi = (uint32_t)((uint64_t)__double_as_longlong(x[k]) >> 32);
+    m = max(m, (int)((hi >> 20) & 0x7ffu));
+  }
+  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+  __shared__ int ws[32];
+  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    int v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
+    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
+    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+  }
+}
+
+__global__ void k_f64_to_df(int64_t n_rows, int64_t n_up, int64_t ld, const double *__restrict__ x,
+                            const int *__restrict__ emax, int nblk, float2 *__restrict__ out) {
+  __shared__ int s_shift;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int k = 0; k < nblk; ++k) m = max(m, emax[k]);
+    s_shift = m == 0 ? 0 : m - 1023;          // max |x| 2^-shift in [1, 2)
+  }
+  __syncthreads();
+  const int shift = s_shift;
+  const int64_t total = n_rows * ld;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = k / ld, u = k - d * ld;
+    out[k] = u < n_up ? f64_to_df(x[d * n_up + u], shift) : make_float2(0.f, 0.f);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass 1: spin-up hops (in-row gather from shared memory) and the diagonal.
+// ---------------------------------------------------------------------------------------
+template <typename Col, bool kStage, bool kEps>
+__global__ void __launch_bounds__(512, 2) k_up(const FastView F, const float2 *__restrict__ x,
+                                               float2 *__restrict__ z) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  float2 *xs = reinterpret_cast<float2 *>(smem_raw);
+  __shared__ __align__(8) uint64_t bar;
+  const int tid = threadIdx.x;
+  const uint32_t bytes = (uint32_t)(F.ld * sizeof(float2));
+  if (kStage) {
+    if (tid == 0) {
+      mbar_init(&bar, 1);
+      fence_mbar_init();
+    }
+    __syncthreads();
+  }
+  uint32_t phase = 0;
+  for (int64_t d = blockIdx.x; d < F.n_dn; d += gridDim.x) {
+    const float2 *__restrict__ xrow = x + d * F.ld;
+    if (kStage) {
+      if (tid == 0) {
+        fence_proxy_async();
+        mbar_expect_tx(&bar, bytes);
+        bulk_g2s(xs, xrow, bytes, &bar);
+      }
+      if (!mbar_wait_bounded(&bar, phase)) {
+        if (tid == 0) atomicExch(F.err, 1);
+        mbar_wait_bounded(&bar, phase);      // give a late copy one more bounded chance to land
+        return;
+      }
+      phase ^= 1u;
+    }
+    const float2 *__restrict__ src = kStage ? xs : xrow;
+    const uint32_t Id = F.basis_dn[d];
+    float2 ed = make_float2(0.f, 0.f);
+    if (kEps) ed = F.eps_dn[d];
+    for (int64_t u = tid; u < F.n_up; u += blockDim.x) {
+      DfAcc ap{0.f, 0.f}, am{0.f, 0.f};
+      const int32_t k0 = F.rp_up[u], ks = F.sp_up[u], k1 = F.rp_up[u + 1];
+      int32_t k = k0;
+      for (; k < ks; ++k) acc_add(ap, src[colat<Col>(F.col_up, k)]);
+      for (; k < k1; ++k) acc_add(am, src[colat<Col>(F.col_up, k)]);
+      const float2 sp = acc_value(ap), sm = acc_value(am);
+      float2 S = df_add(sp, make_float2(-sm.x, -sm.y));
+      if (!F.t_is_one) S = df_mul(S, F.t);
+      float2 dg = F.Utab[__popc(F.basis_up[u] & Id)];
+      if (kEps) dg = df_add(df_add(dg, F.eps_up[u]), ed);
+      z[d * F.ld + u] = df_fma(dg, src[u], S);
+    }
+    if (kStage) __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Pass 2: spin-down hops as combinations of whole rows of a column strip, plus the
+// epilogue.  Tile = 32 rows x 64 columns; blockIdx.x = row tile (fast), blockIdx.y =
+// column strip (slow), so consecutive blocks share a strip.  Lane l of a warp owns the
+// columns u0 + 2l, u0 + 2l + 1 (one 16-byte load per row).
+// ---------------------------------------------------------------------------------------
+constexpr int kDnRows = 32, kDnCols = 64, kDnThreads = 256;
+
+struct LzArgs {                      // Lanczos epilogue operands
+  const float2 *r_cur;               // r_j   (q_j = r_j / beta_cur)
+  const float2 *r_prev;              // r_{j-1}
+  const float2 *coef;                // [0] 1/beta_cur, [1] beta_cur/beta_prev (double-float)
+  double *partials;                  // alpha partial per block
+};
+
+// Coefficients of the recurrence as double-floats, computed once per step by one thread
+// (keeps FP64 divisions out of the wide kernels).  scal: [0] alpha_j, [1] beta_cur,
+// [2] beta_prev.  coef: [0] 1/beta_cur, [1] beta_cur/beta_prev (0 at the first step),
+// [2] -alpha_j/beta_cur.
+__global__ void k_coeffs(const double *__restrict__ scal, float2 *__restrict__ coef) {
+  const double a = scal[0], bc = scal[1], bp = scal[2];
+  coef[0] = f64_to_df(1.0 / bc, 0);
+  coef[1] = f64_to_df(bp > 0.0 ? bc / bp : 0.0, 0);
+  coef[2] = f64_to_df(-a / bc, 0);
+}
+
+// scal[i] = v for the given slots (stream-ordered host -> device scalar writes)
+__global__ void k_set_scal(double *__restrict__ scal, int i0, double v0, int i1, double v1, int i2, double v2) {
+  if (i0 >= 0) scal[i0] = v0;
+  if (i1 >= 0) scal[i1] = v1;
+  if (i2 >= 0) scal[i2] = v2;
+}
+
+// kMode 0: y (FP64, unpadded) = 2^shift (Z + t S_dn).
+// kMode 1: w = (Z + t S_dn)/beta_cur - (beta_cur/beta_prev) r_prev  (double-float, padded),
+//          partials <- <q_j, w> per block.
+template <typename Col, int kMode>
+__global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float2 *__restrict__ x,
+                                                  const float2 *__restrict__ z, double *__restrict__ y,
+                                                  float2 *__restrict__ w, const int *__restrict__ shift_src,
+                                                  int nblk_shift, LzArgs L) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t u = (int64_t)blockIdx.y * kDnCols + 2 * lane;
+  const int64_t r0 = (int64_t)blockIdx.x * kDnRows;
+  int shift = 0;
+  float2 ib = make_float2(1.f, 0.f), cprev = make_float2(0.f, 0.f);
+  if (kMode == 0) {
+    __shared__ int s_shift;
+    if (threadIdx.x == 0) {
+      int m = 0;
+      for (int k = 0; k < nblk_shift; ++k) m = max(m, shift_src[k]);
+      s_shift = m == 0 ? 0 : m - 1023;
+    }
+    __syncthreads();
+    shift = s_shift;
+  } else {
+    ib = L.coef[0];
+    cprev = L.coef[1];
+  }
+  DfAcc dacc{0.f, 0.f};
+  const bool active = u < F.n_up;                      // u even, ld even: u + 1 <= ld - 1
+  for (int rr = warp; rr < kDnRows; rr += kDnThreads / 32) {
+    const int64_t d = r0 + rr;
+    if (d >= F.n_dn) break;
+    const int32_t k0 = F.rp_dn[d], ks = F.sp_dn[d], k1 = F.rp_dn[d + 1];
+    if (!active) continue;
+    DfAcc p0{0.f, 0.f}, p1{0.f, 0.f}, m0{0.f, 0.f}, m1{0.f, 0.f};
+    int32_t k = k0;
+    for (; k < ks; ++k) {
+      const float4 v = *reinterpret_cast<const float4 *>(x + colat<Col>(F.col_dn, k) * F.ld + u);
+      acc_add(p0, make_float2(v.x, v.y));
+      acc_add(p1, make_float2(v.z, v.w));
+    }
+    for (; k < k1; ++k) {
+      const float4 v = *reinterpret_cast<const float4 *>(x + colat<Col>(F.col_dn, k) * F.ld + u);
+      acc_add(m0, make_float2(v.x, v.y));
+      acc_add(m1, make_float2(v.z, v.w));
+    }
+    const float4 zz = *reinterpret_cast<const float4 *>(z + d * F.ld + u);
+    float2 s0 = df_add(acc_value(p0), make_float2(-acc_value(m0).x, -acc_value(m0).y));
+    float2 s1 = df_add(acc_value(p1), make_float2(-acc_value(m1).x, -acc_value(m1).y));
+    if (!F.t_is_one) {
+      s0 = df_mul(s0, F.t);
+      s1 = df_mul(s1, F.t);
+    }
+    const float2 y0 = df_add(make_float2(zz.x, zz.y), s0);
+    const float2 y1 = df_add(make_float2(zz.z, zz.w), s1);
+    if (kMode == 0) {
+      y[d * F.n_up + u] = df_to_f64(y0, shift);
+      if (u + 1 < F.n_up) y[d * F.n_up + u + 1] = df_to_f64(y1, shift);
+    } else {
+      const float4 rc = *reinterpret_cast<const float4 *>(L.r_cur + d * F.ld + u);
+      const float4 rp = *reinterpret_cast<const float4 *>(L.r_prev + d * F.ld + u);
+      const float2 a0 = df_mul(y0, ib), a1 = df_mul(y1, ib);
+      const float2 w0 = df_add(a0, df_mul(cprev, make_float2(-rp.x, -rp.y)));
+      float2 w1 = df_add(a1, df_mul(cprev, make_float2(-rp.z, -rp.w)));
+      if (u + 1 >= F.n_up) w1 = make_float2(0.f, 0.f);      // keep the padding column zero
+      *reinterpret_cast<float4 *>(w + d * F.ld + u) = make_float4(w0.x, w0.y, w1.x, w1.y);
+      // <q_j, w> = <r_j, w> / beta_cur, accumulated in double-float, reduced in FP64
+      const float2 q0 = df_mul(make_float2(rc.x, rc.y), ib), q1 = df_mul(make_float2(rc.z, rc.w), ib);
+      acc_add(dacc, df_mul(q0, w0));
+      acc_add(dacc, df_mul(q1, w1));
+    }
+  }
+  if (kMode == 1) {
+    double dot = df_to_f64(acc_value(dacc), 0);
+    for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
+    __shared__ double ws[kDnThreads / 32];
+    if (lane == 0) ws[warp] = dot;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double s = 0.0;
+      for (int k = 0; k < kDnThreads / 32; ++k) s += ws[k];
+      L.partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Double-float Lanczos vector kernels (padded layout; padding columns stay zero).
+// ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void block_sum_to(double v, double *partials) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __shared__ double ws[32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  if (lane == 0) ws[wid] = v;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double s = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) s += ws[k];
+    partials[blockIdx.x] = s;
+  }
+}
+
+// r_next = w + coef[2] r_cur = w - (alpha / beta_cur) r_cur  (in place over w);
+// partials <- |r_next|^2
+__global__ void k_df_update(int64_t n, float2 *__restrict__ w, const float2 *__restrict__ r_cur,
+                            const float2 *__restrict__ coef, double *__restrict__ partials) {
+  const float2 c = coef[2];
+  DfAcc acc{0.f, 0.f};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const float2 v = df_fma(c, r_cur[k], w[k]);
+    w[k] = v;
+    acc_add(acc, df_mul(v, v));
+  }
+  block_sum_to(df_to_f64(acc_value(acc), 0), partials);
+}
+
+// partials <- |v|^2
+__global__ void k_df_norm2(int64_t n, const float2 *__restrict__ v, double *__restrict__ partials) {
+  DfAcc acc{0.f, 0.f};
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    acc_add(acc, df_mul(v[k], v[k]));
+  block_sum_to(df_to_f64(acc_value(acc), 0), partials);
+}
+
+// psi += c r, c a double-float coefficient in coef[idx]
+__global__ void k_df_axpy(int64_t n, const float2 *__restrict__ coef, int idx, const float2 *__restrict__ r,
+                          float2 *__restrict__ psi) {
+  const float2 a = coef[idx];
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
+    psi[k] = df_fma(a, r[k], psi[k]);
+}
+
+// coef[3] = c / scal[1]  (psi coefficient v_j / beta_cur), one thread
+__global__ void k_psi_coef(const double *__restrict__ scal, double c, float2 *__restrict__ coef) {
+  coef[3] = f64_to_df(c / scal[1], 0);
+}
+
+// out (FP64, unpadded) = v / |v|  with |v| = scal[idx]
+__global__ void k_df_out_normalised(int64_t n_rows, int64_t n_up, int64_t ld, const float2 *__restrict__ v,
+                                    const double *__restrict__ scal, int idx, double *__restrict__ out) {
+  const float2 inv = f64_to_df(1.0 / scal[idx], 0);
+  const int64_t total = n_rows * n_up;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t d = k / n_up, u = k - d * n_up;
+    out[k] = df_to_f64(df_mul(v[d * ld + u], inv), 0);
+  }
+}
+
+// Second-pass recurrence with known coefficients: r_next = (H r_j)/1 ... computed as
+// w = (Z + t S)/beta_cur - (beta_cur/beta_prev) r_prev by k_dn<.,1>, then
+// r_next = w - (alpha/beta_cur) r_cur by k_df_update (alpha written into scal[0]).
+
+// ---------------------------------------------------------------------------------------
+// Host side.
+// ---------------------------------------------------------------------------------------
+static int grid_vec() { return num_sms() * 4; }
+
+struct FastState {
+  bool built = false;
+  float2 *coef = nullptr;                    // recurrence coefficients (double-float)
+  bool col16 = true;
+  int32_t *sp[2] = {nullptr, nullptr};
+  void *col[2] = {nullptr, nullptr};
+  float2 *eps_df[2] = {nullptr, nullptr};
+  float2 *xdf = nullptr, *zdf = nullptr;     // hub_apply scratch
+  float2 *lz[3] = {nullptr, nullptr, nullptr};
+  float2 *psi = nullptr;
+  int *d_emax = nullptr;
+  int *d_err = nullptr;
+  int64_t ld = 0;
+};
+
+static FastState *fast_of(const hub_ctx *h) { return h->fast; }
+
+void fast_release(hub_ctx *h) {
+  FastState *f = fast_of(h);
+  if (!f) return;
+  for (int s = 0; s < 2; ++s) {
+    dev_free(f->sp[s]);
+    dev_free(f->col[s]);
+    dev_free(f->eps_df[s]);
+  }
+  dev_free(f->xdf);
+  dev_free(f->zdf);
+  for (int k = 0; k < 3; ++k) dev_free(f->lz[k]);
+  dev_free(f->psi);
+  dev_free(f->d_emax);
+  dev_free(f->d_err);
+  dev_free(f->coef);
+  delete f;
+  h->fast = nullptr;
+}
+
+bool fast_eligible(const hub_ctx *h) {
+  if (!h->have_hop || !h->have_U || !h->uniform_U) return false;
+  for (double tb : h->t)
+    if (tb != h->t[0]) return false;
+  return h->count[0] > 0 && h->count[1] > 0;
+}
+
+// Build the sign-split CSR and double-float tables (called after hub_hopping).
+int fast_build(hub_ctx *h) {
+  fast_release(h);
+  FastState *f = new (std::nothrow) FastState();
+  if (!f) return fail(HUB_ERR_OOM, "fast path: host allocation failed");
+  h->fast = f;
+  f->col16 = h->count[0] <= 65536 && h->count[1] <= 65536;
+  f->ld = h->count[0] + (h->count[0] & 1);
+  const size_t csz = f->col16 ? sizeof(uint16_t) : sizeof(uint32_t);
+  for (int s = 0; s < 2; ++s) {
+    if (s == 1 && h->shared) break;
+    const SpinCSR &c = h->csr[s];
+    const int64_t n = h->count[s];
+    if (!dev_alloc((void **)&f->sp[s], sizeof(int32_t) * (n + 1), "split CSR") ||
+        !dev_alloc(&f->col[s], csz * (size_t)std::max<int64_t>(c.nnz, 1), "split CSR columns"))
+      return HUB_ERR_OOM;
+    const int g = (int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16);
+    if (f->col16)
+      k_split_csr<uint16_t><<<std::max(g, 1), 256>>>(n, c.rowptr, c.scol, f->sp[s], (uint16_t *)f->col[s]);
+    else
+      k_split_csr<uint32_t><<<std::max(g, 1), 256>>>(n, c.rowptr, c.scol, f->sp[s], (uint32_t *)f->col[s]);
+    HUB_LAUNCH_CHECK();
+    if (h->has_eps) {
+      if (!dev_alloc((void **)&f->eps_df[s], sizeof(float2) * n, "site energies (double-float)")) return HUB_ERR_OOM;
+      k_eps_df<<<std::max(g, 1), 256>>>(n, h->eps_state[s], f->eps_df[s]);
+      HUB_LAUNCH_CHECK();
+    }
+  }
+  if (!dev_alloc((void **)&f->d_err, sizeof(int) * 4, "error flag") ||
+      !dev_alloc((void **)&f->coef, sizeof(float2) * 8, "recurrence coefficients"))
+    return HUB_ERR_OOM;
+  HUB_CUDA(cudaMemset(f->d_err, 0, sizeof(int) * 4));
+  HUB_CUDA(cudaDeviceSynchronize());
+  f->built = true;
+  return HUB_OK;
+}
+
+static FastView fast_view(const hub_ctx *h, const FastState *f) {
+  FastView v{};
+  v.n_up = h->count[0];
+  v.n_dn = h->count[1];
+  v.ld = f->ld;
+  v.basis_up = h->basis[0];
+  v.basis_dn = h->basis[1];
+  const int sd = h->shared ? 0 : 1;
+  v.rp_up = h->csr[0].rowptr;
+  v.sp_up = f->sp[0];
+  v.rp_dn = h->csr[sd].rowptr;
+  v.sp_dn = f->sp[sd];
+  v.col_up = f->col[0];
+  v.col_dn = f->col[sd];
+  v.eps_up = f->eps_df[0];
+  v.eps_dn = f->eps_df[sd];
+  const double t = h->t.empty() ? 0.0 : h->t[0];
+  v.t_is_one = (t == 1.0);
+  // host double -> double-float: hi = float(t), lo = float(t - hi)
+  auto hdf = [](double a) {
+    float hi = (float)a;
+    return make_float2(hi, (float)(a - (double)hi));
+  };
+  v.t = hdf(t);
+  for (int k = 0; k < 32; ++k) v.Utab[k] = hdf(h->U0 * (double)k);
+  v.err = f->d_err;
+  return v;
+}
+
+static size_t up_smem(const FastState *f) { return sizeof(float2) * (size_t)f->ld; }
+constexpr size_t kMaxStage = 200 * 1024;
+
+template <typename Col>
+static int launch_up_t(const FastView &v, const FastState *f, bool eps, const float2 *x, float2 *z, cudaStream_t s) {
+  const bool stage = up_smem(f) <= kMaxStage;
+  const int threads = v.n_up >= 4096 ? 512 : (v.n_up >= 512 ? 256 : 128);
+  int64_t grid = std::min<int64_t>(v.n_dn, (int64_t)num_sms() * (stage ? 2 : 4));
+  const size_t smem = stage ? up_smem(f) : 0;
+#define HUB_UP(ST, EP)                                                                                   \
+  do {                                                                                                   \
+    if (ST) HUB_CUDA(cudaFuncSetAttribute(k_up<Col, ST, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
+                                          (int)kMaxStage));                                              \
+    k_up<Col, ST, EP><<<(int)grid, threads, smem, s>>>(v, x, z);                                         \
+  } while (0)
+  if (stage) {
+    if (eps) HUB_UP(true, true); else HUB_UP(true, false);
+  } else {
+    if (eps) HUB_UP(false, true); else HUB_UP(false, false);
+  }
+#undef HUB_UP
+  HUB_LAUNCH_CHECK();
+  return HUB_OK;
+}
+
+static dim3 dn_grid(const FastView &v) {
+  return dim3((unsigned)((v.n_dn + kDnRows - 1) / kDnRows), (unsigned)((v.n_up + kDnCols - 1) / kDnCols));
+}
+
+template <typename Col, int kMode>
+static int launch_dn_t(const FastView &v, const float2 *x, const float2 *z, double *y, float2 *w,
+                       const int *shift_src, int nblk, LzArgs L, cudaStream_t s) {
+  const dim3 g = dn_grid(v);
+  if (g.y > 65535) return fail(HUB_ERR_ARG, "fast apply: too many column strips");
+  k_dn<Col, kMode><<<g, kDnThreads, 0, s>>>(v, x, z, y, w, shift_src, nblk, L);
+  HUB_LAUNCH_CHECK();
+  return HUB_OK;
+}
+
+// z <- pass 1 (x double-float, padded)
+static int run_up(hub_ctx *h, FastState *f, const float2 *x, float2 *z, cudaStream_t s) {
+  const FastView v = fast_view(h, f);
+  count_launch(h);
+  int rc = prof_mark(h, HUB_PROF_UP, true, s);
+  if (rc) return rc;
+  rc = f->col16 ? launch_up_t<uint16_t>(v, f, h->has_eps, x, z, s)
+                : launch_up_t<uint32_t>(v, f, h->has_eps, x, z, s);
+  if (rc) return rc;
+  return prof_mark(h, HUB_PROF_UP, false, s);
+}
+
+static int run_dn(hub_ctx *h, FastState *f, int mode, const float2 *x, const float2 *z, double *y, float2 *w,
+                  const int *shift_src, int nblk, LzArgs L, cudaStream_t s) {
+  const FastView v = fast_view(h, f);
+  count_launch(h);
+  int rc = prof_mark(h, HUB_PROF_DN, true, s);
+  if (rc) return rc;
+  if (mode == 0)
+    rc = f->col16 ? launch_dn_t<uint16_t, 0>(v, x, z, y, w, shift_src, nblk, L, s)
+                  : launch_dn_t<uint32_t, 0>(v, x, z, y, w, shift_src, nblk, L, s);
+  else
+    rc = f->col16 ? launch_dn_t<uint16_t, 1>(v, x, z, y, w, shift_src, nblk, L, s)
+                  : launch_dn_t<uint32_t, 1>(v, x, z, y, w, shift_src, nblk, L, s);
+  if (rc) return rc;
+  return prof_mark(h, HUB_PROF_DN, false, s);
+}
+
+static int ensure_vec(float2 **p, int64_t n, const char *what) {
+  if (*p) return HUB_OK;
+  return dev_alloc((void **)p, sizeof(float2) * n, what) ? HUB_OK : HUB_ERR_OOM;
+}
+
+// hub_apply on the fast path: FP64 in, FP64 out.
+int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
+  FastState *f = fast_of(h);
+  if (!f || !f->built) return fail(HUB_ERR_STATE, "fast apply: not built");
+  const int64_t Dp = h->count[1] * f->ld, D = h->count[0] * h->count[1];
+  int rc;
+  if ((rc = ensure_vec(&f->xdf, Dp, "apply scratch x")) || (rc = ensure_vec(&f->zdf, Dp, "apply scratch z")))
+    return rc;
+  const int G = grid_vec();
+  if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
+  count_launch(h, 2);
+  k_max_exp<<<G, 256, 0, s>>>(D, x, f->d_emax);
+  k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->xdf);
+  HUB_LAUNCH_CHECK();
+  if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
+  return run_dn(h, f, 0, f->xdf, f->zdf, y, nullptr, f->d_emax, G, LzArgs{}, s);
+}
+
+int fast_check_error(hub_ctx *h) {
+  FastState *f = fast_of(h);
+  if (!f) return HUB_OK;
+  int e = 0;
+  HUB_CUDA(cudaMemcpy(&e, f->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e) {
+    HUB_CUDA(cudaMemset(f->d_err, 0, sizeof(int)));
+    return fail(HUB_ERR_TIMEOUT, "a bounded wait for a staged row gave up (row copy never completed)");
+  }
+  return HUB_OK;
+}
+
+// ---------------------------------------------------------------------------------------
+// Double-float Lanczos (same recurrence as the FP64 driver; vectors kept unnormalised,
+// r_j = beta_{j-1} q_j, so the normalisation is folded into the apply's epilogue).
+// scal: [0] alpha_j, [1] beta_cur = |r_j|, [2] beta_prev = |r_{j-1}| (0 at the start).
+// ---------------------------------------------------------------------------------------
+int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out,
+                 int *iters, cudaStream_t s) {
+  FastState *f = fast_of(h);
+  if (!f || !f->built) return fail(HUB_ERR_STATE, "fast Lanczos: not built");
+  const int64_t Dp = h->count[1] * f->ld;
+  int rc;
+  for (int k = 0; k < 3; ++k)
+    if ((rc = ensure_vec(&f->lz[k], Dp, "Lanczos vector"))) return rc;
+  if ((rc = ensure_vec(&f->zdf, Dp, "apply scratch z"))) return rc;
+  const int G = grid_vec();
+  const FastView v0 = fast_view(h, f);
+  const dim3 gd = dn_grid(v0);
+  const int64_t n_dn_blocks = (int64_t)gd.x * gd.y;
+  if ((rc = ensure_partials(h, std::max<int64_t>(n_dn_blocks, G)))) return rc;
+  if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
+  if (!h->d_scal && !dev_alloc((void **)&h->d_scal, sizeof(double) * 8, "Lanczos scalars")) return HUB_ERR_OOM;
+  if (!h->h_scal) HUB_CUDA(cudaMallocHost((void **)&h->h_scal, sizeof(double) * 8));
+  double *scal = h->d_scal, *P = h->partials;
+  float2 *coef = f->coef;
+
+  // r_1 = x0 as double-float (no scaling), scal[1] = beta_0 = |x0|, scal[2] = 0
+  auto start = [&](float2 *r) -> int {
+    HUB_CUDA(cudaMemsetAsync(f->d_emax, 0, sizeof(int) * G, s));
+    count_launch(h, 3);
+    k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x0, f->d_emax, G, r);
+    k_df_norm2<<<G, 256, 0, s>>>(Dp, r, P);
+    HUB_LAUNCH_CHECK();
+    int rc2 = reduce_partials(P, G, scal + 1, 1, s);
+    if (rc2) return rc2;
+    HUB_CUDA(cudaMemsetAsync(scal + 2, 0, sizeof(double), s));
+    return HUB_OK;
+  };
+  // one step of the recurrence: w = H q_j - beta_prev q_{j-1}, alpha partials, then (with
+  // alpha in scal[0]) r_{j+1} = w - alpha q_j in place and |r_{j+1}|^2 partials
+  auto step_apply = [&](float2 *rp, float2 *rcur, float2 *w) -> int {
+    count_launch(h);
+    k_coeffs<<<1, 1, 0, s>>>(scal, coef);
+    HUB_LAUNCH_CHECK();
+    int rc2 = prof_mark(h, HUB_PROF_APPLY, true, s);
+    if (rc2) return rc2;
+    if ((rc2 = run_up(h, f, rcur, f->zdf, s))) return rc2;
+    LzArgs L{rcur, rp, coef, P};
+    if ((rc2 = run_dn(h, f, 1, rcur, f->zdf, nullptr, w, nullptr, 0, L, s))) return rc2;
+    return prof_mark(h, HUB_PROF_APPLY, false, s);
+  };
+  auto step_update = [&](float2 *rcur, float2 *w) -> int {
+    count_launch(h, 2);
+    k_coeffs<<<1, 1, 0, s>>>(scal, coef);
+    k_df_update<<<G, 256, 0, s>>>(Dp, w, rcur, coef, P);
+    HUB_LAUNCH_CHECK();
+    return HUB_OK;
+  };
+
+  float2 *rp = f->lz[0], *rcur = f->lz[1], *w = f->lz[2];
+  if ((rc = start(rcur))) return rc;
+  HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float2) * Dp, s));
+  HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  HUB_CUDA(cudaStreamSynchronize(s));
+  if (!(h->h_scal[1] > 0.0) || !std::isfinite(h->h_scal[1]))
+    return fail(HUB_ERR_ARG, "hub_lanczos_ground: start vector is zero or not finite");
+  double b_cur = h->h_scal[1];
+
+  h->alpha.clear();
+  h->beta.clear();
+  double E = 0.0, E_prev = 0.0;
+  int status = HUB_ERR_NOCONV;
+  for (int j = 0; j < maxit; ++j) {
+    if ((rc = step_apply(rp, rcur, w))) return rc;
+    if ((rc = reduce_partials(P, (int)n_dn_blocks, scal + 0, 0, s))) return rc;
+    if ((rc = step_update(rcur, w))) return rc;
+    if ((rc = reduce_partials(P, G, scal + 3, 1, s))) return rc;      // beta_j
+    HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    const double a = h->h_scal[0], b = h->h_scal[3];
+    if (!std::isfinite(a) || !std::isfinite(b)) return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha/beta");
+    h->alpha.push_back(a);
+    h->beta.push_back(b);
+    E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
+    if (tol > 0 && j > 0 && std::fabs(E - E_prev) < tol) {
+      status = HUB_OK;
+      break;
+    }
+    E_prev = E;
+    if (b <= 1e-14 * std::fmax(1.0, std::fabs(a))) {
+      status = HUB_CONVERGED_BREAKDOWN;
+      break;
+    }
+    // rotate: beta_prev <- beta_cur, beta_cur <- beta_j; r_{j-1} <- r_j <- r_{j+1}
+    count_launch(h);
+    k_set_scal<<<1, 1, 0, s>>>(scal, 1, b, 2, b_cur, -1, 0.0);
+    HUB_LAUNCH_CHECK();
+    b_cur = b;
+    float2 *t0 = rp;
+    rp = rcur;
+    rcur = w;
+    w = t0;
+  }
+  if (tol <= 0 && status == HUB_ERR_NOCONV) status = HUB_OK;
+  if ((rc = fast_check_error(h))) return rc;
+  *E0 = E;
+  const int k = (int)h->alpha.size();
+  if (iters) *iters = k;
+
+  if (psi_out) {
+    // second pass with the stored coefficients: psi = sum_j v_j q_j = sum_j v_j r_j / beta_{j-1}
+    std::vector<double> vv = tridiag_vector(h->alpha.data(), h->beta.data(), k, E);
+    if ((rc = ensure_vec(&f->psi, Dp, "ground-state vector"))) return rc;
+    rp = f->lz[0];
+    rcur = f->lz[1];
+    w = f->lz[2];
+    if ((rc = start(rcur))) return rc;
+    HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float2) * Dp, s));
+    HUB_CUDA(cudaMemsetAsync(f->psi, 0, sizeof(float2) * Dp, s));
+    double bc = b_cur;
+    HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    bc = h->h_scal[1];
+    for (int j = 0; j < k; ++j) {
+      count_launch(h, 2);
+      k_psi_coef<<<1, 1, 0, s>>>(scal, vv[j], coef);
+      k_df_axpy<<<G, 256, 0, s>>>(Dp, coef, 3, rcur, f->psi);
+      HUB_LAUNCH_CHECK();
+      if (j + 1 == k) break;
+      if ((rc = step_apply(rp, rcur, w))) return rc;
+      count_launch(h);
+      k_set_scal<<<1, 1, 0, s>>>(scal, 0, h->alpha[j], -1, 0.0, -1, 0.0);
+      HUB_LAUNCH_CHECK();
+      if ((rc = step_update(rcur, w))) return rc;
+      count_launch(h);
+      k_set_scal<<<1, 1, 0, s>>>(scal, 1, h->beta[j], 2, bc, -1, 0.0);
+      HUB_LAUNCH_CHECK();
+      bc = h->beta[j];
+      float2 *t0 = rp;
+      rp = rcur;
+      rcur = w;
+      w = t0;
+    }
+    count_launch(h, 3);
+    k_df_norm2<<<G, 256, 0, s>>>(Dp, f->psi, P);
+    HUB_LAUNCH_CHECK();
+    if ((rc = reduce_partials(P, G, scal + 5, 1, s))) return rc;
+    k_df_out_normalised<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, f->psi, scal, 5, psi_out);
+    HUB_LAUNCH_CHECK();
+    HUB_CUDA(cudaStreamSynchronize(s));
+    if ((rc = fast_check_error(h))) return rc;
+  }
+  if (status == HUB_ERR_NOCONV) set_error("hub_lanczos_ground: maxit reached before |dE0| < tol");
+  return status;
+}
+
+}  // namespace hub

@@ -43,7 +43,7 @@ struct SpinCSR {
   int32_t max_row = 0;
 };
 
-struct hub_ctx_impl;
+struct FastState;   // fast-path tables and scratch (hub_fast.cu)
 
 // Read-only view of everything a kernel needs, passed by value.
 struct Ham {
@@ -100,12 +100,16 @@ struct hub_ctx {
   // host-buffer apply
   double *hx = nullptr, *hy = nullptr;
 
-  // measurement: event pairs around apply launches, launch counters
+  // measurement: event pairs per kind (HUB_PROF_*), launch counters
   bool prof = false;
-  std::vector<cudaEvent_t> ev_start, ev_end;
-  int64_t n_apply = 0;                 // apply launches since hub_profile(h, 1)
-  int64_t n_timed = 0;                 // of which timed with an event pair
+  std::vector<cudaEvent_t> ev_start[3], ev_end[3];
+  int64_t n_launch[3] = {0, 0, 0};     // launches per kind since hub_profile(h, 1)
+  int64_t n_timed[3] = {0, 0, 0};      // of which timed with an event pair
   int64_t n_kernels = 0;               // all kernels launched since hub_profile(h, 1)
+
+  // fast path (double-float, two-pass apply) for uniform hopping and interaction
+  hub::FastState *fast = nullptr;
+  int mode = 0;                        // HUB_MODE_AUTO or HUB_MODE_FP64
 
   hub::Ham view() const;
 };
@@ -126,6 +130,19 @@ int reduce_partials(const double *partials, int n, double *out, int mode, cudaSt
 
 // Apply entry used by Lanczos and the VJP (no argument checks).
 int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s);
+
+// Fast path (hub_fast.cu).
+bool fast_eligible(const hub_ctx *h);
+int fast_build(hub_ctx *h);
+void fast_release(hub_ctx *h);
+int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s);
+int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out, int *iters,
+                 cudaStream_t s);
+int fast_check_error(hub_ctx *h);
+inline bool use_fast(const hub_ctx *h) { return h->mode == HUB_MODE_AUTO && h->fast && fast_eligible(h); }
+
+// Event pair around a launch of the given kind (no-op unless profiling).
+int prof_mark(hub_ctx *h, int kind, bool begin, cudaStream_t s);
 
 // Count kernel launches for the measurement hooks.
 inline void count_launch(hub_ctx *h, int n = 1) {

@@ -240,6 +240,16 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
   if (maxit < 1) return fail(HUB_ERR_ARG, "hub_lanczos_ground: maxit < 1");
   const int64_t D = h->count[0] * h->count[1];
   if (D == 0) return fail(HUB_ERR_ARG, "hub_lanczos_ground: empty sector");
+  if (use_fast(h)) {
+    if (!x0_dev) {
+      // the fast driver converts an FP64 start vector: draw it into the FP64 workspace
+      if (!h->work[2] && !dev_alloc((void **)&h->work[2], sizeof(double) * D, "start vector")) return HUB_ERR_OOM;
+      k_splitmix_uniform<<<vec_grid(), kVecThreads, 0, (cudaStream_t)stream>>>(D, h->work[2]);
+      HUB_LAUNCH_CHECK();
+      x0_dev = h->work[2];
+    }
+    return fast_lanczos(h, x0_dev, maxit, tol, E0, psi_dev, iters, (cudaStream_t)stream);
+  }
   rc = ensure_workspace(h, D);
   if (rc) return rc;
   cudaStream_t s = (cudaStream_t)stream;

@@ -471,6 +471,13 @@ extern "C" int hub_hopping(hub_t h, int n_bonds, const int32_t *bonds_host, cons
     if (e != cudaSuccess) return cuda_fail(e, "site-energy tables", __FILE__, __LINE__);
   }
   h->have_hop = true;
+  if (h->count[0] > 0 && h->count[1] > 0) {
+    int rc = fast_build(h);
+    if (rc != HUB_OK) {
+      fast_release(h);
+      return rc;
+    }
+  }
   return HUB_OK;
 }
 
@@ -532,8 +539,11 @@ extern "C" void hub_free(hub_t h) {
   if (h->h_scal) cudaFreeHost(h->h_scal);
   dev_free(h->hx);
   dev_free(h->hy);
-  for (cudaEvent_t e : h->ev_start) cudaEventDestroy(e);
-  for (cudaEvent_t e : h->ev_end) cudaEventDestroy(e);
+  fast_release(h);
+  for (int k = 0; k < 3; ++k) {
+    for (cudaEvent_t e : h->ev_start[k]) cudaEventDestroy(e);
+    for (cudaEvent_t e : h->ev_end[k]) cudaEventDestroy(e);
+  }
   cudaSetDevice(prev);
   delete h;
 }

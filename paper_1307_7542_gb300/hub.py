@@ -44,8 +44,10 @@ SIGNATURES = {
     "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
     "hub_grad": (_i, [_p, _p, _p, _p, _p, _p]),
     "hub_apply_vjp": (_i, [_p, _p, _p, _p, _p, _p, _p, _p]),
+    "hub_set_mode": (_i, [_p, _i]),
+    "hub_check": (_i, [_p]),
     "hub_profile": (_i, [_p, _i]),
-    "hub_profile_read": (_i, [_p, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "hub_profile_read": (_i, [_p, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "hub_free": (None, [_p]),
 }
 
@@ -186,11 +188,23 @@ def hub_profile(h, enable):
     _check(lib().hub_profile(h, 1 if enable else 0))
 
 
-def hub_profile_read(h):
-    """(summed apply milliseconds, apply launches, all kernel launches) since hub_profile(h, 1)."""
+HUB_MODE_AUTO, HUB_MODE_FP64 = 0, 1
+HUB_PROF_APPLY, HUB_PROF_UP, HUB_PROF_DN = 0, 1, 2
+
+
+def hub_profile_read(h, kind=HUB_PROF_APPLY):
+    """(summed milliseconds, launches) of one kind, and all kernel launches, since hub_profile(h, 1)."""
     ms, na, nk = _d(), _i64(), _i64()
-    _check(lib().hub_profile_read(h, ctypes.byref(ms), ctypes.byref(na), ctypes.byref(nk)))
+    _check(lib().hub_profile_read(h, kind, ctypes.byref(ms), ctypes.byref(na), ctypes.byref(nk)))
     return ms.value, na.value, nk.value
+
+
+def hub_set_mode(h, mode):
+    _check(lib().hub_set_mode(h, mode))
+
+
+def hub_check(h):
+    _check(lib().hub_check(h))
 
 
 def hub_free(h):

@@ -484,3 +484,74 @@ def test_autograd_ground_energy(hub):
         assert abs(total.item() - E.item()) < 1e-9
     finally:
         m.close()
+
+
+# -------------------------------------------------------------------------- fast path
+
+FAST_CASES = [
+    ("ring8", dict(M=8, n_up=4, n_dn=4)),                     # shared CSR, even rows
+    ("odd_rows", dict(M=7, n_up=3, n_dn=2)),                  # count_up = 35: padded rows
+    ("unequal", dict(M=10, n_up=3, n_dn=6)),
+    ("with_eps", dict(M=9, n_up=4, n_dn=5, eps=True)),
+    ("t_not_one", dict(M=9, n_up=5, n_dn=4, t=0.37)),
+]
+
+
+@pytest.mark.parametrize("name,kw", FAST_CASES, ids=[c[0] for c in FAST_CASES])
+def test_fast_and_fp64_modes(hub, name, kw):
+    """Uniform t and U select the double-float two-pass apply; HUB_MODE_FP64 the FP64
+    kernel.  Both agree with the oracle entry by entry (1e-13 |H||x|)."""
+    M = kw["M"]
+    bonds = W.ring_bonds(M) if name != "unequal" else np.concatenate([W.ring_bonds(M), [[0, 5], [2, 7]]])
+    w = dict(M=M, n_up=kw["n_up"], n_dn=kw["n_dn"], bonds=bonds, t=np.full(len(bonds), kw.get("t", 1.0)),
+             U=np.full(M, 3.0), eps=W.uniform(5, M, -0.5, 0.5) if kw.get("eps") else np.zeros(M))
+    m = _gpu_model(hub, w)
+    om = oracle_model(w)
+    try:
+        B = O.basis(M, w["n_up"], w["n_dn"])
+        x = W.normal(17, B.shape[0])
+        ref, bound = O.apply(om, B, x), abs_bound(om, B, x)
+        xd = torch.from_numpy(x).cuda()
+        y_fast = m.apply(xd).cpu().numpy()
+        hub.hub_set_mode(m.h, hub.HUB_MODE_FP64)
+        y_f64 = m.apply(xd).cpu().numpy()
+        hub.hub_set_mode(m.h, hub.HUB_MODE_AUTO)
+        assert_entrywise(y_fast, ref, bound)
+        assert_entrywise(y_f64, ref, bound)
+        hub.hub_check(m.h)
+    finally:
+        m.close()
+
+
+def test_fast_wide_dynamic_range(hub):
+    """Entries spanning 1e-18 .. 1e2 (and exact zeros): the per-entry bound still holds."""
+    w = W.ring8()
+    m = _gpu_model(hub, w)
+    om = oracle_model(w)
+    try:
+        B = O.basis(8, 4, 4)
+        x = W.normal(3, B.shape[0]) * 10.0 ** W.uniform(4, B.shape[0], -18, 2)
+        x[::17] = 0.0
+        y = m.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert_entrywise(y, O.apply(om, B, x), abs_bound(om, B, x))
+        for scale in (1e-200, 1e250):
+            ys = m.apply(torch.from_numpy(x * scale).cuda()).cpu().numpy()
+            assert_entrywise(ys, O.apply(om, B, x * scale), abs_bound(om, B, x * scale))
+    finally:
+        m.close()
+
+
+def test_fast_lanczos_matches_fp64_lanczos(hub):
+    """The double-float Lanczos and the FP64 Lanczos reach the same E0 (1e-10 relative)
+    and the same psi, on a sector with unequal spins."""
+    w = dict(M=10, n_up=4, n_dn=5, bonds=W.ring_bonds(10), t=np.ones(10), U=np.full(10, 4.0), eps=np.zeros(10))
+    m = _gpu_model(hub, w)
+    try:
+        x0 = torch.from_numpy(W.normal(2, m.D)).cuda()
+        r1 = m.ground(x0, maxit=400, tol=1e-13, want_psi=True)
+        hub.hub_set_mode(m.h, hub.HUB_MODE_FP64)
+        r2 = m.ground(x0, maxit=400, tol=1e-13, want_psi=True)
+        assert abs(r1["E0"] - r2["E0"]) <= 1e-10 * abs(r2["E0"])
+        assert 1.0 - abs(torch.dot(r1["psi"], r2["psi"]).item()) < 1e-9
+    finally:
+        m.close()
