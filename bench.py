@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--lanczos-iters", type=int, default=200, help="iterations of the E0 wall-time run")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--workload", default="4x4", choices=sorted(WORKLOADS),
+                   help="4x4: the benchmark case; the others are smaller cases for profiling")
     return p.parse_args()
 
 
@@ -117,15 +119,26 @@ def smi_index(local_rank):
     return local_rank
 
 
-def workload(U):
+WORKLOADS = {
+    "4x4": ("4x4 periodic square lattice, half filling (8,8), t=1", 8, 8),
+    "4x4-sector66": ("4x4 periodic square lattice, sector (6,6), t=1 (profiling case)", 6, 6),
+}
+
+
+def workload(U, name="4x4"):
     from paper_1307_7542_gb300 import workloads as W
-    return W.square4x4(U)
+    w = W.square4x4(U)
+    _, nu, nd = WORKLOADS[name]
+    w["n_up"], w["n_dn"] = nu, nd
+    w["label"] = WORKLOADS[name][0]
+    return w
 
 
 def config_json(w, D, n_gpus):
-    return {"workload": f"4x4 periodic square lattice, half filling (8,8), t=1, U={w['U'][0]:g}",
-            "M": 16, "n_up": 8, "n_dn": 8, "dim": D, "step": "one Lanczos iteration (apply + recurrence)",
-            "vector_bytes": 8 * D, "l2": "inputs larger than L2 (1.33 GB per FP64 vector); no flush needed",
+    return {"workload": f"{w['label']}, U={w['U'][0]:g}",
+            "M": 16, "n_up": w["n_up"], "n_dn": w["n_dn"], "dim": D,
+            "step": "one Lanczos iteration (apply + recurrence)",
+            "vector_bytes": 8 * D, "l2": f"inputs larger than L2 ({8 * D / 1e9:.2f} GB per FP64 vector); no flush needed",
             "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}
 
 
@@ -160,11 +173,11 @@ def run_reference(a):
     import numpy as np
     from oracle import hub_oracle as O
     from paper_1307_7542_gb300 import workloads as W
-    w = workload(a.U)
-    D = math.comb(16, 8) ** 2
+    w = workload(a.U, a.workload)
+    D = math.comb(16, w["n_up"]) * math.comb(16, w["n_dn"])
     x = W.normal(0, D)
     om = O.Model(w["M"], w["bonds"], w["t"], w["U"], w["eps"])
-    B = O.basis(16, 8, 8)
+    B = O.basis(16, w["n_up"], w["n_dn"])
     # size one step (a bounded sample of rows) to about 2 s of CPU
     r = 20000
     while True:
@@ -215,7 +228,7 @@ def run_gpu(a):
     from paper_1307_7542_gb300 import hub
     from paper_1307_7542_gb300 import workloads as W
 
-    w = workload(a.U)
+    w = workload(a.U, a.workload)
     t_setup = time.perf_counter()
     m = hub.Hubbard(w["M"], w["n_up"], w["n_dn"], w["bonds"], w["t"], w["U"], w["eps"])
     setup_s = time.perf_counter() - t_setup
@@ -290,34 +303,38 @@ def run_gpu(a):
                     "apply": apply}
 
     # Lanczos E0 wall time: a full run of a.lanczos_iters iterations, energy only
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    rl = m.ground(x0, maxit=a.lanczos_iters, tol=0.0)
-    torch.cuda.synchronize()
-    lanczos = {"E0": rl["E0"], "iterations": rl["iters"], "wall_s": time.perf_counter() - t0}
+    lanczos = None
+    if a.lanczos_iters > 0:
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        rl = m.ground(x0, maxit=a.lanczos_iters, tol=0.0)
+        torch.cuda.synchronize()
+        lanczos = {"E0": rl["E0"], "iterations": rl["iters"], "wall_s": time.perf_counter() - t0}
 
     # end-to-end: the host-buffer apply through the C ABI (H2D + apply + D2H each step)
-    xh = torch.from_numpy(x_host).pin_memory()
-    yh = torch.empty(D, dtype=torch.float64).pin_memory()
-    hub.hub_apply_host(m.h, xh, yh)
-    torch.cuda.synchronize()
-    t0 = time.perf_counter()
-    for _ in range(a.e2e_steps):
+    e2e = None
+    if a.e2e_steps > 0:
+        xh = torch.from_numpy(x_host).pin_memory()
+        yh = torch.empty(D, dtype=torch.float64).pin_memory()
         hub.hub_apply_host(m.h, xh, yh)
-    e2e_s = time.perf_counter() - t0
-    e2e = {"value": world * a.e2e_steps / e2e_s, "unit": "applies/s",
-           "h2d_bytes_per_step": 8 * D, "d2h_bytes_per_step": 8 * D,
-           "call": "hub_apply_host (pinned host x in, host y out)"}
-    del xh, yh
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(a.e2e_steps):
+            hub.hub_apply_host(m.h, xh, yh)
+        e2e_s = time.perf_counter() - t0
+        e2e = {"value": world * a.e2e_steps / e2e_s, "unit": "applies/s",
+               "h2d_bytes_per_step": 8 * D, "d2h_bytes_per_step": 8 * D,
+               "call": "hub_apply_host (pinned host x in, host y out)"}
+        del xh, yh
 
-    line = {"metric": "H.x applies/s (4x4 PBC half filling, U=4); Lanczos E0 wall time",
+    line = {"metric": "H.x applies/s (4x4 PBC half filling, U=4)",
             "value": value, "unit": "applies/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": config_json(w, D, world), "roofline": roofline, "lanczos_e0": lanczos,
             "setup_s": setup_s, "e2e": e2e, "gpu_launches": n_kern, "clocks": clk}
 
-    if rank == 0 and world == 1 and not a.no_cpu_baseline:
+    if rank == 0 and world == 1 and not a.no_cpu_baseline and a.e2e_steps >= 0:
         aps, R, el, thr, _, _ = oracle_sample(w, x_host, a.cpu_seconds)
         line["cpu_baseline"] = {"value": aps, "unit": "applies/s", "cores": thr, "kind": "oracle",
                                 "sample": f"oracle apply of {R} of {D} output rows ({el:.1f} s), scaled to "

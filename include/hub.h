@@ -82,7 +82,7 @@ int hub_get_basis(hub_t h, int spin, uint32_t *basis_host);
 /*
  * One-spin hopping matrices H_up and H_dn (Sec. III.A, Eq. 8; Sec. IV.A, Eqs. 9-10),
  * built on the GPU in CSR form.  bonds_host[2b], bonds_host[2b+1] are the 0-based sites
- * of undirected bond b (b < n_bonds <= 256), i != j, no bond listed twice; t_host[b] its
+ * of undirected bond b (b < n_bonds <= 255), i != j, no bond listed twice; t_host[b] its
  * hopping.  eps_host[M] are site energies or NULL for zero.  For a spin string s and a
  * bond (i, j) with exactly one end occupied the row of s holds the column
  * rank(s ^ (1<<i) ^ (1<<j)) with value -t_b * (-1)^(popcount of s strictly between i

@@ -85,6 +85,12 @@ struct FastView {
   const int32_t *rp_up, *sp_up;      // row start and sign split of H_up
   const int32_t *rp_dn, *sp_dn;
   const void *col_up, *col_dn;       // uint16 or uint32 columns
+  // H_up in sliced column-major form for pass 1: rows in slices of 32 (lane = u % 32);
+  // entry j of row u (add group, then sub group) at off[u/32] + j*32 + u%32, in units of
+  // Col words, with two uint16 columns packed per 32-bit word when Col is uint16.
+  const uint32_t *sl_add, *sl_sub;   // packed words
+  const int32_t *sl_off_add, *sl_off_sub;
+  const uint8_t *len_add, *len_sub;  // per-row entry counts
   const float2 *eps_up, *eps_dn;     // per-state site energies (double-float) or null
   float2 t;                          // uniform hopping t (double-float)
   int t_is_one;
@@ -112,6 +118,41 @@ __global__ void k_split_csr(int64_t n, const int32_t *__restrict__ rp, const uin
     sp[r] = w;
     for (int32_t k = a; k < b; ++k)
       if (!(scol[k] >> 31)) col[w++] = (Col)(scol[k] & 0x7fffffffu);
+  }
+}
+
+// Per-row lengths of the add and sub groups.
+__global__ void k_group_len(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ sp,
+                            uint8_t *__restrict__ la, uint8_t *__restrict__ ls) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    la[r] = (uint8_t)(sp[r] - rp[r]);
+    ls[r] = (uint8_t)(rp[r + 1] - sp[r]);
+  }
+}
+
+// Fill the sliced arrays; per words: 2 uint16 columns per 32-bit word (kPack = 2) or one
+// uint32 column (kPack = 1).  Unused halves are zero and never read.
+template <int kPack>
+__global__ void k_slice_fill(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ sp,
+                             const void *__restrict__ col, const int32_t *__restrict__ off_a,
+                             const int32_t *__restrict__ off_s, uint32_t *__restrict__ wa,
+                             uint32_t *__restrict__ ws) {
+  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t sl = r >> 5, lane = r & 31;
+    for (int g = 0; g < 2; ++g) {
+      const int32_t a = g == 0 ? rp[r] : sp[r], b = g == 0 ? sp[r] : rp[r + 1];
+      uint32_t *dst = (g == 0 ? wa + off_a[sl] : ws + off_s[sl]) + lane;
+      for (int32_t k = a, j = 0; k < b; k += kPack, ++j) {
+        uint32_t word;
+        if (kPack == 2) {
+          const uint16_t *c = (const uint16_t *)col;
+          word = (uint32_t)c[k] | (k + 1 < b ? (uint32_t)c[k + 1] << 16 : 0u);
+        } else {
+          word = ((const uint32_t *)col)[k];
+        }
+        dst[(int64_t)j * 32] = word;
+      }
+    }
   }
 }
 
@@ -168,15 +209,15 @@ __global__ void __launch_bounds__(512, 2) k_up(const FastView F, const float2 *_
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2 *xs = reinterpret_cast<float2 *>(smem_raw);
   __shared__ __align__(8) uint64_t bar;
+  __shared__ float2 utab[32];
   const int tid = threadIdx.x;
   const uint32_t bytes = (uint32_t)(F.ld * sizeof(float2));
-  if (kStage) {
-    if (tid == 0) {
-      mbar_init(&bar, 1);
-      fence_mbar_init();
-    }
-    __syncthreads();
+  if (tid < 32) utab[tid] = F.Utab[tid];
+  if (kStage && tid == 0) {
+    mbar_init(&bar, 1);
+    fence_mbar_init();
   }
+  __syncthreads();
   uint32_t phase = 0;
   for (int64_t d = blockIdx.x; d < F.n_dn; d += gridDim.x) {
     const float2 *__restrict__ xrow = x + d * F.ld;
@@ -199,14 +240,29 @@ __global__ void __launch_bounds__(512, 2) k_up(const FastView F, const float2 *_
     if (kEps) ed = F.eps_dn[d];
     for (int64_t u = tid; u < F.n_up; u += blockDim.x) {
       DfAcc ap{0.f, 0.f}, am{0.f, 0.f};
-      const int32_t k0 = F.rp_up[u], ks = F.sp_up[u], k1 = F.rp_up[u + 1];
-      int32_t k = k0;
-      for (; k < ks; ++k) acc_add(ap, src[colat<Col>(F.col_up, k)]);
-      for (; k < k1; ++k) acc_add(am, src[colat<Col>(F.col_up, k)]);
+      const int64_t sl = u >> 5, lane = u & 31;
+      const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
+      const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
+      const int na = F.len_add[u], ns = F.len_sub[u];
+      if (sizeof(Col) == 2) {
+        for (int j = 0; 2 * j < na; ++j) {
+          const uint32_t wd = wa[j * 32];
+          acc_add(ap, src[wd & 0xffffu]);
+          if (2 * j + 1 < na) acc_add(ap, src[wd >> 16]);
+        }
+        for (int j = 0; 2 * j < ns; ++j) {
+          const uint32_t wd = wsb[j * 32];
+          acc_add(am, src[wd & 0xffffu]);
+          if (2 * j + 1 < ns) acc_add(am, src[wd >> 16]);
+        }
+      } else {
+        for (int j = 0; j < na; ++j) acc_add(ap, src[wa[j * 32]]);
+        for (int j = 0; j < ns; ++j) acc_add(am, src[wsb[j * 32]]);
+      }
       const float2 sp = acc_value(ap), sm = acc_value(am);
       float2 S = df_add(sp, make_float2(-sm.x, -sm.y));
       if (!F.t_is_one) S = df_mul(S, F.t);
-      float2 dg = F.Utab[__popc(F.basis_up[u] & Id)];
+      float2 dg = utab[__popc(F.basis_up[u] & Id)];
       if (kEps) dg = df_add(df_add(dg, F.eps_up[u]), ed);
       z[d * F.ld + u] = df_fma(dg, src[u], S);
     }
@@ -408,6 +464,9 @@ struct FastState {
   float2 *coef = nullptr;                    // recurrence coefficients (double-float)
   bool col16 = true;
   int32_t *sp[2] = {nullptr, nullptr};
+  uint32_t *sl_add = nullptr, *sl_sub = nullptr;
+  int32_t *sl_off_add = nullptr, *sl_off_sub = nullptr;
+  uint8_t *len_add = nullptr, *len_sub = nullptr;
   void *col[2] = {nullptr, nullptr};
   float2 *eps_df[2] = {nullptr, nullptr};
   float2 *xdf = nullptr, *zdf = nullptr;     // hub_apply scratch
@@ -435,6 +494,12 @@ void fast_release(hub_ctx *h) {
   dev_free(f->d_emax);
   dev_free(f->d_err);
   dev_free(f->coef);
+  dev_free(f->sl_add);
+  dev_free(f->sl_sub);
+  dev_free(f->sl_off_add);
+  dev_free(f->sl_off_sub);
+  dev_free(f->len_add);
+  dev_free(f->len_sub);
   delete f;
   h->fast = nullptr;
 }
@@ -474,6 +539,46 @@ int fast_build(hub_ctx *h) {
       HUB_LAUNCH_CHECK();
     }
   }
+  // sliced H_up for pass 1
+  {
+    const int64_t n = h->count[0];
+    const int64_t nsl = (n + 31) / 32;
+    if (!dev_alloc((void **)&f->len_add, n, "row lengths") || !dev_alloc((void **)&f->len_sub, n, "row lengths"))
+      return HUB_ERR_OOM;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
+    k_group_len<<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->len_add, f->len_sub);
+    HUB_LAUNCH_CHECK();
+    std::vector<uint8_t> la(n), ls(n);
+    HUB_CUDA(cudaMemcpy(la.data(), f->len_add, n, cudaMemcpyDeviceToHost));
+    HUB_CUDA(cudaMemcpy(ls.data(), f->len_sub, n, cudaMemcpyDeviceToHost));
+    const int pack = f->col16 ? 2 : 1;
+    std::vector<int32_t> oa(nsl + 1, 0), os(nsl + 1, 0);
+    for (int64_t sl = 0; sl < nsl; ++sl) {
+      int ma = 0, ms = 0;
+      for (int64_t r = sl * 32; r < std::min(n, sl * 32 + 32); ++r) {
+        ma = std::max(ma, (int)la[r]);
+        ms = std::max(ms, (int)ls[r]);
+      }
+      oa[sl + 1] = oa[sl] + 32 * ((ma + pack - 1) / pack);
+      os[sl + 1] = os[sl] + 32 * ((ms + pack - 1) / pack);
+    }
+    if (!dev_alloc((void **)&f->sl_off_add, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
+        !dev_alloc((void **)&f->sl_off_sub, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
+        !dev_alloc((void **)&f->sl_add, sizeof(uint32_t) * std::max<int32_t>(oa[nsl], 1), "sliced columns") ||
+        !dev_alloc((void **)&f->sl_sub, sizeof(uint32_t) * std::max<int32_t>(os[nsl], 1), "sliced columns"))
+      return HUB_ERR_OOM;
+    HUB_CUDA(cudaMemcpy(f->sl_off_add, oa.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+    HUB_CUDA(cudaMemcpy(f->sl_off_sub, os.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+    HUB_CUDA(cudaMemset(f->sl_add, 0, sizeof(uint32_t) * std::max<int32_t>(oa[nsl], 1)));
+    HUB_CUDA(cudaMemset(f->sl_sub, 0, sizeof(uint32_t) * std::max<int32_t>(os[nsl], 1)));
+    if (pack == 2)
+      k_slice_fill<2><<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->col[0], f->sl_off_add, f->sl_off_sub,
+                                  f->sl_add, f->sl_sub);
+    else
+      k_slice_fill<1><<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->col[0], f->sl_off_add, f->sl_off_sub,
+                                  f->sl_add, f->sl_sub);
+    HUB_LAUNCH_CHECK();
+  }
   if (!dev_alloc((void **)&f->d_err, sizeof(int) * 4, "error flag") ||
       !dev_alloc((void **)&f->coef, sizeof(float2) * 8, "recurrence coefficients"))
     return HUB_ERR_OOM;
@@ -497,6 +602,12 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   v.sp_dn = f->sp[sd];
   v.col_up = f->col[0];
   v.col_dn = f->col[sd];
+  v.sl_add = f->sl_add;
+  v.sl_sub = f->sl_sub;
+  v.sl_off_add = f->sl_off_add;
+  v.sl_off_sub = f->sl_off_sub;
+  v.len_add = f->len_add;
+  v.len_sub = f->len_sub;
   v.eps_up = f->eps_df[0];
   v.eps_dn = f->eps_df[sd];
   const double t = h->t.empty() ? 0.0 : h->t[0];

@@ -13,7 +13,7 @@
 namespace hub {
 
 constexpr int kMaxSites = 30;   // spin strings fit in uint32, two-spin index fits in int64
-constexpr int kMaxBonds = 256;
+constexpr int kMaxBonds = 255;   // bond ids and per-row group lengths fit in uint8
 
 // ---------------------------------------------------------------------------------------
 // Errors: every entry point returns a code; the message goes to a thread-local string.

@@ -414,7 +414,7 @@ extern "C" int hub_get_basis(hub_t h, int spin, uint32_t *basis_host) {
 extern "C" int hub_hopping(hub_t h, int n_bonds, const int32_t *bonds_host, const double *t_host,
                            const double *eps_host) {
   if (!h) return fail(HUB_ERR_ARG, "hub_hopping: NULL handle");
-  if (n_bonds < 0 || n_bonds > kMaxBonds) return fail(HUB_ERR_ARG, "hub_hopping: need 0 <= n_bonds <= 256");
+  if (n_bonds < 0 || n_bonds > kMaxBonds) return fail(HUB_ERR_ARG, "hub_hopping: need 0 <= n_bonds <= 255");
   if (n_bonds > 0 && (!bonds_host || !t_host)) return fail(HUB_ERR_ARG, "hub_hopping: NULL bonds or t");
   BondTable bt{};
   bt.n = n_bonds;
