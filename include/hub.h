@@ -143,6 +143,29 @@ int hub_grad(hub_t h, const double *psi_dev, double *dE_dt_host, double *dE_dU_h
              double *dE_deps_host, void *stream);
 
 /*
+ * hub_grad without any memory allocation (the paper has no counterpart; this is a service
+ * for callers).  Some callers cannot allocate device memory at call time: code that
+ * owns the whole device through its own memory pool (the pool would have to give memory
+ * back), code on a latency-critical path (cudaMalloc and cudaFree can synchronise the
+ * device), and code that must not change the device's memory footprint after start-up.
+ * This entry point computes the same quadratic forms as hub_grad, but its scratch (per-
+ * block partial sums and the reduced results) is a fixed array of 779,520 bytes compiled
+ * into the library, which every GPU that loads the library holds until the process exits.
+ * The caller still owns psi and the host output arrays; the handle's own tables were
+ * allocated when it was built.
+ *   - Limit: n_bonds + 2*M <= 160; larger models return HUB_ERR_ARG (use hub_grad).
+ *   - The handle's device must be the current device.  The first call on a device looks
+ *     up the array's device address (cudaGetSymbolAddress); make that first call before
+ *     any stream capture.
+ *   - All calls share the one array: calls that overlap on the GPU (two streams, two
+ *     threads, two handles) race and give wrong results.  Every value a call reads from
+ *     the array is written earlier in the same call, so nothing needs clearing.
+ *   - Blocks until the results are in the host arrays.
+ */
+int hub_grad_noalloc(hub_t h, const double *psi_dev, double *dE_dt_host, double *dE_dU_host,
+                     double *dE_deps_host, void *stream);
+
+/*
  * Vector-Jacobian product of y = H(theta) x for a cotangent ybar:
  *   xbar_dev = H ybar (H is symmetric), and the parameter cotangents
  *   tbar[b] = ybar^T (dH/dt_b) x, Ubar[i] = ybar^T (dH/dU_i) x, epsbar[i] = ybar^T (dH/deps_i) x

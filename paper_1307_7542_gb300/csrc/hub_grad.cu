@@ -161,3 +161,85 @@ extern "C" int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_de
   }
   return HUB_OK;
 }
+
+// ---------------------------------------------------------------------------------------
+// hub_grad_noalloc: the Hellmann-Feynman gradients with no memory allocation at call time.
+// The per-block partial sums and the reduced results live in one file-scope device array
+// of fixed size instead of the handle's lazily allocated scratch.
+// ---------------------------------------------------------------------------------------
+namespace hub {
+
+constexpr int kNoAllocMaxParams = 160;   // n_bonds + 2M that fit the fixed array
+constexpr int kNoAllocMaxBlocks = 608;   // partial sums kept per parameter
+constexpr int64_t kNoAllocDoubles = (int64_t)kNoAllocMaxBlocks * kNoAllocMaxParams + kNoAllocMaxParams;
+
+// 608 * 160 + 160 doubles = 779,520 bytes, held by every GPU that loads the library.
+static __device__ __align__(256) double g_grad_scratch[kNoAllocDoubles];
+
+// Device address of g_grad_scratch, looked up once per device with that device current.
+// In host code the symbol g_grad_scratch is only a host-side stand-in; kernels must be
+// given this address.
+constexpr int kMaxDevices = 64;
+static double *g_scratch_addr[kMaxDevices] = {nullptr};
+
+static int noalloc_scratch(int dev, double **out) {
+  if (dev < 0 || dev >= kMaxDevices) return fail(HUB_ERR_ARG, "hub_grad_noalloc: device ordinal out of range");
+  if (!g_scratch_addr[dev]) {
+    void *p = nullptr;
+    HUB_CUDA(cudaGetSymbolAddress(&p, g_grad_scratch));
+    g_scratch_addr[dev] = static_cast<double *>(p);
+  }
+  *out = g_scratch_addr[dev];
+  return HUB_OK;
+}
+
+}  // namespace hub
+
+extern "C" int hub_grad_noalloc(hub_t h, const double *psi_dev, double *dE_dt_host, double *dE_dU_host,
+                                double *dE_deps_host, void *stream) {
+  int rc = ready(h, "hub_grad_noalloc");
+  if (rc) return rc;
+  if (!psi_dev) return fail(HUB_ERR_ARG, "hub_grad_noalloc: psi is NULL");
+  const int n_par = h->n_bonds + 2 * h->M;
+  if (n_par > kNoAllocMaxParams)
+    return fail(HUB_ERR_ARG, "hub_grad_noalloc: n_bonds + 2*M = " + std::to_string(n_par) +
+                                 " exceeds the fixed scratch capacity of " + std::to_string(kNoAllocMaxParams) +
+                                 " parameters; use hub_grad");
+  int dev = 0;
+  HUB_CUDA(cudaGetDevice(&dev));
+  if (dev != h->device) return fail(HUB_ERR_ARG, "hub_grad_noalloc: the handle's device is not the current device");
+  double *scratch = nullptr;
+  if ((rc = noalloc_scratch(dev, &scratch))) return rc;
+
+  const Ham H = h->view();
+  GradArgs G;
+  G.n_bonds = h->n_bonds;
+  G.n_par = n_par;
+  G.bond_up = h->csr[0].bond;
+  G.bond_dn = h->csr[h->shared ? 0 : 1].bond;
+  int nblk = (int)std::min<int64_t>(H.n_dn, (int64_t)num_sms() * 4);
+  nblk = std::max(1, std::min(nblk, kNoAllocMaxBlocks));
+  // every partial the reduction reads is written by this call's first kernel, and every
+  // result by its second, so nothing needs clearing between calls
+  double *P = scratch, *out = scratch + (int64_t)n_par * nblk;
+  cudaStream_t s = (cudaStream_t)stream;
+  const size_t bins_bytes = sizeof(double) * ((n_par + 1) & ~1);
+  const size_t row_bytes = sizeof(double) * (size_t)H.n_up;
+  if (bins_bytes + row_bytes <= 200 * 1024) {
+    HUB_CUDA(cudaFuncSetAttribute(k_bilinear<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    k_bilinear<true><<<nblk, 256, bins_bytes + row_bytes, s>>>(H, G, psi_dev, psi_dev, P);
+  } else {
+    k_bilinear<false><<<nblk, 256, bins_bytes, s>>>(H, G, psi_dev, psi_dev, P);
+  }
+  HUB_LAUNCH_CHECK();
+  k_reduce_rows<<<n_par, 256, 0, s>>>(P, nblk, out);
+  HUB_LAUNCH_CHECK();
+  if (dE_dt_host && h->n_bonds)
+    HUB_CUDA(cudaMemcpyAsync(dE_dt_host, out, sizeof(double) * h->n_bonds, cudaMemcpyDeviceToHost, s));
+  if (dE_dU_host)
+    HUB_CUDA(cudaMemcpyAsync(dE_dU_host, out + h->n_bonds, sizeof(double) * h->M, cudaMemcpyDeviceToHost, s));
+  if (dE_deps_host)
+    HUB_CUDA(cudaMemcpyAsync(dE_deps_host, out + h->n_bonds + h->M, sizeof(double) * h->M, cudaMemcpyDeviceToHost, s));
+  HUB_CUDA(cudaStreamSynchronize(s));
+  return HUB_OK;
+}

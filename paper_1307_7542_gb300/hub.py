@@ -44,6 +44,7 @@ SIGNATURES = {
     "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
     "hub_grad": (_i, [_p, _p, _p, _p, _p, _p]),
     "hub_apply_vjp": (_i, [_p, _p, _p, _p, _p, _p, _p, _p]),
+    "hub_grad_noalloc": (_i, [_p, _p, _p, _p, _p, _p]),
     "hub_set_mode": (_i, [_p, _i]),
     "hub_check": (_i, [_p]),
     "hub_profile": (_i, [_p, _i]),
@@ -172,6 +173,13 @@ def hub_lanczos_coeffs(h, cap=100000):
 def hub_grad(h, psi, n_bonds, M, stream=None):
     dt, dU, de = np.empty(n_bonds), np.empty(M), np.empty(M)
     _check(lib().hub_grad(h, _ptr(psi), _ptr(dt), _ptr(dU), _ptr(de), _stream(stream)))
+    return dt, dU, de
+
+
+def hub_grad_noalloc(h, psi, n_bonds, M, stream=None):
+    """hub_grad with its scratch in a fixed device array (no allocation at call time)."""
+    dt, dU, de = np.empty(n_bonds), np.empty(M), np.empty(M)
+    _check(lib().hub_grad_noalloc(h, _ptr(psi), _ptr(dt), _ptr(dU), _ptr(de), _stream(stream)))
     return dt, dU, de
 
 
