@@ -80,6 +80,52 @@ __device__ __forceinline__ float2 df_mul(float2 a, float2 b) {
 // a * b + c for double-floats.
 __device__ __forceinline__ float2 df_fma(float2 a, float2 b, float2 c) { return df_add(df_mul(a, b), c); }
 
+// ---------------------------------------------------------------------------------------
+// Two independent double-float accumulators advanced together with the packed FP32x2
+// instructions of sm_100+ (add.rn.f32x2 / sub.rn.f32x2: two IEEE round-to-nearest FP32
+// operations per instruction), so TwoSum costs 6 instructions for two sums.
+// ---------------------------------------------------------------------------------------
+typedef unsigned long long f2x;   // (lane a, lane b) packed in one 64-bit register
+
+__device__ __forceinline__ f2x pk2(float a, float b) {
+  f2x r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ float2 upk2(f2x r) {
+  float a, b;
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
+  return make_float2(a, b);
+}
+__device__ __forceinline__ f2x add2(f2x a, f2x b) {
+  f2x r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+  f2x r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+
+struct DfAcc2 {
+  f2x H, L;   // high parts (exact running sums) and low parts + TwoSum errors, per lane
+};
+
+__device__ __forceinline__ void acc2_add(DfAcc2 &a, f2x vh, f2x vl) {
+  const f2x s = add2(a.H, vh);
+  const f2x bb = sub2(s, a.H);
+  const f2x e = add2(sub2(a.H, sub2(s, bb)), sub2(vh, bb));
+  a.H = s;
+  a.L = add2(add2(a.L, vl), e);
+}
+
+// Lane a / lane b of a paired accumulator as a plain accumulator.
+__device__ __forceinline__ DfAcc acc2_lane(const DfAcc2 &a, int lane) {
+  const float2 h = upk2(a.H), l = upk2(a.L);
+  return lane == 0 ? DfAcc{h.x, l.x} : DfAcc{h.y, l.y};
+}
+
 // 2^k as a float for -126 <= k <= 127.
 __device__ __forceinline__ float pow2f(int k) { return __uint_as_float((uint32_t)(k + 127) << 23); }
 

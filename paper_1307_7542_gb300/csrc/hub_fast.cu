@@ -17,7 +17,12 @@
 //     128-bit loads of whole rows of the strip.
 //
 // Vectors are double-float (hub_df.cuh) with rows padded to an even length so that every
-// row starts on a 16-byte boundary (bulk copies and 16-byte loads).  The hopping rows are
+// row starts on a 16-byte boundary (bulk copies and 16-byte loads).  Inside this file the
+// columns of X are kept in "slot" order: spin-up states sorted by the lengths of their
+// two hopping groups, so that the 32 rows of H_up a warp sums in pass 1 have nearly equal
+// lengths (little divergence) while its loads and stores stay contiguous.  Pass 2 combines
+// whole rows and does not care about column order.  Only the FP64 <-> double-float
+// conversions at the boundary of this file map slots back to ranks.  The hopping rows are
 // reordered by sign (entries adding x first, then entries subtracting x), so no per-term
 // sign handling is needed, and columns are stored as uint16 when count <= 65536.
 #include <algorithm>
@@ -85,13 +90,16 @@ struct FastView {
   const int32_t *rp_up, *sp_up;      // row start and sign split of H_up
   const int32_t *rp_dn, *sp_dn;
   const void *col_up, *col_dn;       // uint16 or uint32 columns
-  // H_up in sliced column-major form for pass 1: rows in slices of 32 (lane = u % 32);
-  // entry j of row u (add group, then sub group) at off[u/32] + j*32 + u%32, in units of
-  // Col words, with two uint16 columns packed per 32-bit word when Col is uint16.
+  // H_up in sliced column-major form for pass 1.  Rows are placed in slots ordered by their
+  // (add, sub) group lengths so that the 32 rows a warp handles have nearly equal lengths;
+  // slot k holds row slot_row[k]; entry j of slot k is word off[k/32] + j*32 + k%32, with
+  // two uint16 columns packed per 32-bit word when Col is uint16.
   const uint32_t *sl_add, *sl_sub;   // packed words
   const int32_t *sl_off_add, *sl_off_sub;
-  const uint8_t *len_add, *len_sub;  // per-row entry counts
-  const float2 *eps_up, *eps_dn;     // per-state site energies (double-float) or null
+  const uint8_t *len_add, *len_sub;  // per-slot entry counts
+  const int32_t *slot_row;           // spin-up rank held by slot k
+  const uint32_t *basis_up_slot;     // spin-up strings in slot order
+  const float2 *eps_up, *eps_dn;     // per-state site energies (double-float; up: slot order) or null
   float2 t;                          // uniform hopping t (double-float)
   int t_is_one;
   float2 Utab[32];                   // U * k for k = popcount(I_up & I_dn)
@@ -135,24 +143,34 @@ __global__ void k_group_len(int64_t n, const int32_t *__restrict__ rp, const int
 template <int kPack>
 __global__ void k_slice_fill(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ sp,
                              const void *__restrict__ col, const int32_t *__restrict__ off_a,
-                             const int32_t *__restrict__ off_s, uint32_t *__restrict__ wa,
+                             const int32_t *__restrict__ off_s, const int32_t *__restrict__ slot_row,
+                             const int32_t *__restrict__ slot_of, uint32_t *__restrict__ wa,
                              uint32_t *__restrict__ ws) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t sl = r >> 5, lane = r & 31;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t r = slot_row[k], sl = k >> 5, lane = k & 31;
     for (int g = 0; g < 2; ++g) {
       const int32_t a = g == 0 ? rp[r] : sp[r], b = g == 0 ? sp[r] : rp[r + 1];
       uint32_t *dst = (g == 0 ? wa + off_a[sl] : ws + off_s[sl]) + lane;
-      for (int32_t k = a, j = 0; k < b; k += kPack, ++j) {
+      for (int32_t e = a, j = 0; e < b; e += kPack, ++j) {
         uint32_t word;
         if (kPack == 2) {
           const uint16_t *c = (const uint16_t *)col;
-          word = (uint32_t)c[k] | (k + 1 < b ? (uint32_t)c[k + 1] << 16 : 0u);
+          word = (uint32_t)slot_of[c[e]] | (e + 1 < b ? (uint32_t)slot_of[c[e + 1]] << 16 : 0u);
         } else {
-          word = ((const uint32_t *)col)[k];
+          word = (uint32_t)slot_of[((const uint32_t *)col)[e]];
         }
         dst[(int64_t)j * 32] = word;
       }
     }
+  }
+}
+
+// basis and site energies of the spin-up states in slot order
+__global__ void k_to_slots(int64_t n, const int32_t *__restrict__ slot_row, const uint32_t *__restrict__ basis,
+                           uint32_t *__restrict__ basis_slot, const float2 *__restrict__ eps, float2 *__restrict__ eps_slot) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    basis_slot[k] = basis[slot_row[k]];
+    if (eps) eps_slot[k] = eps[slot_row[k]];
   }
 }
 
@@ -184,7 +202,8 @@ __global__ void k_max_exp(int64_t D, const double *__restrict__ x, int *__restri
 }
 
 __global__ void k_f64_to_df(int64_t n_rows, int64_t n_up, int64_t ld, const double *__restrict__ x,
-                            const int *__restrict__ emax, int nblk, float2 *__restrict__ out) {
+                            const int *__restrict__ emax, int nblk, const int32_t *__restrict__ slot_row,
+                            float2 *__restrict__ out) {
   __shared__ int s_shift;
   if (threadIdx.x == 0) {
     int m = 0;
@@ -196,18 +215,27 @@ __global__ void k_f64_to_df(int64_t n_rows, int64_t n_up, int64_t ld, const doub
   const int64_t total = n_rows * ld;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = k / ld, u = k - d * ld;
-    out[k] = u < n_up ? f64_to_df(x[d * n_up + u], shift) : make_float2(0.f, 0.f);
+    out[k] = u < n_up ? f64_to_df(x[d * n_up + slot_row[u]], shift) : make_float2(0.f, 0.f);
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass 1: spin-up hops (in-row gather from shared memory) and the diagonal.
+// Pass 1: spin-up hops (in-row gather from shared memory) and the diagonal.  A CTA takes
+// two rows (d0, d1) at a time: both are staged (two bulk copies completing on one
+// mbarrier), every column index is loaded once for both rows, and the two rows' TwoSum
+// chains run as one packed FP32x2 chain.  While a pair is computed, the CTA's next pair is
+// prefetched into L2.
 // ---------------------------------------------------------------------------------------
+__device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <typename Col, bool kStage, bool kEps>
-__global__ void __launch_bounds__(512, 2) k_up(const FastView F, const float2 *__restrict__ x,
-                                               float2 *__restrict__ z) {
+__global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *__restrict__ x,
+                                                float2 *__restrict__ z) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2 *xs = reinterpret_cast<float2 *>(smem_raw);
+  float2 *xs0 = reinterpret_cast<float2 *>(smem_raw);
+  float2 *xs1 = xs0 + F.ld;
   __shared__ __align__(8) uint64_t bar;
   __shared__ float2 utab[32];
   const int tid = threadIdx.x;
@@ -218,14 +246,23 @@ __global__ void __launch_bounds__(512, 2) k_up(const FastView F, const float2 *_
     fence_mbar_init();
   }
   __syncthreads();
+  const int64_t n_pairs = (F.n_dn + 1) / 2;
   uint32_t phase = 0;
-  for (int64_t d = blockIdx.x; d < F.n_dn; d += gridDim.x) {
-    const float2 *__restrict__ xrow = x + d * F.ld;
+  for (int64_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+    const int64_t d0 = 2 * p, d1 = (2 * p + 1 < F.n_dn) ? 2 * p + 1 : 2 * p;   // odd tail: same row twice
+    const float2 *__restrict__ r0 = x + d0 * F.ld;
+    const float2 *__restrict__ r1 = x + d1 * F.ld;
     if (kStage) {
       if (tid == 0) {
         fence_proxy_async();
-        mbar_expect_tx(&bar, bytes);
-        bulk_g2s(xs, xrow, bytes, &bar);
+        mbar_expect_tx(&bar, 2 * bytes);
+        bulk_g2s(xs0, r0, bytes, &bar);
+        bulk_g2s(xs1, r1, bytes, &bar);
+        const int64_t pn = p + gridDim.x;
+        if (pn < n_pairs) {
+          prefetch_l2(x + 2 * pn * F.ld, bytes);
+          if (2 * pn + 1 < F.n_dn) prefetch_l2(x + (2 * pn + 1) * F.ld, bytes);
+        }
       }
       if (!mbar_wait_bounded(&bar, phase)) {
         if (tid == 0) atomicExch(F.err, 1);
@@ -234,37 +271,62 @@ __global__ void __launch_bounds__(512, 2) k_up(const FastView F, const float2 *_
       }
       phase ^= 1u;
     }
-    const float2 *__restrict__ src = kStage ? xs : xrow;
-    const uint32_t Id = F.basis_dn[d];
-    float2 ed = make_float2(0.f, 0.f);
-    if (kEps) ed = F.eps_dn[d];
-    for (int64_t u = tid; u < F.n_up; u += blockDim.x) {
-      DfAcc ap{0.f, 0.f}, am{0.f, 0.f};
-      const int64_t sl = u >> 5, lane = u & 31;
+    const float2 *__restrict__ s0 = kStage ? xs0 : r0;
+    const float2 *__restrict__ s1 = kStage ? xs1 : r1;
+    const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
+    float2 e0 = make_float2(0.f, 0.f), e1 = e0;
+    if (kEps) {
+      e0 = F.eps_dn[d0];
+      e1 = F.eps_dn[d1];
+    }
+    for (int64_t slot = tid; slot < F.n_up; slot += blockDim.x) {
+      DfAcc2 ap{0ull, 0ull}, am{0ull, 0ull};
+      const int64_t sl = slot >> 5, lane = slot & 31;
       const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
       const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
-      const int na = F.len_add[u], ns = F.len_sub[u];
-      if (sizeof(Col) == 2) {
-        for (int j = 0; 2 * j < na; ++j) {
-          const uint32_t wd = wa[j * 32];
-          acc_add(ap, src[wd & 0xffffu]);
-          if (2 * j + 1 < na) acc_add(ap, src[wd >> 16]);
-        }
-        for (int j = 0; 2 * j < ns; ++j) {
-          const uint32_t wd = wsb[j * 32];
-          acc_add(am, src[wd & 0xffffu]);
-          if (2 * j + 1 < ns) acc_add(am, src[wd >> 16]);
-        }
-      } else {
-        for (int j = 0; j < na; ++j) acc_add(ap, src[wa[j * 32]]);
-        for (int j = 0; j < ns; ++j) acc_add(am, src[wsb[j * 32]]);
+      const int na = F.len_add[slot], ns = F.len_sub[slot];
+#define HUB_TERM(ACC, C)                                   \
+  do {                                                     \
+    const float2 v0 = s0[C], v1 = s1[C];                   \
+    acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));       \
+  } while (0)
+      // column words are loaded four at a time so that their L2 latencies overlap
+#define HUB_GROUP(ACC, W, N)                                                         \
+  do {                                                                               \
+    const int nw = sizeof(Col) == 2 ? ((N) + 1) >> 1 : (N);                          \
+    for (int j0 = 0; j0 < nw; j0 += 4) {                                             \
+      uint32_t wd[4];                                                                \
+      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : 0u; \
+      _Pragma("unroll") for (int q = 0; q < 4; ++q) {                                \
+        if (j0 + q < nw) {                                                           \
+          if (sizeof(Col) == 2) {                                                    \
+            HUB_TERM(ACC, wd[q] & 0xffffu);                                          \
+            if (2 * (j0 + q) + 1 < (N)) HUB_TERM(ACC, wd[q] >> 16);                  \
+          } else {                                                                   \
+            HUB_TERM(ACC, wd[q]);                                                    \
+          }                                                                          \
+        }                                                                            \
+      }                                                                              \
+    }                                                                                \
+  } while (0)
+      HUB_GROUP(ap, wa, na);
+      HUB_GROUP(am, wsb, ns);
+#undef HUB_GROUP
+#undef HUB_TERM
+      const int64_t u = slot;                            // columns are in slot order
+      const uint32_t Iu = F.basis_up_slot[u];
+      float2 ep = make_float2(0.f, 0.f);
+      if (kEps) ep = F.eps_up[u];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        const float2 sp = acc_value(acc2_lane(ap, r)), sm = acc_value(acc2_lane(am, r));
+        float2 S = df_add(sp, make_float2(-sm.x, -sm.y));
+        if (!F.t_is_one) S = df_mul(S, F.t);
+        float2 dg = utab[__popc(Iu & (r == 0 ? I0 : I1))];
+        if (kEps) dg = df_add(df_add(dg, ep), r == 0 ? e0 : e1);
+        const float2 xv = r == 0 ? s0[u] : s1[u];
+        if (r == 0 || d1 != d0) z[(r == 0 ? d0 : d1) * F.ld + u] = df_fma(dg, xv, S);
       }
-      const float2 sp = acc_value(ap), sm = acc_value(am);
-      float2 S = df_add(sp, make_float2(-sm.x, -sm.y));
-      if (!F.t_is_one) S = df_mul(S, F.t);
-      float2 dg = utab[__popc(F.basis_up[u] & Id)];
-      if (kEps) dg = df_add(df_add(dg, F.eps_up[u]), ed);
-      z[d * F.ld + u] = df_fma(dg, src[u], S);
     }
     if (kStage) __syncthreads();
   }
@@ -274,9 +336,13 @@ __global__ void __launch_bounds__(512, 2) k_up(const FastView F, const float2 *_
 // Pass 2: spin-down hops as combinations of whole rows of a column strip, plus the
 // epilogue.  Tile = 32 rows x 64 columns; blockIdx.x = row tile (fast), blockIdx.y =
 // column strip (slow), so consecutive blocks share a strip.  Lane l of a warp owns the
-// columns u0 + 2l, u0 + 2l + 1 (one 16-byte load per row).
+// columns u0 + 2l, u0 + 2l + 1 (one 16-byte load per row), and sums both with one packed
+// FP32x2 TwoSum chain.
 // ---------------------------------------------------------------------------------------
 constexpr int kDnRows = 32, kDnCols = 64, kDnThreads = 256;
+#ifndef HUB_DN_BATCH
+#define HUB_DN_BATCH 4   // strip rows whose loads are issued together in pass 2
+#endif
 
 struct LzArgs {                      // Lanczos epilogue operands
   const float2 *r_cur;               // r_j   (q_j = r_j / beta_cur)
@@ -336,21 +402,23 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     if (d >= F.n_dn) break;
     const int32_t k0 = F.rp_dn[d], ks = F.sp_dn[d], k1 = F.rp_dn[d + 1];
     if (!active) continue;
-    DfAcc p0{0.f, 0.f}, p1{0.f, 0.f}, m0{0.f, 0.f}, m1{0.f, 0.f};
-    int32_t k = k0;
-    for (; k < ks; ++k) {
-      const float4 v = *reinterpret_cast<const float4 *>(x + colat<Col>(F.col_dn, k) * F.ld + u);
-      acc_add(p0, make_float2(v.x, v.y));
-      acc_add(p1, make_float2(v.z, v.w));
-    }
-    for (; k < k1; ++k) {
-      const float4 v = *reinterpret_cast<const float4 *>(x + colat<Col>(F.col_dn, k) * F.ld + u);
-      acc_add(m0, make_float2(v.x, v.y));
-      acc_add(m1, make_float2(v.z, v.w));
+    DfAcc2 pp{0ull, 0ull}, mm{0ull, 0ull};
+    // rows of the strip are loaded four at a time so that their L2 latencies overlap
+    for (int32_t kb = k0; kb < k1; kb += HUB_DN_BATCH) {
+      float4 v[HUB_DN_BATCH];
+#pragma unroll
+      for (int q = 0; q < HUB_DN_BATCH; ++q)
+        if (kb + q < k1) v[q] = *reinterpret_cast<const float4 *>(x + colat<Col>(F.col_dn, kb + q) * F.ld + u);
+#pragma unroll
+      for (int q = 0; q < HUB_DN_BATCH; ++q) {
+        if (kb + q < ks) acc2_add(pp, pk2(v[q].x, v[q].z), pk2(v[q].y, v[q].w));
+        else if (kb + q < k1) acc2_add(mm, pk2(v[q].x, v[q].z), pk2(v[q].y, v[q].w));
+      }
     }
     const float4 zz = *reinterpret_cast<const float4 *>(z + d * F.ld + u);
-    float2 s0 = df_add(acc_value(p0), make_float2(-acc_value(m0).x, -acc_value(m0).y));
-    float2 s1 = df_add(acc_value(p1), make_float2(-acc_value(m1).x, -acc_value(m1).y));
+    const float2 mv0 = acc_value(acc2_lane(mm, 0)), mv1 = acc_value(acc2_lane(mm, 1));
+    float2 s0 = df_add(acc_value(acc2_lane(pp, 0)), make_float2(-mv0.x, -mv0.y));
+    float2 s1 = df_add(acc_value(acc2_lane(pp, 1)), make_float2(-mv1.x, -mv1.y));
     if (!F.t_is_one) {
       s0 = df_mul(s0, F.t);
       s1 = df_mul(s1, F.t);
@@ -358,8 +426,8 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     const float2 y0 = df_add(make_float2(zz.x, zz.y), s0);
     const float2 y1 = df_add(make_float2(zz.z, zz.w), s1);
     if (kMode == 0) {
-      y[d * F.n_up + u] = df_to_f64(y0, shift);
-      if (u + 1 < F.n_up) y[d * F.n_up + u + 1] = df_to_f64(y1, shift);
+      y[d * F.n_up + F.slot_row[u]] = df_to_f64(y0, shift);
+      if (u + 1 < F.n_up) y[d * F.n_up + F.slot_row[u + 1]] = df_to_f64(y1, shift);
     } else {
       const float4 rc = *reinterpret_cast<const float4 *>(L.r_cur + d * F.ld + u);
       const float4 rp = *reinterpret_cast<const float4 *>(L.r_prev + d * F.ld + u);
@@ -441,12 +509,13 @@ __global__ void k_psi_coef(const double *__restrict__ scal, double c, float2 *__
 
 // out (FP64, unpadded) = v / |v|  with |v| = scal[idx]
 __global__ void k_df_out_normalised(int64_t n_rows, int64_t n_up, int64_t ld, const float2 *__restrict__ v,
-                                    const double *__restrict__ scal, int idx, double *__restrict__ out) {
+                                    const double *__restrict__ scal, int idx, const int32_t *__restrict__ slot_row,
+                                    double *__restrict__ out) {
   const float2 inv = f64_to_df(1.0 / scal[idx], 0);
   const int64_t total = n_rows * n_up;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = k / n_up, u = k - d * n_up;
-    out[k] = df_to_f64(df_mul(v[d * ld + u], inv), 0);
+    const int64_t d = k / n_up, slot = k - d * n_up;
+    out[d * n_up + slot_row[slot]] = df_to_f64(df_mul(v[d * ld + slot], inv), 0);
   }
 }
 
@@ -467,6 +536,9 @@ struct FastState {
   uint32_t *sl_add = nullptr, *sl_sub = nullptr;
   int32_t *sl_off_add = nullptr, *sl_off_sub = nullptr;
   uint8_t *len_add = nullptr, *len_sub = nullptr;
+  int32_t *slot_row = nullptr, *slot_of = nullptr;
+  uint32_t *basis_slot = nullptr;
+  float2 *eps_up_slot = nullptr;
   void *col[2] = {nullptr, nullptr};
   float2 *eps_df[2] = {nullptr, nullptr};
   float2 *xdf = nullptr, *zdf = nullptr;     // hub_apply scratch
@@ -500,6 +572,10 @@ void fast_release(hub_ctx *h) {
   dev_free(f->sl_off_sub);
   dev_free(f->len_add);
   dev_free(f->len_sub);
+  dev_free(f->slot_row);
+  dev_free(f->slot_of);
+  dev_free(f->basis_slot);
+  dev_free(f->eps_up_slot);
   delete f;
   h->fast = nullptr;
 }
@@ -548,9 +624,35 @@ int fast_build(hub_ctx *h) {
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
     k_group_len<<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->len_add, f->len_sub);
     HUB_LAUNCH_CHECK();
+    std::vector<uint8_t> la0(n), ls0(n);
+    HUB_CUDA(cudaMemcpy(la0.data(), f->len_add, n, cudaMemcpyDeviceToHost));
+    HUB_CUDA(cudaMemcpy(ls0.data(), f->len_sub, n, cudaMemcpyDeviceToHost));
+    // slots: rows ordered by (add length, sub length), stable
+    std::vector<int32_t> slot_row(n);
+    for (int64_t r = 0; r < n; ++r) slot_row[r] = (int32_t)r;
+    std::stable_sort(slot_row.begin(), slot_row.end(), [&](int32_t a, int32_t b) {
+      return la0[a] != la0[b] ? la0[a] > la0[b] : ls0[a] > ls0[b];
+    });
     std::vector<uint8_t> la(n), ls(n);
-    HUB_CUDA(cudaMemcpy(la.data(), f->len_add, n, cudaMemcpyDeviceToHost));
-    HUB_CUDA(cudaMemcpy(ls.data(), f->len_sub, n, cudaMemcpyDeviceToHost));
+    for (int64_t k = 0; k < n; ++k) {
+      la[k] = la0[slot_row[k]];
+      ls[k] = ls0[slot_row[k]];
+    }
+    std::vector<int32_t> slot_of(n);
+    for (int64_t k = 0; k < n; ++k) slot_of[slot_row[k]] = (int32_t)k;
+    if (!dev_alloc((void **)&f->slot_row, sizeof(int32_t) * n, "slot order") ||
+        !dev_alloc((void **)&f->slot_of, sizeof(int32_t) * n, "slot order") ||
+        !dev_alloc((void **)&f->basis_slot, sizeof(uint32_t) * n, "basis in slot order"))
+      return HUB_ERR_OOM;
+    HUB_CUDA(cudaMemcpy(f->slot_row, slot_row.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    HUB_CUDA(cudaMemcpy(f->slot_of, slot_of.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
+    if (h->has_eps && !dev_alloc((void **)&f->eps_up_slot, sizeof(float2) * n, "site energies in slot order"))
+      return HUB_ERR_OOM;
+    k_to_slots<<<g, 256>>>(n, f->slot_row, h->basis[0], f->basis_slot, h->has_eps ? f->eps_df[0] : nullptr,
+                           f->eps_up_slot);
+    HUB_LAUNCH_CHECK();
+    HUB_CUDA(cudaMemcpy(f->len_add, la.data(), n, cudaMemcpyHostToDevice));
+    HUB_CUDA(cudaMemcpy(f->len_sub, ls.data(), n, cudaMemcpyHostToDevice));
     const int pack = f->col16 ? 2 : 1;
     std::vector<int32_t> oa(nsl + 1, 0), os(nsl + 1, 0);
     for (int64_t sl = 0; sl < nsl; ++sl) {
@@ -573,10 +675,10 @@ int fast_build(hub_ctx *h) {
     HUB_CUDA(cudaMemset(f->sl_sub, 0, sizeof(uint32_t) * std::max<int32_t>(os[nsl], 1)));
     if (pack == 2)
       k_slice_fill<2><<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->col[0], f->sl_off_add, f->sl_off_sub,
-                                  f->sl_add, f->sl_sub);
+                                  f->slot_row, f->slot_of, f->sl_add, f->sl_sub);
     else
       k_slice_fill<1><<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->col[0], f->sl_off_add, f->sl_off_sub,
-                                  f->sl_add, f->sl_sub);
+                                  f->slot_row, f->slot_of, f->sl_add, f->sl_sub);
     HUB_LAUNCH_CHECK();
   }
   if (!dev_alloc((void **)&f->d_err, sizeof(int) * 4, "error flag") ||
@@ -608,7 +710,9 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   v.sl_off_sub = f->sl_off_sub;
   v.len_add = f->len_add;
   v.len_sub = f->len_sub;
-  v.eps_up = f->eps_df[0];
+  v.slot_row = f->slot_row;
+  v.basis_up_slot = f->basis_slot;
+  v.eps_up = f->eps_up_slot;
   v.eps_dn = f->eps_df[sd];
   const double t = h->t.empty() ? 0.0 : h->t[0];
   v.t_is_one = (t == 1.0);
@@ -623,14 +727,14 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   return v;
 }
 
-static size_t up_smem(const FastState *f) { return sizeof(float2) * (size_t)f->ld; }
-constexpr size_t kMaxStage = 200 * 1024;
+static size_t up_smem(const FastState *f) { return 2 * sizeof(float2) * (size_t)f->ld; }
+constexpr size_t kMaxStage = 224 * 1024;
 
 template <typename Col>
 static int launch_up_t(const FastView &v, const FastState *f, bool eps, const float2 *x, float2 *z, cudaStream_t s) {
   const bool stage = up_smem(f) <= kMaxStage;
-  const int threads = v.n_up >= 4096 ? 512 : (v.n_up >= 512 ? 256 : 128);
-  int64_t grid = std::min<int64_t>(v.n_dn, (int64_t)num_sms() * (stage ? 2 : 4));
+  const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
+  int64_t grid = std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms() * (stage ? 1 : 2) * (1024 / threads));
   const size_t smem = stage ? up_smem(f) : 0;
 #define HUB_UP(ST, EP)                                                                                   \
   do {                                                                                                   \
@@ -707,7 +811,7 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
   count_launch(h, 2);
   k_max_exp<<<G, 256, 0, s>>>(D, x, f->d_emax);
-  k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->xdf);
+  k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->slot_row, f->xdf);
   HUB_LAUNCH_CHECK();
   if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
   return run_dn(h, f, 0, f->xdf, f->zdf, y, nullptr, f->d_emax, G, LzArgs{}, s);
@@ -743,7 +847,8 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   const FastView v0 = fast_view(h, f);
   const dim3 gd = dn_grid(v0);
   const int64_t n_dn_blocks = (int64_t)gd.x * gd.y;
-  if ((rc = ensure_partials(h, std::max<int64_t>(n_dn_blocks, G)))) return rc;
+  constexpr int kTmp = 2048;                      // first-stage slots of the alpha reduction
+  if ((rc = ensure_partials(h, std::max<int64_t>(n_dn_blocks, G) + kTmp))) return rc;
   if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
   if (!h->d_scal && !dev_alloc((void **)&h->d_scal, sizeof(double) * 8, "Lanczos scalars")) return HUB_ERR_OOM;
   if (!h->h_scal) HUB_CUDA(cudaMallocHost((void **)&h->h_scal, sizeof(double) * 8));
@@ -754,7 +859,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   auto start = [&](float2 *r) -> int {
     HUB_CUDA(cudaMemsetAsync(f->d_emax, 0, sizeof(int) * G, s));
     count_launch(h, 3);
-    k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x0, f->d_emax, G, r);
+    k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x0, f->d_emax, G, f->slot_row, r);
     k_df_norm2<<<G, 256, 0, s>>>(Dp, r, P);
     HUB_LAUNCH_CHECK();
     int rc2 = reduce_partials(P, G, scal + 1, 1, s);
@@ -798,7 +903,9 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   int status = HUB_ERR_NOCONV;
   for (int j = 0; j < maxit; ++j) {
     if ((rc = step_apply(rp, rcur, w))) return rc;
-    if ((rc = reduce_partials(P, (int)n_dn_blocks, scal + 0, 0, s))) return rc;
+    if ((rc = reduce_partials_2stage(P, (int)n_dn_blocks, P + std::max<int64_t>(n_dn_blocks, G), kTmp, scal + 0, 0,
+                                     s)))
+      return rc;
     if ((rc = step_update(rcur, w))) return rc;
     if ((rc = reduce_partials(P, G, scal + 3, 1, s))) return rc;      // beta_j
     HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -871,7 +978,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
     k_df_norm2<<<G, 256, 0, s>>>(Dp, f->psi, P);
     HUB_LAUNCH_CHECK();
     if ((rc = reduce_partials(P, G, scal + 5, 1, s))) return rc;
-    k_df_out_normalised<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, f->psi, scal, 5, psi_out);
+    k_df_out_normalised<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, f->psi, scal, 5, f->slot_row, psi_out);
     HUB_LAUNCH_CHECK();
     HUB_CUDA(cudaStreamSynchronize(s));
     if ((rc = fast_check_error(h))) return rc;

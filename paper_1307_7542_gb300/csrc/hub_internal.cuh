@@ -127,6 +127,9 @@ constexpr int kReduceThreads = 256;
 
 // Deterministic FP64 reduction of partials[0..n) into *out (device), one block.
 int reduce_partials(const double *partials, int n, double *out, int mode, cudaStream_t s);
+// Same, in two fixed-order stages through tmp[ntmp] (for long partial lists).
+int reduce_partials_2stage(const double *partials, int n, double *tmp, int ntmp, double *out, int mode,
+                           cudaStream_t s);
 
 // Apply entry used by Lanczos and the VJP (no argument checks).
 int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s);

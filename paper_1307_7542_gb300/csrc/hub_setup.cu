@@ -243,8 +243,36 @@ __global__ void k_reduce(const double *__restrict__ p, int n, double *__restrict
   if (threadIdx.x == 0) out[0] = mode == 1 ? sqrt(s[0]) : s[0];
 }
 
+// First stage for long partial lists: block b sums the contiguous chunk b (fixed order).
+__global__ void k_reduce_chunks(const double *__restrict__ p, int n, int chunk, double *__restrict__ out) {
+  __shared__ double s[kReduceThreads];
+  const int a = blockIdx.x * chunk, b = min(n, a + chunk);
+  double v = 0.0;
+  for (int k = a + threadIdx.x; k < b; k += blockDim.x) v += p[k];
+  s[threadIdx.x] = v;
+  __syncthreads();
+  for (int w = blockDim.x / 2; w > 0; w >>= 1) {
+    if (threadIdx.x < w) s[threadIdx.x] += s[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) out[blockIdx.x] = s[0];
+}
+
 int reduce_partials(const double *partials, int n, double *out, int mode, cudaStream_t s) {
   k_reduce<<<1, kReduceThreads, 0, s>>>(partials, n, out, mode);
+  HUB_LAUNCH_CHECK();
+  return HUB_OK;
+}
+
+int reduce_partials_2stage(const double *partials, int n, double *tmp, int ntmp, double *out, int mode,
+                           cudaStream_t s) {
+  if (n <= 4 * kReduceThreads || ntmp < 2) return reduce_partials(partials, n, out, mode, s);
+  const int chunks = std::min(ntmp, (n + 1023) / 1024);
+  const int chunk = (n + chunks - 1) / chunks;
+  const int nb = (n + chunk - 1) / chunk;
+  k_reduce_chunks<<<nb, kReduceThreads, 0, s>>>(partials, n, chunk, tmp);
+  HUB_LAUNCH_CHECK();
+  k_reduce<<<1, kReduceThreads, 0, s>>>(tmp, nb, out, mode);
   HUB_LAUNCH_CHECK();
   return HUB_OK;
 }
