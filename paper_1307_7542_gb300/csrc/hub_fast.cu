@@ -341,7 +341,7 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
 // ---------------------------------------------------------------------------------------
 constexpr int kDnRows = 32, kDnCols = 64, kDnThreads = 256;
 #ifndef HUB_DN_BATCH
-#define HUB_DN_BATCH 4   // strip rows whose loads are issued together in pass 2
+#define HUB_DN_BATCH 2   // strip rows whose loads are issued together in pass 2
 #endif
 
 struct LzArgs {                      // Lanczos epilogue operands
