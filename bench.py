@@ -43,6 +43,8 @@ def parse():
     p.add_argument("--lanczos-iters", type=int, default=200, help="iterations of the E0 wall-time run")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
+    p.add_argument("--no-extras", action="store_true",
+                   help="skip the batched, adjoint and 3x6 measurements reported beside the headline")
     p.add_argument("--workload", default="4x4", choices=sorted(WORKLOADS),
                    help="4x4: the benchmark case; the others are smaller cases for profiling")
     return p.parse_args()
@@ -211,6 +213,88 @@ def run_reference(a):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def extras(hub, W, torch):
+    """Measurements beside the headline: batched vs one-at-a-time impurity solves, adjoint
+    gradients vs finite differences, and the 3x6 bandwidth-stress Lanczos step."""
+    import numpy as np
+    out = {}
+    # (1) AIM star M=8: 81 sectors x 64 parameter sets, one persistent launch
+    ps = [W.aim_star(k) for k in range(64)]
+    bonds = ps[0]["bonds"]
+    t = np.stack([p["t"] for p in ps]); U = np.stack([p["U"] for p in ps]); eps = np.stack([p["eps"] for p in ps])
+    jobs = [(a_, b_, p_) for p_ in range(64) for a_ in range(9) for b_ in range(9)]
+    jn, jd, jp = (np.array(c) for c in zip(*jobs))
+    hub.hub_batch_ground(8, bonds, t, U, eps, jn[:81], jd[:81], jp[:81], maxit=400, tol=1e-12)   # warm-up
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    E0, it, st = hub.hub_batch_ground(8, bonds, t, U, eps, jn, jd, jp, maxit=400, tol=1e-12)
+    t_batch = time.perf_counter() - t0
+    # one at a time: the 81 sectors of parameter set 0 through hub_lanczos_ground
+    t0 = time.perf_counter()
+    maxdiff = 0.0
+    for k in range(81):
+        a_, b_, p_ = jobs[k]
+        m = hub.Hubbard(8, a_, b_, bonds, t[p_], U[p_], eps[p_])
+        r = m.ground(None, maxit=400, tol=1e-12)
+        maxdiff = max(maxdiff, abs(r["E0"] - E0[k]) / max(1.0, abs(E0[k])))
+        m.close()
+    t_one = (time.perf_counter() - t0) / 81
+    out["batched"] = {"workload": "AIM star M=8 (impurity + 7 bath sites), 81 sectors x 64 parameter sets",
+                      "jobs": len(jobs), "batched_s": t_batch, "jobs_per_s": len(jobs) / t_batch,
+                      "one_at_a_time_s_per_job": t_one, "one_at_a_time_total_s_extrapolated": t_one * len(jobs),
+                      "speedup": t_one * len(jobs) / t_batch, "max_rel_dE0_vs_one_at_a_time": maxdiff,
+                      "iterations_mean": float(np.mean(it)), "all_converged": bool(np.all(np.isin(st, [0, 1])))}
+    # (2) disordered 3x4 open lattice: adjoint (one solve + hub_grad) vs central differences
+    w = W.disordered3x4()
+    m = hub.Hubbard(12, 6, 6, w["bonds"], w["t"], w["U"], w["eps"])
+    x0 = torch.from_numpy(W.normal(0, m.D)).cuda()
+    m.ground(x0, maxit=400, tol=1e-12)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = m.ground(x0, maxit=400, tol=1e-12, want_psi=True)
+    dt, dU, de = m.grad(r["psi"])
+    t_adj = time.perf_counter() - t0
+    n_par = len(w["t"]) + 24
+    h = 1e-4
+    fd_err = 0.0
+    t0 = time.perf_counter()
+    sample = [0, 5, 11, 16]
+    for k in sample:
+        tp, tm = w["t"].copy(), w["t"].copy()
+        tp[k] += h
+        tm[k] -= h
+        m.set_params(tp, w["U"], w["eps"]); Ep = m.ground(x0, maxit=400, tol=1e-12)["E0"]
+        m.set_params(tm, w["U"], w["eps"]); Em = m.ground(x0, maxit=400, tol=1e-12)["E0"]
+        fd_err = max(fd_err, abs((Ep - Em) / (2 * h) - dt[k]))
+    t_fd_solve = (time.perf_counter() - t0) / (2 * len(sample))
+    m.close()
+    out["adjoint"] = {"workload": "3x4 open lattice (6,6), D=853776, 41 parameters (17 t_b, 12 U_i, 12 eps_i)",
+                      "adjoint_s": t_adj, "fd_s_per_solve": t_fd_solve, "fd_total_s_extrapolated": t_fd_solve * 2 * n_par,
+                      "speedup": t_fd_solve * 2 * n_par / t_adj, "max_abs_diff_vs_fd_h1e-4": fd_err,
+                      "fd_params_timed": len(sample)}
+    # (3) 3x6 periodic lattice, (9,9): D = 2,363,904,400 (18.9 GB per FP64 vector)
+    w = W.square3x6(4.0)
+    m = hub.Hubbard(18, 9, 9, w["bonds"], w["t"], w["U"], w["eps"])
+    m.ground(None, maxit=2, tol=0.0)
+    hub.hub_profile(m.h, True)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r = m.ground(None, maxit=4, tol=0.0)
+    torch.cuda.synchronize()
+    el = time.perf_counter() - t0
+    up_ms, n_up_l, _ = hub.hub_profile_read(m.h, hub.HUB_PROF_UP)
+    dn_ms, n_dn_l, _ = hub.hub_profile_read(m.h, hub.HUB_PROF_DN)
+    ap_ms, n_ap, _ = hub.hub_profile_read(m.h, hub.HUB_PROF_APPLY)
+    D = m.D
+    m.close()
+    torch.cuda.empty_cache()
+    out["square3x6"] = {"workload": "3x6 PBC (9,9), t=1, U=4", "dim": D, "lanczos_step_ms": 1000 * el / 4,
+                        "apply_ms": ap_ms / max(n_ap, 1), "k_up_ms": up_ms / max(n_up_l, 1),
+                        "k_dn_ms": dn_ms / max(n_dn_l, 1),
+                        "apply_gbs_16B_per_element": 16 * D / (ap_ms / max(n_ap, 1) / 1000) / 1e9}
+    return out
+
+
 def run_gpu(a):
     import numpy as np
     import torch
@@ -340,6 +424,9 @@ def run_gpu(a):
                                 "sample": f"oracle apply of {R} of {D} output rows ({el:.1f} s), scaled to "
                                           f"whole applies"}
     m.close()
+    if world == 1 and not a.no_extras:
+        torch.cuda.empty_cache()
+        line["extras"] = extras(hub, W, torch)
     if rank == 0:
         print(json.dumps(line))
     if world > 1:

@@ -132,6 +132,25 @@ int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, dou
 int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host, int cap, int *n);
 
 /*
+ * Many small ground states in one persistent kernel launch (Sec. VIII: an impurity solver
+ * repeats the ground-state search for every sector and bath-parameter set).  One lattice
+ * (1 <= M <= 16 sites, n_bonds bonds as in hub_hopping), n_params parameter sets
+ * t_host[n_params][n_bonds], U_host[n_params][M], eps_host[n_params][M] (or NULL), and
+ * n_jobs jobs: job k finds the lowest eigenvalue of sector (job_nup[k], job_ndn[k]) with
+ * parameter set job_param[k] by the plain Lanczos of hub_lanczos_ground (FP64; E0_j of T_j
+ * is checked every 8 iterations, stop when it changes by less than tol between checks;
+ * start vector SplitMix64 uniform [-1, 1) with counter (k << 32) | (element + 1)).  Each
+ * job's vectors live in shared memory: count_up * count_dn <= 8192 per job, else
+ * HUB_ERR_ARG.  Host outputs E0_host[n_jobs], iters_host[n_jobs], status_host[n_jobs]
+ * (HUB_OK, HUB_CONVERGED_BREAKDOWN or HUB_ERR_NOCONV per job).  Returns HUB_ERR_NOCONV if any
+ * job hit maxit (1 <= maxit <= 1000).  Allocates and frees its own device copies; blocks.
+ */
+int hub_batch_ground(int M, int n_bonds, const int32_t *bonds_host, int n_params, const double *t_host,
+                     const double *U_host, const double *eps_host, int n_jobs, const int32_t *job_nup,
+                     const int32_t *job_ndn, const int32_t *job_param, int maxit, double tol,
+                     double *E0_host, int32_t *iters_host, int32_t *status_host, void *stream);
+
+/*
  * Hellmann-Feynman gradients of E0 = <psi|H|psi> for a normalised eigenvector psi:
  *   dE_dt[b]   = <psi| -sum_sigma (c+_i c_j + h.c.) |psi>     (dH/dt_b, per bond)
  *   dE_dU[i]   = <psi| n_{i up} n_{i dn} |psi>                (double occupancy, per site)

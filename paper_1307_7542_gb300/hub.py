@@ -45,6 +45,7 @@ SIGNATURES = {
     "hub_grad": (_i, [_p, _p, _p, _p, _p, _p]),
     "hub_apply_vjp": (_i, [_p, _p, _p, _p, _p, _p, _p, _p]),
     "hub_grad_noalloc": (_i, [_p, _p, _p, _p, _p, _p]),
+    "hub_batch_ground": (_i, [_i, _i, _p, _i, _p, _p, _p, _i, _p, _p, _p, _i, _d, _p, _p, _p, _p]),
     "hub_set_mode": (_i, [_p, _i]),
     "hub_check": (_i, [_p]),
     "hub_profile": (_i, [_p, _i]),
@@ -174,6 +175,25 @@ def hub_grad(h, psi, n_bonds, M, stream=None):
     dt, dU, de = np.empty(n_bonds), np.empty(M), np.empty(M)
     _check(lib().hub_grad(h, _ptr(psi), _ptr(dt), _ptr(dU), _ptr(de), _stream(stream)))
     return dt, dU, de
+
+
+def hub_batch_ground(M, bonds, t, U, eps, job_nup, job_ndn, job_param, maxit=300, tol=1e-12, stream=None):
+    """Ground-state energies of many (sector, parameter set) jobs in one persistent launch.
+    t: [n_params, n_bonds]; U, eps: [n_params, M] (eps may be None).  Returns (E0, iters, status)."""
+    bonds = np.ascontiguousarray(np.asarray(bonds, dtype=np.int32).reshape(-1, 2))
+    t = np.ascontiguousarray(np.asarray(t, dtype=np.float64).reshape(-1, bonds.shape[0]))
+    U = np.ascontiguousarray(np.asarray(U, dtype=np.float64).reshape(t.shape[0], M))
+    e = None if eps is None else np.ascontiguousarray(np.asarray(eps, dtype=np.float64).reshape(t.shape[0], M))
+    jn = np.ascontiguousarray(np.asarray(job_nup, dtype=np.int32))
+    jd = np.ascontiguousarray(np.asarray(job_ndn, dtype=np.int32))
+    jp = np.ascontiguousarray(np.asarray(job_param, dtype=np.int32))
+    n = jn.shape[0]
+    E0, it, st = np.empty(n), np.empty(n, dtype=np.int32), np.empty(n, dtype=np.int32)
+    rc = lib().hub_batch_ground(M, bonds.shape[0], _ptr(bonds), t.shape[0], _ptr(t), _ptr(U), _ptr(e), n,
+                                _ptr(jn), _ptr(jd), _ptr(jp), maxit, tol, _ptr(E0), _ptr(it), _ptr(st),
+                                _stream(stream))
+    _check(rc, ok=(HUB_OK, HUB_ERR_NOCONV))
+    return E0, it, st
 
 
 def hub_grad_noalloc(h, psi, n_bonds, M, stream=None):
