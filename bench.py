@@ -213,6 +213,18 @@ def run_reference(a):
 
 # ----------------------------------------------------------------------------- GPU arm
 
+def combine_ranks(elapsed_ms, steps, world, device):
+    """Whole-job timing over replicas: the slowest rank's time, and the steps all ranks did
+    divided by it (each rank runs its own replica; no data-path collective)."""
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(elapsed_ms)], dtype=torch.float64, device=device)
+    if world > 1:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    t_max = float(t.item())
+    return t_max, world * steps / (t_max / 1000.0)
+
+
 def extras(hub, W, torch):
     """Measurements beside the headline: batched vs one-at-a-time impurity solves, adjoint
     gradients vs finite differences, and the 3x6 bandwidth-stress Lanczos step."""
@@ -347,11 +359,7 @@ def run_gpu(a):
     clk = clocks.stop() if clocks else None
     assert r["iters"] == a.steps, r
 
-    t_max = torch.tensor([elapsed_ms], dtype=torch.float64, device="cuda")
-    if world > 1:
-        dist.all_reduce(t_max, op=dist.ReduceOp.MAX)
-    elapsed_ms = float(t_max.item())
-    value = world * a.steps / (elapsed_ms / 1000.0)
+    elapsed_ms, value = combine_ranks(elapsed_ms, a.steps, world, "cuda")
 
     # roofline of the product and of its dominant kernel
     apply_avg_ms = apply_ms / max(n_apply, 1)
