@@ -92,11 +92,14 @@ struct FastView {
   const void *col_up, *col_dn;       // uint16 or uint32 columns
   // H_up in sliced column-major form for pass 1.  Rows are placed in slots ordered by their
   // (add, sub) group lengths so that the 32 rows a warp handles have nearly equal lengths;
-  // slot k holds row slot_row[k]; entry j of slot k is word off[k/32] + j*32 + k%32, with
-  // two uint16 columns packed per 32-bit word when Col is uint16.
+  // slot k holds row slot_row[k].  Each slice of 32 slots has, per group, a schedule of
+  // steps: in one step every lane reads at most one of its entries, chosen so that the lanes
+  // of each half-warp hit distinct shared-memory bank pairs (column mod 16).  Step j of slot
+  // k is word off[k/32] + (j/2)*32 + k%32 (two uint16 columns per word; idle = 0xffff) or
+  // off[k/32] + j*32 + k%32 (uint32 columns; idle = 0xffffffff).
   const uint32_t *sl_add, *sl_sub;   // packed words
   const int32_t *sl_off_add, *sl_off_sub;
-  const uint8_t *len_add, *len_sub;  // per-slot entry counts
+  const uint16_t *steps_add, *steps_sub;   // per slice: scheduled steps (entries per lane)
   const int32_t *slot_row;           // spin-up rank held by slot k
   const uint32_t *basis_up_slot;     // spin-up strings in slot order
   const float2 *eps_up, *eps_dn;     // per-state site energies (double-float; up: slot order) or null
@@ -126,42 +129,6 @@ __global__ void k_split_csr(int64_t n, const int32_t *__restrict__ rp, const uin
     sp[r] = w;
     for (int32_t k = a; k < b; ++k)
       if (!(scol[k] >> 31)) col[w++] = (Col)(scol[k] & 0x7fffffffu);
-  }
-}
-
-// Per-row lengths of the add and sub groups.
-__global__ void k_group_len(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ sp,
-                            uint8_t *__restrict__ la, uint8_t *__restrict__ ls) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x) {
-    la[r] = (uint8_t)(sp[r] - rp[r]);
-    ls[r] = (uint8_t)(rp[r + 1] - sp[r]);
-  }
-}
-
-// Fill the sliced arrays; per words: 2 uint16 columns per 32-bit word (kPack = 2) or one
-// uint32 column (kPack = 1).  Unused halves are zero and never read.
-template <int kPack>
-__global__ void k_slice_fill(int64_t n, const int32_t *__restrict__ rp, const int32_t *__restrict__ sp,
-                             const void *__restrict__ col, const int32_t *__restrict__ off_a,
-                             const int32_t *__restrict__ off_s, const int32_t *__restrict__ slot_row,
-                             const int32_t *__restrict__ slot_of, uint32_t *__restrict__ wa,
-                             uint32_t *__restrict__ ws) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t r = slot_row[k], sl = k >> 5, lane = k & 31;
-    for (int g = 0; g < 2; ++g) {
-      const int32_t a = g == 0 ? rp[r] : sp[r], b = g == 0 ? sp[r] : rp[r + 1];
-      uint32_t *dst = (g == 0 ? wa + off_a[sl] : ws + off_s[sl]) + lane;
-      for (int32_t e = a, j = 0; e < b; e += kPack, ++j) {
-        uint32_t word;
-        if (kPack == 2) {
-          const uint16_t *c = (const uint16_t *)col;
-          word = (uint32_t)slot_of[c[e]] | (e + 1 < b ? (uint32_t)slot_of[c[e + 1]] << 16 : 0u);
-        } else {
-          word = (uint32_t)slot_of[((const uint32_t *)col)[e]];
-        }
-        dst[(int64_t)j * 32] = word;
-      }
-    }
   }
 }
 
@@ -284,11 +251,15 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
       const int64_t sl = slot >> 5, lane = slot & 31;
       const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
       const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
-      const int na = F.len_add[slot], ns = F.len_sub[slot];
-#define HUB_TERM(ACC, C)                                   \
-  do {                                                     \
-    const float2 v0 = s0[C], v1 = s1[C];                   \
-    acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));       \
+      const int na = F.steps_add[sl], ns = F.steps_sub[sl];
+      // one scheduled entry: idle steps (sentinel column) add nothing
+#define HUB_TERM(ACC, C, IDLE)                                                 \
+  do {                                                                         \
+    const uint32_t c_ = (C);                                                   \
+    if (c_ != (IDLE)) {                                                        \
+      const float2 v0 = s0[c_], v1 = s1[c_];                                   \
+      acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));                         \
+    }                                                                          \
   } while (0)
       // column words are loaded four at a time so that their L2 latencies overlap
 #define HUB_GROUP(ACC, W, N)                                                         \
@@ -296,15 +267,13 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
     const int nw = sizeof(Col) == 2 ? ((N) + 1) >> 1 : (N);                          \
     for (int j0 = 0; j0 < nw; j0 += 4) {                                             \
       uint32_t wd[4];                                                                \
-      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : 0u; \
+      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : 0xffffffffu; \
       _Pragma("unroll") for (int q = 0; q < 4; ++q) {                                \
-        if (j0 + q < nw) {                                                           \
-          if (sizeof(Col) == 2) {                                                    \
-            HUB_TERM(ACC, wd[q] & 0xffffu);                                          \
-            if (2 * (j0 + q) + 1 < (N)) HUB_TERM(ACC, wd[q] >> 16);                  \
-          } else {                                                                   \
-            HUB_TERM(ACC, wd[q]);                                                    \
-          }                                                                          \
+        if (sizeof(Col) == 2) {                                                      \
+          HUB_TERM(ACC, wd[q] & 0xffffu, 0xffffu);                                   \
+          HUB_TERM(ACC, wd[q] >> 16, 0xffffu);                                       \
+        } else {                                                                     \
+          HUB_TERM(ACC, wd[q], 0xffffffffu);                                         \
         }                                                                            \
       }                                                                              \
     }                                                                                \
@@ -535,7 +504,7 @@ struct FastState {
   int32_t *sp[2] = {nullptr, nullptr};
   uint32_t *sl_add = nullptr, *sl_sub = nullptr;
   int32_t *sl_off_add = nullptr, *sl_off_sub = nullptr;
-  uint8_t *len_add = nullptr, *len_sub = nullptr;
+  uint16_t *steps_add = nullptr, *steps_sub = nullptr;
   int32_t *slot_row = nullptr, *slot_of = nullptr;
   uint32_t *basis_slot = nullptr;
   float2 *eps_up_slot = nullptr;
@@ -570,8 +539,8 @@ void fast_release(hub_ctx *h) {
   dev_free(f->sl_sub);
   dev_free(f->sl_off_add);
   dev_free(f->sl_off_sub);
-  dev_free(f->len_add);
-  dev_free(f->len_sub);
+  dev_free(f->steps_add);
+  dev_free(f->steps_sub);
   dev_free(f->slot_row);
   dev_free(f->slot_of);
   dev_free(f->basis_slot);
@@ -615,31 +584,33 @@ int fast_build(hub_ctx *h) {
       HUB_LAUNCH_CHECK();
     }
   }
-  // sliced H_up for pass 1
+  // sliced, bank-scheduled H_up for pass 1 (built on the host from the sign-split CSR)
   {
     const int64_t n = h->count[0];
     const int64_t nsl = (n + 31) / 32;
-    if (!dev_alloc((void **)&f->len_add, n, "row lengths") || !dev_alloc((void **)&f->len_sub, n, "row lengths"))
-      return HUB_ERR_OOM;
-    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
-    k_group_len<<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->len_add, f->len_sub);
-    HUB_LAUNCH_CHECK();
-    std::vector<uint8_t> la0(n), ls0(n);
-    HUB_CUDA(cudaMemcpy(la0.data(), f->len_add, n, cudaMemcpyDeviceToHost));
-    HUB_CUDA(cudaMemcpy(ls0.data(), f->len_sub, n, cudaMemcpyDeviceToHost));
+    const int64_t nnz = h->csr[0].nnz;
+    std::vector<int32_t> rp(n + 1), spv(n);
+    std::vector<uint32_t> col(std::max<int64_t>(nnz, 1));
+    HUB_CUDA(cudaMemcpy(rp.data(), h->csr[0].rowptr, sizeof(int32_t) * (n + 1), cudaMemcpyDeviceToHost));
+    HUB_CUDA(cudaMemcpy(spv.data(), f->sp[0], sizeof(int32_t) * n, cudaMemcpyDeviceToHost));
+    if (f->col16) {
+      std::vector<uint16_t> c16(std::max<int64_t>(nnz, 1));
+      if (nnz) HUB_CUDA(cudaMemcpy(c16.data(), f->col[0], sizeof(uint16_t) * nnz, cudaMemcpyDeviceToHost));
+      for (int64_t k = 0; k < nnz; ++k) col[k] = c16[k];
+    } else if (nnz) {
+      HUB_CUDA(cudaMemcpy(col.data(), f->col[0], sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost));
+    }
     // slots: rows ordered by (add length, sub length), stable
     std::vector<int32_t> slot_row(n);
     for (int64_t r = 0; r < n; ++r) slot_row[r] = (int32_t)r;
     std::stable_sort(slot_row.begin(), slot_row.end(), [&](int32_t a, int32_t b) {
-      return la0[a] != la0[b] ? la0[a] > la0[b] : ls0[a] > ls0[b];
+      const int la = spv[a] - rp[a], lb = spv[b] - rp[b];
+      const int sa = rp[a + 1] - spv[a], sb = rp[b + 1] - spv[b];
+      return la != lb ? la > lb : sa > sb;
     });
-    std::vector<uint8_t> la(n), ls(n);
-    for (int64_t k = 0; k < n; ++k) {
-      la[k] = la0[slot_row[k]];
-      ls[k] = ls0[slot_row[k]];
-    }
     std::vector<int32_t> slot_of(n);
     for (int64_t k = 0; k < n; ++k) slot_of[slot_row[k]] = (int32_t)k;
+    const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
     if (!dev_alloc((void **)&f->slot_row, sizeof(int32_t) * n, "slot order") ||
         !dev_alloc((void **)&f->slot_of, sizeof(int32_t) * n, "slot order") ||
         !dev_alloc((void **)&f->basis_slot, sizeof(uint32_t) * n, "basis in slot order"))
@@ -651,35 +622,105 @@ int fast_build(hub_ctx *h) {
     k_to_slots<<<g, 256>>>(n, f->slot_row, h->basis[0], f->basis_slot, h->has_eps ? f->eps_df[0] : nullptr,
                            f->eps_up_slot);
     HUB_LAUNCH_CHECK();
-    HUB_CUDA(cudaMemcpy(f->len_add, la.data(), n, cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(f->len_sub, ls.data(), n, cudaMemcpyHostToDevice));
+    // per slice and group: schedule the lanes' entries into steps in which at most two lanes
+    // of a half-warp hit the same bank pair (slot mod 16), i.e. at most two shared-memory
+    // wavefronts per half-warp load.  Greedy: lanes with the most remaining entries are
+    // served first; each takes the entry of the most loaded bank that still has room.
+    // (A conflict-free schedule needs about 1.7x more steps on the 4x4 lattice because the
+    // bank loads are uneven; two per bank costs about 4 % more steps for 1.5x fewer
+    // wavefronts than the unscheduled order.)
+    constexpr int kBankCap = 2;
+    const uint32_t idle = f->col16 ? 0xffffu : 0xffffffffu;
     const int pack = f->col16 ? 2 : 1;
-    std::vector<int32_t> oa(nsl + 1, 0), os(nsl + 1, 0);
+    std::vector<uint16_t> st[2] = {std::vector<uint16_t>(nsl), std::vector<uint16_t>(nsl)};
+    std::vector<int32_t> off[2] = {std::vector<int32_t>(nsl + 1, 0), std::vector<int32_t>(nsl + 1, 0)};
+    std::vector<uint32_t> words[2];
+    std::vector<uint32_t> steps;                   // [S][32] entries of one slice
     for (int64_t sl = 0; sl < nsl; ++sl) {
-      int ma = 0, ms = 0;
-      for (int64_t r = sl * 32; r < std::min(n, sl * 32 + 32); ++r) {
-        ma = std::max(ma, (int)la[r]);
-        ms = std::max(ms, (int)ls[r]);
+      for (int grp = 0; grp < 2; ++grp) {
+        std::vector<std::vector<uint32_t>> half_steps[2];
+        for (int hw = 0; hw < 2; ++hw) {
+          std::vector<uint32_t> rem[16];
+          int bankload[16] = {0};
+          for (int l = 0; l < 16; ++l) {
+            const int64_t slot = sl * 32 + hw * 16 + l;
+            if (slot >= n) continue;
+            const int32_t r = slot_row[slot];
+            const int32_t a = grp == 0 ? rp[r] : spv[r], b = grp == 0 ? spv[r] : rp[r + 1];
+            for (int32_t k = a; k < b; ++k) {
+              rem[l].push_back((uint32_t)slot_of[col[k]]);
+              ++bankload[slot_of[col[k]] & 15];
+            }
+          }
+          for (;;) {
+            int lanes[16], nl = 0;
+            for (int l = 0; l < 16; ++l)
+              if (!rem[l].empty()) lanes[nl++] = l;
+            if (!nl) break;
+            std::stable_sort(lanes, lanes + nl, [&](int x, int y) { return rem[x].size() > rem[y].size(); });
+            std::vector<uint32_t> step(16, idle);
+            int used[16] = {0};
+            for (int q = 0; q < nl; ++q) {
+              const int l = lanes[q];
+              int best = -1;
+              for (int e = 0; e < (int)rem[l].size(); ++e) {
+                const int bk = rem[l][e] & 15;
+                if (used[bk] >= kBankCap) continue;
+                if (best < 0) {
+                  best = e;
+                  continue;
+                }
+                const int bb = rem[l][best] & 15;
+                if (bankload[bk] > bankload[bb] || (bankload[bk] == bankload[bb] && used[bk] < used[bb])) best = e;
+              }
+              if (best < 0) continue;
+              const uint32_t c = rem[l][best];
+              step[l] = c;
+              ++used[c & 15];
+              --bankload[c & 15];
+              rem[l].erase(rem[l].begin() + best);
+            }
+            half_steps[hw].push_back(step);
+          }
+        }
+        const int S = (int)std::max(half_steps[0].size(), half_steps[1].size());
+        if (S > 65535) return fail(HUB_ERR_ARG, "fast path: hopping row schedule too long");
+        st[grp][sl] = (uint16_t)S;
+        steps.assign((size_t)S * 32, idle);
+        for (int hw = 0; hw < 2; ++hw)
+          for (size_t j = 0; j < half_steps[hw].size(); ++j)
+            for (int l = 0; l < 16; ++l) steps[j * 32 + hw * 16 + l] = half_steps[hw][j][l];
+        const int nw = (S + pack - 1) / pack;
+        off[grp][sl + 1] = off[grp][sl] + 32 * nw;
+        for (int j = 0; j < nw; ++j)
+          for (int l = 0; l < 32; ++l) {
+            uint32_t wd;
+            if (pack == 2) {
+              const uint32_t lo = steps[(size_t)(2 * j) * 32 + l];
+              const uint32_t hi = 2 * j + 1 < S ? steps[(size_t)(2 * j + 1) * 32 + l] : idle;
+              wd = lo | (hi << 16);
+            } else {
+              wd = steps[(size_t)j * 32 + l];
+            }
+            words[grp].push_back(wd);
+          }
       }
-      oa[sl + 1] = oa[sl] + 32 * ((ma + pack - 1) / pack);
-      os[sl + 1] = os[sl] + 32 * ((ms + pack - 1) / pack);
     }
     if (!dev_alloc((void **)&f->sl_off_add, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
         !dev_alloc((void **)&f->sl_off_sub, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
-        !dev_alloc((void **)&f->sl_add, sizeof(uint32_t) * std::max<int32_t>(oa[nsl], 1), "sliced columns") ||
-        !dev_alloc((void **)&f->sl_sub, sizeof(uint32_t) * std::max<int32_t>(os[nsl], 1), "sliced columns"))
+        !dev_alloc((void **)&f->sl_add, sizeof(uint32_t) * std::max<size_t>(words[0].size(), 1), "sliced columns") ||
+        !dev_alloc((void **)&f->sl_sub, sizeof(uint32_t) * std::max<size_t>(words[1].size(), 1), "sliced columns") ||
+        !dev_alloc((void **)&f->steps_add, sizeof(uint16_t) * nsl, "slice steps") ||
+        !dev_alloc((void **)&f->steps_sub, sizeof(uint16_t) * nsl, "slice steps"))
       return HUB_ERR_OOM;
-    HUB_CUDA(cudaMemcpy(f->sl_off_add, oa.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(f->sl_off_sub, os.data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemset(f->sl_add, 0, sizeof(uint32_t) * std::max<int32_t>(oa[nsl], 1)));
-    HUB_CUDA(cudaMemset(f->sl_sub, 0, sizeof(uint32_t) * std::max<int32_t>(os[nsl], 1)));
-    if (pack == 2)
-      k_slice_fill<2><<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->col[0], f->sl_off_add, f->sl_off_sub,
-                                  f->slot_row, f->slot_of, f->sl_add, f->sl_sub);
-    else
-      k_slice_fill<1><<<g, 256>>>(n, h->csr[0].rowptr, f->sp[0], f->col[0], f->sl_off_add, f->sl_off_sub,
-                                  f->slot_row, f->slot_of, f->sl_add, f->sl_sub);
-    HUB_LAUNCH_CHECK();
+    HUB_CUDA(cudaMemcpy(f->sl_off_add, off[0].data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+    HUB_CUDA(cudaMemcpy(f->sl_off_sub, off[1].data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+    if (!words[0].empty())
+      HUB_CUDA(cudaMemcpy(f->sl_add, words[0].data(), sizeof(uint32_t) * words[0].size(), cudaMemcpyHostToDevice));
+    if (!words[1].empty())
+      HUB_CUDA(cudaMemcpy(f->sl_sub, words[1].data(), sizeof(uint32_t) * words[1].size(), cudaMemcpyHostToDevice));
+    HUB_CUDA(cudaMemcpy(f->steps_add, st[0].data(), sizeof(uint16_t) * nsl, cudaMemcpyHostToDevice));
+    HUB_CUDA(cudaMemcpy(f->steps_sub, st[1].data(), sizeof(uint16_t) * nsl, cudaMemcpyHostToDevice));
   }
   if (!dev_alloc((void **)&f->d_err, sizeof(int) * 4, "error flag") ||
       !dev_alloc((void **)&f->coef, sizeof(float2) * 8, "recurrence coefficients"))
@@ -708,8 +749,8 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   v.sl_sub = f->sl_sub;
   v.sl_off_add = f->sl_off_add;
   v.sl_off_sub = f->sl_off_sub;
-  v.len_add = f->len_add;
-  v.len_sub = f->len_sub;
+  v.steps_add = f->steps_add;
+  v.steps_sub = f->steps_sub;
   v.slot_row = f->slot_row;
   v.basis_up_slot = f->basis_slot;
   v.eps_up = f->eps_up_slot;
