@@ -372,18 +372,26 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     const int32_t k0 = F.rp_dn[d], ks = F.sp_dn[d], k1 = F.rp_dn[d + 1];
     if (!active) continue;
     DfAcc2 pp{0ull, 0ull}, mm{0ull, 0ull};
-    // rows of the strip are loaded four at a time so that their L2 latencies overlap
-    for (int32_t kb = k0; kb < k1; kb += HUB_DN_BATCH) {
-      float4 v[HUB_DN_BATCH];
-#pragma unroll
-      for (int q = 0; q < HUB_DN_BATCH; ++q)
-        if (kb + q < k1) v[q] = *reinterpret_cast<const float4 *>(x + colat<Col>(F.col_dn, kb + q) * F.ld + u);
-#pragma unroll
-      for (int q = 0; q < HUB_DN_BATCH; ++q) {
-        if (kb + q < ks) acc2_add(pp, pk2(v[q].x, v[q].z), pk2(v[q].y, v[q].w));
-        else if (kb + q < k1) acc2_add(mm, pk2(v[q].x, v[q].z), pk2(v[q].y, v[q].w));
-      }
-    }
+    const float2 *__restrict__ xu = x + u;
+    // strip rows of each group, HUB_DN_BATCH loads in flight; the bounds are warp-uniform
+#define HUB_DN_GROUP(ACC, KA, KB)                                                          \
+  do {                                                                                     \
+    int32_t k = (KA);                                                                      \
+    for (; k + HUB_DN_BATCH <= (KB); k += HUB_DN_BATCH) {                                  \
+      float4 v[HUB_DN_BATCH];                                                              \
+      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q)                             \
+        v[q] = *reinterpret_cast<const float4 *>(xu + colat<Col>(F.col_dn, k + q) * F.ld); \
+      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q)                             \
+        acc2_add(ACC, pk2(v[q].x, v[q].z), pk2(v[q].y, v[q].w));                           \
+    }                                                                                      \
+    for (; k < (KB); ++k) {                                                                \
+      const float4 v = *reinterpret_cast<const float4 *>(xu + colat<Col>(F.col_dn, k) * F.ld); \
+      acc2_add(ACC, pk2(v.x, v.z), pk2(v.y, v.w));                                         \
+    }                                                                                      \
+  } while (0)
+    HUB_DN_GROUP(pp, k0, ks);
+    HUB_DN_GROUP(mm, ks, k1);
+#undef HUB_DN_GROUP
     const float4 zz = *reinterpret_cast<const float4 *>(z + d * F.ld + u);
     const float2 mv0 = acc_value(acc2_lane(mm, 0)), mv1 = acc_value(acc2_lane(mm, 1));
     float2 s0 = df_add(acc_value(acc2_lane(pp, 0)), make_float2(-mv0.x, -mv0.y));
@@ -447,10 +455,17 @@ __global__ void k_df_update(int64_t n, float2 *__restrict__ w, const float2 *__r
                             const float2 *__restrict__ coef, double *__restrict__ partials) {
   const float2 c = coef[2];
   DfAcc acc{0.f, 0.f};
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const float2 v = df_fma(c, r_cur[k], w[k]);
-    w[k] = v;
-    acc_add(acc, df_mul(v, v));
+  // two elements per thread and step (16-byte accesses; n is even: rows have even length)
+  float4 *__restrict__ w4 = reinterpret_cast<float4 *>(w);
+  const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(r_cur);
+  const int64_t n2 = n >> 1;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2; k += (int64_t)gridDim.x * blockDim.x) {
+    const float4 rv = r4[k], wv = w4[k];
+    const float2 v0 = df_fma(c, make_float2(rv.x, rv.y), make_float2(wv.x, wv.y));
+    const float2 v1 = df_fma(c, make_float2(rv.z, rv.w), make_float2(wv.z, wv.w));
+    w4[k] = make_float4(v0.x, v0.y, v1.x, v1.y);
+    acc_add(acc, df_mul(v0, v0));
+    acc_add(acc, df_mul(v1, v1));
   }
   block_sum_to(df_to_f64(acc_value(acc), 0), partials);
 }
