@@ -128,7 +128,8 @@ int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream);
 int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, double *E0,
                        double *psi_dev, int *iters, void *stream);
 
-/* The alpha_j, beta_j of the last hub_lanczos_ground (host arrays of length >= cap). */
+/* The alpha_j, beta_j of the last hub_lanczos_ground (host arrays of length >= cap; *n =
+ * number of steps).  beta_{n-1} is 0 when the run stopped before computing it. */
 int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host, int cap, int *n);
 
 /*

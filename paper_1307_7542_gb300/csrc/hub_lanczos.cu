@@ -364,7 +364,7 @@ extern "C" int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host
   if (n) *n = k;
   for (int i = 0; i < k && i < cap; ++i) {
     if (alpha_host) alpha_host[i] = h->alpha[i];
-    if (beta_host) beta_host[i] = h->beta[i];
+    if (beta_host) beta_host[i] = i < (int)h->beta.size() ? h->beta[i] : 0.0;   // last beta may be unknown
   }
   return HUB_OK;
 }
