@@ -100,6 +100,7 @@ struct FastView {
   const uint32_t *sl_add, *sl_sub;   // packed words
   const int32_t *sl_off_add, *sl_off_sub;
   const uint16_t *steps_add, *steps_sub;   // per slice: scheduled steps (entries per lane)
+  uint32_t idle_word;                // a column word whose entries are all idle steps
   const int32_t *slot_row;           // spin-up rank held by slot k
   const uint32_t *basis_up_slot;     // spin-up strings in slot order
   const float2 *eps_up, *eps_dn;     // per-state site energies (double-float; up: slot order) or null
@@ -197,17 +198,26 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
+// Staged rows: row 0 at entry 0, row 1 at entry kUpStride (a compile-time offset, so the
+// second load of a term needs no address arithmetic); entries ld and ld+1 after each row
+// are zero and serve as the column of idle schedule steps (adding zero is exact).
+constexpr int kUpStride = 14080;
+
 template <typename Col, bool kStage, bool kEps>
 __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *__restrict__ x,
                                                 float2 *__restrict__ z) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float2 *xs0 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *xs1 = xs0 + F.ld;
+  float2 *xs1 = xs0 + kUpStride;
   __shared__ __align__(8) uint64_t bar;
   __shared__ float2 utab[32];
   const int tid = threadIdx.x;
   const uint32_t bytes = (uint32_t)(F.ld * sizeof(float2));
   if (tid < 32) utab[tid] = F.Utab[tid];
+  if (kStage && tid < 2) {
+    xs0[F.ld + tid] = make_float2(0.f, 0.f);
+    xs1[F.ld + tid] = make_float2(0.f, 0.f);
+  }
   if (kStage && tid == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
@@ -256,7 +266,10 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
 #define HUB_TERM(ACC, C, IDLE)                                                 \
   do {                                                                         \
     const uint32_t c_ = (C);                                                   \
-    if (c_ != (IDLE)) {                                                        \
+    if (kStage) {                                  /* idle steps read zeros */ \
+      const float2 v0 = xs0[c_], v1 = xs0[c_ + kUpStride];                     \
+      acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));                         \
+    } else if (c_ != (IDLE)) {                                                 \
       const float2 v0 = s0[c_], v1 = s1[c_];                                   \
       acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));                         \
     }                                                                          \
@@ -267,7 +280,7 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
     const int nw = sizeof(Col) == 2 ? ((N) + 1) >> 1 : (N);                          \
     for (int j0 = 0; j0 < nw; j0 += 4) {                                             \
       uint32_t wd[4];                                                                \
-      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : 0xffffffffu; \
+      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : F.idle_word; \
       _Pragma("unroll") for (int q = 0; q < 4; ++q) {                                \
         if (sizeof(Col) == 2) {                                                      \
           HUB_TERM(ACC, wd[q] & 0xffffu, 0xffffu);                                   \
@@ -520,6 +533,7 @@ struct FastState {
   uint32_t *sl_add = nullptr, *sl_sub = nullptr;
   int32_t *sl_off_add = nullptr, *sl_off_sub = nullptr;
   uint16_t *steps_add = nullptr, *steps_sub = nullptr;
+  uint32_t idle_word = 0xffffffffu;
   int32_t *slot_row = nullptr, *slot_of = nullptr;
   uint32_t *basis_slot = nullptr;
   float2 *eps_up_slot = nullptr;
@@ -645,7 +659,10 @@ int fast_build(hub_ctx *h) {
     // bank loads are uneven; two per bank costs about 4 % more steps for 1.5x fewer
     // wavefronts than the unscheduled order.)
     constexpr int kBankCap = 2;
-    const uint32_t idle = f->col16 ? 0xffffu : 0xffffffffu;
+    // idle steps: the zero entry after the staged row when rows are staged, else a sentinel
+    const bool staged = f->ld + 2 <= kUpStride;
+    const uint32_t idle = staged ? (uint32_t)f->ld : (f->col16 ? 0xffffu : 0xffffffffu);
+    f->idle_word = f->col16 ? (idle | (idle << 16)) : idle;
     const int pack = f->col16 ? 2 : 1;
     std::vector<uint16_t> st[2] = {std::vector<uint16_t>(nsl), std::vector<uint16_t>(nsl)};
     std::vector<int32_t> off[2] = {std::vector<int32_t>(nsl + 1, 0), std::vector<int32_t>(nsl + 1, 0)};
@@ -767,6 +784,7 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   v.steps_add = f->steps_add;
   v.steps_sub = f->steps_sub;
   v.slot_row = f->slot_row;
+  v.idle_word = f->idle_word;
   v.basis_up_slot = f->basis_slot;
   v.eps_up = f->eps_up_slot;
   v.eps_dn = f->eps_df[sd];
@@ -783,12 +801,15 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   return v;
 }
 
-static size_t up_smem(const FastState *f) { return 2 * sizeof(float2) * (size_t)f->ld; }
+static size_t up_smem(const FastState *f) { return sizeof(float2) * ((size_t)kUpStride + (size_t)f->ld + 2); }
 constexpr size_t kMaxStage = 224 * 1024;
+static_assert(sizeof(float2) * 2 * kUpStride <= kMaxStage, "two staged rows must fit");
+
+static bool up_staged(const FastState *f) { return f->ld + 2 <= kUpStride; }
 
 template <typename Col>
 static int launch_up_t(const FastView &v, const FastState *f, bool eps, const float2 *x, float2 *z, cudaStream_t s) {
-  const bool stage = up_smem(f) <= kMaxStage;
+  const bool stage = up_staged(f);
   const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
   int64_t grid = std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms() * (stage ? 1 : 2) * (1024 / threads));
   const size_t smem = stage ? up_smem(f) : 0;
