@@ -315,6 +315,72 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
 }
 
 // ---------------------------------------------------------------------------------------
+// Pass 1 for rows too long to stage (e.g. C(18, 9) = 48620 columns, 389 KB per row): the
+// gathers read the rows through L2.  To keep the rows being gathered resident in L2, the
+// grid is (slot chunk, row pair) with the chunk index fastest, so the blocks in flight at
+// any time all work on one or two row pairs instead of one pair per SM.
+// ---------------------------------------------------------------------------------------
+constexpr int kL2Threads = 512;
+
+template <typename Col, bool kEps>
+__global__ void __launch_bounds__(kL2Threads) k_up_l2(const FastView F, const float2 *__restrict__ x,
+                                                      float2 *__restrict__ z, int64_t pair0) {
+  __shared__ float2 utab[32];
+  const int tid = threadIdx.x;
+  if (tid < 32) utab[tid] = F.Utab[tid];
+  __syncthreads();
+  const int64_t p = pair0 + blockIdx.y;
+  const int64_t d0 = 2 * p, d1 = (2 * p + 1 < F.n_dn) ? 2 * p + 1 : 2 * p;
+  const float2 *__restrict__ s0 = x + d0 * F.ld;
+  const float2 *__restrict__ s1 = x + d1 * F.ld;
+  const int64_t slot = (int64_t)blockIdx.x * kL2Threads + tid;
+  if (slot >= F.n_up) return;
+  const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
+  DfAcc2 ap{0ull, 0ull}, am{0ull, 0ull};
+  const int64_t sl = slot >> 5, lane = slot & 31;
+  const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
+  const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
+  const int na = F.steps_add[sl], ns = F.steps_sub[sl];
+  const uint32_t idle = sizeof(Col) == 2 ? 0xffffu : 0xffffffffu;
+#define HUB_LGROUP(ACC, W, N)                                                                \
+  do {                                                                                       \
+    const int nw = sizeof(Col) == 2 ? ((N) + 1) >> 1 : (N);                                  \
+    for (int j0 = 0; j0 < nw; j0 += 4) {                                                     \
+      uint32_t wd[4];                                                                        \
+      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : F.idle_word; \
+      _Pragma("unroll") for (int q = 0; q < (sizeof(Col) == 2 ? 8 : 4); ++q) {              \
+        const uint32_t c_ = sizeof(Col) == 2 ? ((q & 1) ? (wd[q >> 1] >> 16) : (wd[q >> 1] & 0xffffu)) : wd[q]; \
+        if (c_ != idle) {                                                                    \
+          const float2 v0 = s0[c_], v1 = s1[c_];                                             \
+          acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));                                   \
+        }                                                                                    \
+      }                                                                                      \
+    }                                                                                        \
+  } while (0)
+  HUB_LGROUP(ap, wa, na);
+  HUB_LGROUP(am, wsb, ns);
+#undef HUB_LGROUP
+  const int64_t u = slot;
+  const uint32_t Iu = F.basis_up_slot[u];
+  float2 ep = make_float2(0.f, 0.f), e0 = ep, e1 = ep;
+  if (kEps) {
+    ep = F.eps_up[u];
+    e0 = F.eps_dn[d0];
+    e1 = F.eps_dn[d1];
+  }
+#pragma unroll
+  for (int r = 0; r < 2; ++r) {
+    const float2 sp = acc_value(acc2_lane(ap, r)), sm = acc_value(acc2_lane(am, r));
+    float2 S = df_add(sp, make_float2(-sm.x, -sm.y));
+    if (!F.t_is_one) S = df_mul(S, F.t);
+    float2 dg = utab[__popc(Iu & (r == 0 ? I0 : I1))];
+    if (kEps) dg = df_add(df_add(dg, ep), r == 0 ? e0 : e1);
+    const float2 xv = r == 0 ? s0[u] : s1[u];
+    if (r == 0 || d1 != d0) z[(r == 0 ? d0 : d1) * F.ld + u] = df_fma(dg, xv, S);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
 // Pass 2: spin-down hops as combinations of whole rows of a column strip, plus the
 // epilogue.  Tile = 32 rows x 64 columns; blockIdx.x = row tile (fast), blockIdx.y =
 // column strip (slow), so consecutive blocks share a strip.  Lane l of a warp owns the
@@ -810,6 +876,17 @@ static bool up_staged(const FastState *f) { return f->ld + 2 <= kUpStride; }
 template <typename Col>
 static int launch_up_t(const FastView &v, const FastState *f, bool eps, const float2 *x, float2 *z, cudaStream_t s) {
   const bool stage = up_staged(f);
+  if (!stage) {
+    const int64_t n_pairs = (v.n_dn + 1) / 2;
+    const unsigned chunks = (unsigned)((v.n_up + kL2Threads - 1) / kL2Threads);
+    for (int64_t p0 = 0; p0 < n_pairs; p0 += 65535) {
+      const dim3 g(chunks, (unsigned)std::min<int64_t>(65535, n_pairs - p0));
+      if (eps) k_up_l2<Col, true><<<g, kL2Threads, 0, s>>>(v, x, z, p0);
+      else k_up_l2<Col, false><<<g, kL2Threads, 0, s>>>(v, x, z, p0);
+      HUB_LAUNCH_CHECK();
+    }
+    return HUB_OK;
+  }
   const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
   int64_t grid = std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms() * (stage ? 1 : 2) * (1024 / threads));
   const size_t smem = stage ? up_smem(f) : 0;
