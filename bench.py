@@ -189,7 +189,9 @@ def run_reference(a):
         if dt >= 0.5 or r >= D:
             break
         r = min(D, r * 4)
-    R = int(min(D - 1, max(r, r * 2.0 / max(dt, 1e-6))))
+    # about 1 s per step, and at most ~150 s for the whole run however many steps are asked
+    per_step = min(1.0, 150.0 / max(1, a.steps + a.warmup))
+    R = int(min(D - 1, max(1000, r * per_step / max(dt, 1e-6))))
     for k in range(a.warmup):
         O.apply(om, B, x, rows=(0, R))
     t0 = time.perf_counter()
