@@ -417,29 +417,22 @@ __global__ void k_set_scal(double *__restrict__ scal, int i0, double v0, int i1,
   if (i2 >= 0) scal[i2] = v2;
 }
 
-// kMode 0: y (FP64, unpadded) = 2^shift (Z + t S_dn).
+// kMode 0: w (double-float, slot order; may alias z) = Z + t S_dn, for hub_apply (the FP64
+//          output in rank order is written afterwards by k_unpermute).
 // kMode 1: w = (Z + t S_dn)/beta_cur - (beta_cur/beta_prev) r_prev  (double-float, padded),
 //          partials <- <q_j, w> per block.
 template <typename Col, int kMode>
 __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float2 *__restrict__ x,
-                                                  const float2 *__restrict__ z, double *__restrict__ y,
-                                                  float2 *__restrict__ w, const int *__restrict__ shift_src,
-                                                  int nblk_shift, LzArgs L) {
+                                                  const float2 *z, double *__restrict__ y, float2 *w,
+                                                  const int *__restrict__ shift_src, int nblk_shift, LzArgs L) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t u = (int64_t)blockIdx.y * kDnCols + 2 * lane;
   const int64_t r0 = (int64_t)blockIdx.x * kDnRows;
-  int shift = 0;
   float2 ib = make_float2(1.f, 0.f), cprev = make_float2(0.f, 0.f);
-  if (kMode == 0) {
-    __shared__ int s_shift;
-    if (threadIdx.x == 0) {
-      int m = 0;
-      for (int k = 0; k < nblk_shift; ++k) m = max(m, shift_src[k]);
-      s_shift = m == 0 ? 0 : m - 1023;
-    }
-    __syncthreads();
-    shift = s_shift;
-  } else {
+  (void)shift_src;
+  (void)nblk_shift;
+  (void)y;
+  if (kMode == 1) {
     ib = L.coef[0];
     cprev = L.coef[1];
   }
@@ -482,8 +475,7 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     const float2 y0 = df_add(make_float2(zz.x, zz.y), s0);
     const float2 y1 = df_add(make_float2(zz.z, zz.w), s1);
     if (kMode == 0) {
-      y[d * F.n_up + F.slot_row[u]] = df_to_f64(y0, shift);
-      if (u + 1 < F.n_up) y[d * F.n_up + F.slot_row[u + 1]] = df_to_f64(y1, shift);
+      *reinterpret_cast<float4 *>(w + d * F.ld + u) = make_float4(y0.x, y0.y, y1.x, y1.y);
     } else {
       const float4 rc = *reinterpret_cast<const float4 *>(L.r_cur + d * F.ld + u);
       const float4 rp = *reinterpret_cast<const float4 *>(L.r_prev + d * F.ld + u);
@@ -579,6 +571,25 @@ __global__ void k_df_out_normalised(int64_t n_rows, int64_t n_up, int64_t ld, co
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t d = k / n_up, slot = k - d * n_up;
     out[d * n_up + slot_row[slot]] = df_to_f64(df_mul(v[d * ld + slot], inv), 0);
+  }
+}
+
+// y[d][u] (FP64, rank order) = 2^shift * v[d][slot_of[u]] (double-float, slot order), one
+// row per block so that the gathers of a row are served from L1.
+__global__ void k_unpermute(int64_t n_rows, int64_t n_up, int64_t ld, const float2 *__restrict__ v,
+                            const int32_t *__restrict__ slot_of, const int *__restrict__ emax, int nblk,
+                            double *__restrict__ y) {
+  __shared__ int s_shift;
+  if (threadIdx.x == 0) {
+    int m = 0;
+    for (int k = 0; k < nblk; ++k) m = max(m, emax[k]);
+    s_shift = m == 0 ? 0 : m - 1023;
+  }
+  __syncthreads();
+  const int shift = s_shift;
+  for (int64_t d = blockIdx.x; d < n_rows; d += gridDim.x) {
+    const float2 *__restrict__ row = v + d * ld;
+    for (int64_t u = threadIdx.x; u < n_up; u += blockDim.x) y[d * n_up + u] = df_to_f64(row[slot_of[u]], shift);
   }
 }
 
@@ -968,7 +979,12 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->slot_row, f->xdf);
   HUB_LAUNCH_CHECK();
   if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
-  return run_dn(h, f, 0, f->xdf, f->zdf, y, nullptr, f->d_emax, G, LzArgs{}, s);
+  if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, nullptr, f->zdf, nullptr, 0, LzArgs{}, s))) return rc;
+  count_launch(h);
+  k_unpermute<<<(int)std::min<int64_t>(h->count[1], (int64_t)num_sms() * 8), 512, 0, s>>>(
+      h->count[1], h->count[0], f->ld, f->zdf, f->slot_of, f->d_emax, G, y);
+  HUB_LAUNCH_CHECK();
+  return HUB_OK;
 }
 
 int fast_check_error(hub_ctx *h) {
