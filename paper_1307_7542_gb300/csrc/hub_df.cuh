@@ -108,16 +108,67 @@ __device__ __forceinline__ f2x sub2(f2x a, f2x b) {
   return r;
 }
 
+__device__ __forceinline__ f2x bcast2(float a) { return pk2(a, a); }
+
 struct DfAcc2 {
   f2x H, L;   // high parts (exact running sums) and low parts + TwoSum errors, per lane
 };
 
+// a += v (v = vh + vl per lane): TwoSum of the high parts, errors and low parts into L.
 __device__ __forceinline__ void acc2_add(DfAcc2 &a, f2x vh, f2x vl) {
   const f2x s = add2(a.H, vh);
   const f2x bb = sub2(s, a.H);
   const f2x e = add2(sub2(a.H, sub2(s, bb)), sub2(vh, bb));
   a.H = s;
   a.L = add2(add2(a.L, vl), e);
+}
+
+// a -= v: the TwoSum of (a.H, -vh) written with subtractions (negation is exact, so this
+// is the same error-free transformation as acc2_add of -v).
+__device__ __forceinline__ void acc2_sub(DfAcc2 &a, f2x vh, f2x vl) {
+  const f2x s = sub2(a.H, vh);
+  const f2x bb = sub2(s, a.H);
+  const f2x e = sub2(sub2(a.H, sub2(s, bb)), add2(vh, bb));
+  a.H = s;
+  a.L = add2(sub2(a.L, vl), e);
+}
+
+// Normalised (hi, lo) per lane of a paired accumulator.
+__device__ __forceinline__ void acc2_norm(const DfAcc2 &a, f2x &h, f2x &l) {
+  const f2x s = add2(a.H, a.L);
+  const f2x bb = sub2(s, a.H);
+  l = add2(sub2(a.H, sub2(s, bb)), sub2(a.L, bb));
+  h = s;
+}
+
+// Packed double-float arithmetic on two lanes; the same operation sequences as df_add and
+// df_mul.
+__device__ __forceinline__ void df2_add(f2x ah, f2x al, f2x bh, f2x bl, f2x &rh, f2x &rl) {
+  const f2x s = add2(ah, bh);
+  const f2x bb = sub2(s, ah);
+  f2x e = add2(sub2(ah, sub2(s, bb)), sub2(bh, bb));
+  e = add2(e, add2(al, bl));
+  rh = add2(s, e);
+  rl = sub2(e, sub2(rh, s));
+}
+__device__ __forceinline__ void df2_sub(f2x ah, f2x al, f2x bh, f2x bl, f2x &rh, f2x &rl) {
+  const f2x s = sub2(ah, bh);
+  const f2x bb = sub2(s, ah);
+  f2x e = sub2(sub2(ah, sub2(s, bb)), add2(bh, bb));
+  e = add2(e, sub2(al, bl));
+  rh = add2(s, e);
+  rl = sub2(e, sub2(rh, s));
+}
+// The product is taken lane by lane with the scalar df_mul: a packed TwoProd (mul.rn.f32x2
+// followed by fma.rn.f32x2 of the same operands against the negated product) was measured
+// on this GPU to return the high-part product without its rounding error in some code
+// shapes (relative error up to 2^-24), while the scalar sequence is exact.
+__device__ __forceinline__ void df2_mul(f2x ah, f2x al, f2x bh, f2x bl, f2x &rh, f2x &rl) {
+  const float2 a_h = upk2(ah), a_l = upk2(al), b_h = upk2(bh), b_l = upk2(bl);
+  const float2 r0 = df_mul(make_float2(a_h.x, a_l.x), make_float2(b_h.x, b_l.x));
+  const float2 r1 = df_mul(make_float2(a_h.y, a_l.y), make_float2(b_h.y, b_l.y));
+  rh = pk2(r0.x, r1.x);
+  rl = pk2(r0.y, r1.y);
 }
 
 // Lane a / lane b of a paired accumulator as a plain accumulator.

@@ -6,25 +6,31 @@
 // (Eq. 8) and diag = U popcount(I_up & I_dn) + eps(I_up) + eps(I_dn) (Sec. III.B).  The
 // two hopping terms want different memory orders, so they run as two passes:
 //
-//   pass 1 (k_up): one CTA per row d.  Row d of X is copied whole into shared memory by
-//     one bulk asynchronous copy (cp.async.bulk, completion on an mbarrier), then each
-//     thread sums the H_up row of its columns u from shared memory (in-row gather) and
-//     adds the diagonal: Z[d][u] = t S_up + diag X[d][u].
+//   pass 1 (k_up): a CTA takes two rows (d0, d1) of X at a time.  Both rows are copied
+//     whole into shared memory by bulk asynchronous copies (cp.async.bulk, completion on
+//     an mbarrier), then each thread sums the H_up row of its column u for both rows from
+//     shared memory (in-row gather) and adds the diagonal:
+//     Z[d][u] = t S_up + diag X[d][u].
 //   pass 2 (k_dn): tiles of 32 rows x 64 columns, launched strip-major (all tiles of one
 //     column strip are adjacent in the grid), so the strip of X that the H_dn rows
 //     combine -- count_dn x 64 values -- stays in L2 while the whole strip is processed
 //     and X is read from HBM about once.  Each warp adds t S_dn to Z for its rows with
-//     128-bit loads of whole rows of the strip.
+//     64-bit loads of whole rows of the strip.
 //
-// Vectors are double-float (hub_df.cuh) with rows padded to an even length so that every
-// row starts on a 16-byte boundary (bulk copies and 16-byte loads).  Inside this file the
-// columns of X are kept in "slot" order: spin-up states sorted by the lengths of their
-// two hopping groups, so that the 32 rows of H_up a warp sums in pass 1 have nearly equal
-// lengths (little divergence) while its loads and stores stay contiguous.  Pass 2 combines
-// whole rows and does not care about column order.  Only the FP64 <-> double-float
-// conversions at the boundary of this file map slots back to ranks.  The hopping rows are
-// reordered by sign (entries adding x first, then entries subtracting x), so no per-term
-// sign handling is needed, and columns are stored as uint16 when count <= 65536.
+// Vectors are double-float (hub_df.cuh), stored planar per row: row d of a vector is 2 ld
+// floats, the ld high parts followed by the ld low parts (ld >= count_up, a multiple of 4,
+// padding columns zero).  Both planes of a row start on 16-byte boundaries (bulk copies),
+// and the two values a packed FP32x2 instruction combines always sit in adjacent words:
+// (hi of row d0, hi of row d1) come from two 32-bit shared loads in pass 1, and the
+// (hi, hi) / (lo, lo) pairs of columns u, u+1 from two 64-bit loads in pass 2, so no
+// register shuffling is needed around the TwoSum chains.  Inside this file the columns of X
+// are kept in "slot" order: spin-up states sorted by the lengths of their two hopping
+// groups, so that the 32 rows of H_up a warp sums in pass 1 have nearly equal lengths
+// (little divergence) while its loads and stores stay contiguous.  Pass 2 combines whole
+// rows and does not care about column order.  Only the FP64 <-> double-float conversions
+// at the boundary of this file map slots back to ranks.  The hopping rows are reordered by
+// sign (entries adding x first, then entries subtracting x), so no per-term sign handling
+// is needed, and columns are stored as uint16 when count <= 65536.
 #include <algorithm>
 #include <cmath>
 #include <new>
@@ -85,7 +91,7 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t *bar, uint32_t phase)
 // Fast-path view (passed by value).
 // ---------------------------------------------------------------------------------------
 struct FastView {
-  int64_t n_up, n_dn, ld;            // ld: padded row length (even)
+  int64_t n_up, n_dn, ld;            // ld: plane length of a row (multiple of 4); row stride 2 ld
   const uint32_t *basis_up, *basis_dn;
   const int32_t *rp_up, *sp_up;      // row start and sign split of H_up
   const int32_t *rp_dn, *sp_dn;
@@ -93,10 +99,11 @@ struct FastView {
   // H_up in sliced column-major form for pass 1.  Rows are placed in slots ordered by their
   // (add, sub) group lengths so that the 32 rows a warp handles have nearly equal lengths;
   // slot k holds row slot_row[k].  Each slice of 32 slots has, per group, a schedule of
-  // steps: in one step every lane reads at most one of its entries, chosen so that the lanes
-  // of each half-warp hit distinct shared-memory bank pairs (column mod 16).  Step j of slot
-  // k is word off[k/32] + (j/2)*32 + k%32 (two uint16 columns per word; idle = 0xffff) or
-  // off[k/32] + j*32 + k%32 (uint32 columns; idle = 0xffffffff).
+  // steps: in one step every lane reads at most one of its entries, chosen so that at most
+  // two lanes of the warp hit the same shared-memory bank (column mod 32).  Step j of slot
+  // k is word off[k/32] + (j/2)*32 + k%32 (two uint16 columns per word) or
+  // off[k/32] + j*32 + k%32 (uint32 columns).  Idle steps name a zero column (staged rows)
+  // or the sentinel 0xffff / 0xffffffff (rows read through L2).
   const uint32_t *sl_add, *sl_sub;   // packed words
   const int32_t *sl_off_add, *sl_off_sub;
   const uint16_t *steps_add, *steps_sub;   // per slice: scheduled steps (entries per lane)
@@ -111,8 +118,8 @@ struct FastView {
 };
 
 template <typename Col>
-__device__ __forceinline__ int64_t colat(const void *c, int64_t k) {
-  return (int64_t)((const Col *)c)[k];
+__device__ __forceinline__ uint32_t colat(const void *c, int64_t k) {
+  return (uint32_t)((const Col *)c)[k];
 }
 
 // ---------------------------------------------------------------------------------------
@@ -148,8 +155,8 @@ __global__ void k_eps_df(int64_t n, const double *__restrict__ e, float2 *__rest
 }
 
 // ---------------------------------------------------------------------------------------
-// Conversions between the ABI's FP64 layout (row length n_up) and the padded double-float
-// layout (row length ld), with a power-of-two scale.
+// Conversions between the ABI's FP64 layout (row length n_up, rank order) and the planar
+// double-float layout (slot order), with a power-of-two scale.
 // ---------------------------------------------------------------------------------------
 // partials[block] = max biased FP64 exponent of |x| over the block's elements
 __global__ void k_max_exp(int64_t D, const double *__restrict__ x, int *__restrict__ partials) {
@@ -169,28 +176,54 @@ __global__ void k_max_exp(int64_t D, const double *__restrict__ x, int *__restri
   }
 }
 
-__global__ void k_f64_to_df(int64_t n_rows, int64_t n_up, int64_t ld, const double *__restrict__ x,
-                            const int *__restrict__ emax, int nblk, const int32_t *__restrict__ slot_row,
-                            float2 *__restrict__ out) {
+// shift such that max |x| 2^-shift lies in [1, 2) (0 for a zero vector); block-uniform call
+__device__ __forceinline__ int block_shift(const int *__restrict__ emax, int nblk) {
   __shared__ int s_shift;
   if (threadIdx.x == 0) {
     int m = 0;
     for (int k = 0; k < nblk; ++k) m = max(m, emax[k]);
-    s_shift = m == 0 ? 0 : m - 1023;          // max |x| 2^-shift in [1, 2)
+    s_shift = m == 0 ? 0 : m - 1023;
   }
   __syncthreads();
-  const int shift = s_shift;
-  const int64_t total = n_rows * ld;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = k / ld, u = k - d * ld;
-    out[k] = u < n_up ? f64_to_df(x[d * n_up + slot_row[u]], shift) : make_float2(0.f, 0.f);
+  return s_shift;
+}
+
+// out (planar, slot order) = 2^-shift x (FP64, rank order), shift from emax (0 when emax is
+// null); one row per block and step
+__global__ void k_f64_to_df(int64_t n_rows, int64_t n_up, int64_t ld, const double *__restrict__ x,
+                            const int *__restrict__ emax, int nblk, const int32_t *__restrict__ slot_row,
+                            float *__restrict__ out) {
+  const int shift = emax ? block_shift(emax, nblk) : 0;
+  for (int64_t d = blockIdx.x; d < n_rows; d += gridDim.x) {
+    float *__restrict__ row = out + d * 2 * ld;
+    const double *__restrict__ xr = x + d * n_up;
+    for (int64_t u = threadIdx.x; u < ld; u += blockDim.x) {
+      const float2 v = u < n_up ? f64_to_df(xr[slot_row[u]], shift) : make_float2(0.f, 0.f);
+      row[u] = v.x;
+      row[ld + u] = v.y;
+    }
+  }
+}
+
+// y[d][u] (FP64, rank order) = 2^shift * v[d][slot_of[u]] (planar double-float, slot
+// order), one row per block and step so that the gathers of a row are served from L1.
+__global__ void k_unpermute(int64_t n_rows, int64_t n_up, int64_t ld, const float *__restrict__ v,
+                            const int32_t *__restrict__ slot_of, const int *__restrict__ emax, int nblk,
+                            double *__restrict__ y) {
+  const int shift = block_shift(emax, nblk);
+  for (int64_t d = blockIdx.x; d < n_rows; d += gridDim.x) {
+    const float *__restrict__ row = v + d * 2 * ld;
+    for (int64_t u = threadIdx.x; u < n_up; u += blockDim.x) {
+      const int32_t s = slot_of[u];
+      y[d * n_up + u] = df_to_f64(make_float2(row[s], row[ld + s]), shift);
+    }
   }
 }
 
 // ---------------------------------------------------------------------------------------
 // Pass 1: spin-up hops (in-row gather from shared memory) and the diagonal.  A CTA takes
-// two rows (d0, d1) at a time: both are staged (two bulk copies completing on one
-// mbarrier), every column index is loaded once for both rows, and the two rows' TwoSum
+// two rows (d0, d1) at a time: their four planes are staged (four bulk copies completing on
+// one mbarrier), every column index is loaded once for both rows, and the two rows' TwoSum
 // chains run as one packed FP32x2 chain.  While a pair is computed, the CTA's next pair is
 // prefetched into L2.
 // ---------------------------------------------------------------------------------------
@@ -198,27 +231,25 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-// Staged rows: row 0 at entry 0, row 1 at entry kUpStride (a compile-time offset, so the
-// second load of a term needs no address arithmetic); entries ld and ld+1 after each row
-// are zero and serve as the column of idle schedule steps (adding zero is exact).
-constexpr int kUpStride = 14080;
+// Staged planes: hi(d0), lo(d0), hi(d1), lo(d1) at k * kUpPlane floats (compile-time
+// offsets, so the four loads of a term share one address; kUpPlane is a multiple of 32, so
+// all planes have the same bank alignment).  Entries ld and ld + 1 of every plane are zero
+// and serve as the column of idle schedule steps (adding zero is exact).
+constexpr int kUpPlane = 14080;
 
-template <typename Col, bool kStage, bool kEps>
-__global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *__restrict__ x,
-                                                float2 *__restrict__ z) {
+template <typename Col, bool kEps>
+__global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *__restrict__ x,
+                                                float *__restrict__ z) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  float2 *xs0 = reinterpret_cast<float2 *>(smem_raw);
-  float2 *xs1 = xs0 + kUpStride;
+  float *xs = reinterpret_cast<float *>(smem_raw);
   __shared__ __align__(8) uint64_t bar;
   __shared__ float2 utab[32];
   const int tid = threadIdx.x;
-  const uint32_t bytes = (uint32_t)(F.ld * sizeof(float2));
+  const int64_t ld = F.ld;
+  const uint32_t pbytes = (uint32_t)(ld * sizeof(float));
   if (tid < 32) utab[tid] = F.Utab[tid];
-  if (kStage && tid < 2) {
-    xs0[F.ld + tid] = make_float2(0.f, 0.f);
-    xs1[F.ld + tid] = make_float2(0.f, 0.f);
-  }
-  if (kStage && tid == 0) {
+  if (tid < 8) xs[(tid >> 1) * kUpPlane + ld + (tid & 1)] = 0.f;
+  if (tid == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
   }
@@ -227,90 +258,116 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
   uint32_t phase = 0;
   for (int64_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
     const int64_t d0 = 2 * p, d1 = (2 * p + 1 < F.n_dn) ? 2 * p + 1 : 2 * p;   // odd tail: same row twice
-    const float2 *__restrict__ r0 = x + d0 * F.ld;
-    const float2 *__restrict__ r1 = x + d1 * F.ld;
-    if (kStage) {
-      if (tid == 0) {
-        fence_proxy_async();
-        mbar_expect_tx(&bar, 2 * bytes);
-        bulk_g2s(xs0, r0, bytes, &bar);
-        bulk_g2s(xs1, r1, bytes, &bar);
-        const int64_t pn = p + gridDim.x;
-        if (pn < n_pairs) {
-          prefetch_l2(x + 2 * pn * F.ld, bytes);
-          if (2 * pn + 1 < F.n_dn) prefetch_l2(x + (2 * pn + 1) * F.ld, bytes);
-        }
+    if (tid == 0) {
+      const float *r0 = x + d0 * 2 * ld, *r1 = x + d1 * 2 * ld;
+      fence_proxy_async();
+      mbar_expect_tx(&bar, 4 * pbytes);
+      bulk_g2s(xs, r0, pbytes, &bar);
+      bulk_g2s(xs + kUpPlane, r0 + ld, pbytes, &bar);
+      bulk_g2s(xs + 2 * kUpPlane, r1, pbytes, &bar);
+      bulk_g2s(xs + 3 * kUpPlane, r1 + ld, pbytes, &bar);
+      const int64_t pn = p + gridDim.x;
+      if (pn < n_pairs) {
+        prefetch_l2(x + 2 * pn * 2 * ld, 2 * pbytes);
+        if (2 * pn + 1 < F.n_dn) prefetch_l2(x + (2 * pn + 1) * 2 * ld, 2 * pbytes);
       }
-      if (!mbar_wait_bounded(&bar, phase)) {
-        if (tid == 0) atomicExch(F.err, 1);
-        mbar_wait_bounded(&bar, phase);      // give a late copy one more bounded chance to land
-        return;
-      }
-      phase ^= 1u;
     }
-    const float2 *__restrict__ s0 = kStage ? xs0 : r0;
-    const float2 *__restrict__ s1 = kStage ? xs1 : r1;
+    if (!mbar_wait_bounded(&bar, phase)) {
+      if (tid == 0) atomicExch(F.err, 1);
+      mbar_wait_bounded(&bar, phase);      // give a late copy one more bounded chance to land
+      return;
+    }
+    phase ^= 1u;
     const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
     float2 e0 = make_float2(0.f, 0.f), e1 = e0;
     if (kEps) {
       e0 = F.eps_dn[d0];
       e1 = F.eps_dn[d1];
     }
-    for (int64_t slot = tid; slot < F.n_up; slot += blockDim.x) {
-      DfAcc2 ap{0ull, 0ull}, am{0ull, 0ull};
+    float *__restrict__ z0 = z + d0 * 2 * ld;
+    float *__restrict__ z1 = z + d1 * 2 * ld;
+    for (int64_t slot = tid; slot < ld; slot += blockDim.x) {
+      if (slot >= F.n_up) {                        // padding columns of Z stay zero
+        z0[slot] = 0.f;
+        z0[ld + slot] = 0.f;
+        z1[slot] = 0.f;
+        z1[ld + slot] = 0.f;
+        continue;
+      }
+      DfAcc2 acc{0ull, 0ull};
       const int64_t sl = slot >> 5, lane = slot & 31;
       const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
       const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
       const int na = F.steps_add[sl], ns = F.steps_sub[sl];
-      // one scheduled entry: idle steps (sentinel column) add nothing
-#define HUB_TERM(ACC, C, IDLE)                                                 \
-  do {                                                                         \
-    const uint32_t c_ = (C);                                                   \
-    if (kStage) {                                  /* idle steps read zeros */ \
-      const float2 v0 = xs0[c_], v1 = xs0[c_ + kUpStride];                     \
-      acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));                         \
-    } else if (c_ != (IDLE)) {                                                 \
-      const float2 v0 = s0[c_], v1 = s1[c_];                                   \
-      acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));                         \
-    }                                                                          \
+      // one scheduled entry (idle steps read the zero column): (hi d0, hi d1), (lo d0, lo d1)
+#define HUB_TERM(OP, C)                                                                  \
+  do {                                                                                   \
+    const uint32_t c_ = (C);                                                             \
+    OP(acc, pk2(xs[c_], xs[c_ + 2 * kUpPlane]), pk2(xs[c_ + kUpPlane], xs[c_ + 3 * kUpPlane])); \
   } while (0)
-      // column words are loaded four at a time so that their L2 latencies overlap
-#define HUB_GROUP(ACC, W, N)                                                         \
+      // Column words are loaded four at a time so that their L2 latencies overlap; the
+      // last one to three words are loaded together too, and only the steps that exist
+      // are summed (N is uniform over the warp, so these branches do not diverge).
+#define HUB_GROUP(OP, W, N)                                                          \
   do {                                                                               \
-    const int nw = sizeof(Col) == 2 ? ((N) + 1) >> 1 : (N);                          \
-    for (int j0 = 0; j0 < nw; j0 += 4) {                                             \
+    const int nst = (N);                                                             \
+    const int nw = sizeof(Col) == 2 ? (nst + 1) >> 1 : nst;                          \
+    int j0 = 0;                                                                      \
+    for (; j0 + 4 <= nw; j0 += 4) {                                                  \
       uint32_t wd[4];                                                                \
-      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : F.idle_word; \
+      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = W[(j0 + q) * 32];        \
       _Pragma("unroll") for (int q = 0; q < 4; ++q) {                                \
         if (sizeof(Col) == 2) {                                                      \
-          HUB_TERM(ACC, wd[q] & 0xffffu, 0xffffu);                                   \
-          HUB_TERM(ACC, wd[q] >> 16, 0xffffu);                                       \
+          HUB_TERM(OP, wd[q] & 0xffffu);                                             \
+          if (2 * (j0 + q) + 1 < nst) HUB_TERM(OP, wd[q] >> 16);                      \
         } else {                                                                     \
-          HUB_TERM(ACC, wd[q], 0xffffffffu);                                         \
+          HUB_TERM(OP, wd[q]);                                                       \
+        }                                                                            \
+      }                                                                              \
+    }                                                                                \
+    if (j0 < nw) {                                                                   \
+      uint32_t wd[3];                                                                \
+      _Pragma("unroll") for (int q = 0; q < 3; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : F.idle_word; \
+      _Pragma("unroll") for (int q = 0; q < 3; ++q) {                                \
+        if (j0 + q < nw) {                                                           \
+          if (sizeof(Col) == 2) {                                                    \
+            HUB_TERM(OP, wd[q] & 0xffffu);                                           \
+            if (2 * (j0 + q) + 1 < nst) HUB_TERM(OP, wd[q] >> 16);                    \
+          } else {                                                                   \
+            HUB_TERM(OP, wd[q]);                                                     \
+          }                                                                          \
         }                                                                            \
       }                                                                              \
     }                                                                                \
   } while (0)
-      HUB_GROUP(ap, wa, na);
-      HUB_GROUP(am, wsb, ns);
+      HUB_GROUP(acc2_add, wa, na);
+      HUB_GROUP(acc2_sub, wsb, ns);
 #undef HUB_GROUP
 #undef HUB_TERM
-      const int64_t u = slot;                            // columns are in slot order
-      const uint32_t Iu = F.basis_up_slot[u];
-      float2 ep = make_float2(0.f, 0.f);
-      if (kEps) ep = F.eps_up[u];
-#pragma unroll
-      for (int r = 0; r < 2; ++r) {
-        const float2 sp = acc_value(acc2_lane(ap, r)), sm = acc_value(acc2_lane(am, r));
-        float2 S = df_add(sp, make_float2(-sm.x, -sm.y));
-        if (!F.t_is_one) S = df_mul(S, F.t);
-        float2 dg = utab[__popc(Iu & (r == 0 ? I0 : I1))];
-        if (kEps) dg = df_add(df_add(dg, ep), r == 0 ? e0 : e1);
-        const float2 xv = r == 0 ? s0[u] : s1[u];
-        if (r == 0 || d1 != d0) z[(r == 0 ? d0 : d1) * F.ld + u] = df_fma(dg, xv, S);
+      // Z = diag x + t S for both rows (packed)
+      f2x Sh, Sl;
+      acc2_norm(acc, Sh, Sl);
+      if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+      const uint32_t Iu = F.basis_up_slot[slot];
+      float2 dg0 = utab[__popc(Iu & I0)], dg1 = utab[__popc(Iu & I1)];
+      if (kEps) {
+        const float2 ep = F.eps_up[slot];
+        dg0 = df_add(df_add(dg0, ep), e0);
+        dg1 = df_add(df_add(dg1, ep), e1);
+      }
+      f2x ph, pl, zh, zl;
+      df2_mul(pk2(dg0.x, dg1.x), pk2(dg0.y, dg1.y), pk2(xs[slot], xs[slot + 2 * kUpPlane]),
+              pk2(xs[slot + kUpPlane], xs[slot + 3 * kUpPlane]), ph, pl);
+      df2_add(ph, pl, Sh, Sl, zh, zl);
+      const float2 h = upk2(zh), l = upk2(zl);
+      z0[slot] = h.x;
+      z0[ld + slot] = l.x;
+      if (d1 != d0) {
+        z1[slot] = h.y;
+        z1[ld + slot] = l.y;
       }
     }
-    if (kStage) __syncthreads();
+    __syncthreads();
   }
 }
 
@@ -323,60 +380,72 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float2 *
 constexpr int kL2Threads = 512;
 
 template <typename Col, bool kEps>
-__global__ void __launch_bounds__(kL2Threads) k_up_l2(const FastView F, const float2 *__restrict__ x,
-                                                      float2 *__restrict__ z, int64_t pair0) {
+__global__ void __launch_bounds__(kL2Threads) k_up_l2(const FastView F, const float *__restrict__ x,
+                                                      float *__restrict__ z, int64_t pair0) {
   __shared__ float2 utab[32];
   const int tid = threadIdx.x;
   if (tid < 32) utab[tid] = F.Utab[tid];
   __syncthreads();
+  const int64_t ld = F.ld;
   const int64_t p = pair0 + blockIdx.y;
   const int64_t d0 = 2 * p, d1 = (2 * p + 1 < F.n_dn) ? 2 * p + 1 : 2 * p;
-  const float2 *__restrict__ s0 = x + d0 * F.ld;
-  const float2 *__restrict__ s1 = x + d1 * F.ld;
+  const float *__restrict__ s0 = x + d0 * 2 * ld;
+  const float *__restrict__ s1 = x + d1 * 2 * ld;
+  float *__restrict__ z0 = z + d0 * 2 * ld;
+  float *__restrict__ z1 = z + d1 * 2 * ld;
   const int64_t slot = (int64_t)blockIdx.x * kL2Threads + tid;
-  if (slot >= F.n_up) return;
+  if (slot >= ld) return;
+  if (slot >= F.n_up) {
+    z0[slot] = 0.f;
+    z0[ld + slot] = 0.f;
+    z1[slot] = 0.f;
+    z1[ld + slot] = 0.f;
+    return;
+  }
   const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
-  DfAcc2 ap{0ull, 0ull}, am{0ull, 0ull};
+  DfAcc2 acc{0ull, 0ull};
   const int64_t sl = slot >> 5, lane = slot & 31;
   const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
   const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
   const int na = F.steps_add[sl], ns = F.steps_sub[sl];
   const uint32_t idle = sizeof(Col) == 2 ? 0xffffu : 0xffffffffu;
-#define HUB_LGROUP(ACC, W, N)                                                                \
+#define HUB_LGROUP(OP, W, N)                                                                 \
   do {                                                                                       \
-    const int nw = sizeof(Col) == 2 ? ((N) + 1) >> 1 : (N);                                  \
+    const int nst = (N);                                                                     \
+    const int nw = sizeof(Col) == 2 ? (nst + 1) >> 1 : nst;                                  \
     for (int j0 = 0; j0 < nw; j0 += 4) {                                                     \
       uint32_t wd[4];                                                                        \
       _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : F.idle_word; \
       _Pragma("unroll") for (int q = 0; q < (sizeof(Col) == 2 ? 8 : 4); ++q) {              \
+        if ((sizeof(Col) == 2 ? 2 * j0 + q : j0 + q) >= nst) break;   /* uniform */          \
         const uint32_t c_ = sizeof(Col) == 2 ? ((q & 1) ? (wd[q >> 1] >> 16) : (wd[q >> 1] & 0xffffu)) : wd[q]; \
-        if (c_ != idle) {                                                                    \
-          const float2 v0 = s0[c_], v1 = s1[c_];                                             \
-          acc2_add(ACC, pk2(v0.x, v1.x), pk2(v0.y, v1.y));                                   \
-        }                                                                                    \
+        if (c_ != idle) OP(acc, pk2(s0[c_], s1[c_]), pk2(s0[ld + c_], s1[ld + c_]));         \
       }                                                                                      \
     }                                                                                        \
   } while (0)
-  HUB_LGROUP(ap, wa, na);
-  HUB_LGROUP(am, wsb, ns);
+  HUB_LGROUP(acc2_add, wa, na);
+  HUB_LGROUP(acc2_sub, wsb, ns);
 #undef HUB_LGROUP
-  const int64_t u = slot;
-  const uint32_t Iu = F.basis_up_slot[u];
-  float2 ep = make_float2(0.f, 0.f), e0 = ep, e1 = ep;
+  f2x Sh, Sl;
+  acc2_norm(acc, Sh, Sl);
+  if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+  const uint32_t Iu = F.basis_up_slot[slot];
+  float2 dg0 = utab[__popc(Iu & I0)], dg1 = utab[__popc(Iu & I1)];
   if (kEps) {
-    ep = F.eps_up[u];
-    e0 = F.eps_dn[d0];
-    e1 = F.eps_dn[d1];
+    const float2 ep = F.eps_up[slot];
+    dg0 = df_add(df_add(dg0, ep), F.eps_dn[d0]);
+    dg1 = df_add(df_add(dg1, ep), F.eps_dn[d1]);
   }
-#pragma unroll
-  for (int r = 0; r < 2; ++r) {
-    const float2 sp = acc_value(acc2_lane(ap, r)), sm = acc_value(acc2_lane(am, r));
-    float2 S = df_add(sp, make_float2(-sm.x, -sm.y));
-    if (!F.t_is_one) S = df_mul(S, F.t);
-    float2 dg = utab[__popc(Iu & (r == 0 ? I0 : I1))];
-    if (kEps) dg = df_add(df_add(dg, ep), r == 0 ? e0 : e1);
-    const float2 xv = r == 0 ? s0[u] : s1[u];
-    if (r == 0 || d1 != d0) z[(r == 0 ? d0 : d1) * F.ld + u] = df_fma(dg, xv, S);
+  f2x ph, pl, zh, zl;
+  df2_mul(pk2(dg0.x, dg1.x), pk2(dg0.y, dg1.y), pk2(s0[slot], s1[slot]), pk2(s0[ld + slot], s1[ld + slot]), ph,
+          pl);
+  df2_add(ph, pl, Sh, Sl, zh, zl);
+  const float2 h = upk2(zh), l = upk2(zl);
+  z0[slot] = h.x;
+  z0[ld + slot] = l.x;
+  if (d1 != d0) {
+    z1[slot] = h.y;
+    z1[ld + slot] = l.y;
   }
 }
 
@@ -384,8 +453,8 @@ __global__ void __launch_bounds__(kL2Threads) k_up_l2(const FastView F, const fl
 // Pass 2: spin-down hops as combinations of whole rows of a column strip, plus the
 // epilogue.  Tile = 32 rows x 64 columns; blockIdx.x = row tile (fast), blockIdx.y =
 // column strip (slow), so consecutive blocks share a strip.  Lane l of a warp owns the
-// columns u0 + 2l, u0 + 2l + 1 (one 16-byte load per row), and sums both with one packed
-// FP32x2 TwoSum chain.
+// columns u0 + 2l, u0 + 2l + 1 (one 64-bit load per plane and row), and sums both with one
+// packed FP32x2 TwoSum chain.
 // ---------------------------------------------------------------------------------------
 constexpr int kDnRows = 32, kDnCols = 64, kDnThreads = 256;
 #ifndef HUB_DN_BATCH
@@ -393,18 +462,20 @@ constexpr int kDnRows = 32, kDnCols = 64, kDnThreads = 256;
 #endif
 
 struct LzArgs {                      // Lanczos epilogue operands
-  const float2 *r_cur;               // r_j   (q_j = r_j / beta_cur)
-  const float2 *r_prev;              // r_{j-1}
+  const float *r_cur;                // r_j   (q_j = r_j / beta_cur)
+  const float *r_prev;               // r_{j-1}
   const float2 *coef;                // [0] 1/beta_cur, [1] beta_cur/beta_prev (double-float)
+  const double *inv_beta;            // 1/beta_cur (FP64)
   double *partials;                  // alpha partial per block
 };
 
-// Coefficients of the recurrence as double-floats, computed once per step by one thread
-// (keeps FP64 divisions out of the wide kernels).  scal: [0] alpha_j, [1] beta_cur,
-// [2] beta_prev.  coef: [0] 1/beta_cur, [1] beta_cur/beta_prev (0 at the first step),
-// [2] -alpha_j/beta_cur.
-__global__ void k_coeffs(const double *__restrict__ scal, float2 *__restrict__ coef) {
+// Coefficients of the recurrence, computed once per step by one thread (keeps FP64
+// divisions out of the wide kernels).  scal: [0] alpha_j, [1] beta_cur, [2] beta_prev;
+// writes scal[6] = 1/beta_cur and, as double-floats, coef[0] = 1/beta_cur,
+// coef[1] = beta_cur/beta_prev (0 at the first step), coef[2] = -alpha_j/beta_cur.
+__global__ void k_coeffs(double *__restrict__ scal, float2 *__restrict__ coef) {
   const double a = scal[0], bc = scal[1], bp = scal[2];
+  scal[6] = 1.0 / bc;
   coef[0] = f64_to_df(1.0 / bc, 0);
   coef[1] = f64_to_df(bp > 0.0 ? bc / bp : 0.0, 0);
   coef[2] = f64_to_df(-a / bc, 0);
@@ -417,81 +488,102 @@ __global__ void k_set_scal(double *__restrict__ scal, int i0, double v0, int i1,
   if (i2 >= 0) scal[i2] = v2;
 }
 
-// kMode 0: w (double-float, slot order; may alias z) = Z + t S_dn, for hub_apply (the FP64
-//          output in rank order is written afterwards by k_unpermute).
-// kMode 1: w = (Z + t S_dn)/beta_cur - (beta_cur/beta_prev) r_prev  (double-float, padded),
-//          partials <- <q_j, w> per block.
+__device__ __forceinline__ f2x ld2(const float *p) { return *reinterpret_cast<const f2x *>(p); }
+__device__ __forceinline__ void st2(float *p, f2x v) { *reinterpret_cast<f2x *>(p) = v; }
+
+// FP64 value of lane a + lane b of a packed (hi, lo) pair
+__device__ __forceinline__ double df2_lanes_to_f64(f2x h, f2x l) {
+  const float2 hh = upk2(h), ll = upk2(l);
+  return df_to_f64(make_float2(hh.x, ll.x), 0) + df_to_f64(make_float2(hh.y, ll.y), 0);
+}
+
+// kMode 0: w (planar double-float, slot order; may alias z) = Z + t S_dn, for hub_apply
+//          (the FP64 output in rank order is written afterwards by k_unpermute).
+// kMode 1: w = (Z + t S_dn)/beta_cur - (beta_cur/beta_prev) r_prev, partials <- <q_j, w>
+//          per block (= <r_j, w>/beta_cur).
 template <typename Col, int kMode>
-__global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float2 *__restrict__ x,
-                                                  const float2 *z, double *__restrict__ y, float2 *w,
-                                                  const int *__restrict__ shift_src, int nblk_shift, LzArgs L) {
+__global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float *__restrict__ x, const float *z,
+                                                  float *w, LzArgs L) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int64_t ld = F.ld;
   const int64_t u = (int64_t)blockIdx.y * kDnCols + 2 * lane;
   const int64_t r0 = (int64_t)blockIdx.x * kDnRows;
-  float2 ib = make_float2(1.f, 0.f), cprev = make_float2(0.f, 0.f);
-  (void)shift_src;
-  (void)nblk_shift;
-  (void)y;
+  const uint32_t row_bytes = (uint32_t)(2 * ld * sizeof(float));
+  f2x ibh = 0ull, ibl = 0ull, cph = 0ull, cpl = 0ull;
   if (kMode == 1) {
-    ib = L.coef[0];
-    cprev = L.coef[1];
+    const float2 ib = L.coef[0], cp = L.coef[1];
+    ibh = bcast2(ib.x);
+    ibl = bcast2(ib.y);
+    cph = bcast2(cp.x);
+    cpl = bcast2(cp.y);
   }
-  DfAcc dacc{0.f, 0.f};
-  const bool active = u < F.n_up;                      // u even, ld even: u + 1 <= ld - 1
+  DfAcc2 dacc{0ull, 0ull};
+  const bool active = u < F.n_up;                      // u even, ld multiple of 4: u + 1 < ld
+  const char *__restrict__ xh = reinterpret_cast<const char *>(x + u);
+  const char *__restrict__ xl = reinterpret_cast<const char *>(x + ld + u);
   for (int rr = warp; rr < kDnRows; rr += kDnThreads / 32) {
     const int64_t d = r0 + rr;
     if (d >= F.n_dn) break;
     const int32_t k0 = F.rp_dn[d], ks = F.sp_dn[d], k1 = F.rp_dn[d + 1];
-    if (!active) continue;
-    DfAcc2 pp{0ull, 0ull}, mm{0ull, 0ull};
-    const float2 *__restrict__ xu = x + u;
+    if (!active) {
+      if (u < ld) {                                      // padding columns of w stay zero
+        st2(w + d * 2 * ld + u, 0ull);
+        st2(w + d * 2 * ld + ld + u, 0ull);
+      }
+      continue;
+    }
+    DfAcc2 acc{0ull, 0ull};
     // strip rows of each group, HUB_DN_BATCH loads in flight; the bounds are warp-uniform
-#define HUB_DN_GROUP(ACC, KA, KB)                                                          \
+#define HUB_DN_GROUP(OP, KA, KB)                                                           \
   do {                                                                                     \
     int32_t k = (KA);                                                                      \
     for (; k + HUB_DN_BATCH <= (KB); k += HUB_DN_BATCH) {                                  \
-      float4 v[HUB_DN_BATCH];                                                              \
-      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q)                             \
-        v[q] = *reinterpret_cast<const float4 *>(xu + colat<Col>(F.col_dn, k + q) * F.ld); \
-      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q)                             \
-        acc2_add(ACC, pk2(v[q].x, v[q].z), pk2(v[q].y, v[q].w));                           \
+      f2x vh[HUB_DN_BATCH], vl[HUB_DN_BATCH];                                              \
+      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q) {                           \
+        const uint64_t o = (uint64_t)colat<Col>(F.col_dn, k + q) * row_bytes;              \
+        vh[q] = *reinterpret_cast<const f2x *>(xh + o);                                    \
+        vl[q] = *reinterpret_cast<const f2x *>(xl + o);                                    \
+      }                                                                                    \
+      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q) OP(acc, vh[q], vl[q]);      \
     }                                                                                      \
     for (; k < (KB); ++k) {                                                                \
-      const float4 v = *reinterpret_cast<const float4 *>(xu + colat<Col>(F.col_dn, k) * F.ld); \
-      acc2_add(ACC, pk2(v.x, v.z), pk2(v.y, v.w));                                         \
+      const uint64_t o = (uint64_t)colat<Col>(F.col_dn, k) * row_bytes;                    \
+      OP(acc, *reinterpret_cast<const f2x *>(xh + o), *reinterpret_cast<const f2x *>(xl + o)); \
     }                                                                                      \
   } while (0)
-    HUB_DN_GROUP(pp, k0, ks);
-    HUB_DN_GROUP(mm, ks, k1);
+    HUB_DN_GROUP(acc2_add, k0, ks);
+    HUB_DN_GROUP(acc2_sub, ks, k1);
 #undef HUB_DN_GROUP
-    const float4 zz = *reinterpret_cast<const float4 *>(z + d * F.ld + u);
-    const float2 mv0 = acc_value(acc2_lane(mm, 0)), mv1 = acc_value(acc2_lane(mm, 1));
-    float2 s0 = df_add(acc_value(acc2_lane(pp, 0)), make_float2(-mv0.x, -mv0.y));
-    float2 s1 = df_add(acc_value(acc2_lane(pp, 1)), make_float2(-mv1.x, -mv1.y));
-    if (!F.t_is_one) {
-      s0 = df_mul(s0, F.t);
-      s1 = df_mul(s1, F.t);
-    }
-    const float2 y0 = df_add(make_float2(zz.x, zz.y), s0);
-    const float2 y1 = df_add(make_float2(zz.z, zz.w), s1);
+    f2x Sh, Sl, yh, yl;
+    acc2_norm(acc, Sh, Sl);
+    if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+    const float *zr = z + d * 2 * ld;
+    df2_add(ld2(zr + u), ld2(zr + ld + u), Sh, Sl, yh, yl);
+    float *wr = w + d * 2 * ld;
     if (kMode == 0) {
-      *reinterpret_cast<float4 *>(w + d * F.ld + u) = make_float4(y0.x, y0.y, y1.x, y1.y);
+      st2(wr + u, yh);
+      st2(wr + ld + u, yl);
     } else {
-      const float4 rc = *reinterpret_cast<const float4 *>(L.r_cur + d * F.ld + u);
-      const float4 rp = *reinterpret_cast<const float4 *>(L.r_prev + d * F.ld + u);
-      const float2 a0 = df_mul(y0, ib), a1 = df_mul(y1, ib);
-      const float2 w0 = df_add(a0, df_mul(cprev, make_float2(-rp.x, -rp.y)));
-      float2 w1 = df_add(a1, df_mul(cprev, make_float2(-rp.z, -rp.w)));
-      if (u + 1 >= F.n_up) w1 = make_float2(0.f, 0.f);      // keep the padding column zero
-      *reinterpret_cast<float4 *>(w + d * F.ld + u) = make_float4(w0.x, w0.y, w1.x, w1.y);
-      // <q_j, w> = <r_j, w> / beta_cur, accumulated in double-float, reduced in FP64
-      const float2 q0 = df_mul(make_float2(rc.x, rc.y), ib), q1 = df_mul(make_float2(rc.z, rc.w), ib);
-      acc_add(dacc, df_mul(q0, w0));
-      acc_add(dacc, df_mul(q1, w1));
+      const float *rc = L.r_cur + d * 2 * ld, *rp = L.r_prev + d * 2 * ld;
+      f2x ah, al, bh, bl, wh, wl, qh, ql;
+      df2_mul(yh, yl, ibh, ibl, ah, al);
+      df2_mul(cph, cpl, ld2(rp + u), ld2(rp + ld + u), bh, bl);
+      df2_sub(ah, al, bh, bl, wh, wl);
+      if (u + 1 >= F.n_up) {                             // keep the padding column zero
+        wh &= 0xffffffffull;
+        wl &= 0xffffffffull;
+      }
+      st2(wr + u, wh);
+      st2(wr + ld + u, wl);
+      // <r_j, w>, accumulated in double-float, reduced in FP64 and scaled by 1/beta_cur
+      df2_mul(ld2(rc + u), ld2(rc + ld + u), wh, wl, qh, ql);
+      acc2_add(dacc, qh, ql);
     }
   }
   if (kMode == 1) {
-    double dot = df_to_f64(acc_value(dacc), 0);
+    f2x h, l;
+    acc2_norm(dacc, h, l);
+    double dot = df2_lanes_to_f64(h, l);
     for (int o = 16; o > 0; o >>= 1) dot += __shfl_xor_sync(0xffffffffu, dot, o);
     __shared__ double ws[kDnThreads / 32];
     if (lane == 0) ws[warp] = dot;
@@ -499,13 +591,14 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     if (threadIdx.x == 0) {
       double s = 0.0;
       for (int k = 0; k < kDnThreads / 32; ++k) s += ws[k];
-      L.partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s;
+      L.partials[(int64_t)blockIdx.y * gridDim.x + blockIdx.x] = s * L.inv_beta[0];
     }
   }
 }
 
 // ---------------------------------------------------------------------------------------
-// Double-float Lanczos vector kernels (padded layout; padding columns stay zero).
+// Double-float Lanczos vector kernels (planar rows; padding columns stay zero).  Each
+// thread step takes four columns of one row: a 16-byte load per plane, two packed pairs.
 // ---------------------------------------------------------------------------------------
 __device__ __forceinline__ void block_sum_to(double v, double *partials) {
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
@@ -520,41 +613,97 @@ __device__ __forceinline__ void block_sum_to(double v, double *partials) {
   }
 }
 
+// Column quads of a planar vector: quad k of n_rows * (ld / 4) starts at float offset
+// row * 2 ld + 4 q (hi) and + ld (lo).  The host keeps n_rows * ld / 4 below 2^32.
+struct Quads {
+  uint32_t per_row, n;
+  int64_t ld;
+  __device__ __forceinline__ int64_t at(uint32_t k) const {
+    const uint32_t d = k / per_row, q = k - d * per_row;
+    return (int64_t)d * 2 * ld + 4 * (int64_t)q;
+  }
+};
+__device__ __forceinline__ void ld4(const float *p, f2x &a, f2x &b) {
+  const float4 v = *reinterpret_cast<const float4 *>(p);
+  a = pk2(v.x, v.y);
+  b = pk2(v.z, v.w);
+}
+__device__ __forceinline__ void st4(float *p, f2x a, f2x b) {
+  const float2 u = upk2(a), v = upk2(b);
+  *reinterpret_cast<float4 *>(p) = make_float4(u.x, u.y, v.x, v.y);
+}
+
 // r_next = w + coef[2] r_cur = w - (alpha / beta_cur) r_cur  (in place over w);
 // partials <- |r_next|^2
-__global__ void k_df_update(int64_t n, float2 *__restrict__ w, const float2 *__restrict__ r_cur,
+__global__ void k_df_update(Quads Q, float *__restrict__ w, const float *__restrict__ r_cur,
                             const float2 *__restrict__ coef, double *__restrict__ partials) {
   const float2 c = coef[2];
-  DfAcc acc{0.f, 0.f};
-  // two elements per thread and step (16-byte accesses; n is even: rows have even length)
-  float4 *__restrict__ w4 = reinterpret_cast<float4 *>(w);
-  const float4 *__restrict__ r4 = reinterpret_cast<const float4 *>(r_cur);
-  const int64_t n2 = n >> 1;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n2; k += (int64_t)gridDim.x * blockDim.x) {
-    const float4 rv = r4[k], wv = w4[k];
-    const float2 v0 = df_fma(c, make_float2(rv.x, rv.y), make_float2(wv.x, wv.y));
-    const float2 v1 = df_fma(c, make_float2(rv.z, rv.w), make_float2(wv.z, wv.w));
-    w4[k] = make_float4(v0.x, v0.y, v1.x, v1.y);
-    acc_add(acc, df_mul(v0, v0));
-    acc_add(acc, df_mul(v1, v1));
+  const f2x ch = bcast2(c.x), cl = bcast2(c.y);
+  DfAcc2 acc{0ull, 0ull};
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < Q.n; k += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t o = Q.at((uint32_t)k);
+    f2x wh[2], wl[2], rh[2], rl[2];
+    ld4(w + o, wh[0], wh[1]);
+    ld4(w + o + Q.ld, wl[0], wl[1]);
+    ld4(r_cur + o, rh[0], rh[1]);
+    ld4(r_cur + o + Q.ld, rl[0], rl[1]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      f2x ph, pl;
+      df2_mul(ch, cl, rh[i], rl[i], ph, pl);
+      df2_add(ph, pl, wh[i], wl[i], wh[i], wl[i]);
+      df2_mul(wh[i], wl[i], wh[i], wl[i], ph, pl);
+      acc2_add(acc, ph, pl);
+    }
+    st4(w + o, wh[0], wh[1]);
+    st4(w + o + Q.ld, wl[0], wl[1]);
   }
-  block_sum_to(df_to_f64(acc_value(acc), 0), partials);
+  f2x h, l;
+  acc2_norm(acc, h, l);
+  block_sum_to(df2_lanes_to_f64(h, l), partials);
 }
 
 // partials <- |v|^2
-__global__ void k_df_norm2(int64_t n, const float2 *__restrict__ v, double *__restrict__ partials) {
-  DfAcc acc{0.f, 0.f};
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    acc_add(acc, df_mul(v[k], v[k]));
-  block_sum_to(df_to_f64(acc_value(acc), 0), partials);
+__global__ void k_df_norm2(Quads Q, const float *__restrict__ v, double *__restrict__ partials) {
+  DfAcc2 acc{0ull, 0ull};
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < Q.n; k += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t o = Q.at((uint32_t)k);
+    f2x vh[2], vl[2];
+    ld4(v + o, vh[0], vh[1]);
+    ld4(v + o + Q.ld, vl[0], vl[1]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      f2x ph, pl;
+      df2_mul(vh[i], vl[i], vh[i], vl[i], ph, pl);
+      acc2_add(acc, ph, pl);
+    }
+  }
+  f2x h, l;
+  acc2_norm(acc, h, l);
+  block_sum_to(df2_lanes_to_f64(h, l), partials);
 }
 
 // psi += c r, c a double-float coefficient in coef[idx]
-__global__ void k_df_axpy(int64_t n, const float2 *__restrict__ coef, int idx, const float2 *__restrict__ r,
-                          float2 *__restrict__ psi) {
+__global__ void k_df_axpy(Quads Q, const float2 *__restrict__ coef, int idx, const float *__restrict__ r,
+                          float *__restrict__ psi) {
   const float2 a = coef[idx];
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
-    psi[k] = df_fma(a, r[k], psi[k]);
+  const f2x ah = bcast2(a.x), al = bcast2(a.y);
+  for (uint64_t k = blockIdx.x * (uint64_t)blockDim.x + threadIdx.x; k < Q.n; k += (uint64_t)gridDim.x * blockDim.x) {
+    const int64_t o = Q.at((uint32_t)k);
+    f2x ph[2], pl[2], rh[2], rl[2];
+    ld4(psi + o, ph[0], ph[1]);
+    ld4(psi + o + Q.ld, pl[0], pl[1]);
+    ld4(r + o, rh[0], rh[1]);
+    ld4(r + o + Q.ld, rl[0], rl[1]);
+#pragma unroll
+    for (int i = 0; i < 2; ++i) {
+      f2x mh, ml;
+      df2_mul(ah, al, rh[i], rl[i], mh, ml);
+      df2_add(mh, ml, ph[i], pl[i], ph[i], pl[i]);
+    }
+    st4(psi + o, ph[0], ph[1]);
+    st4(psi + o + Q.ld, pl[0], pl[1]);
+  }
 }
 
 // coef[3] = c / scal[1]  (psi coefficient v_j / beta_cur), one thread
@@ -562,34 +711,17 @@ __global__ void k_psi_coef(const double *__restrict__ scal, double c, float2 *__
   coef[3] = f64_to_df(c / scal[1], 0);
 }
 
-// out (FP64, unpadded) = v / |v|  with |v| = scal[idx]
-__global__ void k_df_out_normalised(int64_t n_rows, int64_t n_up, int64_t ld, const float2 *__restrict__ v,
-                                    const double *__restrict__ scal, int idx, const int32_t *__restrict__ slot_row,
+// out (FP64, rank order) = v / |v|  with |v| = scal[idx]; one row per block and step
+__global__ void k_df_out_normalised(int64_t n_rows, int64_t n_up, int64_t ld, const float *__restrict__ v,
+                                    const double *__restrict__ scal, int idx, const int32_t *__restrict__ slot_of,
                                     double *__restrict__ out) {
   const float2 inv = f64_to_df(1.0 / scal[idx], 0);
-  const int64_t total = n_rows * n_up;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < total; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t d = k / n_up, slot = k - d * n_up;
-    out[d * n_up + slot_row[slot]] = df_to_f64(df_mul(v[d * ld + slot], inv), 0);
-  }
-}
-
-// y[d][u] (FP64, rank order) = 2^shift * v[d][slot_of[u]] (double-float, slot order), one
-// row per block so that the gathers of a row are served from L1.
-__global__ void k_unpermute(int64_t n_rows, int64_t n_up, int64_t ld, const float2 *__restrict__ v,
-                            const int32_t *__restrict__ slot_of, const int *__restrict__ emax, int nblk,
-                            double *__restrict__ y) {
-  __shared__ int s_shift;
-  if (threadIdx.x == 0) {
-    int m = 0;
-    for (int k = 0; k < nblk; ++k) m = max(m, emax[k]);
-    s_shift = m == 0 ? 0 : m - 1023;
-  }
-  __syncthreads();
-  const int shift = s_shift;
   for (int64_t d = blockIdx.x; d < n_rows; d += gridDim.x) {
-    const float2 *__restrict__ row = v + d * ld;
-    for (int64_t u = threadIdx.x; u < n_up; u += blockDim.x) y[d * n_up + u] = df_to_f64(row[slot_of[u]], shift);
+    const float *__restrict__ row = v + d * 2 * ld;
+    for (int64_t u = threadIdx.x; u < n_up; u += blockDim.x) {
+      const int32_t s = slot_of[u];
+      out[d * n_up + u] = df_to_f64(df_mul(make_float2(row[s], row[ld + s]), inv), 0);
+    }
   }
 }
 
@@ -616,9 +748,9 @@ struct FastState {
   float2 *eps_up_slot = nullptr;
   void *col[2] = {nullptr, nullptr};
   float2 *eps_df[2] = {nullptr, nullptr};
-  float2 *xdf = nullptr, *zdf = nullptr;     // hub_apply scratch
-  float2 *lz[3] = {nullptr, nullptr, nullptr};
-  float2 *psi = nullptr;
+  float *xdf = nullptr, *zdf = nullptr;      // hub_apply scratch (planar double-float)
+  float *lz[3] = {nullptr, nullptr, nullptr};
+  float *psi = nullptr;
   int *d_emax = nullptr;
   int *d_err = nullptr;
   int64_t ld = 0;
@@ -659,7 +791,10 @@ bool fast_eligible(const hub_ctx *h) {
   if (!h->have_hop || !h->have_U || !h->uniform_U) return false;
   for (double tb : h->t)
     if (tb != h->t[0]) return false;
-  return h->count[0] > 0 && h->count[1] > 0;
+  if (h->count[0] <= 0 || h->count[1] <= 0) return false;
+  // element quads of a vector are indexed with 32-bit integers
+  const int64_t ld = (h->count[0] + 3) & ~(int64_t)3;
+  return h->count[1] * (ld / 4) < ((int64_t)1 << 32);
 }
 
 // Build the sign-split CSR and double-float tables (called after hub_hopping).
@@ -669,7 +804,7 @@ int fast_build(hub_ctx *h) {
   if (!f) return fail(HUB_ERR_OOM, "fast path: host allocation failed");
   h->fast = f;
   f->col16 = h->count[0] <= 65536 && h->count[1] <= 65536;
-  f->ld = h->count[0] + (h->count[0] & 1);
+  f->ld = (h->count[0] + 3) & ~(int64_t)3;
   const size_t csz = f->col16 ? sizeof(uint16_t) : sizeof(uint32_t);
   for (int s = 0; s < 2; ++s) {
     if (s == 1 && h->shared) break;
@@ -729,87 +864,80 @@ int fast_build(hub_ctx *h) {
                            f->eps_up_slot);
     HUB_LAUNCH_CHECK();
     // per slice and group: schedule the lanes' entries into steps in which at most two lanes
-    // of a half-warp hit the same bank pair (slot mod 16), i.e. at most two shared-memory
-    // wavefronts per half-warp load.  Greedy: lanes with the most remaining entries are
-    // served first; each takes the entry of the most loaded bank that still has room.
-    // (A conflict-free schedule needs about 1.7x more steps on the 4x4 lattice because the
-    // bank loads are uneven; two per bank costs about 4 % more steps for 1.5x fewer
-    // wavefronts than the unscheduled order.)
+    // of the warp hit the same bank (slot mod 32), i.e. at most two shared-memory wavefronts
+    // per 32-bit load.  Greedy: lanes with the most remaining entries are served first; each
+    // takes the entry of the most loaded bank that still has room.  (A conflict-free
+    // schedule needs about 1.7x more steps on the 4x4 lattice because the bank loads are
+    // uneven; two per bank costs a few per cent more steps than the longest row.)
     constexpr int kBankCap = 2;
     // idle steps: the zero entry after the staged row when rows are staged, else a sentinel
-    const bool staged = f->ld + 2 <= kUpStride;
+    const bool staged = f->ld + 2 <= kUpPlane;
     const uint32_t idle = staged ? (uint32_t)f->ld : (f->col16 ? 0xffffu : 0xffffffffu);
     f->idle_word = f->col16 ? (idle | (idle << 16)) : idle;
     const int pack = f->col16 ? 2 : 1;
     std::vector<uint16_t> st[2] = {std::vector<uint16_t>(nsl), std::vector<uint16_t>(nsl)};
     std::vector<int32_t> off[2] = {std::vector<int32_t>(nsl + 1, 0), std::vector<int32_t>(nsl + 1, 0)};
     std::vector<uint32_t> words[2];
-    std::vector<uint32_t> steps;                   // [S][32] entries of one slice
+    std::vector<std::vector<uint32_t>> warp_steps;  // [S][32] entries of one slice
     for (int64_t sl = 0; sl < nsl; ++sl) {
       for (int grp = 0; grp < 2; ++grp) {
-        std::vector<std::vector<uint32_t>> half_steps[2];
-        for (int hw = 0; hw < 2; ++hw) {
-          std::vector<uint32_t> rem[16];
-          int bankload[16] = {0};
-          for (int l = 0; l < 16; ++l) {
-            const int64_t slot = sl * 32 + hw * 16 + l;
-            if (slot >= n) continue;
-            const int32_t r = slot_row[slot];
-            const int32_t a = grp == 0 ? rp[r] : spv[r], b = grp == 0 ? spv[r] : rp[r + 1];
-            for (int32_t k = a; k < b; ++k) {
-              rem[l].push_back((uint32_t)slot_of[col[k]]);
-              ++bankload[slot_of[col[k]] & 15];
-            }
-          }
-          for (;;) {
-            int lanes[16], nl = 0;
-            for (int l = 0; l < 16; ++l)
-              if (!rem[l].empty()) lanes[nl++] = l;
-            if (!nl) break;
-            std::stable_sort(lanes, lanes + nl, [&](int x, int y) { return rem[x].size() > rem[y].size(); });
-            std::vector<uint32_t> step(16, idle);
-            int used[16] = {0};
-            for (int q = 0; q < nl; ++q) {
-              const int l = lanes[q];
-              int best = -1;
-              for (int e = 0; e < (int)rem[l].size(); ++e) {
-                const int bk = rem[l][e] & 15;
-                if (used[bk] >= kBankCap) continue;
-                if (best < 0) {
-                  best = e;
-                  continue;
-                }
-                const int bb = rem[l][best] & 15;
-                if (bankload[bk] > bankload[bb] || (bankload[bk] == bankload[bb] && used[bk] < used[bb])) best = e;
-              }
-              if (best < 0) continue;
-              const uint32_t c = rem[l][best];
-              step[l] = c;
-              ++used[c & 15];
-              --bankload[c & 15];
-              rem[l].erase(rem[l].begin() + best);
-            }
-            half_steps[hw].push_back(step);
+        std::vector<uint32_t> rem[32];
+        int bankload[32] = {0};
+        for (int l = 0; l < 32; ++l) {
+          const int64_t slot = sl * 32 + l;
+          if (slot >= n) continue;
+          const int32_t r = slot_row[slot];
+          const int32_t a = grp == 0 ? rp[r] : spv[r], b = grp == 0 ? spv[r] : rp[r + 1];
+          for (int32_t k = a; k < b; ++k) {
+            rem[l].push_back((uint32_t)slot_of[col[k]]);
+            ++bankload[slot_of[col[k]] & 31];
           }
         }
-        const int S = (int)std::max(half_steps[0].size(), half_steps[1].size());
+        warp_steps.clear();
+        for (;;) {
+          int lanes[32], nl = 0;
+          for (int l = 0; l < 32; ++l)
+            if (!rem[l].empty()) lanes[nl++] = l;
+          if (!nl) break;
+          std::stable_sort(lanes, lanes + nl, [&](int a, int b) { return rem[a].size() > rem[b].size(); });
+          std::vector<uint32_t> step(32, idle);
+          int used[32] = {0};
+          for (int q = 0; q < nl; ++q) {
+            const int l = lanes[q];
+            int best = -1;
+            for (int e = 0; e < (int)rem[l].size(); ++e) {
+              const int bk = rem[l][e] & 31;
+              if (used[bk] >= kBankCap) continue;
+              if (best < 0) {
+                best = e;
+                continue;
+              }
+              const int bb = rem[l][best] & 31;
+              if (bankload[bk] > bankload[bb] || (bankload[bk] == bankload[bb] && used[bk] < used[bb])) best = e;
+            }
+            if (best < 0) continue;
+            const uint32_t c = rem[l][best];
+            step[l] = c;
+            ++used[c & 31];
+            --bankload[c & 31];
+            rem[l].erase(rem[l].begin() + best);
+          }
+          warp_steps.push_back(step);
+        }
+        const int S = (int)warp_steps.size();
         if (S > 65535) return fail(HUB_ERR_ARG, "fast path: hopping row schedule too long");
         st[grp][sl] = (uint16_t)S;
-        steps.assign((size_t)S * 32, idle);
-        for (int hw = 0; hw < 2; ++hw)
-          for (size_t j = 0; j < half_steps[hw].size(); ++j)
-            for (int l = 0; l < 16; ++l) steps[j * 32 + hw * 16 + l] = half_steps[hw][j][l];
         const int nw = (S + pack - 1) / pack;
         off[grp][sl + 1] = off[grp][sl] + 32 * nw;
         for (int j = 0; j < nw; ++j)
           for (int l = 0; l < 32; ++l) {
             uint32_t wd;
             if (pack == 2) {
-              const uint32_t lo = steps[(size_t)(2 * j) * 32 + l];
-              const uint32_t hi = 2 * j + 1 < S ? steps[(size_t)(2 * j + 1) * 32 + l] : idle;
+              const uint32_t lo = warp_steps[2 * j][l];
+              const uint32_t hi = 2 * j + 1 < S ? warp_steps[2 * j + 1][l] : idle;
               wd = lo | (hi << 16);
             } else {
-              wd = steps[(size_t)j * 32 + l];
+              wd = warp_steps[j][l];
             }
             words[grp].push_back(wd);
           }
@@ -878,18 +1006,25 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   return v;
 }
 
-static size_t up_smem(const FastState *f) { return sizeof(float2) * ((size_t)kUpStride + (size_t)f->ld + 2); }
-constexpr size_t kMaxStage = 224 * 1024;
-static_assert(sizeof(float2) * 2 * kUpStride <= kMaxStage, "two staged rows must fit");
+static Quads quads(const hub_ctx *h, const FastState *f) {
+  Quads q;
+  q.per_row = (uint32_t)(f->ld / 4);
+  q.n = (uint32_t)(h->count[1] * (f->ld / 4));
+  q.ld = f->ld;
+  return q;
+}
 
-static bool up_staged(const FastState *f) { return f->ld + 2 <= kUpStride; }
+static size_t up_smem(const FastState *f) { return sizeof(float) * (3 * (size_t)kUpPlane + (size_t)f->ld + 2); }
+constexpr size_t kMaxStage = 224 * 1024;
+static_assert(sizeof(float) * 4 * kUpPlane <= kMaxStage, "four staged planes must fit");
+
+static bool up_staged(const FastState *f) { return f->ld + 2 <= kUpPlane; }
 
 template <typename Col>
-static int launch_up_t(const FastView &v, const FastState *f, bool eps, const float2 *x, float2 *z, cudaStream_t s) {
-  const bool stage = up_staged(f);
-  if (!stage) {
+static int launch_up_t(const FastView &v, const FastState *f, bool eps, const float *x, float *z, cudaStream_t s) {
+  if (!up_staged(f)) {
     const int64_t n_pairs = (v.n_dn + 1) / 2;
-    const unsigned chunks = (unsigned)((v.n_up + kL2Threads - 1) / kL2Threads);
+    const unsigned chunks = (unsigned)((v.ld + kL2Threads - 1) / kL2Threads);
     for (int64_t p0 = 0; p0 < n_pairs; p0 += 65535) {
       const dim3 g(chunks, (unsigned)std::min<int64_t>(65535, n_pairs - p0));
       if (eps) k_up_l2<Col, true><<<g, kL2Threads, 0, s>>>(v, x, z, p0);
@@ -899,20 +1034,15 @@ static int launch_up_t(const FastView &v, const FastState *f, bool eps, const fl
     return HUB_OK;
   }
   const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
-  int64_t grid = std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms() * (stage ? 1 : 2) * (1024 / threads));
-  const size_t smem = stage ? up_smem(f) : 0;
-#define HUB_UP(ST, EP)                                                                                   \
-  do {                                                                                                   \
-    if (ST) HUB_CUDA(cudaFuncSetAttribute(k_up<Col, ST, EP>, cudaFuncAttributeMaxDynamicSharedMemorySize, \
-                                          (int)kMaxStage));                                              \
-    k_up<Col, ST, EP><<<(int)grid, threads, smem, s>>>(v, x, z);                                         \
-  } while (0)
-  if (stage) {
-    if (eps) HUB_UP(true, true); else HUB_UP(true, false);
+  const int64_t grid = std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms());
+  const size_t smem = up_smem(f);
+  if (eps) {
+    HUB_CUDA(cudaFuncSetAttribute(k_up<Col, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage));
+    k_up<Col, true><<<(int)grid, threads, smem, s>>>(v, x, z);
   } else {
-    if (eps) HUB_UP(false, true); else HUB_UP(false, false);
+    HUB_CUDA(cudaFuncSetAttribute(k_up<Col, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage));
+    k_up<Col, false><<<(int)grid, threads, smem, s>>>(v, x, z);
   }
-#undef HUB_UP
   HUB_LAUNCH_CHECK();
   return HUB_OK;
 }
@@ -922,17 +1052,16 @@ static dim3 dn_grid(const FastView &v) {
 }
 
 template <typename Col, int kMode>
-static int launch_dn_t(const FastView &v, const float2 *x, const float2 *z, double *y, float2 *w,
-                       const int *shift_src, int nblk, LzArgs L, cudaStream_t s) {
+static int launch_dn_t(const FastView &v, const float *x, const float *z, float *w, LzArgs L, cudaStream_t s) {
   const dim3 g = dn_grid(v);
   if (g.y > 65535) return fail(HUB_ERR_ARG, "fast apply: too many column strips");
-  k_dn<Col, kMode><<<g, kDnThreads, 0, s>>>(v, x, z, y, w, shift_src, nblk, L);
+  k_dn<Col, kMode><<<g, kDnThreads, 0, s>>>(v, x, z, w, L);
   HUB_LAUNCH_CHECK();
   return HUB_OK;
 }
 
-// z <- pass 1 (x double-float, padded)
-static int run_up(hub_ctx *h, FastState *f, const float2 *x, float2 *z, cudaStream_t s) {
+// z <- pass 1 (x planar double-float)
+static int run_up(hub_ctx *h, FastState *f, const float *x, float *z, cudaStream_t s) {
   const FastView v = fast_view(h, f);
   count_launch(h);
   int rc = prof_mark(h, HUB_PROF_UP, true, s);
@@ -943,32 +1072,32 @@ static int run_up(hub_ctx *h, FastState *f, const float2 *x, float2 *z, cudaStre
   return prof_mark(h, HUB_PROF_UP, false, s);
 }
 
-static int run_dn(hub_ctx *h, FastState *f, int mode, const float2 *x, const float2 *z, double *y, float2 *w,
-                  const int *shift_src, int nblk, LzArgs L, cudaStream_t s) {
+static int run_dn(hub_ctx *h, FastState *f, int mode, const float *x, const float *z, float *w, LzArgs L,
+                  cudaStream_t s) {
   const FastView v = fast_view(h, f);
   count_launch(h);
   int rc = prof_mark(h, HUB_PROF_DN, true, s);
   if (rc) return rc;
   if (mode == 0)
-    rc = f->col16 ? launch_dn_t<uint16_t, 0>(v, x, z, y, w, shift_src, nblk, L, s)
-                  : launch_dn_t<uint32_t, 0>(v, x, z, y, w, shift_src, nblk, L, s);
+    rc = f->col16 ? launch_dn_t<uint16_t, 0>(v, x, z, w, L, s) : launch_dn_t<uint32_t, 0>(v, x, z, w, L, s);
   else
-    rc = f->col16 ? launch_dn_t<uint16_t, 1>(v, x, z, y, w, shift_src, nblk, L, s)
-                  : launch_dn_t<uint32_t, 1>(v, x, z, y, w, shift_src, nblk, L, s);
+    rc = f->col16 ? launch_dn_t<uint16_t, 1>(v, x, z, w, L, s) : launch_dn_t<uint32_t, 1>(v, x, z, w, L, s);
   if (rc) return rc;
   return prof_mark(h, HUB_PROF_DN, false, s);
 }
 
-static int ensure_vec(float2 **p, int64_t n, const char *what) {
+static int ensure_vec(float **p, int64_t n, const char *what) {
   if (*p) return HUB_OK;
-  return dev_alloc((void **)p, sizeof(float2) * n, what) ? HUB_OK : HUB_ERR_OOM;
+  return dev_alloc((void **)p, sizeof(float) * n, what) ? HUB_OK : HUB_ERR_OOM;
 }
+
+static int row_grid(const hub_ctx *h) { return (int)std::min<int64_t>(h->count[1], (int64_t)num_sms() * 8); }
 
 // hub_apply on the fast path: FP64 in, FP64 out.
 int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   FastState *f = fast_of(h);
   if (!f || !f->built) return fail(HUB_ERR_STATE, "fast apply: not built");
-  const int64_t Dp = h->count[1] * f->ld, D = h->count[0] * h->count[1];
+  const int64_t Dp = h->count[1] * 2 * f->ld, D = h->count[0] * h->count[1];
   int rc;
   if ((rc = ensure_vec(&f->xdf, Dp, "apply scratch x")) || (rc = ensure_vec(&f->zdf, Dp, "apply scratch z")))
     return rc;
@@ -976,13 +1105,12 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
   count_launch(h, 2);
   k_max_exp<<<G, 256, 0, s>>>(D, x, f->d_emax);
-  k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->slot_row, f->xdf);
+  k_f64_to_df<<<row_grid(h), 256, 0, s>>>(h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->slot_row, f->xdf);
   HUB_LAUNCH_CHECK();
   if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
-  if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, nullptr, f->zdf, nullptr, 0, LzArgs{}, s))) return rc;
+  if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s))) return rc;
   count_launch(h);
-  k_unpermute<<<(int)std::min<int64_t>(h->count[1], (int64_t)num_sms() * 8), 512, 0, s>>>(
-      h->count[1], h->count[0], f->ld, f->zdf, f->slot_of, f->d_emax, G, y);
+  k_unpermute<<<row_grid(h), 512, 0, s>>>(h->count[1], h->count[0], f->ld, f->zdf, f->slot_of, f->d_emax, G, y);
   HUB_LAUNCH_CHECK();
   return HUB_OK;
 }
@@ -1002,18 +1130,20 @@ int fast_check_error(hub_ctx *h) {
 // ---------------------------------------------------------------------------------------
 // Double-float Lanczos (same recurrence as the FP64 driver; vectors kept unnormalised,
 // r_j = beta_{j-1} q_j, so the normalisation is folded into the apply's epilogue).
-// scal: [0] alpha_j, [1] beta_cur = |r_j|, [2] beta_prev = |r_{j-1}| (0 at the start).
+// scal: [0] alpha_j, [1] beta_cur = |r_j|, [2] beta_prev = |r_{j-1}| (0 at the start),
+// [3] beta_j, [5] |psi|, [6] 1/beta_cur.
 // ---------------------------------------------------------------------------------------
 int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out,
                  int *iters, cudaStream_t s) {
   FastState *f = fast_of(h);
   if (!f || !f->built) return fail(HUB_ERR_STATE, "fast Lanczos: not built");
-  const int64_t Dp = h->count[1] * f->ld;
+  const int64_t Dp = h->count[1] * 2 * f->ld;
   int rc;
   for (int k = 0; k < 3; ++k)
     if ((rc = ensure_vec(&f->lz[k], Dp, "Lanczos vector"))) return rc;
   if ((rc = ensure_vec(&f->zdf, Dp, "apply scratch z"))) return rc;
   const int G = grid_vec();
+  const Quads Q = quads(h, f);
   const FastView v0 = fast_view(h, f);
   const dim3 gd = dn_grid(v0);
   const int64_t n_dn_blocks = (int64_t)gd.x * gd.y;
@@ -1026,11 +1156,10 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   float2 *coef = f->coef;
 
   // r_1 = x0 as double-float (no scaling), scal[1] = beta_0 = |x0|, scal[2] = 0
-  auto start = [&](float2 *r) -> int {
-    HUB_CUDA(cudaMemsetAsync(f->d_emax, 0, sizeof(int) * G, s));
+  auto start = [&](float *r) -> int {
     count_launch(h, 3);
-    k_f64_to_df<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, x0, f->d_emax, G, f->slot_row, r);
-    k_df_norm2<<<G, 256, 0, s>>>(Dp, r, P);
+    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(h->count[1], h->count[0], f->ld, x0, nullptr, 0, f->slot_row, r);
+    k_df_norm2<<<G, 256, 0, s>>>(Q, r, P);
     HUB_LAUNCH_CHECK();
     int rc2 = reduce_partials(P, G, scal + 1, 1, s);
     if (rc2) return rc2;
@@ -1039,28 +1168,28 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   };
   // one step of the recurrence: w = H q_j - beta_prev q_{j-1}, alpha partials, then (with
   // alpha in scal[0]) r_{j+1} = w - alpha q_j in place and |r_{j+1}|^2 partials
-  auto step_apply = [&](float2 *rp, float2 *rcur, float2 *w) -> int {
+  auto step_apply = [&](float *rp, float *rcur, float *w) -> int {
     count_launch(h);
     k_coeffs<<<1, 1, 0, s>>>(scal, coef);
     HUB_LAUNCH_CHECK();
     int rc2 = prof_mark(h, HUB_PROF_APPLY, true, s);
     if (rc2) return rc2;
     if ((rc2 = run_up(h, f, rcur, f->zdf, s))) return rc2;
-    LzArgs L{rcur, rp, coef, P};
-    if ((rc2 = run_dn(h, f, 1, rcur, f->zdf, nullptr, w, nullptr, 0, L, s))) return rc2;
+    LzArgs L{rcur, rp, coef, scal + 6, P};
+    if ((rc2 = run_dn(h, f, 1, rcur, f->zdf, w, L, s))) return rc2;
     return prof_mark(h, HUB_PROF_APPLY, false, s);
   };
-  auto step_update = [&](float2 *rcur, float2 *w) -> int {
+  auto step_update = [&](float *rcur, float *w) -> int {
     count_launch(h, 2);
     k_coeffs<<<1, 1, 0, s>>>(scal, coef);
-    k_df_update<<<G, 256, 0, s>>>(Dp, w, rcur, coef, P);
+    k_df_update<<<G, 256, 0, s>>>(Q, w, rcur, coef, P);
     HUB_LAUNCH_CHECK();
     return HUB_OK;
   };
 
-  float2 *rp = f->lz[0], *rcur = f->lz[1], *w = f->lz[2];
+  float *rp = f->lz[0], *rcur = f->lz[1], *w = f->lz[2];
   if ((rc = start(rcur))) return rc;
-  HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float2) * Dp, s));
+  HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float) * Dp, s));
   HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   HUB_CUDA(cudaStreamSynchronize(s));
   if (!(h->h_scal[1] > 0.0) || !std::isfinite(h->h_scal[1]))
@@ -1099,7 +1228,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
     k_set_scal<<<1, 1, 0, s>>>(scal, 1, b, 2, b_cur, -1, 0.0);
     HUB_LAUNCH_CHECK();
     b_cur = b;
-    float2 *t0 = rp;
+    float *t0 = rp;
     rp = rcur;
     rcur = w;
     w = t0;
@@ -1118,8 +1247,8 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
     rcur = f->lz[1];
     w = f->lz[2];
     if ((rc = start(rcur))) return rc;
-    HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float2) * Dp, s));
-    HUB_CUDA(cudaMemsetAsync(f->psi, 0, sizeof(float2) * Dp, s));
+    HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float) * Dp, s));
+    HUB_CUDA(cudaMemsetAsync(f->psi, 0, sizeof(float) * Dp, s));
     double bc = b_cur;
     HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     HUB_CUDA(cudaStreamSynchronize(s));
@@ -1127,7 +1256,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
     for (int j = 0; j < k; ++j) {
       count_launch(h, 2);
       k_psi_coef<<<1, 1, 0, s>>>(scal, vv[j], coef);
-      k_df_axpy<<<G, 256, 0, s>>>(Dp, coef, 3, rcur, f->psi);
+      k_df_axpy<<<G, 256, 0, s>>>(Q, coef, 3, rcur, f->psi);
       HUB_LAUNCH_CHECK();
       if (j + 1 == k) break;
       if ((rc = step_apply(rp, rcur, w))) return rc;
@@ -1139,16 +1268,17 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
       k_set_scal<<<1, 1, 0, s>>>(scal, 1, h->beta[j], 2, bc, -1, 0.0);
       HUB_LAUNCH_CHECK();
       bc = h->beta[j];
-      float2 *t0 = rp;
+      float *t0 = rp;
       rp = rcur;
       rcur = w;
       w = t0;
     }
     count_launch(h, 3);
-    k_df_norm2<<<G, 256, 0, s>>>(Dp, f->psi, P);
+    k_df_norm2<<<G, 256, 0, s>>>(Q, f->psi, P);
     HUB_LAUNCH_CHECK();
     if ((rc = reduce_partials(P, G, scal + 5, 1, s))) return rc;
-    k_df_out_normalised<<<G, 256, 0, s>>>(h->count[1], h->count[0], f->ld, f->psi, scal, 5, f->slot_row, psi_out);
+    k_df_out_normalised<<<row_grid(h), 256, 0, s>>>(h->count[1], h->count[0], f->ld, f->psi, scal, 5, f->slot_of,
+                                                    psi_out);
     HUB_LAUNCH_CHECK();
     HUB_CUDA(cudaStreamSynchronize(s));
     if ((rc = fast_check_error(h))) return rc;
