@@ -456,7 +456,10 @@ __global__ void __launch_bounds__(kL2Threads) k_up_l2(const FastView F, const fl
 // columns u0 + 2l, u0 + 2l + 1 (one 64-bit load per plane and row), and sums both with one
 // packed FP32x2 TwoSum chain.
 // ---------------------------------------------------------------------------------------
-constexpr int kDnRows = 32, kDnCols = 64, kDnThreads = 256;
+#ifndef HUB_DN_LANE_COLS
+#define HUB_DN_LANE_COLS 4   // columns per lane in pass 2 (2: 64-bit loads, 4: 128-bit loads)
+#endif
+constexpr int kDnRows = 32, kDnLaneCols = HUB_DN_LANE_COLS, kDnCols = 32 * kDnLaneCols, kDnThreads = 256;
 #ifndef HUB_DN_BATCH
 #define HUB_DN_BATCH 2   // strip rows whose loads are issued together in pass 2
 #endif
@@ -497,6 +500,39 @@ __device__ __forceinline__ double df2_lanes_to_f64(f2x h, f2x l) {
   return df_to_f64(make_float2(hh.x, ll.x), 0) + df_to_f64(make_float2(hh.y, ll.y), 0);
 }
 
+// kLane packed pairs per lane: columns u .. u + 2 kLane - 1 (16-byte loads for even kLane)
+template <int kLane>
+struct Vec {
+  f2x v[kLane];
+};
+template <int kLane>
+__device__ __forceinline__ Vec<kLane> ldv(const float *p) {
+  Vec<kLane> r;
+  if (kLane % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < kLane / 2; ++i) {
+      const float4 q = reinterpret_cast<const float4 *>(p)[i];
+      r.v[2 * i] = pk2(q.x, q.y);
+      r.v[(2 * i + 1) % kLane] = pk2(q.z, q.w);
+    }
+  } else {
+    r.v[0] = *reinterpret_cast<const f2x *>(p);
+  }
+  return r;
+}
+template <int kLane>
+__device__ __forceinline__ void stv(float *p, const Vec<kLane> &a) {
+  if (kLane % 2 == 0) {
+#pragma unroll
+    for (int i = 0; i < kLane / 2; ++i) {
+      const float2 x = upk2(a.v[2 * i]), y = upk2(a.v[(2 * i + 1) % kLane]);
+      reinterpret_cast<float4 *>(p)[i] = make_float4(x.x, x.y, y.x, y.y);
+    }
+  } else {
+    *reinterpret_cast<f2x *>(p) = a.v[0];
+  }
+}
+
 // kMode 0: w (planar double-float, slot order; may alias z) = Z + t S_dn, for hub_apply
 //          (the FP64 output in rank order is written afterwards by k_unpermute).
 // kMode 1: w = (Z + t S_dn)/beta_cur - (beta_cur/beta_prev) r_prev, partials <- <q_j, w>
@@ -504,9 +540,10 @@ __device__ __forceinline__ double df2_lanes_to_f64(f2x h, f2x l) {
 template <typename Col, int kMode>
 __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float *__restrict__ x, const float *z,
                                                   float *w, LzArgs L) {
+  constexpr int kLane = kDnLaneCols / 2;               // packed pairs per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int64_t ld = F.ld;
-  const int64_t u = (int64_t)blockIdx.y * kDnCols + 2 * lane;
+  const int64_t u = (int64_t)blockIdx.y * kDnCols + kDnLaneCols * lane;
   const int64_t r0 = (int64_t)blockIdx.x * kDnRows;
   const uint32_t row_bytes = (uint32_t)(2 * ld * sizeof(float));
   f2x ibh = 0ull, ibl = 0ull, cph = 0ull, cpl = 0ull;
@@ -518,66 +555,87 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     cpl = bcast2(cp.y);
   }
   DfAcc2 dacc{0ull, 0ull};
-  const bool active = u < F.n_up;                      // u even, ld multiple of 4: u + 1 < ld
+  const bool active = u < F.n_up;                      // u + kDnLaneCols <= ld (see fast_build)
   const char *__restrict__ xh = reinterpret_cast<const char *>(x + u);
   const char *__restrict__ xl = reinterpret_cast<const char *>(x + ld + u);
   for (int rr = warp; rr < kDnRows; rr += kDnThreads / 32) {
     const int64_t d = r0 + rr;
     if (d >= F.n_dn) break;
     const int32_t k0 = F.rp_dn[d], ks = F.sp_dn[d], k1 = F.rp_dn[d + 1];
+    float *wr = w + d * 2 * ld;
     if (!active) {
       if (u < ld) {                                      // padding columns of w stay zero
-        st2(w + d * 2 * ld + u, 0ull);
-        st2(w + d * 2 * ld + ld + u, 0ull);
+        stv<kLane>(wr + u, Vec<kLane>{});
+        stv<kLane>(wr + ld + u, Vec<kLane>{});
       }
       continue;
     }
-    DfAcc2 acc{0ull, 0ull};
+    DfAcc2 acc[kLane];
+#pragma unroll
+    for (int i = 0; i < kLane; ++i) acc[i] = DfAcc2{0ull, 0ull};
     // strip rows of each group, HUB_DN_BATCH loads in flight; the bounds are warp-uniform
 #define HUB_DN_GROUP(OP, KA, KB)                                                           \
   do {                                                                                     \
     int32_t k = (KA);                                                                      \
     for (; k + HUB_DN_BATCH <= (KB); k += HUB_DN_BATCH) {                                  \
-      f2x vh[HUB_DN_BATCH], vl[HUB_DN_BATCH];                                              \
+      Vec<kLane> vh[HUB_DN_BATCH], vl[HUB_DN_BATCH];                                       \
       _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q) {                           \
         const uint64_t o = (uint64_t)colat<Col>(F.col_dn, k + q) * row_bytes;              \
-        vh[q] = *reinterpret_cast<const f2x *>(xh + o);                                    \
-        vl[q] = *reinterpret_cast<const f2x *>(xl + o);                                    \
+        vh[q] = ldv<kLane>(reinterpret_cast<const float *>(xh + o));                       \
+        vl[q] = ldv<kLane>(reinterpret_cast<const float *>(xl + o));                       \
       }                                                                                    \
-      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q) OP(acc, vh[q], vl[q]);      \
+      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q)                             \
+        _Pragma("unroll") for (int i = 0; i < kLane; ++i) OP(acc[i], vh[q].v[i], vl[q].v[i]); \
     }                                                                                      \
     for (; k < (KB); ++k) {                                                                \
       const uint64_t o = (uint64_t)colat<Col>(F.col_dn, k) * row_bytes;                    \
-      OP(acc, *reinterpret_cast<const f2x *>(xh + o), *reinterpret_cast<const f2x *>(xl + o)); \
+      const Vec<kLane> vh = ldv<kLane>(reinterpret_cast<const float *>(xh + o));           \
+      const Vec<kLane> vl = ldv<kLane>(reinterpret_cast<const float *>(xl + o));           \
+      _Pragma("unroll") for (int i = 0; i < kLane; ++i) OP(acc[i], vh.v[i], vl.v[i]);      \
     }                                                                                      \
   } while (0)
     HUB_DN_GROUP(acc2_add, k0, ks);
     HUB_DN_GROUP(acc2_sub, ks, k1);
 #undef HUB_DN_GROUP
-    f2x Sh, Sl, yh, yl;
-    acc2_norm(acc, Sh, Sl);
-    if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
     const float *zr = z + d * 2 * ld;
-    df2_add(ld2(zr + u), ld2(zr + ld + u), Sh, Sl, yh, yl);
-    float *wr = w + d * 2 * ld;
+    const Vec<kLane> zh = ldv<kLane>(zr + u), zl = ldv<kLane>(zr + ld + u);
+    Vec<kLane> yh, yl;
+#pragma unroll
+    for (int i = 0; i < kLane; ++i) {
+      f2x Sh, Sl;
+      acc2_norm(acc[i], Sh, Sl);
+      if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+      df2_add(zh.v[i], zl.v[i], Sh, Sl, yh.v[i], yl.v[i]);
+    }
     if (kMode == 0) {
-      st2(wr + u, yh);
-      st2(wr + ld + u, yl);
+      stv<kLane>(wr + u, yh);
+      stv<kLane>(wr + ld + u, yl);
     } else {
       const float *rc = L.r_cur + d * 2 * ld, *rp = L.r_prev + d * 2 * ld;
-      f2x ah, al, bh, bl, wh, wl, qh, ql;
-      df2_mul(yh, yl, ibh, ibl, ah, al);
-      df2_mul(cph, cpl, ld2(rp + u), ld2(rp + ld + u), bh, bl);
-      df2_sub(ah, al, bh, bl, wh, wl);
-      if (u + 1 >= F.n_up) {                             // keep the padding column zero
-        wh &= 0xffffffffull;
-        wl &= 0xffffffffull;
+      const Vec<kLane> rph = ldv<kLane>(rp + u), rpl = ldv<kLane>(rp + ld + u);
+      const Vec<kLane> rch = ldv<kLane>(rc + u), rcl = ldv<kLane>(rc + ld + u);
+      Vec<kLane> wh, wl;
+#pragma unroll
+      for (int i = 0; i < kLane; ++i) {
+        f2x ah, al, bh, bl, qh, ql;
+        df2_mul(yh.v[i], yl.v[i], ibh, ibl, ah, al);
+        df2_mul(cph, cpl, rph.v[i], rpl.v[i], bh, bl);
+        df2_sub(ah, al, bh, bl, wh.v[i], wl.v[i]);
+        // keep padding columns zero: column u + 2i + 1 (lane b) and u + 2i (both lanes)
+        const int64_t c0 = u + 2 * i;
+        if (c0 >= F.n_up) {
+          wh.v[i] = 0ull;
+          wl.v[i] = 0ull;
+        } else if (c0 + 1 >= F.n_up) {
+          wh.v[i] &= 0xffffffffull;
+          wl.v[i] &= 0xffffffffull;
+        }
+        // <r_j, w>, accumulated in double-float, reduced in FP64 and scaled by 1/beta_cur
+        df2_mul(rch.v[i], rcl.v[i], wh.v[i], wl.v[i], qh, ql);
+        acc2_add(dacc, qh, ql);
       }
-      st2(wr + u, wh);
-      st2(wr + ld + u, wl);
-      // <r_j, w>, accumulated in double-float, reduced in FP64 and scaled by 1/beta_cur
-      df2_mul(ld2(rc + u), ld2(rc + ld + u), wh, wl, qh, ql);
-      acc2_add(dacc, qh, ql);
+      stv<kLane>(wr + u, wh);
+      stv<kLane>(wr + ld + u, wl);
     }
   }
   if (kMode == 1) {
@@ -787,14 +845,20 @@ void fast_release(hub_ctx *h) {
   h->fast = nullptr;
 }
 
+// Plane length of a row: count_up rounded up to a multiple of 4 (16-byte plane starts) and
+// of the columns a pass-2 lane loads at once.
+static int64_t padded_ld(int64_t n_up) {
+  const int64_t a = kDnLaneCols > 4 ? kDnLaneCols : 4;
+  return (n_up + a - 1) / a * a;
+}
+
 bool fast_eligible(const hub_ctx *h) {
   if (!h->have_hop || !h->have_U || !h->uniform_U) return false;
   for (double tb : h->t)
     if (tb != h->t[0]) return false;
   if (h->count[0] <= 0 || h->count[1] <= 0) return false;
   // element quads of a vector are indexed with 32-bit integers
-  const int64_t ld = (h->count[0] + 3) & ~(int64_t)3;
-  return h->count[1] * (ld / 4) < ((int64_t)1 << 32);
+  return h->count[1] * (padded_ld(h->count[0]) / 4) < ((int64_t)1 << 32);
 }
 
 // Build the sign-split CSR and double-float tables (called after hub_hopping).
@@ -804,7 +868,7 @@ int fast_build(hub_ctx *h) {
   if (!f) return fail(HUB_ERR_OOM, "fast path: host allocation failed");
   h->fast = f;
   f->col16 = h->count[0] <= 65536 && h->count[1] <= 65536;
-  f->ld = (h->count[0] + 3) & ~(int64_t)3;
+  f->ld = padded_ld(h->count[0]);
   const size_t csz = f->col16 ? sizeof(uint16_t) : sizeof(uint32_t);
   for (int s = 0; s < 2; ++s) {
     if (s == 1 && h->shared) break;
