@@ -100,10 +100,12 @@ struct FastView {
   // (add, sub) group lengths so that the 32 rows a warp handles have nearly equal lengths;
   // slot k holds row slot_row[k].  Each slice of 32 slots has, per group, a schedule of
   // steps: in one step every lane reads at most one of its entries, chosen so that at most
-  // two lanes of the warp hit the same shared-memory bank (column mod 32).  Step j of slot
-  // k is word off[k/32] + (j/2)*32 + k%32 (two uint16 columns per word) or
-  // off[k/32] + j*32 + k%32 (uint32 columns).  Idle steps name a zero column (staged rows)
-  // or the sentinel 0xffff / 0xffffffff (rows read through L2).
+  // two lanes of the warp hit the same shared-memory bank (column mod 32).  A word holds the
+  // columns of two steps (uint16) or one (uint32); the words of a slice are stored in
+  // batches of four per lane, word i of batch b of slot k at off[k/32] + (b*32 + k%32)*4 + i,
+  // so that one 16-byte load brings a lane 8 (uint16) or 4 (uint32) steps.  Idle steps
+  // (schedule gaps, padding of the last word and batch) name a zero column (staged rows) or
+  // the sentinel 0xffff / 0xffffffff (rows read through L2).
   const uint32_t *sl_add, *sl_sub;   // packed words
   const int32_t *sl_off_add, *sl_off_sub;
   const uint16_t *steps_add, *steps_sub;   // per slice: scheduled steps (entries per lane)
@@ -296,53 +298,52 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
       }
       DfAcc2 acc{0ull, 0ull};
       const int64_t sl = slot >> 5, lane = slot & 31;
-      const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
-      const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
+      const uint4 *__restrict__ wa = reinterpret_cast<const uint4 *>(F.sl_add + F.sl_off_add[sl]) + lane;
+      const uint4 *__restrict__ wsb = reinterpret_cast<const uint4 *>(F.sl_sub + F.sl_off_sub[sl]) + lane;
       const int na = F.steps_add[sl], ns = F.steps_sub[sl];
       // one scheduled entry (idle steps read the zero column): (hi d0, hi d1), (lo d0, lo d1)
 #define HUB_TERM(OP, C)                                                                  \
   do {                                                                                   \
-    const uint32_t c_ = (C);                                                             \
-    OP(acc, pk2(xs[c_], xs[c_ + 2 * kUpPlane]), pk2(xs[c_ + kUpPlane], xs[c_ + 3 * kUpPlane])); \
+    const float *p_ = xs + (C);                                                          \
+    OP(acc, pk2(p_[0], p_[2 * kUpPlane]), pk2(p_[kUpPlane], p_[3 * kUpPlane]));          \
   } while (0)
-      // Column words are loaded four at a time so that their L2 latencies overlap; the
-      // last one to three words are loaded together too, and only the steps that exist
-      // are summed (N is uniform over the warp, so these branches do not diverge).
-#define HUB_GROUP(OP, W, N)                                                          \
-  do {                                                                               \
-    const int nst = (N);                                                             \
-    const int nw = sizeof(Col) == 2 ? (nst + 1) >> 1 : nst;                          \
-    int j0 = 0;                                                                      \
-    for (; j0 + 4 <= nw; j0 += 4) {                                                  \
-      uint32_t wd[4];                                                                \
-      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = W[(j0 + q) * 32];        \
-      _Pragma("unroll") for (int q = 0; q < 4; ++q) {                                \
-        if (sizeof(Col) == 2) {                                                      \
-          HUB_TERM(OP, wd[q] & 0xffffu);                                             \
-          if (2 * (j0 + q) + 1 < nst) HUB_TERM(OP, wd[q] >> 16);                      \
-        } else {                                                                     \
-          HUB_TERM(OP, wd[q]);                                                       \
-        }                                                                            \
-      }                                                                              \
-    }                                                                                \
-    if (j0 < nw) {                                                                   \
-      uint32_t wd[3];                                                                \
-      _Pragma("unroll") for (int q = 0; q < 3; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : F.idle_word; \
-      _Pragma("unroll") for (int q = 0; q < 3; ++q) {                                \
-        if (j0 + q < nw) {                                                           \
-          if (sizeof(Col) == 2) {                                                    \
-            HUB_TERM(OP, wd[q] & 0xffffu);                                           \
-            if (2 * (j0 + q) + 1 < nst) HUB_TERM(OP, wd[q] >> 16);                    \
-          } else {                                                                   \
-            HUB_TERM(OP, wd[q]);                                                     \
-          }                                                                          \
-        }                                                                            \
-      }                                                                              \
-    }                                                                                \
+#define HUB_WORD(OP, WD)                                                                 \
+  do {                                                                                   \
+    if (sizeof(Col) == 2) {                                                              \
+      HUB_TERM(OP, (WD) & 0xffffu);                                                      \
+      HUB_TERM(OP, (WD) >> 16);                                                          \
+    } else {                                                                             \
+      HUB_TERM(OP, (WD));                                                                \
+    }                                                                                    \
+  } while (0)
+      // Full batches of four words run unguarded; the last batch is taken word by word
+      // (a word's padding step reads the zero column).  N is uniform over the warp.
+#define HUB_GROUP(OP, W, N)                                                              \
+  do {                                                                                   \
+    constexpr int kPer = sizeof(Col) == 2 ? 8 : 4;       /* steps per batch */           \
+    constexpr int kPerWord = sizeof(Col) == 2 ? 2 : 1;                                   \
+    const int nst = (N);                                                                 \
+    int b = 0;                                                                           \
+    for (; kPer * (b + 1) <= nst; ++b) {                                                 \
+      const uint4 q = W[b * 32];                                                         \
+      HUB_WORD(OP, q.x);                                                                 \
+      HUB_WORD(OP, q.y);                                                                 \
+      HUB_WORD(OP, q.z);                                                                 \
+      HUB_WORD(OP, q.w);                                                                 \
+    }                                                                                    \
+    const int rem = nst - kPer * b;                                                      \
+    if (rem > 0) {                                                                       \
+      const uint4 q = W[b * 32];                                                         \
+      HUB_WORD(OP, q.x);                                                                 \
+      if (rem > kPerWord) HUB_WORD(OP, q.y);                                             \
+      if (rem > 2 * kPerWord) HUB_WORD(OP, q.z);                                         \
+      if (rem > 3 * kPerWord) HUB_WORD(OP, q.w);                                         \
+    }                                                                                    \
   } while (0)
       HUB_GROUP(acc2_add, wa, na);
       HUB_GROUP(acc2_sub, wsb, ns);
 #undef HUB_GROUP
+#undef HUB_WORD
 #undef HUB_TERM
       // Z = diag x + t S for both rows (packed)
       f2x Sh, Sl;
@@ -379,8 +380,12 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
 // ---------------------------------------------------------------------------------------
 constexpr int kL2Threads = 512;
 
+__device__ __forceinline__ uint32_t word_at(const uint4 &q, int i) {
+  return i == 0 ? q.x : (i == 1 ? q.y : (i == 2 ? q.z : q.w));
+}
+
 template <typename Col, bool kEps>
-__global__ void __launch_bounds__(kL2Threads) k_up_l2(const FastView F, const float *__restrict__ x,
+__global__ void __launch_bounds__(kL2Threads, 3) k_up_l2(const FastView F, const float *__restrict__ x,
                                                       float *__restrict__ z, int64_t pair0) {
   __shared__ float2 utab[32];
   const int tid = threadIdx.x;
@@ -405,21 +410,20 @@ __global__ void __launch_bounds__(kL2Threads) k_up_l2(const FastView F, const fl
   const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
   DfAcc2 acc{0ull, 0ull};
   const int64_t sl = slot >> 5, lane = slot & 31;
-  const uint32_t *__restrict__ wa = F.sl_add + F.sl_off_add[sl] + lane;
-  const uint32_t *__restrict__ wsb = F.sl_sub + F.sl_off_sub[sl] + lane;
+  const uint4 *__restrict__ wa = reinterpret_cast<const uint4 *>(F.sl_add + F.sl_off_add[sl]) + lane;
+  const uint4 *__restrict__ wsb = reinterpret_cast<const uint4 *>(F.sl_sub + F.sl_off_sub[sl]) + lane;
   const int na = F.steps_add[sl], ns = F.steps_sub[sl];
   const uint32_t idle = sizeof(Col) == 2 ? 0xffffu : 0xffffffffu;
 #define HUB_LGROUP(OP, W, N)                                                                 \
   do {                                                                                       \
+    constexpr int kPer = sizeof(Col) == 2 ? 8 : 4;                                           \
     const int nst = (N);                                                                     \
-    const int nw = sizeof(Col) == 2 ? (nst + 1) >> 1 : nst;                                  \
-    for (int j0 = 0; j0 < nw; j0 += 4) {                                                     \
-      uint32_t wd[4];                                                                        \
-      _Pragma("unroll") for (int q = 0; q < 4; ++q) wd[q] = j0 + q < nw ? W[(j0 + q) * 32] : F.idle_word; \
-      _Pragma("unroll") for (int q = 0; q < (sizeof(Col) == 2 ? 8 : 4); ++q) {              \
-        if ((sizeof(Col) == 2 ? 2 * j0 + q : j0 + q) >= nst) break;   /* uniform */          \
-        const uint32_t c_ = sizeof(Col) == 2 ? ((q & 1) ? (wd[q >> 1] >> 16) : (wd[q >> 1] & 0xffffu)) : wd[q]; \
-        if (c_ != idle) OP(acc, pk2(s0[c_], s1[c_]), pk2(s0[ld + c_], s1[ld + c_]));         \
+    for (int b = 0; kPer * b < nst; ++b) {                                                   \
+      const uint4 q4 = W[b * 32];                                                            \
+      _Pragma("unroll") for (int q = 0; q < kPer; ++q) {                                     \
+        const uint32_t wq = word_at(q4, sizeof(Col) == 2 ? q >> 1 : q);                      \
+        const uint32_t c_ = sizeof(Col) == 2 ? ((q & 1) ? (wq >> 16) : (wq & 0xffffu)) : wq; \
+        if (kPer * b + q < nst && c_ != idle) OP(acc, pk2(s0[c_], s1[c_]), pk2(s0[ld + c_], s1[ld + c_])); \
       }                                                                                      \
     }                                                                                        \
   } while (0)
@@ -991,20 +995,22 @@ int fast_build(hub_ctx *h) {
         const int S = (int)warp_steps.size();
         if (S > 65535) return fail(HUB_ERR_ARG, "fast path: hopping row schedule too long");
         st[grp][sl] = (uint16_t)S;
-        const int nw = (S + pack - 1) / pack;
-        off[grp][sl + 1] = off[grp][sl] + 32 * nw;
-        for (int j = 0; j < nw; ++j)
-          for (int l = 0; l < 32; ++l) {
-            uint32_t wd;
-            if (pack == 2) {
-              const uint32_t lo = warp_steps[2 * j][l];
-              const uint32_t hi = 2 * j + 1 < S ? warp_steps[2 * j + 1][l] : idle;
-              wd = lo | (hi << 16);
-            } else {
-              wd = warp_steps[j][l];
+        const int nw = (S + pack - 1) / pack, nb = (nw + 3) / 4;
+        off[grp][sl + 1] = off[grp][sl] + 32 * 4 * nb;
+        for (int bt = 0; bt < nb; ++bt)
+          for (int l = 0; l < 32; ++l)
+            for (int i = 0; i < 4; ++i) {
+              const int j = 4 * bt + i;
+              uint32_t wd = f->idle_word;
+              if (j < nw && pack == 2) {
+                const uint32_t lo = warp_steps[2 * j][l];
+                const uint32_t hi = 2 * j + 1 < S ? warp_steps[2 * j + 1][l] : idle;
+                wd = lo | (hi << 16);
+              } else if (j < nw) {
+                wd = warp_steps[j][l];
+              }
+              words[grp].push_back(wd);
             }
-            words[grp].push_back(wd);
-          }
       }
     }
     if (!dev_alloc((void **)&f->sl_off_add, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
