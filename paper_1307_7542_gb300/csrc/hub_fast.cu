@@ -373,83 +373,37 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
 }
 
 // ---------------------------------------------------------------------------------------
-// Pass 1 for rows too long to stage (e.g. C(18, 9) = 48620 columns, 389 KB per row): the
-// gathers read the rows through L2.  To keep the rows being gathered resident in L2, the
-// grid is (slot chunk, row pair) with the chunk index fastest, so the blocks in flight at
-// any time all work on one or two row pairs instead of one pair per SM.
+// Rows too long to stage (e.g. C(18, 9) = 48620 columns, 194 KB per plane): pass 1 runs on
+// the transposed matrix instead.  X^T is formed by a tiled transpose, the spin-up hops then
+// combine whole rows of X^T exactly as pass 2 combines rows of X (k_dn in mode 2, diagonal
+// in the epilogue), and the result is transposed back into Z.  Each transpose moves a
+// vector once through HBM; gathers through L2 would instead touch two sectors per term.
 // ---------------------------------------------------------------------------------------
-constexpr int kL2Threads = 512;
+constexpr int kTile = 32;
 
-__device__ __forceinline__ uint32_t word_at(const uint4 &q, int i) {
-  return i == 0 ? q.x : (i == 1 ? q.y : (i == 2 ? q.z : q.w));
-}
-
-template <typename Col, bool kEps>
-__global__ void __launch_bounds__(kL2Threads, 3) k_up_l2(const FastView F, const float *__restrict__ x,
-                                                      float *__restrict__ z, int64_t pair0) {
-  __shared__ float2 utab[32];
-  const int tid = threadIdx.x;
-  if (tid < 32) utab[tid] = F.Utab[tid];
+// dst[c][r] = src[r][c] for planar matrices: src has n_r rows (plane length ld_s, n_c valid
+// columns), dst has n_c rows of plane length ld_d; dst columns n_r .. ld_d - 1 are zeroed.
+// Block (32, 8): a 32 x 32 tile of both planes through shared memory.
+__global__ void __launch_bounds__(256) k_transpose(int64_t n_r, int64_t n_c, int64_t ld_s, int64_t ld_d,
+                                                   const float *__restrict__ src, float *__restrict__ dst) {
+  __shared__ float th[kTile][kTile + 1], tl[kTile][kTile + 1];
+  const int tx = threadIdx.x, ty = threadIdx.y;
+  const int64_t c0 = (int64_t)blockIdx.x * kTile, r0 = (int64_t)blockIdx.y * kTile;
+#pragma unroll
+  for (int j = 0; j < kTile; j += 8) {
+    const int64_t r = r0 + ty + j, c = c0 + tx;
+    const bool in = r < n_r && c < n_c;
+    th[ty + j][tx] = in ? src[r * 2 * ld_s + c] : 0.f;
+    tl[ty + j][tx] = in ? src[r * 2 * ld_s + ld_s + c] : 0.f;
+  }
   __syncthreads();
-  const int64_t ld = F.ld;
-  const int64_t p = pair0 + blockIdx.y;
-  const int64_t d0 = 2 * p, d1 = (2 * p + 1 < F.n_dn) ? 2 * p + 1 : 2 * p;
-  const float *__restrict__ s0 = x + d0 * 2 * ld;
-  const float *__restrict__ s1 = x + d1 * 2 * ld;
-  float *__restrict__ z0 = z + d0 * 2 * ld;
-  float *__restrict__ z1 = z + d1 * 2 * ld;
-  const int64_t slot = (int64_t)blockIdx.x * kL2Threads + tid;
-  if (slot >= ld) return;
-  if (slot >= F.n_up) {
-    z0[slot] = 0.f;
-    z0[ld + slot] = 0.f;
-    z1[slot] = 0.f;
-    z1[ld + slot] = 0.f;
-    return;
-  }
-  const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
-  DfAcc2 acc{0ull, 0ull};
-  const int64_t sl = slot >> 5, lane = slot & 31;
-  const uint4 *__restrict__ wa = reinterpret_cast<const uint4 *>(F.sl_add + F.sl_off_add[sl]) + lane;
-  const uint4 *__restrict__ wsb = reinterpret_cast<const uint4 *>(F.sl_sub + F.sl_off_sub[sl]) + lane;
-  const int na = F.steps_add[sl], ns = F.steps_sub[sl];
-  const uint32_t idle = sizeof(Col) == 2 ? 0xffffu : 0xffffffffu;
-#define HUB_LGROUP(OP, W, N)                                                                 \
-  do {                                                                                       \
-    constexpr int kPer = sizeof(Col) == 2 ? 8 : 4;                                           \
-    const int nst = (N);                                                                     \
-    for (int b = 0; kPer * b < nst; ++b) {                                                   \
-      const uint4 q4 = W[b * 32];                                                            \
-      _Pragma("unroll") for (int q = 0; q < kPer; ++q) {                                     \
-        const uint32_t wq = word_at(q4, sizeof(Col) == 2 ? q >> 1 : q);                      \
-        const uint32_t c_ = sizeof(Col) == 2 ? ((q & 1) ? (wq >> 16) : (wq & 0xffffu)) : wq; \
-        if (kPer * b + q < nst && c_ != idle) OP(acc, pk2(s0[c_], s1[c_]), pk2(s0[ld + c_], s1[ld + c_])); \
-      }                                                                                      \
-    }                                                                                        \
-  } while (0)
-  HUB_LGROUP(acc2_add, wa, na);
-  HUB_LGROUP(acc2_sub, wsb, ns);
-#undef HUB_LGROUP
-  f2x Sh, Sl;
-  acc2_norm(acc, Sh, Sl);
-  if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
-  const uint32_t Iu = F.basis_up_slot[slot];
-  float2 dg0 = utab[__popc(Iu & I0)], dg1 = utab[__popc(Iu & I1)];
-  if (kEps) {
-    const float2 ep = F.eps_up[slot];
-    dg0 = df_add(df_add(dg0, ep), F.eps_dn[d0]);
-    dg1 = df_add(df_add(dg1, ep), F.eps_dn[d1]);
-  }
-  f2x ph, pl, zh, zl;
-  df2_mul(pk2(dg0.x, dg1.x), pk2(dg0.y, dg1.y), pk2(s0[slot], s1[slot]), pk2(s0[ld + slot], s1[ld + slot]), ph,
-          pl);
-  df2_add(ph, pl, Sh, Sl, zh, zl);
-  const float2 h = upk2(zh), l = upk2(zl);
-  z0[slot] = h.x;
-  z0[ld + slot] = l.x;
-  if (d1 != d0) {
-    z1[slot] = h.y;
-    z1[ld + slot] = l.y;
+#pragma unroll
+  for (int j = 0; j < kTile; j += 8) {
+    const int64_t c = c0 + ty + j, r = r0 + tx;
+    if (c < n_c && r < ld_d) {
+      dst[c * 2 * ld_d + r] = th[tx][ty + j];
+      dst[c * 2 * ld_d + ld_d + r] = tl[tx][ty + j];
+    }
   }
 }
 
@@ -467,6 +421,14 @@ constexpr int kDnRows = 32, kDnLaneCols = HUB_DN_LANE_COLS, kDnCols = 32 * kDnLa
 #ifndef HUB_DN_BATCH
 #define HUB_DN_BATCH 2   // strip rows whose loads are issued together in pass 2
 #endif
+
+// The hopping side a row-combination pass works on: the rows of the matrix it reads are the
+// states of this side, its columns (n_cols valid of ld) the states of the other side.
+struct Side {
+  int64_t n_rows, n_cols, ld;
+  const int32_t *rp, *sp;            // sign-split CSR of this side's hopping matrix
+  const void *col;
+};
 
 struct LzArgs {                      // Lanczos epilogue operands
   const float *r_cur;                // r_j   (q_j = r_j / beta_cur)
@@ -541,12 +503,19 @@ __device__ __forceinline__ void stv(float *p, const Vec<kLane> &a) {
 //          (the FP64 output in rank order is written afterwards by k_unpermute).
 // kMode 1: w = (Z + t S_dn)/beta_cur - (beta_cur/beta_prev) r_prev, partials <- <q_j, w>
 //          per block (= <r_j, w>/beta_cur).
+// kMode 2: pass 1 on X^T (side = spin up, rows of x are spin-up states, columns spin-down
+//          states): w = t S_up + diag x, diag from the two basis strings (no z).
 template <typename Col, int kMode>
-__global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float *__restrict__ x, const float *z,
-                                                  float *w, LzArgs L) {
+__global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const Side S, const float *__restrict__ x,
+                                                  const float *z, float *w, LzArgs L) {
   constexpr int kLane = kDnLaneCols / 2;               // packed pairs per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int64_t ld = F.ld;
+  const int64_t ld = S.ld;
+  __shared__ float2 utab[kMode == 2 ? 32 : 1];
+  if (kMode == 2) {
+    if (threadIdx.x < 32) utab[threadIdx.x] = F.Utab[threadIdx.x];
+    __syncthreads();
+  }
   const int64_t u = (int64_t)blockIdx.y * kDnCols + kDnLaneCols * lane;
   const int64_t r0 = (int64_t)blockIdx.x * kDnRows;
   const uint32_t row_bytes = (uint32_t)(2 * ld * sizeof(float));
@@ -559,13 +528,13 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     cpl = bcast2(cp.y);
   }
   DfAcc2 dacc{0ull, 0ull};
-  const bool active = u < F.n_up;                      // u + kDnLaneCols <= ld (see fast_build)
+  const bool active = u < S.n_cols;                    // u + kDnLaneCols <= ld (see fast_build)
   const char *__restrict__ xh = reinterpret_cast<const char *>(x + u);
   const char *__restrict__ xl = reinterpret_cast<const char *>(x + ld + u);
   for (int rr = warp; rr < kDnRows; rr += kDnThreads / 32) {
     const int64_t d = r0 + rr;
-    if (d >= F.n_dn) break;
-    const int32_t k0 = F.rp_dn[d], ks = F.sp_dn[d], k1 = F.rp_dn[d + 1];
+    if (d >= S.n_rows) break;
+    const int32_t k0 = S.rp[d], ks = S.sp[d], k1 = S.rp[d + 1];
     float *wr = w + d * 2 * ld;
     if (!active) {
       if (u < ld) {                                      // padding columns of w stay zero
@@ -584,7 +553,7 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     for (; k + HUB_DN_BATCH <= (KB); k += HUB_DN_BATCH) {                                  \
       Vec<kLane> vh[HUB_DN_BATCH], vl[HUB_DN_BATCH];                                       \
       _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q) {                           \
-        const uint64_t o = (uint64_t)colat<Col>(F.col_dn, k + q) * row_bytes;              \
+        const uint64_t o = (uint64_t)colat<Col>(S.col, k + q) * row_bytes;                 \
         vh[q] = ldv<kLane>(reinterpret_cast<const float *>(xh + o));                       \
         vl[q] = ldv<kLane>(reinterpret_cast<const float *>(xl + o));                       \
       }                                                                                    \
@@ -592,7 +561,7 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
         _Pragma("unroll") for (int i = 0; i < kLane; ++i) OP(acc[i], vh[q].v[i], vl[q].v[i]); \
     }                                                                                      \
     for (; k < (KB); ++k) {                                                                \
-      const uint64_t o = (uint64_t)colat<Col>(F.col_dn, k) * row_bytes;                    \
+      const uint64_t o = (uint64_t)colat<Col>(S.col, k) * row_bytes;                       \
       const Vec<kLane> vh = ldv<kLane>(reinterpret_cast<const float *>(xh + o));           \
       const Vec<kLane> vl = ldv<kLane>(reinterpret_cast<const float *>(xl + o));           \
       _Pragma("unroll") for (int i = 0; i < kLane; ++i) OP(acc[i], vh.v[i], vl.v[i]);      \
@@ -601,17 +570,43 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
     HUB_DN_GROUP(acc2_add, k0, ks);
     HUB_DN_GROUP(acc2_sub, ks, k1);
 #undef HUB_DN_GROUP
-    const float *zr = z + d * 2 * ld;
-    const Vec<kLane> zh = ldv<kLane>(zr + u), zl = ldv<kLane>(zr + ld + u);
     Vec<kLane> yh, yl;
+    if (kMode == 2) {
+      // diag x for the columns (spin-down states) u .. u + kDnLaneCols - 1 of spin-up row d
+      const float *xr = x + d * 2 * ld;
+      const Vec<kLane> xvh = ldv<kLane>(xr + u), xvl = ldv<kLane>(xr + ld + u);
+      const uint32_t Iu = F.basis_up[d];
+      const float2 ep = F.eps_up ? F.eps_up[d] : make_float2(0.f, 0.f);
 #pragma unroll
-    for (int i = 0; i < kLane; ++i) {
-      f2x Sh, Sl;
-      acc2_norm(acc[i], Sh, Sl);
-      if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
-      df2_add(zh.v[i], zl.v[i], Sh, Sl, yh.v[i], yl.v[i]);
+      for (int i = 0; i < kLane; ++i) {
+        float2 dg[2];
+#pragma unroll
+        for (int b = 0; b < 2; ++b) {
+          const int64_t c = u + 2 * i + b;
+          dg[b] = make_float2(0.f, 0.f);
+          if (c < S.n_cols) {
+            dg[b] = utab[__popc(Iu & F.basis_dn[c])];
+            if (F.eps_up) dg[b] = df_add(df_add(dg[b], ep), F.eps_dn[c]);
+          }
+        }
+        f2x Sh, Sl, ph, pl;
+        acc2_norm(acc[i], Sh, Sl);
+        if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+        df2_mul(pk2(dg[0].x, dg[1].x), pk2(dg[0].y, dg[1].y), xvh.v[i], xvl.v[i], ph, pl);
+        df2_add(ph, pl, Sh, Sl, yh.v[i], yl.v[i]);
+      }
+    } else {
+      const float *zr = z + d * 2 * ld;
+      const Vec<kLane> zh = ldv<kLane>(zr + u), zl = ldv<kLane>(zr + ld + u);
+#pragma unroll
+      for (int i = 0; i < kLane; ++i) {
+        f2x Sh, Sl;
+        acc2_norm(acc[i], Sh, Sl);
+        if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+        df2_add(zh.v[i], zl.v[i], Sh, Sl, yh.v[i], yl.v[i]);
+      }
     }
-    if (kMode == 0) {
+    if (kMode != 1) {
       stv<kLane>(wr + u, yh);
       stv<kLane>(wr + ld + u, yl);
     } else {
@@ -627,10 +622,10 @@ __global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const float
         df2_sub(ah, al, bh, bl, wh.v[i], wl.v[i]);
         // keep padding columns zero: column u + 2i + 1 (lane b) and u + 2i (both lanes)
         const int64_t c0 = u + 2 * i;
-        if (c0 >= F.n_up) {
+        if (c0 >= S.n_cols) {
           wh.v[i] = 0ull;
           wl.v[i] = 0ull;
-        } else if (c0 + 1 >= F.n_up) {
+        } else if (c0 + 1 >= S.n_cols) {
           wh.v[i] &= 0xffffffffull;
           wl.v[i] &= 0xffffffffull;
         }
@@ -811,6 +806,9 @@ struct FastState {
   void *col[2] = {nullptr, nullptr};
   float2 *eps_df[2] = {nullptr, nullptr};
   float *xdf = nullptr, *zdf = nullptr;      // hub_apply scratch (planar double-float)
+  bool staged = true;                        // pass 1 stages rows; else it runs on X^T
+  int64_t ld_t = 0;                          // plane length of X^T rows (count_dn padded)
+  float *xt = nullptr, *zt = nullptr;        // X^T and Z^T (rows too long to stage)
   float *lz[3] = {nullptr, nullptr, nullptr};
   float *psi = nullptr;
   int *d_emax = nullptr;
@@ -830,6 +828,8 @@ void fast_release(hub_ctx *h) {
   }
   dev_free(f->xdf);
   dev_free(f->zdf);
+  dev_free(f->xt);
+  dev_free(f->zt);
   for (int k = 0; k < 3; ++k) dev_free(f->lz[k]);
   dev_free(f->psi);
   dev_free(f->d_emax);
@@ -873,6 +873,8 @@ int fast_build(hub_ctx *h) {
   h->fast = f;
   f->col16 = h->count[0] <= 65536 && h->count[1] <= 65536;
   f->ld = padded_ld(h->count[0]);
+  f->ld_t = padded_ld(h->count[1]);
+  f->staged = f->ld + 2 <= kUpPlane;
   const size_t csz = f->col16 ? sizeof(uint16_t) : sizeof(uint32_t);
   for (int s = 0; s < 2; ++s) {
     if (s == 1 && h->shared) break;
@@ -909,10 +911,11 @@ int fast_build(hub_ctx *h) {
     } else if (nnz) {
       HUB_CUDA(cudaMemcpy(col.data(), f->col[0], sizeof(uint32_t) * nnz, cudaMemcpyDeviceToHost));
     }
-    // slots: rows ordered by (add length, sub length), stable
+    // slots: rows ordered by (add length, sub length), stable (identity when pass 1 runs
+    // on X^T, which has no use for the order)
     std::vector<int32_t> slot_row(n);
     for (int64_t r = 0; r < n; ++r) slot_row[r] = (int32_t)r;
-    std::stable_sort(slot_row.begin(), slot_row.end(), [&](int32_t a, int32_t b) {
+    if (f->staged) std::stable_sort(slot_row.begin(), slot_row.end(), [&](int32_t a, int32_t b) {
       const int la = spv[a] - rp[a], lb = spv[b] - rp[b];
       const int sa = rp[a + 1] - spv[a], sb = rp[b + 1] - spv[b];
       return la != lb ? la > lb : sa > sb;
@@ -931,103 +934,105 @@ int fast_build(hub_ctx *h) {
     k_to_slots<<<g, 256>>>(n, f->slot_row, h->basis[0], f->basis_slot, h->has_eps ? f->eps_df[0] : nullptr,
                            f->eps_up_slot);
     HUB_LAUNCH_CHECK();
-    // per slice and group: schedule the lanes' entries into steps in which at most two lanes
-    // of the warp hit the same bank (slot mod 32), i.e. at most two shared-memory wavefronts
-    // per 32-bit load.  Greedy: lanes with the most remaining entries are served first; each
-    // takes the entry of the most loaded bank that still has room.  (A conflict-free
-    // schedule needs about 1.7x more steps on the 4x4 lattice because the bank loads are
-    // uneven; two per bank costs a few per cent more steps than the longest row.)
-    constexpr int kBankCap = 2;
-    // idle steps: the zero entry after the staged row when rows are staged, else a sentinel
-    const bool staged = f->ld + 2 <= kUpPlane;
-    const uint32_t idle = staged ? (uint32_t)f->ld : (f->col16 ? 0xffffu : 0xffffffffu);
-    f->idle_word = f->col16 ? (idle | (idle << 16)) : idle;
-    const int pack = f->col16 ? 2 : 1;
-    std::vector<uint16_t> st[2] = {std::vector<uint16_t>(nsl), std::vector<uint16_t>(nsl)};
-    std::vector<int32_t> off[2] = {std::vector<int32_t>(nsl + 1, 0), std::vector<int32_t>(nsl + 1, 0)};
-    std::vector<uint32_t> words[2];
-    std::vector<std::vector<uint32_t>> warp_steps;  // [S][32] entries of one slice
-    for (int64_t sl = 0; sl < nsl; ++sl) {
-      for (int grp = 0; grp < 2; ++grp) {
-        std::vector<uint32_t> rem[32];
-        int bankload[32] = {0};
-        for (int l = 0; l < 32; ++l) {
-          const int64_t slot = sl * 32 + l;
-          if (slot >= n) continue;
-          const int32_t r = slot_row[slot];
-          const int32_t a = grp == 0 ? rp[r] : spv[r], b = grp == 0 ? spv[r] : rp[r + 1];
-          for (int32_t k = a; k < b; ++k) {
-            rem[l].push_back((uint32_t)slot_of[col[k]]);
-            ++bankload[slot_of[col[k]] & 31];
-          }
-        }
-        warp_steps.clear();
-        for (;;) {
-          int lanes[32], nl = 0;
-          for (int l = 0; l < 32; ++l)
-            if (!rem[l].empty()) lanes[nl++] = l;
-          if (!nl) break;
-          std::stable_sort(lanes, lanes + nl, [&](int a, int b) { return rem[a].size() > rem[b].size(); });
-          std::vector<uint32_t> step(32, idle);
-          int used[32] = {0};
-          for (int q = 0; q < nl; ++q) {
-            const int l = lanes[q];
-            int best = -1;
-            for (int e = 0; e < (int)rem[l].size(); ++e) {
-              const int bk = rem[l][e] & 31;
-              if (used[bk] >= kBankCap) continue;
-              if (best < 0) {
-                best = e;
-                continue;
-              }
-              const int bb = rem[l][best] & 31;
-              if (bankload[bk] > bankload[bb] || (bankload[bk] == bankload[bb] && used[bk] < used[bb])) best = e;
+    if (f->staged) {
+      // per slice and group: schedule the lanes' entries into steps in which at most two lanes
+      // of the warp hit the same bank (slot mod 32), i.e. at most two shared-memory wavefronts
+      // per 32-bit load.  Greedy: lanes with the most remaining entries are served first; each
+      // takes the entry of the most loaded bank that still has room.  (A conflict-free
+      // schedule needs about 1.7x more steps on the 4x4 lattice because the bank loads are
+      // uneven; two per bank costs a few per cent more steps than the longest row.)
+      constexpr int kBankCap = 2;
+      // idle steps: the zero entry after the staged row when rows are staged, else a sentinel
+      const bool staged = f->ld + 2 <= kUpPlane;
+      const uint32_t idle = staged ? (uint32_t)f->ld : (f->col16 ? 0xffffu : 0xffffffffu);
+      f->idle_word = f->col16 ? (idle | (idle << 16)) : idle;
+      const int pack = f->col16 ? 2 : 1;
+      std::vector<uint16_t> st[2] = {std::vector<uint16_t>(nsl), std::vector<uint16_t>(nsl)};
+      std::vector<int32_t> off[2] = {std::vector<int32_t>(nsl + 1, 0), std::vector<int32_t>(nsl + 1, 0)};
+      std::vector<uint32_t> words[2];
+      std::vector<std::vector<uint32_t>> warp_steps;  // [S][32] entries of one slice
+      for (int64_t sl = 0; sl < nsl; ++sl) {
+        for (int grp = 0; grp < 2; ++grp) {
+          std::vector<uint32_t> rem[32];
+          int bankload[32] = {0};
+          for (int l = 0; l < 32; ++l) {
+            const int64_t slot = sl * 32 + l;
+            if (slot >= n) continue;
+            const int32_t r = slot_row[slot];
+            const int32_t a = grp == 0 ? rp[r] : spv[r], b = grp == 0 ? spv[r] : rp[r + 1];
+            for (int32_t k = a; k < b; ++k) {
+              rem[l].push_back((uint32_t)slot_of[col[k]]);
+              ++bankload[slot_of[col[k]] & 31];
             }
-            if (best < 0) continue;
-            const uint32_t c = rem[l][best];
-            step[l] = c;
-            ++used[c & 31];
-            --bankload[c & 31];
-            rem[l].erase(rem[l].begin() + best);
           }
-          warp_steps.push_back(step);
-        }
-        const int S = (int)warp_steps.size();
-        if (S > 65535) return fail(HUB_ERR_ARG, "fast path: hopping row schedule too long");
-        st[grp][sl] = (uint16_t)S;
-        const int nw = (S + pack - 1) / pack, nb = (nw + 3) / 4;
-        off[grp][sl + 1] = off[grp][sl] + 32 * 4 * nb;
-        for (int bt = 0; bt < nb; ++bt)
-          for (int l = 0; l < 32; ++l)
-            for (int i = 0; i < 4; ++i) {
-              const int j = 4 * bt + i;
-              uint32_t wd = f->idle_word;
-              if (j < nw && pack == 2) {
-                const uint32_t lo = warp_steps[2 * j][l];
-                const uint32_t hi = 2 * j + 1 < S ? warp_steps[2 * j + 1][l] : idle;
-                wd = lo | (hi << 16);
-              } else if (j < nw) {
-                wd = warp_steps[j][l];
+          warp_steps.clear();
+          for (;;) {
+            int lanes[32], nl = 0;
+            for (int l = 0; l < 32; ++l)
+              if (!rem[l].empty()) lanes[nl++] = l;
+            if (!nl) break;
+            std::stable_sort(lanes, lanes + nl, [&](int a, int b) { return rem[a].size() > rem[b].size(); });
+            std::vector<uint32_t> step(32, idle);
+            int used[32] = {0};
+            for (int q = 0; q < nl; ++q) {
+              const int l = lanes[q];
+              int best = -1;
+              for (int e = 0; e < (int)rem[l].size(); ++e) {
+                const int bk = rem[l][e] & 31;
+                if (used[bk] >= kBankCap) continue;
+                if (best < 0) {
+                  best = e;
+                  continue;
+                }
+                const int bb = rem[l][best] & 31;
+                if (bankload[bk] > bankload[bb] || (bankload[bk] == bankload[bb] && used[bk] < used[bb])) best = e;
               }
-              words[grp].push_back(wd);
+              if (best < 0) continue;
+              const uint32_t c = rem[l][best];
+              step[l] = c;
+              ++used[c & 31];
+              --bankload[c & 31];
+              rem[l].erase(rem[l].begin() + best);
             }
+            warp_steps.push_back(step);
+          }
+          const int S = (int)warp_steps.size();
+          if (S > 65535) return fail(HUB_ERR_ARG, "fast path: hopping row schedule too long");
+          st[grp][sl] = (uint16_t)S;
+          const int nw = (S + pack - 1) / pack, nb = (nw + 3) / 4;
+          off[grp][sl + 1] = off[grp][sl] + 32 * 4 * nb;
+          for (int bt = 0; bt < nb; ++bt)
+            for (int l = 0; l < 32; ++l)
+              for (int i = 0; i < 4; ++i) {
+                const int j = 4 * bt + i;
+                uint32_t wd = f->idle_word;
+                if (j < nw && pack == 2) {
+                  const uint32_t lo = warp_steps[2 * j][l];
+                  const uint32_t hi = 2 * j + 1 < S ? warp_steps[2 * j + 1][l] : idle;
+                  wd = lo | (hi << 16);
+                } else if (j < nw) {
+                  wd = warp_steps[j][l];
+                }
+                words[grp].push_back(wd);
+              }
+        }
       }
+      if (!dev_alloc((void **)&f->sl_off_add, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
+          !dev_alloc((void **)&f->sl_off_sub, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
+          !dev_alloc((void **)&f->sl_add, sizeof(uint32_t) * std::max<size_t>(words[0].size(), 1), "sliced columns") ||
+          !dev_alloc((void **)&f->sl_sub, sizeof(uint32_t) * std::max<size_t>(words[1].size(), 1), "sliced columns") ||
+          !dev_alloc((void **)&f->steps_add, sizeof(uint16_t) * nsl, "slice steps") ||
+          !dev_alloc((void **)&f->steps_sub, sizeof(uint16_t) * nsl, "slice steps"))
+        return HUB_ERR_OOM;
+      HUB_CUDA(cudaMemcpy(f->sl_off_add, off[0].data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+      HUB_CUDA(cudaMemcpy(f->sl_off_sub, off[1].data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
+      if (!words[0].empty())
+        HUB_CUDA(cudaMemcpy(f->sl_add, words[0].data(), sizeof(uint32_t) * words[0].size(), cudaMemcpyHostToDevice));
+      if (!words[1].empty())
+        HUB_CUDA(cudaMemcpy(f->sl_sub, words[1].data(), sizeof(uint32_t) * words[1].size(), cudaMemcpyHostToDevice));
+      HUB_CUDA(cudaMemcpy(f->steps_add, st[0].data(), sizeof(uint16_t) * nsl, cudaMemcpyHostToDevice));
+      HUB_CUDA(cudaMemcpy(f->steps_sub, st[1].data(), sizeof(uint16_t) * nsl, cudaMemcpyHostToDevice));
     }
-    if (!dev_alloc((void **)&f->sl_off_add, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
-        !dev_alloc((void **)&f->sl_off_sub, sizeof(int32_t) * (nsl + 1), "slice offsets") ||
-        !dev_alloc((void **)&f->sl_add, sizeof(uint32_t) * std::max<size_t>(words[0].size(), 1), "sliced columns") ||
-        !dev_alloc((void **)&f->sl_sub, sizeof(uint32_t) * std::max<size_t>(words[1].size(), 1), "sliced columns") ||
-        !dev_alloc((void **)&f->steps_add, sizeof(uint16_t) * nsl, "slice steps") ||
-        !dev_alloc((void **)&f->steps_sub, sizeof(uint16_t) * nsl, "slice steps"))
-      return HUB_ERR_OOM;
-    HUB_CUDA(cudaMemcpy(f->sl_off_add, off[0].data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(f->sl_off_sub, off[1].data(), sizeof(int32_t) * (nsl + 1), cudaMemcpyHostToDevice));
-    if (!words[0].empty())
-      HUB_CUDA(cudaMemcpy(f->sl_add, words[0].data(), sizeof(uint32_t) * words[0].size(), cudaMemcpyHostToDevice));
-    if (!words[1].empty())
-      HUB_CUDA(cudaMemcpy(f->sl_sub, words[1].data(), sizeof(uint32_t) * words[1].size(), cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(f->steps_add, st[0].data(), sizeof(uint16_t) * nsl, cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(f->steps_sub, st[1].data(), sizeof(uint16_t) * nsl, cudaMemcpyHostToDevice));
   }
   if (!dev_alloc((void **)&f->d_err, sizeof(int) * 4, "error flag") ||
       !dev_alloc((void **)&f->coef, sizeof(float2) * 8, "recurrence coefficients"))
@@ -1088,57 +1093,78 @@ static size_t up_smem(const FastState *f) { return sizeof(float) * (3 * (size_t)
 constexpr size_t kMaxStage = 224 * 1024;
 static_assert(sizeof(float) * 4 * kUpPlane <= kMaxStage, "four staged planes must fit");
 
-static bool up_staged(const FastState *f) { return f->ld + 2 <= kUpPlane; }
-
-template <typename Col>
-static int launch_up_t(const FastView &v, const FastState *f, bool eps, const float *x, float *z, cudaStream_t s) {
-  if (!up_staged(f)) {
-    const int64_t n_pairs = (v.n_dn + 1) / 2;
-    const unsigned chunks = (unsigned)((v.ld + kL2Threads - 1) / kL2Threads);
-    for (int64_t p0 = 0; p0 < n_pairs; p0 += 65535) {
-      const dim3 g(chunks, (unsigned)std::min<int64_t>(65535, n_pairs - p0));
-      if (eps) k_up_l2<Col, true><<<g, kL2Threads, 0, s>>>(v, x, z, p0);
-      else k_up_l2<Col, false><<<g, kL2Threads, 0, s>>>(v, x, z, p0);
-      HUB_LAUNCH_CHECK();
-    }
-    return HUB_OK;
-  }
-  const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
-  const int64_t grid = std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms());
-  const size_t smem = up_smem(f);
-  if (eps) {
-    HUB_CUDA(cudaFuncSetAttribute(k_up<Col, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage));
-    k_up<Col, true><<<(int)grid, threads, smem, s>>>(v, x, z);
-  } else {
-    HUB_CUDA(cudaFuncSetAttribute(k_up<Col, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage));
-    k_up<Col, false><<<(int)grid, threads, smem, s>>>(v, x, z);
-  }
-  HUB_LAUNCH_CHECK();
-  return HUB_OK;
+// the spin-down side (pass 2 on X) and the spin-up side (pass 1 on X^T)
+static Side side_dn(const hub_ctx *h, const FastState *f) {
+  const int sd = h->shared ? 0 : 1;
+  return Side{h->count[1], h->count[0], f->ld, h->csr[sd].rowptr, f->sp[sd], f->col[sd]};
+}
+static Side side_up(const hub_ctx *h, const FastState *f) {
+  return Side{h->count[0], h->count[1], f->ld_t, h->csr[0].rowptr, f->sp[0], f->col[0]};
 }
 
-static dim3 dn_grid(const FastView &v) {
-  return dim3((unsigned)((v.n_dn + kDnRows - 1) / kDnRows), (unsigned)((v.n_up + kDnCols - 1) / kDnCols));
+static dim3 dn_grid(const Side &S) {
+  return dim3((unsigned)((S.n_rows + kDnRows - 1) / kDnRows), (unsigned)((S.n_cols + kDnCols - 1) / kDnCols));
 }
 
 template <typename Col, int kMode>
-static int launch_dn_t(const FastView &v, const float *x, const float *z, float *w, LzArgs L, cudaStream_t s) {
-  const dim3 g = dn_grid(v);
+static int launch_dn_t(const FastView &v, const Side &S, const float *x, const float *z, float *w, LzArgs L,
+                       cudaStream_t s) {
+  const dim3 g = dn_grid(S);
   if (g.y > 65535) return fail(HUB_ERR_ARG, "fast apply: too many column strips");
-  k_dn<Col, kMode><<<g, kDnThreads, 0, s>>>(v, x, z, w, L);
+  k_dn<Col, kMode><<<g, kDnThreads, 0, s>>>(v, S, x, z, w, L);
   HUB_LAUNCH_CHECK();
   return HUB_OK;
 }
+
+template <int kMode>
+static int launch_dn(const FastState *f, const FastView &v, const Side &S, const float *x, const float *z, float *w,
+                     LzArgs L, cudaStream_t s) {
+  return f->col16 ? launch_dn_t<uint16_t, kMode>(v, S, x, z, w, L, s)
+                  : launch_dn_t<uint32_t, kMode>(v, S, x, z, w, L, s);
+}
+
+// dst = src^T for planar matrices (see k_transpose)
+static int transpose(int64_t n_r, int64_t n_c, int64_t ld_s, int64_t ld_d, const float *src, float *dst,
+                     cudaStream_t s) {
+  const dim3 g((unsigned)((n_c + kTile - 1) / kTile), (unsigned)((ld_d + kTile - 1) / kTile));
+  if (g.y > 65535) return fail(HUB_ERR_ARG, "fast apply: matrix too large to transpose");
+  k_transpose<<<g, dim3(kTile, 8), 0, s>>>(n_r, n_c, ld_s, ld_d, src, dst);
+  HUB_LAUNCH_CHECK();
+  return HUB_OK;
+}
+
+static int ensure_vec(float **p, int64_t n, const char *what);
 
 // z <- pass 1 (x planar double-float)
 static int run_up(hub_ctx *h, FastState *f, const float *x, float *z, cudaStream_t s) {
   const FastView v = fast_view(h, f);
-  count_launch(h);
   int rc = prof_mark(h, HUB_PROF_UP, true, s);
   if (rc) return rc;
-  rc = f->col16 ? launch_up_t<uint16_t>(v, f, h->has_eps, x, z, s)
-                : launch_up_t<uint32_t>(v, f, h->has_eps, x, z, s);
-  if (rc) return rc;
+  if (f->staged) {
+    count_launch(h);
+    const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
+    const int grid = (int)std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms());
+    const size_t smem = up_smem(f);
+#define HUB_UP(C, E)                                                                                      \
+  do {                                                                                                    \
+    HUB_CUDA(cudaFuncSetAttribute(k_up<C, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage)); \
+    k_up<C, E><<<grid, threads, smem, s>>>(v, x, z);                                                     \
+  } while (0)
+    if (f->col16) {
+      if (h->has_eps) HUB_UP(uint16_t, true); else HUB_UP(uint16_t, false);
+    } else {
+      if (h->has_eps) HUB_UP(uint32_t, true); else HUB_UP(uint32_t, false);
+    }
+#undef HUB_UP
+    HUB_LAUNCH_CHECK();
+  } else {
+    const int64_t Dt = h->count[0] * 2 * f->ld_t;
+    if ((rc = ensure_vec(&f->xt, Dt, "transposed x")) || (rc = ensure_vec(&f->zt, Dt, "transposed z"))) return rc;
+    count_launch(h, 3);
+    if ((rc = transpose(h->count[1], h->count[0], f->ld, f->ld_t, x, f->xt, s))) return rc;
+    if ((rc = launch_dn<2>(f, v, side_up(h, f), f->xt, nullptr, f->zt, LzArgs{}, s))) return rc;
+    if ((rc = transpose(h->count[0], h->count[1], f->ld_t, f->ld, f->zt, z, s))) return rc;
+  }
   return prof_mark(h, HUB_PROF_UP, false, s);
 }
 
@@ -1148,10 +1174,8 @@ static int run_dn(hub_ctx *h, FastState *f, int mode, const float *x, const floa
   count_launch(h);
   int rc = prof_mark(h, HUB_PROF_DN, true, s);
   if (rc) return rc;
-  if (mode == 0)
-    rc = f->col16 ? launch_dn_t<uint16_t, 0>(v, x, z, w, L, s) : launch_dn_t<uint32_t, 0>(v, x, z, w, L, s);
-  else
-    rc = f->col16 ? launch_dn_t<uint16_t, 1>(v, x, z, w, L, s) : launch_dn_t<uint32_t, 1>(v, x, z, w, L, s);
+  const Side S = side_dn(h, f);
+  rc = mode == 0 ? launch_dn<0>(f, v, S, x, z, w, L, s) : launch_dn<1>(f, v, S, x, z, w, L, s);
   if (rc) return rc;
   return prof_mark(h, HUB_PROF_DN, false, s);
 }
@@ -1214,8 +1238,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   if ((rc = ensure_vec(&f->zdf, Dp, "apply scratch z"))) return rc;
   const int G = grid_vec();
   const Quads Q = quads(h, f);
-  const FastView v0 = fast_view(h, f);
-  const dim3 gd = dn_grid(v0);
+  const dim3 gd = dn_grid(side_dn(h, f));
   const int64_t n_dn_blocks = (int64_t)gd.x * gd.y;
   constexpr int kTmp = 2048;                      // first-stage slots of the alpha reduction
   if ((rc = ensure_partials(h, std::max<int64_t>(n_dn_blocks, G) + kTmp))) return rc;
