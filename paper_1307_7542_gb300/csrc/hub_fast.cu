@@ -421,6 +421,9 @@ constexpr int kDnRows = 32, kDnLaneCols = HUB_DN_LANE_COLS, kDnCols = 32 * kDnLa
 #ifndef HUB_DN_BATCH
 #define HUB_DN_BATCH 2   // strip rows whose loads are issued together in pass 2
 #endif
+#ifndef HUB_DN_MINB
+#define HUB_DN_MINB 5    // resident pass-2 CTAs per SM that the register allocation aims for
+#endif
 
 // The hopping side a row-combination pass works on: the rows of the matrix it reads are the
 // states of this side, its columns (n_cols valid of ld) the states of the other side.
@@ -506,7 +509,7 @@ __device__ __forceinline__ void stv(float *p, const Vec<kLane> &a) {
 // kMode 2: pass 1 on X^T (side = spin up, rows of x are spin-up states, columns spin-down
 //          states): w = t S_up + diag x, diag from the two basis strings (no z).
 template <typename Col, int kMode>
-__global__ void __launch_bounds__(kDnThreads) k_dn(const FastView F, const Side S, const float *__restrict__ x,
+__global__ void __launch_bounds__(kDnThreads, HUB_DN_MINB) k_dn(const FastView F, const Side S, const float *__restrict__ x,
                                                   const float *z, float *w, LzArgs L) {
   constexpr int kLane = kDnLaneCols / 2;               // packed pairs per lane
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
