@@ -938,13 +938,20 @@ int fast_build(hub_ctx *h) {
                            f->eps_up_slot);
     HUB_LAUNCH_CHECK();
     if (f->staged) {
-      // per slice and group: schedule the lanes' entries into steps in which at most two lanes
-      // of the warp hit the same bank (slot mod 32), i.e. at most two shared-memory wavefronts
-      // per 32-bit load.  Greedy: lanes with the most remaining entries are served first; each
-      // takes the entry of the most loaded bank that still has room.  (A conflict-free
-      // schedule needs about 1.7x more steps on the 4x4 lattice because the bank loads are
-      // uneven; two per bank costs a few per cent more steps than the longest row.)
-      constexpr int kBankCap = 2;
+      // Per slice and group, the lanes' entries are scheduled into steps; the 32-bit loads of
+      // one step cost as many shared-memory wavefronts as the most used bank (column mod 32)
+      // has distinct columns in it.  Greedy: lanes with the most remaining entries first; each
+      // takes a column already used in the step (a broadcast), else one of the most loaded bank
+      // that is still under the cap.  Pass 1 is limited by both instruction issue (steps) and
+      // shared-memory wavefronts: on the 4x4 lattice a cap of two columns per bank and step
+      // runs fastest (steps within a few per cent of the longest lane); a cap of three saves
+      // steps but costs 20 % in time, and an adaptive cap (the busiest bank's remaining load
+      // over the remaining steps) saves 17 % of the wavefronts for 5 % more steps and runs 1 %
+      // slower.
+#ifndef HUB_BANK_CAP
+#define HUB_BANK_CAP 2   // columns per bank and step: k > 0 fixed, 0 adaptive, -k adaptive capped at k
+#endif
+      constexpr int kBankCap = HUB_BANK_CAP;
       // idle steps: the zero entry after the staged row when rows are staged, else a sentinel
       const bool staged = f->ld + 2 <= kUpPlane;
       const uint32_t idle = staged ? (uint32_t)f->ld : (f->col16 ? 0xffffu : 0xffffffffu);
@@ -957,44 +964,65 @@ int fast_build(hub_ctx *h) {
       for (int64_t sl = 0; sl < nsl; ++sl) {
         for (int grp = 0; grp < 2; ++grp) {
           std::vector<uint32_t> rem[32];
-          int bankload[32] = {0};
           for (int l = 0; l < 32; ++l) {
             const int64_t slot = sl * 32 + l;
             if (slot >= n) continue;
             const int32_t r = slot_row[slot];
             const int32_t a = grp == 0 ? rp[r] : spv[r], b = grp == 0 ? spv[r] : rp[r + 1];
-            for (int32_t k = a; k < b; ++k) {
-              rem[l].push_back((uint32_t)slot_of[col[k]]);
-              ++bankload[slot_of[col[k]] & 31];
-            }
+            for (int32_t k = a; k < b; ++k) rem[l].push_back((uint32_t)slot_of[col[k]]);
           }
           warp_steps.clear();
+          std::vector<uint32_t> distinct;
           for (;;) {
             int lanes[32], nl = 0;
+            size_t left = 0;
+            distinct.clear();
             for (int l = 0; l < 32; ++l)
-              if (!rem[l].empty()) lanes[nl++] = l;
+              if (!rem[l].empty()) {
+                lanes[nl++] = l;
+                left = std::max(left, rem[l].size());
+                distinct.insert(distinct.end(), rem[l].begin(), rem[l].end());
+              }
             if (!nl) break;
+            std::sort(distinct.begin(), distinct.end());
+            distinct.erase(std::unique(distinct.begin(), distinct.end()), distinct.end());
+            int bankload[32] = {0};
+            for (uint32_t c : distinct) ++bankload[c & 31];
+            const int maxload = *std::max_element(bankload, bankload + 32);
+            const int need = std::max(1, (int)((maxload + left - 1) / left));
+            const int cap = kBankCap > 0 ? kBankCap : (kBankCap < 0 ? std::min(-kBankCap, need) : need);
             std::stable_sort(lanes, lanes + nl, [&](int a, int b) { return rem[a].size() > rem[b].size(); });
             std::vector<uint32_t> step(32, idle);
+            uint32_t used_col[32][8];
             int used[32] = {0};
+            auto in_step = [&](uint32_t c) {
+              const int bk = c & 31;
+              for (int i = 0; i < used[bk]; ++i)
+                if (used_col[bk][i] == c) return true;
+              return false;
+            };
             for (int q = 0; q < nl; ++q) {
               const int l = lanes[q];
-              int best = -1;
+              int best = -1, best_shared = 0, best_load = 0, best_used = 0;
               for (int e = 0; e < (int)rem[l].size(); ++e) {
-                const int bk = rem[l][e] & 31;
-                if (used[bk] >= kBankCap) continue;
-                if (best < 0) {
+                const uint32_t c = rem[l][e];
+                const int bk = c & 31;
+                const int shared = in_step(c) ? 1 : 0;
+                if (!shared && (used[bk] >= cap || used[bk] >= 8)) continue;
+                const bool better = best < 0 || shared > best_shared ||
+                                    (shared == best_shared && (bankload[bk] > best_load ||
+                                                               (bankload[bk] == best_load && used[bk] < best_used)));
+                if (better) {
                   best = e;
-                  continue;
+                  best_shared = shared;
+                  best_load = bankload[bk];
+                  best_used = used[bk];
                 }
-                const int bb = rem[l][best] & 31;
-                if (bankload[bk] > bankload[bb] || (bankload[bk] == bankload[bb] && used[bk] < used[bb])) best = e;
               }
               if (best < 0) continue;
               const uint32_t c = rem[l][best];
               step[l] = c;
-              ++used[c & 31];
-              --bankload[c & 31];
+              if (!best_shared) used_col[c & 31][used[c & 31]++] = c;
               rem[l].erase(rem[l].begin() + best);
             }
             warp_steps.push_back(step);
