@@ -30,6 +30,8 @@ FALLBACK_HBM_GBS = 6800.0
 # FP64 issue rate of the GB300: the nominal 1.25 TFLOP/s dense FP64 counts an FMA as two
 # flops, i.e. 152 SMs x 2 FP64 instructions/clock x 2.07 GHz = 0.629e12 instructions/s.
 FP64_INSTR_PEAK = 152 * 2 * 2.07e9
+SMEM_PEAK_TBS = 28.7          # shared-memory load bandwidth, conflict-free, all SMs (probe)
+STAGE_MAX_COLS = 14076        # rows up to this length are staged in shared memory by pass 1
 
 
 def parse():
@@ -384,6 +386,14 @@ def run_gpu(a):
         up_avg, dn_avg = up_ms / n_up_l, dn_ms / n_dn_l
         passes = {"k_up": {"ms": up_avg, "algorithmic_bytes": 16 * D, "gbs": gb(16 * D, up_avg)},
                   "k_dn": {"ms": dn_avg, "algorithmic_bytes": 40 * D, "gbs": gb(40 * D, dn_avg)}}
+        if m.count_up <= STAGE_MAX_COLS:
+            # pass 1 gathers from shared memory: 8 B (high and low word) per spin-up hop and
+            # for the diagonal's own element, per element of X
+            smem_bytes = 8 * (nnz_u + m.count_up) * m.count_dn
+            passes["k_up"]["shared_memory"] = {
+                "algorithmic_bytes": smem_bytes, "tbs": gb(smem_bytes, up_avg) / 1000.0,
+                "peak_tbs": SMEM_PEAK_TBS, "frac": gb(smem_bytes, up_avg) / 1000.0 / SMEM_PEAK_TBS,
+                "peak_source": "probe: conflict-free 64-bit shared loads, all SMs (GB300)"}
         dom = max(passes, key=lambda k: passes[k]["ms"])
         roofline = {"bound": "hbm", "kernel": dom, "achieved": passes[dom]["gbs"], "peak": hbm_gbs,
                     "unit": "GB/s", "frac": passes[dom]["gbs"] / hbm_gbs, "traffic": None,
