@@ -31,6 +31,10 @@ FALLBACK_HBM_GBS = 6800.0
 # flops, i.e. 152 SMs x 2 FP64 instructions/clock x 2.07 GHz = 0.629e12 instructions/s.
 FP64_INSTR_PEAK = 152 * 2 * 2.07e9
 SMEM_PEAK_TBS = 28.7          # shared-memory load bandwidth, conflict-free, all SMs (probe)
+# DRAM bytes (read + write) per element of X from one ncu capture of the same kernels on the
+# 4x4 (6,6) sector (profiles/k_up_k_dn_4x4_sector66.md); the per-element traffic does not depend
+# on the sector, so a launch's traffic is this times D
+NCU_DRAM_BYTES_PER_ELEMENT = {"k_up": 0.982509e9 / 64128064, "k_dn": 2.137257e9 / 64128064}
 STAGE_MAX_COLS = 14076        # rows up to this length are staged in shared memory by pass 1
 
 
@@ -395,8 +399,12 @@ def run_gpu(a):
                 "peak_tbs": SMEM_PEAK_TBS, "frac": gb(smem_bytes, up_avg) / 1000.0 / SMEM_PEAK_TBS,
                 "peak_source": "probe: conflict-free 64-bit shared loads, all SMs (GB300)"}
         dom = max(passes, key=lambda k: passes[k]["ms"])
+        staged_4x4 = a.workload.startswith("4x4") and m.count_up <= STAGE_MAX_COLS
+        traffic = NCU_DRAM_BYTES_PER_ELEMENT[dom] * D if staged_4x4 else None
         roofline = {"bound": "hbm", "kernel": dom, "achieved": passes[dom]["gbs"], "peak": hbm_gbs,
-                    "unit": "GB/s", "frac": passes[dom]["gbs"] / hbm_gbs, "traffic": None,
+                    "unit": "GB/s", "frac": passes[dom]["gbs"] / hbm_gbs, "traffic": traffic,
+                    "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on "
+                                       "the 4x4 (6,6) sector, scaled by elements" if traffic else None),
                     "peak_source": peak_src, "passes": passes, "apply": apply}
     else:
         # native FP64 kernel: bound by the FP64 pipe
