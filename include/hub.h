@@ -133,6 +133,51 @@ int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, dou
 int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host, int cap, int *n);
 
 /*
+ * One-particle Green's function at zero temperature (Sec. VII, Eq. count8):
+ *   G_s(p, z) = <psi0| c_ps (z + E0 - H)^-1 c+_ps |psi0> + <psi0| c+_ps (z - E0 + H)^-1 c_ps |psi0>,
+ * each term a continued fraction from the Lanczos recurrence started at c+_ps psi0 or
+ * c_ps psi0.  Three calls: hub_ladder forms the start vector, hub_green_coeffs runs the
+ * recurrence, hub_green_eval sums the continued fraction.
+ *
+ * hub_ladder: y = c+_{site,spin} x (create != 0) or c_{site,spin} x (create == 0), the vecin
+ * construction of Sec. VII.  x (device, length count_up * count_dn of `from`) is a vector of
+ * the sector of `from`; y (device, length of `to`) is written in the sector of `to`, which
+ * must have the same M, one more (create) or one fewer electron of the given spin and the
+ * same number of the other spin.  Layout of hub_apply (n = d * count_up + u).  The sign is
+ * the Jordan-Wigner sign of the operator order of Sec. II, Eq. 7 (all up operators before
+ * all down operators, ascending sites): (-1)^(electrons of the same spin on sites below
+ * `site`), times (-1)^N_up for a down-spin operator.  Entries of y whose state has no
+ * preimage are 0.  Every entry of y is +-1 times one entry of x or 0, so the result is exact.
+ * site in [0, M), spin HUB_SPIN_UP / HUB_SPIN_DN; x and y must not overlap.  The handles need
+ * only their bases (hub_basis); `to` keeps a map of count_{spin} ints of `to`.  Asynchronous
+ * on `stream`.  HUB_ERR_ARG on bad arguments or mismatched sectors.
+ */
+int hub_ladder(hub_t from, hub_t to, int site, int spin, int create, const double *x_dev, double *y_dev,
+               void *stream);
+
+/*
+ * Continued-fraction coefficients: k steps of the plain Lanczos recurrence of
+ * hub_lanczos_ground on handle h started from v (device, unnormalised, e.g. from
+ * hub_ladder).  Host outputs: alpha_host[k], beta_host[k] (alpha_j, beta_j as in
+ * hub_lanczos_coeffs; fewer than k when the Krylov space is exhausted, beta of the last
+ * step is then ~0), *norm2_host = |v|^2 and *k_out = steps done (0 with |v| = 0).  Blocks
+ * until done.  Uses h's Lanczos workspace.
+ */
+int hub_green_coeffs(hub_t h, const double *v_dev, int k, double *alpha_host, double *beta_host,
+                     double *norm2_host, int *k_out, void *stream);
+
+/*
+ * G(z) = norm2 / (z - s (alpha_0 - E0) - beta_0^2 / (z - s (alpha_1 - E0) - ... -
+ *        beta_{k-2}^2 / (z - s (alpha_{k-1} - E0))))
+ * at n_z complex points z = z_re[i] + i z_im[i]; s = +1 for the particle term (coefficients
+ * of c+ psi0 in sector N + 1), s = -1 for the hole term (c psi0 in sector N - 1) of
+ * Eq. count8.  Host arrays only, no GPU work; G = 0 when k = 0.  HUB_ERR_ARG on bad
+ * arguments.
+ */
+int hub_green_eval(int k, const double *alpha, const double *beta, double norm2, double E0, int sign, int n_z,
+                   const double *z_re, const double *z_im, double *g_re, double *g_im);
+
+/*
  * Many small ground states in one persistent kernel launch (Sec. VIII: an impurity solver
  * repeats the ground-state search for every sector and bath-parameter set).  One lattice
  * (1 <= M <= 16 sites, n_bonds bonds as in hub_hopping), n_params parameter sets

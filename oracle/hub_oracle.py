@@ -19,6 +19,11 @@ What it computes (all in FP64):
                     brute-force checks (no hop rule, no sign rule).
 * ``expectations`` -- <psi| dH/dtheta |psi> for every bond and site
                     (Hellmann-Feynman gradients), from the definition of H.
+* ``ladder``, ``green_cf`` -- c+ / c of one site and spin between two-spin
+                    sectors and the zero-temperature Green's function as the two
+                    continued fractions of Sec. VII, Eq. count8; ``green_lehmann``
+                    (dense eigenvectors) and ``free_green`` (U = 0, one-body
+                    orbitals) are independent routes to the same function.
 
 Every function states the passage it follows.  Where the paper is silent, the
 reading taken is stated in the docstring.
@@ -363,3 +368,117 @@ def nnz_spin(M: int, n_sigma: int, n_bonds: int) -> int:
     """Nonzeros of H_sigma: F * C(M-2, N_sigma - 1) with F = 2 * (number of bonds)
     (Sec. IV.A, for M > 2 and 0 < N_sigma < M)."""
     return 2 * n_bonds * comb(M - 2, n_sigma - 1)
+
+
+# --------------------------------------------------------------------------------------
+# One-particle Green's function at zero temperature (Sec. VII, Eq. count8).
+# --------------------------------------------------------------------------------------
+
+def _popcount(a: np.ndarray, bits: int) -> np.ndarray:
+    cnt = np.zeros(a.shape, dtype=np.int64)
+    for m in range(bits):
+        cnt += (a >> m) & 1
+    return cnt
+
+
+def ladder(M: int, B_from: np.ndarray, B_to: np.ndarray, site: int, spin: int, create: bool,
+           x: np.ndarray) -> np.ndarray:
+    """y = c+_{site,spin} x (create) or c_{site,spin} x, x in the sector with two-spin basis
+    B_from, y in the sector with basis B_to (Sec. VII, the vecin construction).  The mode of
+    (site, spin) is bit site + M*spin of the two-spin integer (Sec. II, Eq. 5), and the modes
+    are ordered as in Eq. 7, so the operator passes the occupied modes below its own:
+    c+_k |I> = (-1)^(set bits of I below k) |I + 2^k> and c_k |I> = (-1)^(...) |I - 2^k>.
+    A target state comes from the source state with its bit flipped, if that exists."""
+    bit = np.int64(1) << np.int64(site + M * spin)
+    I_to = B_to.astype(np.int64)
+    has = (I_to & bit) != 0
+    ok = has if create else ~has
+    I_src = I_to ^ bit
+    sign = np.where(_popcount(I_src & (bit - 1), 2 * M) % 2 == 0, 1.0, -1.0)
+    Bf = B_from.astype(np.int64)
+    idx = np.searchsorted(Bf, I_src)
+    idx_c = np.minimum(idx, Bf.size - 1) if Bf.size else idx
+    found = ok & (idx < Bf.size) & (Bf[idx_c] == I_src) if Bf.size else np.zeros(I_to.shape, bool)
+    y = np.zeros(B_to.size)
+    y[found] = sign[found] * np.asarray(x, dtype=np.float64)[idx[found]]
+    return y
+
+
+def continued_fraction(alpha, beta, norm2: float, E0: float, sign: int, z) -> np.ndarray:
+    """<v|(z - s (H - E0))^-1|v> from the Lanczos coefficients of v (Sec. VII): the (0, 0)
+    element of the resolvent of the tridiagonal T, norm2 / (z - s(a_0 - E0) - b_0^2 /
+    (z - s(a_1 - E0) - ...)), s = +1 particle term, -1 hole term of Eq. count8."""
+    z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
+    k = len(alpha)
+    if k == 0:
+        return np.zeros(z.shape, dtype=np.complex128)
+    f = z - sign * (alpha[k - 1] - E0)
+    for j in range(k - 2, -1, -1):
+        f = z - sign * (alpha[j] - E0) - beta[j] ** 2 / f
+    return norm2 / f
+
+
+def green_cf(model_plus: Model, B_plus: np.ndarray, v_plus: np.ndarray, model_minus: Model,
+             B_minus: np.ndarray, v_minus: np.ndarray, E0: float, z, k: int = 400) -> np.ndarray:
+    """Eq. count8 as the sum of the two continued fractions, each from up to k steps of the
+    plain Lanczos recurrence (``lanczos``) started at v_plus = c+ psi0 (sector N + 1) and
+    v_minus = c psi0 (sector N - 1); an empty or zero start vector contributes 0."""
+    g = np.zeros(np.atleast_1d(z).shape, dtype=np.complex128)
+    for model, B, v, s in ((model_plus, B_plus, v_plus, 1), (model_minus, B_minus, v_minus, -1)):
+        if v is None or v.size == 0 or not np.any(v):
+            continue
+        r = lanczos(model, B, v, maxit=min(k, v.size), fixed_iters=True)
+        g += continued_fraction(r["alpha"], r["beta"], float(np.dot(v, v)), E0, s, z)
+    return g
+
+
+def green_lehmann(model: Model, n_up: int, n_dn: int, site: int, spin: int, z) -> np.ndarray:
+    """Eq. count8 from the Lehmann sum over dense eigenvectors (tiny clusters, 2M <= 14):
+    sum_m |<m|c+|psi0>|^2 / (z - (E_m - E0)) + sum_m |<m|c|psi0>|^2 / (z + (E_m - E0)), with
+    H from Jordan-Wigner operator matrices (``dense_fock``) and c from ``_annihilator``
+    (no ladder rule).  The ground state of (n_up, n_dn) must be non-degenerate."""
+    M = model.M
+    L = 2 * M
+    k = site + M * spin
+    c = _annihilator(L, k).toarray()
+    I = np.arange(1 << L)
+    pu = np.array([bin(v & ((1 << M) - 1)).count("1") for v in I])
+    pd = np.array([bin(v >> M).count("1") for v in I])
+
+    def sector(nu, nd):
+        return I[(pu == nu) & (pd == nd)]
+
+    S0 = sector(n_up, n_dn)
+    w0, V0 = np.linalg.eigh(dense_fock(model, n_up, n_dn))
+    assert w0.size < 2 or w0[1] - w0[0] > 1e-8, "degenerate ground state"
+    E0, psi = w0[0], V0[:, 0]
+    z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
+    g = np.zeros(z.shape, dtype=np.complex128)
+    for dn_, s, op in ((1, 1, c.T), (-1, -1, c)):
+        nu, nd = (n_up + dn_, n_dn) if spin == 0 else (n_up, n_dn + dn_)
+        if not (0 <= nu <= M and 0 <= nd <= M):
+            continue
+        S1 = sector(nu, nd)
+        v = op[np.ix_(S1, S0)] @ psi
+        w1, V1 = np.linalg.eigh(dense_fock(model, nu, nd))
+        amp = V1.T @ v
+        for a2, Em in zip(amp ** 2, w1):
+            g += a2 / (z - s * (Em - E0))
+    return g
+
+
+def free_green(model: Model, n_sigma: int, site: int, z) -> np.ndarray:
+    """U = 0: the Green's function of a non-interacting ground state (lowest n_sigma one-body
+    orbitals phi_k of h_ij = -t_ij, h_ii = eps_i filled, gap above them) is
+    sum_k |phi_k(site)|^2 / (z - e_k) over all orbitals: adding an electron to an empty
+    orbital costs e_k, removing one from a filled orbital gives E_m - E0 = -e_k."""
+    M = model.M
+    h = np.diag(model.eps.copy())
+    for b, (i, j) in enumerate(model.bonds.tolist()):
+        h[i, j] -= model.t[b]
+        h[j, i] -= model.t[b]
+    e, phi = np.linalg.eigh(h)
+    if 0 < n_sigma < M:
+        assert e[n_sigma] - e[n_sigma - 1] > 1e-8, "open shell: degenerate ground state"
+    z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
+    return np.sum(phi[site, :] ** 2 / (z[:, None] - e[None, :]), axis=1)

@@ -1316,6 +1316,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float) * Dp, s));
   HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
   HUB_CUDA(cudaStreamSynchronize(s));
+  h->start_norm = h->h_scal[1];
   if (!(h->h_scal[1] > 0.0) || !std::isfinite(h->h_scal[1]))
     return fail(HUB_ERR_ARG, "hub_lanczos_ground: start vector is zero or not finite");
   double b_cur = h->h_scal[1];

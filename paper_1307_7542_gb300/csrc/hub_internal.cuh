@@ -100,6 +100,12 @@ struct hub_ctx {
   // host-buffer apply
   double *hx = nullptr, *hy = nullptr;
 
+  // |x0| of the last Lanczos run (the continued fraction of the Green's function needs it)
+  double start_norm = 0.0;
+  // source index and sign per state of this handle's sector for hub_ladder
+  int32_t *ladder_map = nullptr;
+  int64_t ladder_cap = 0;
+
   // measurement: event pairs per kind (HUB_PROF_*), launch counters
   bool prof = false;
   std::vector<cudaEvent_t> ev_start[3], ev_end[3];
@@ -153,6 +159,23 @@ inline void count_launch(hub_ctx *h, int n = 1) {
 }
 
 // Device helpers ------------------------------------------------------------------------
+// Combinatorial number system (Sec. II, App. A).  binom[n * kB + k] = C(n, k);
+// rank(s) = sum_j C(b_j, j) over the set bits b_1 < b_2 < ... of s (j = 1, 2, ...), the
+// position of s in the ascending list of strings with its number of ones.
+constexpr int kB = kMaxSites + 1;
+
+__device__ __forceinline__ uint32_t rank_of(uint32_t s, const uint64_t *__restrict__ C) {
+  uint32_t r = 0;
+  int j = 1;
+  while (s) {
+    int b = __ffs(s) - 1;
+    r += (uint32_t)C[b * kB + j];
+    ++j;
+    s &= s - 1;
+  }
+  return r;
+}
+
 __host__ __device__ inline int popc32(uint32_t v) {
 #ifdef __CUDA_ARCH__
   return __popc(v);

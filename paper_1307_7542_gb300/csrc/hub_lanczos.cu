@@ -273,6 +273,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
   HUB_CUDA(cudaMemsetAsync(scal + 2, 0, sizeof(double), s));
   HUB_CUDA(cudaMemcpyAsync(h->h_scal + 3, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
   HUB_CUDA(cudaStreamSynchronize(s));
+  h->start_norm = h->h_scal[3];
   if (!(h->h_scal[3] > 0.0) || !std::isfinite(h->h_scal[3]))
     return fail(HUB_ERR_ARG, "hub_lanczos_ground: start vector is zero or not finite");
 

@@ -76,23 +76,6 @@ int ensure_partials(hub_ctx *h, int64_t n) {
   return HUB_OK;
 }
 
-// ---------------------------------------------------------------------------------------
-// Combinatorial number system.  binom[n * (kMaxSites + 1) + k] = C(n, k).
-// rank(s) = sum_j C(b_j, j) over the set bits b_1 < b_2 < ... of s (j = 1, 2, ...).
-// ---------------------------------------------------------------------------------------
-constexpr int kB = kMaxSites + 1;
-
-__device__ __forceinline__ uint32_t rank_of(uint32_t s, const uint64_t *__restrict__ C) {
-  uint32_t r = 0;
-  int j = 1;
-  while (s) {
-    int b = __ffs(s) - 1;
-    r += (uint32_t)C[b * kB + j];
-    ++j;
-    s &= s - 1;
-  }
-  return r;
-}
 
 // K1: thread r writes the r-th M-bit string with N ones in ascending order.  Walking from
 // the top bit down, C(b, k) strings keep bit b clear with k ones left in bits 0..b-1, and
@@ -562,6 +545,7 @@ extern "C" void hub_free(hub_t h) {
   }
   for (int k = 0; k < 3; ++k) dev_free(h->work[k]);
   dev_free(h->psi_tmp);
+  dev_free(h->ladder_map);
   dev_free(h->d_scal);
   dev_free(h->partials);
   if (h->h_scal) cudaFreeHost(h->h_scal);

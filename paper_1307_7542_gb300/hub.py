@@ -42,6 +42,9 @@ SIGNATURES = {
     "hub_apply_host": (_i, [_p, _p, _p, _p]),
     "hub_lanczos_ground": (_i, [_p, _p, _i, _d, ctypes.POINTER(_d), _p, ctypes.POINTER(_i), _p]),
     "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
+    "hub_ladder": (_i, [_p, _p, _i, _i, _i, _p, _p, _p]),
+    "hub_green_coeffs": (_i, [_p, _p, _i, _p, _p, ctypes.POINTER(_d), ctypes.POINTER(_i), _p]),
+    "hub_green_eval": (_i, [_i, _p, _p, _d, _d, _i, _i, _p, _p, _p, _p]),
     "hub_grad": (_i, [_p, _p, _p, _p, _p, _p]),
     "hub_apply_vjp": (_i, [_p, _p, _p, _p, _p, _p, _p, _p]),
     "hub_grad_noalloc": (_i, [_p, _p, _p, _p, _p, _p]),
@@ -175,6 +178,32 @@ def hub_grad(h, psi, n_bonds, M, stream=None):
     dt, dU, de = np.empty(n_bonds), np.empty(M), np.empty(M)
     _check(lib().hub_grad(h, _ptr(psi), _ptr(dt), _ptr(dU), _ptr(de), _stream(stream)))
     return dt, dU, de
+
+
+def hub_ladder(h_from, h_to, site, spin, create, x, y, stream=None):
+    """y = c+_{site,spin} x (create) or c_{site,spin} x, from the sector of h_from to that of h_to."""
+    _check(lib().hub_ladder(h_from, h_to, site, spin, 1 if create else 0, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def hub_green_coeffs(h, v, k, stream=None):
+    """k Lanczos steps from v: (alpha, beta, |v|^2) of the continued fraction."""
+    a, b = np.empty(k), np.empty(k)
+    n2, n = _d(), _i()
+    _check(lib().hub_green_coeffs(h, _ptr(v), k, _ptr(a), _ptr(b), ctypes.byref(n2), ctypes.byref(n),
+                                  _stream(stream)))
+    return a[: n.value], b[: n.value], n2.value
+
+
+def hub_green_eval(alpha, beta, norm2, E0, sign, z):
+    """Continued fraction of the particle (sign +1) or hole (sign -1) term at complex points z."""
+    a = np.ascontiguousarray(alpha, dtype=np.float64)
+    b = np.ascontiguousarray(beta, dtype=np.float64)
+    z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
+    zr, zi = np.ascontiguousarray(z.real), np.ascontiguousarray(z.imag)
+    gr, gi = np.empty(z.size), np.empty(z.size)
+    _check(lib().hub_green_eval(a.size, _ptr(a), _ptr(b), norm2, E0, sign, z.size, _ptr(zr), _ptr(zi),
+                                _ptr(gr), _ptr(gi)))
+    return gr + 1j * gi
 
 
 def hub_batch_ground(M, bonds, t, U, eps, job_nup, job_ndn, job_param, maxit=300, tol=1e-12, stream=None):

@@ -252,3 +252,126 @@ def test_table4_ring14():
     res = O.lanczos(m, B, W.normal(0, B.shape[0]), maxit=300, tol=1e-12)
     assert res["converged"]
     assert abs(res["E0"] - ref) < 2e-10
+
+
+# ---------------------------------------------------------------- Green's function (Sec. VII)
+
+def _sector_after(nu, nd, spin, d):
+    return (nu + d, nd) if spin == 0 else (nu, nd + d)
+
+
+@pytest.mark.parametrize("M,nu,nd", [(4, 2, 1), (5, 2, 3), (4, 0, 2), (5, 5, 1)])
+def test_ladder_canonical_anticommutators(M, nu, nd):
+    """The ladder operators obey {c_k, c+_l} = delta_kl and {c_k, c_l} = 0 on every vector:
+    both orders of a pair of ladder steps reach the same sector, and their sum is x for
+    k = l and 0 otherwise.  Any error in the Jordan-Wigner sign (a missing string, the wrong
+    side of the site, a missing N_up factor for spin down) breaks one of these."""
+    rng = np.random.default_rng(M * 100 + nu * 10 + nd)
+    B = O.basis(M, nu, nd)
+    x = rng.standard_normal(B.size)
+
+    def op(B_from, n_from, mode, create, v):
+        site, spin = mode % M, mode // M
+        n_to = _sector_after(*n_from, spin, 1 if create else -1)
+        if not (0 <= n_to[0] <= M and 0 <= n_to[1] <= M):
+            return None, n_to, None
+        B_to = O.basis(M, *n_to)
+        return O.ladder(M, B_from, B_to, site, spin, create, v), n_to, B_to
+
+    for k in range(2 * M):
+        for l in range(2 * M):
+            # c_k c+_l x + c+_l c_k x
+            total = None
+            for first, second in (((l, True), (k, False)), ((k, False), (l, True))):
+                v1, n1, B1 = op(B, (nu, nd), first[0], first[1], x)
+                if v1 is None:
+                    continue
+                v2, n2, B2 = op(B1, n1, second[0], second[1], v1)
+                if v2 is None:
+                    continue
+                total = v2 if total is None else total + v2
+            if total is not None:
+                want = x if k == l else np.zeros_like(total)
+                assert np.allclose(total, want, atol=1e-14), (k, l)
+            # c_k c_l x + c_l c_k x = 0
+            if k != l:
+                total = None
+                for a_, b_ in ((k, l), (l, k)):
+                    v1, n1, B1 = op(B, (nu, nd), b_, False, x)
+                    if v1 is None:
+                        continue
+                    v2, n2, B2 = op(B1, n1, a_, False, v1)
+                    if v2 is None:
+                        continue
+                    total = v2 if total is None else total + v2
+                if total is not None:
+                    assert np.allclose(total, 0.0, atol=1e-14), (k, l)
+
+
+@pytest.mark.parametrize("M,nu,nd,spin,site", [(4, 2, 1, 0, 1), (5, 2, 2, 1, 3), (5, 1, 3, 0, 0)])
+def test_ladder_matches_jordan_wigner_matrices(M, nu, nd, spin, site):
+    """The ladder rule equals the Jordan-Wigner operator matrices of the dense Fock-space
+    construction restricted to the two sectors (Sec. II, Eq. 7 operator order)."""
+    rng = np.random.default_rng(7)
+    L = 2 * M
+    c = O._annihilator(L, site + M * spin).toarray()
+    I = np.arange(1 << L)
+    B0 = O.basis(M, nu, nd)
+    x = rng.standard_normal(B0.size)
+    for create, d in ((True, 1), (False, -1)):
+        n1 = _sector_after(nu, nd, spin, d)
+        if not (0 <= n1[0] <= M and 0 <= n1[1] <= M):
+            continue
+        B1 = O.basis(M, *n1)
+        mat = (c.T if create else c)[np.ix_(B1.astype(np.int64), B0.astype(np.int64))]
+        assert np.array_equal(O.ladder(M, B0, B1, site, spin, create, x), mat @ x)
+
+
+def _disordered(M, seed, U=True):
+    r = W.uniform(seed, 3 * M + 8)
+    bonds = [tuple(b) for b in W.chain_bonds(M).tolist()] + [(0, M - 1), (1, M - 2)]
+    t = 1.0 + 0.3 * (r[: len(bonds)] - 0.5)
+    Uv = 4.0 + 2.0 * r[len(bonds): len(bonds) + M] if U else np.zeros(M)
+    eps = 0.4 * (r[2 * M + 2: 3 * M + 2] - 0.5)
+    return O.Model(M, np.array(bonds, dtype=np.int32), t, Uv, eps)
+
+
+@pytest.mark.parametrize("M,nu,nd,spin,site,seed", [(5, 2, 2, 0, 0, 1), (5, 2, 3, 1, 2, 2), (6, 3, 2, 0, 4, 3)])
+def test_green_continued_fraction_matches_lehmann(M, nu, nd, spin, site, seed):
+    """Eq. count8 as two Lanczos continued fractions (Sec. VII) equals the Lehmann sum over
+    the dense eigenvectors of the neighbouring sectors, for an interacting, disordered
+    cluster (per-bond t, per-site U and eps); psi0 from the dense ground state."""
+    m = _disordered(M, seed)
+    w, V = np.linalg.eigh(O.dense_fock(m, nu, nd))
+    assert w[1] - w[0] > 1e-6
+    E0, psi = w[0], V[:, 0]
+    B0 = O.basis(M, nu, nd)
+    vs = []
+    for create, d in ((True, 1), (False, -1)):
+        n1 = _sector_after(nu, nd, spin, d)
+        B1 = O.basis(M, *n1) if 0 <= min(n1) and max(n1) <= M else None
+        vs.append((B1, None if B1 is None else O.ladder(M, B0, B1, site, spin, create, psi)))
+    z = np.array([0.4 + 0.1j, -2.0 + 0.3j, 5.0 + 0.05j, 0.0 + 2.0j])
+    g = O.green_cf(m, vs[0][0], vs[0][1], m, vs[1][0], vs[1][1], E0, z, k=400)
+    ref = O.green_lehmann(m, nu, nd, site, spin, z)
+    assert np.max(np.abs(g - ref) / np.abs(ref)) < 1e-11
+    # spectral sum rule: |c+ psi0|^2 + |c psi0|^2 = <psi0|{c, c+}|psi0> = 1
+    assert abs(sum(float(v @ v) for _, v in vs if v is not None) - 1.0) < 1e-13
+
+
+@pytest.mark.parametrize("spin,site", [(0, 0), (0, 2), (1, 1)])
+def test_green_free_fermions(spin, site):
+    """U = 0 (open chain M = 6, three electrons of each spin, closed shell): the continued
+    fractions reproduce sum_k |phi_k(site)|^2 / (z - e_k) of the one-body orbitals."""
+    M = 6
+    m = O.Model(M, W.chain_bonds(M), 1.0, 0.0)
+    w, V = np.linalg.eigh(O.dense_fock(m, 3, 3))
+    E0, psi = w[0], V[:, 0]
+    B0 = O.basis(M, 3, 3)
+    Bp, Bm = O.basis(M, *_sector_after(3, 3, spin, 1)), O.basis(M, *_sector_after(3, 3, spin, -1))
+    vp = O.ladder(M, B0, Bp, site, spin, True, psi)
+    vm = O.ladder(M, B0, Bm, site, spin, False, psi)
+    z = np.array([0.3 + 0.2j, -1.1 + 0.05j, 2.5 + 0.5j, 1.0j])
+    g = O.green_cf(m, Bp, vp, m, Bm, vm, E0, z, k=400)
+    ref = O.free_green(m, 3, site, z)
+    assert np.max(np.abs(g - ref) / np.abs(ref)) < 1e-11
