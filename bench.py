@@ -235,7 +235,8 @@ def combine_ranks(elapsed_ms, steps, world, device):
 
 def extras(hub, W, torch):
     """Measurements beside the headline: batched vs one-at-a-time impurity solves, adjoint
-    gradients vs finite differences, and the 3x6 bandwidth-stress Lanczos step."""
+    gradients vs finite differences, the 3x6 bandwidth-stress Lanczos step and the 4x4
+    zero-temperature Green's function."""
     import numpy as np
     out = {}
     # (1) AIM star M=8: 81 sectors x 64 parameter sets, one persistent launch
@@ -312,6 +313,44 @@ def extras(hub, W, torch):
                         "apply_ms": ap_ms / max(n_ap, 1), "k_up_ms": up_ms / max(n_up_l, 1),
                         "k_dn_ms": dn_ms / max(n_dn_l, 1),
                         "apply_gbs_16B_per_element": 16 * D / (ap_ms / max(n_ap, 1) / 1000) / 1e9}
+    # (4) zero-temperature Green's function (Sec. VII) at 4x4 PBC, half filling, site 0, spin up:
+    # ground state of (8,8), c+ psi0 into (9,8) and c psi0 into (7,8), 100 continued-fraction
+    # steps for each term, G on 400 frequencies
+    w = W.square4x4(4.0)
+    m0 = hub.Hubbard(16, 8, 8, w["bonds"], w["t"], w["U"], w["eps"])
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    r0 = m0.ground(None, maxit=400, tol=1e-10, want_psi=True)
+    torch.cuda.synchronize()
+    t_gs = time.perf_counter() - t0
+    omega = np.linspace(-12.0, 12.0, 400) + 0.1j
+    G = np.zeros(omega.shape, dtype=np.complex128)
+    stages, norms, k_steps = {}, [], 100
+    for create, sign, nu in ((True, 1, 9), (False, -1, 7)):
+        m1 = hub.Hubbard(16, nu, 8, w["bonds"], w["t"], w["U"], w["eps"])
+        v = torch.empty(m1.D, dtype=torch.float64, device="cuda")
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        hub.hub_ladder(m0.h, m1.h, 0, 0, create, r0["psi"], v)
+        torch.cuda.synchronize()
+        t1 = time.perf_counter()
+        a_, b_, n2 = hub.hub_green_coeffs(m1.h, v, k_steps)
+        t2 = time.perf_counter()
+        G += hub.hub_green_eval(a_, b_, n2, r0["E0"], sign, omega)
+        t3 = time.perf_counter()
+        norms.append(n2)
+        key = "particle" if create else "hole"
+        stages[key] = {"sector": [nu, 8], "dim": m1.D, "ladder_ms": 1000 * (t1 - t0),
+                       "coeffs_s": t2 - t1, "steps": len(a_), "ms_per_step": 1000 * (t2 - t1) / max(len(a_), 1),
+                       "eval_ms": 1000 * (t3 - t2)}
+        m1.close()
+        del v
+    m0.close()
+    torch.cuda.empty_cache()
+    out["green_4x4"] = {"workload": "4x4 PBC (8,8), U=4: G_up(site 0, omega + 0.1i), 400 frequencies",
+                        "ground_state_s": t_gs, "ground_state_iters": r0["iters"], "E0": r0["E0"],
+                        "terms": stages, "sum_rule_norm2_total": sum(norms),
+                        "total_s": t_gs + sum(v_["coeffs_s"] + v_["ladder_ms"] / 1000 for v_ in stages.values())}
     return out
 
 
