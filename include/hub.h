@@ -133,6 +133,23 @@ int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, dou
 int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host, int cap, int *n);
 
 /*
+ * The ground state and a few low-lying excited states (Sec. IV: Lanczos for "the ground
+ * state and a few low-lying excited states"): maxit steps of the plain recurrence of
+ * hub_lanczos_ground from x0_dev (NULL: the seeded uniform start vector), then the
+ * eigenvalues of the tridiagonal T (bisection on Sturm counts).  Without
+ * re-orthogonalisation T acquires spurious copies of converged eigenvalues; they are removed
+ * by the Cullum-Willoughby test: numerically multiple eigenvalues of T are kept once, and a
+ * simple eigenvalue is discarded when T without its first row and column has it too
+ * (tolerance 1e-10 max(1, |T|)).  Returns the lowest n_found <= n_eig distinct values in
+ * eig_host (ascending) and, if resid_host != NULL, the residual estimate
+ * |beta_{k-1} s_{k-1}| of each (s the normalised eigenvector of T): values whose estimate
+ * is not small have not converged.  A single start vector resolves each eigenvalue once,
+ * whatever its multiplicity.  1 <= maxit <= 10000; blocks until done; host outputs.
+ */
+int hub_lanczos_spectrum(hub_t h, const double *x0_dev, int maxit, int n_eig, double *eig_host, double *resid_host,
+                         int *n_found, void *stream);
+
+/*
  * One-particle Green's function at zero temperature (Sec. VII, Eq. count8):
  *   G_s(p, z) = <psi0| c_ps (z + E0 - H)^-1 c+_ps |psi0> + <psi0| c+_ps (z - E0 + H)^-1 c_ps |psi0>,
  * each term a continued fraction from the Lanczos recurrence started at c+_ps psi0 or

@@ -482,3 +482,34 @@ def free_green(model: Model, n_sigma: int, site: int, z) -> np.ndarray:
         assert e[n_sigma] - e[n_sigma - 1] > 1e-8, "open shell: degenerate ground state"
     z = np.atleast_1d(np.asarray(z, dtype=np.complex128))
     return np.sum(phi[site, :] ** 2 / (z[:, None] - e[None, :]), axis=1)
+
+
+# --------------------------------------------------------------------------------------
+# A few low-lying eigenvalues from plain Lanczos (Sec. IV).
+# --------------------------------------------------------------------------------------
+
+def lanczos_spectrum(model: Model, B: np.ndarray, x0: np.ndarray, maxit: int, n_eig: int, rtol: float = 1e-10):
+    """The ground state and a few low-lying excited states (Sec. IV) from maxit steps of the
+    plain recurrence (``lanczos``).  Without re-orthogonalisation the tridiagonal T acquires
+    spurious copies of converged eigenvalues; reading: they are removed by the test of
+    Cullum and Willoughby (Lanczos Algorithms for Large Symmetric Eigenvalue Computations,
+    1985): a numerically multiple eigenvalue of T is kept once, a simple one is spurious if
+    T without its first row and column has it too (tolerance rtol * max(1, |T|)).  Returns
+    the lowest n_eig distinct kept values (ascending)."""
+    from scipy.linalg import eigvalsh_tridiagonal
+    r = lanczos(model, B, x0, maxit=maxit, fixed_iters=True)
+    a, b = r["alpha"], r["beta"]
+    k = a.size
+    mu = eigvalsh_tridiagonal(a, b[: k - 1]) if k > 1 else a.copy()
+    nu = eigvalsh_tridiagonal(a[1:], b[1: k - 1]) if k > 2 else (a[1:].copy() if k == 2 else np.zeros(0))
+    tol = rtol * max(1.0, float(np.max(np.abs(mu))))
+    good = []
+    i = 0
+    while i < k:
+        j = i + 1
+        while j < k and mu[j] - mu[j - 1] <= tol:
+            j += 1
+        if j - i > 1 or not np.any(np.abs(nu - mu[i]) <= tol):
+            good.append(float(mu[i]))
+        i = j
+    return np.array(good[:n_eig])

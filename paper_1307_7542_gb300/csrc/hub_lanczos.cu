@@ -8,6 +8,7 @@
 // do not depend on scheduling.  E0_j, the lowest eigenvalue of the tridiagonal T_j, is
 // found on the host by Sturm-sequence bisection; the ground-state vector comes from a
 // second pass with the eigenvector of T (inverse iteration).
+#include <algorithm>
 #include <cmath>
 #include <cstring>
 #include <vector>
@@ -220,6 +221,30 @@ std::vector<double> tridiag_vector(const double *a, const double *b, int k, doub
   return v;
 }
 
+// All eigenvalues of T in ascending order: the i-th is the smallest x with at least i + 1
+// eigenvalues below it, found by bisection on the Sturm count inside the Gershgorin interval.
+std::vector<double> tridiag_all(const double *a, const double *b, int k) {
+  std::vector<double> ev(k);
+  if (k <= 0) return ev;
+  double glo = INFINITY, ghi = -INFINITY;
+  for (int i = 0; i < k; ++i) {
+    const double r = (i ? fabs(b[i - 1]) : 0.0) + (i < k - 1 ? fabs(b[i]) : 0.0);
+    glo = fmin(glo, a[i] - r);
+    ghi = fmax(ghi, a[i] + r);
+  }
+  for (int j = 0; j < k; ++j) {
+    double lo = j ? ev[j - 1] : glo, hi = ghi;   // eigenvalues are sorted: start at the previous one
+    if (sturm_count(a, b, k, lo) >= j + 1) lo = glo;
+    for (int it = 0; it < 200; ++it) {
+      const double mid = 0.5 * (lo + hi);
+      if (mid <= lo || mid >= hi) break;
+      if (sturm_count(a, b, k, mid) >= j + 1) hi = mid; else lo = mid;
+    }
+    ev[j] = 0.5 * (lo + hi);
+  }
+  return ev;
+}
+
 static int ensure_workspace(hub_ctx *h, int64_t D) {
   for (int k = 0; k < 3; ++k)
     if (!h->work[k] && !dev_alloc((void **)&h->work[k], sizeof(double) * D, "Lanczos vector")) return HUB_ERR_OOM;
@@ -367,5 +392,52 @@ extern "C" int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host
     if (alpha_host) alpha_host[i] = h->alpha[i];
     if (beta_host) beta_host[i] = i < (int)h->beta.size() ? h->beta[i] : 0.0;   // last beta may be unknown
   }
+  return HUB_OK;
+}
+
+extern "C" int hub_lanczos_spectrum(hub_t h, const double *x0_dev, int maxit, int n_eig, double *eig_host,
+                                    double *resid_host, int *n_found, void *stream) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_lanczos_spectrum: NULL handle");
+  if (n_eig < 1 || !eig_host || !n_found || maxit < 1 || maxit > 10000)
+    return fail(HUB_ERR_ARG, "hub_lanczos_spectrum: bad argument");
+  double E0 = 0.0;
+  int it = 0;
+  int rc = hub_lanczos_ground(h, x0_dev, maxit, 0.0, &E0, nullptr, &it, stream);
+  if (rc < 0) return rc;
+  const int k = (int)h->alpha.size();
+  const double *a = h->alpha.data();
+  std::vector<double> b(h->beta.begin(), h->beta.end());
+  b.resize(k, 0.0);
+  const std::vector<double> mu = tridiag_all(a, b.data(), k);
+  const std::vector<double> nu = k > 1 ? tridiag_all(a + 1, b.data() + 1, k - 1) : std::vector<double>();
+  double scale = 1.0;
+  for (double m : mu) scale = fmax(scale, fabs(m));
+  const double tol = 1e-10 * scale;
+  // Cullum-Willoughby: numerically multiple eigenvalues of T are kept once; a simple one is
+  // spurious if the matrix without its first row and column has it as well.
+  std::vector<double> good;
+  for (int i = 0; i < k;) {
+    int j = i + 1;
+    while (j < k && mu[j] - mu[j - 1] <= tol) ++j;
+    const double m = mu[i];
+    bool keep = j - i > 1;
+    if (!keep) {
+      keep = true;
+      const auto p = std::lower_bound(nu.begin(), nu.end(), m - tol);
+      if (p != nu.end() && *p <= m + tol) keep = false;
+    }
+    if (keep) good.push_back(m);
+    i = j;
+  }
+  const int n = std::min<int>(n_eig, (int)good.size());
+  for (int i = 0; i < n; ++i) {
+    eig_host[i] = good[i];
+    if (resid_host) {
+      // |H y - theta y| for the Ritz pair: beta_{k-1} times the last component of T's eigenvector
+      const std::vector<double> v = tridiag_vector(a, b.data(), k, good[i]);
+      resid_host[i] = fabs(b[k - 1] * v[k - 1]);
+    }
+  }
+  *n_found = n;
   return HUB_OK;
 }

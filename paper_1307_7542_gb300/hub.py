@@ -42,6 +42,7 @@ SIGNATURES = {
     "hub_apply_host": (_i, [_p, _p, _p, _p]),
     "hub_lanczos_ground": (_i, [_p, _p, _i, _d, ctypes.POINTER(_d), _p, ctypes.POINTER(_i), _p]),
     "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
+    "hub_lanczos_spectrum": (_i, [_p, _p, _i, _i, _p, _p, ctypes.POINTER(_i), _p]),
     "hub_ladder": (_i, [_p, _p, _i, _i, _i, _p, _p, _p]),
     "hub_green_coeffs": (_i, [_p, _p, _i, _p, _p, ctypes.POINTER(_d), ctypes.POINTER(_i), _p]),
     "hub_green_eval": (_i, [_i, _p, _p, _d, _d, _i, _i, _p, _p, _p, _p]),
@@ -178,6 +179,15 @@ def hub_grad(h, psi, n_bonds, M, stream=None):
     dt, dU, de = np.empty(n_bonds), np.empty(M), np.empty(M)
     _check(lib().hub_grad(h, _ptr(psi), _ptr(dt), _ptr(dU), _ptr(de), _stream(stream)))
     return dt, dU, de
+
+
+def hub_lanczos_spectrum(h, x0, maxit, n_eig, stream=None):
+    """Lowest n_eig distinct Ritz values (Cullum-Willoughby filtered) and their residual estimates."""
+    e, r = np.empty(n_eig), np.empty(n_eig)
+    n = _i()
+    _check(lib().hub_lanczos_spectrum(h, _ptr(x0), maxit, n_eig, _ptr(e), _ptr(r), ctypes.byref(n),
+                                      _stream(stream)))
+    return e[: n.value], r[: n.value]
 
 
 def hub_ladder(h_from, h_to, site, spin, create, x, y, stream=None):

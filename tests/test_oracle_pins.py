@@ -375,3 +375,45 @@ def test_green_free_fermions(spin, site):
     g = O.green_cf(m, Bp, vp, m, Bm, vm, E0, z, k=400)
     ref = O.free_green(m, 3, site, z)
     assert np.max(np.abs(g - ref) / np.abs(ref)) < 1e-11
+
+
+# ------------------------------------------------------- low-lying spectrum (Sec. IV)
+
+def _distinct(w, tol=1e-8):
+    out = []
+    for x in np.sort(w):
+        if not out or x - out[-1] > tol:
+            out.append(x)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("M,nu,nd,U", [(6, 3, 3, 4.0), (5, 2, 3, 2.0), (6, 2, 2, 8.0)])
+def test_lanczos_spectrum_matches_dense(M, nu, nd, U):
+    """Plain Lanczos run well past convergence (2x the dimension, so copies of converged
+    eigenvalues appear in T) and filtered by the Cullum-Willoughby test gives the lowest
+    distinct eigenvalues of the dense Hamiltonian."""
+    m = O.Model(M, W.chain_bonds(M), 1.0, U)
+    B = O.basis(M, nu, nd)
+    ref = _distinct(np.linalg.eigvalsh(O.dense_fock(m, nu, nd)))[:6]
+    got = O.lanczos_spectrum(m, B, W.normal(1, B.size), maxit=2 * B.size, n_eig=6)
+    assert got.size == ref.size
+    assert np.max(np.abs(got - ref)) < 1e-9 * max(1.0, np.max(np.abs(ref)))
+    # the unfiltered T does hold spurious copies: the test is not vacuous
+    r = O.lanczos(m, B, W.normal(1, B.size), maxit=2 * B.size, fixed_iters=True)
+    from scipy.linalg import eigvalsh_tridiagonal
+    mu = eigvalsh_tridiagonal(r["alpha"], r["beta"][:-1])
+    assert np.sum(np.abs(mu - ref[0]) < 1e-8) > 1
+
+
+def test_lanczos_spectrum_matches_arpack():
+    """Ring M = 8, (4,4), U = 4 (dimension 4900): the lowest distinct values equal those of
+    ARPACK (scipy eigsh) on the oracle's own apply."""
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    m = O.Model(8, W.ring_bonds(8), 1.0, 4.0)
+    B = O.basis(8, 4, 4)
+    op = LinearOperator((B.size, B.size), matvec=lambda v: O.apply(m, B, np.ascontiguousarray(v, dtype=np.float64)),
+                        dtype=np.float64)
+    w = eigsh(op, k=24, which="SA", tol=1e-13, v0=W.normal(3, B.size))[0]
+    ref = _distinct(w)[:5]
+    got = O.lanczos_spectrum(m, B, W.normal(2, B.size), maxit=400, n_eig=5)
+    assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
