@@ -7,6 +7,7 @@ declared in ``include/hub.h``.
 from __future__ import annotations
 
 import glob
+import json
 import os
 import shutil
 import subprocess
@@ -32,19 +33,36 @@ def sources():
     return sorted(glob.glob(os.path.join(CSRC, "*.cu")))
 
 
+TUNED = os.path.join(PKG, "tuned.json")
+
+
+def tuned_defines() -> list:
+    """Kernel shape knobs chosen by autotune.py on this GPU (tuned.json), as NAME=value."""
+    if not os.path.exists(TUNED):
+        return []
+    with open(TUNED) as f:
+        knobs = json.load(f).get("defines", {})
+    return [f"{k}={v}" for k, v in sorted(knobs.items())]
+
+
 def _stale() -> bool:
     if not os.path.exists(LIB):
         return True
     t = os.path.getmtime(LIB)
     deps = sources() + glob.glob(os.path.join(CSRC, "*.cuh")) + [os.path.join(ROOT, "include", "hub.h")]
+    if os.path.exists(TUNED):
+        deps.append(TUNED)
     return any(os.path.getmtime(p) > t for p in deps)
 
 
-def build(force: bool = False, verbose: bool = False, out: str | None = None, defines=()) -> str:
-    """Build libhub.so if any source is newer than it; return its path.  `out` and
-    `defines` (extra -D macros, e.g. kernel shape knobs) build a separate copy."""
+def build(force: bool = False, verbose: bool = False, out: str | None = None, defines=None) -> str:
+    """Build libhub.so if any source is newer than it; return its path.  The kernel knobs
+    come from tuned.json; `out` and `defines` (-D macros replacing those knobs) build a
+    separate copy, as the autotuner does for each candidate."""
     if out is None and not force and not _stale():
         return LIB
+    if defines is None:
+        defines = tuned_defines()
     lib_path = LIB if out is None else out
     build_dir = BUILD if out is None else os.path.dirname(os.path.abspath(out))
     os.makedirs(build_dir, exist_ok=True)

@@ -23,7 +23,10 @@ namespace hub {
 
 constexpr int kBatchMaxSites = 16;
 constexpr int kBatchMaxDim = 8192;      // three FP64 vectors of this length in shared memory
-constexpr int kBatchThreads = 512;
+#ifndef HUB_BATCH_THREADS
+#define HUB_BATCH_THREADS 512            // threads per CTA (one job per CTA at a time)
+#endif
+constexpr int kBatchThreads = HUB_BATCH_THREADS;
 constexpr int kBatchCheckEvery = 8;     // E0 of T_j is evaluated every this many iterations
 
 struct BatchTables {
