@@ -147,6 +147,7 @@ extern "C" int hub_apply_host(hub_t h, const double *x_host, double *y_host, voi
     }
   }
   cudaStream_t s = (cudaStream_t)stream;
+  if (use_fast(h)) return fast_apply_host(h, x_host, y_host, h->hx, h->hy, s);
   HUB_CUDA(cudaMemcpyAsync(h->hx, x_host, sizeof(double) * D, cudaMemcpyHostToDevice, s));
   rc = apply_launch(h, h->hx, h->hy, s);
   if (rc) return rc;

@@ -190,13 +190,13 @@ __device__ __forceinline__ int block_shift(const int *__restrict__ emax, int nbl
   return s_shift;
 }
 
-// out (planar, slot order) = 2^-shift x (FP64, rank order), shift from emax (0 when emax is
-// null); one row per block and step
-__global__ void k_f64_to_df(int64_t n_rows, int64_t n_up, int64_t ld, const double *__restrict__ x,
+// out (planar, slot order) = 2^-shift x (FP64, rank order) for rows r0 .. r1 - 1, shift from
+// emax (0 when emax is null); one row per block and step
+__global__ void k_f64_to_df(int64_t r0, int64_t r1, int64_t n_up, int64_t ld, const double *__restrict__ x,
                             const int *__restrict__ emax, int nblk, const int32_t *__restrict__ slot_row,
                             float *__restrict__ out) {
   const int shift = emax ? block_shift(emax, nblk) : 0;
-  for (int64_t d = blockIdx.x; d < n_rows; d += gridDim.x) {
+  for (int64_t d = r0 + blockIdx.x; d < r1; d += gridDim.x) {
     float *__restrict__ row = out + d * 2 * ld;
     const double *__restrict__ xr = x + d * n_up;
     for (int64_t u = threadIdx.x; u < ld; u += blockDim.x) {
@@ -208,17 +208,46 @@ __global__ void k_f64_to_df(int64_t n_rows, int64_t n_up, int64_t ld, const doub
 }
 
 // y[d][u] (FP64, rank order) = 2^shift * v[d][slot_of[u]] (planar double-float, slot
-// order), one row per block and step so that the gathers of a row are served from L1.
-__global__ void k_unpermute(int64_t n_rows, int64_t n_up, int64_t ld, const float *__restrict__ v,
+// order) for rows r0 .. r1 - 1, one row per block and step so that the gathers of a row are
+// served from L1.
+__global__ void k_unpermute(int64_t r0, int64_t r1, int64_t n_up, int64_t ld, const float *__restrict__ v,
                             const int32_t *__restrict__ slot_of, const int *__restrict__ emax, int nblk,
                             double *__restrict__ y) {
   const int shift = block_shift(emax, nblk);
-  for (int64_t d = blockIdx.x; d < n_rows; d += gridDim.x) {
+  for (int64_t d = r0 + blockIdx.x; d < r1; d += gridDim.x) {
     const float *__restrict__ row = v + d * 2 * ld;
     for (int64_t u = threadIdx.x; u < n_up; u += blockDim.x) {
       const int32_t s = slot_of[u];
       y[d * n_up + u] = df_to_f64(make_float2(row[s], row[ld + s]), shift);
     }
+  }
+}
+
+// flag = 1 if the largest exponent among emax[0 .. n_all) exceeds that of emax[0 .. n_first)
+__global__ void k_shift_check(const int *__restrict__ emax, int n_all, int n_first, int *__restrict__ flag) {
+  int a = 0, f = 0;
+  for (int k = threadIdx.x; k < n_all; k += blockDim.x) {
+    a = max(a, emax[k]);
+    if (k < n_first) f = max(f, emax[k]);
+  }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+    f = max(f, __shfl_xor_sync(0xffffffffu, f, o));
+  }
+  __shared__ int wa[32], wf[32];
+  if ((threadIdx.x & 31) == 0) {
+    wa[threadIdx.x >> 5] = a;
+    wf[threadIdx.x >> 5] = f;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
+      a = max(a, wa[k]);
+      f = max(f, wf[k]);
+    }
+    a = max(a, wa[0]);
+    f = max(f, wf[0]);
+    flag[0] = a > f ? 1 : 0;
   }
 }
 
@@ -241,7 +270,7 @@ constexpr int kUpPlane = 14080;
 
 template <typename Col, bool kEps>
 __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *__restrict__ x,
-                                                float *__restrict__ z) {
+                                                float *__restrict__ z, int64_t p_begin, int64_t p_end) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *xs = reinterpret_cast<float *>(smem_raw);
   __shared__ __align__(8) uint64_t bar;
@@ -256,9 +285,8 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
     fence_mbar_init();
   }
   __syncthreads();
-  const int64_t n_pairs = (F.n_dn + 1) / 2;
   uint32_t phase = 0;
-  for (int64_t p = blockIdx.x; p < n_pairs; p += gridDim.x) {
+  for (int64_t p = p_begin + blockIdx.x; p < p_end; p += gridDim.x) {   // row pairs p_begin .. p_end - 1
     const int64_t d0 = 2 * p, d1 = (2 * p + 1 < F.n_dn) ? 2 * p + 1 : 2 * p;   // odd tail: same row twice
     if (tid == 0) {
       const float *r0 = x + d0 * 2 * ld, *r1 = x + d1 * 2 * ld;
@@ -269,7 +297,7 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
       bulk_g2s(xs + 2 * kUpPlane, r1, pbytes, &bar);
       bulk_g2s(xs + 3 * kUpPlane, r1 + ld, pbytes, &bar);
       const int64_t pn = p + gridDim.x;
-      if (pn < n_pairs) {
+      if (pn < p_end) {
         prefetch_l2(x + 2 * pn * 2 * ld, 2 * pbytes);
         if (2 * pn + 1 < F.n_dn) prefetch_l2(x + (2 * pn + 1) * 2 * ld, 2 * pbytes);
       }
@@ -817,6 +845,10 @@ struct FastState {
   int *d_emax = nullptr;
   int *d_err = nullptr;
   int64_t ld = 0;
+  // pipelined host-buffer apply: copy stream, per-chunk events, exponent partials, flag
+  cudaStream_t copy_stream = nullptr;
+  std::vector<cudaEvent_t> events;
+  int *d_emax_chunks = nullptr, *d_flag = nullptr, *h_flag = nullptr;
 };
 
 static FastState *fast_of(const hub_ctx *h) { return h->fast; }
@@ -837,6 +869,11 @@ void fast_release(hub_ctx *h) {
   dev_free(f->psi);
   dev_free(f->d_emax);
   dev_free(f->d_err);
+  dev_free(f->d_emax_chunks);
+  dev_free(f->d_flag);
+  if (f->h_flag) cudaFreeHost(f->h_flag);
+  for (cudaEvent_t e : f->events) cudaEventDestroy(e);
+  if (f->copy_stream) cudaStreamDestroy(f->copy_stream);
   dev_free(f->coef);
   dev_free(f->sl_add);
   dev_free(f->sl_sub);
@@ -1166,20 +1203,25 @@ static int transpose(int64_t n_r, int64_t n_c, int64_t ld_s, int64_t ld_d, const
 
 static int ensure_vec(float **p, int64_t n, const char *what);
 
-// z <- pass 1 (x planar double-float)
-static int run_up(hub_ctx *h, FastState *f, const float *x, float *z, cudaStream_t s) {
+// z <- pass 1 (x planar double-float); with staged rows, only the row pairs p0 .. p1 - 1
+// (p1 < 0: all pairs)
+static int run_up(hub_ctx *h, FastState *f, const float *x, float *z, cudaStream_t s, int64_t p0 = 0,
+                  int64_t p1 = -1) {
   const FastView v = fast_view(h, f);
+  if (p1 < 0) p1 = (v.n_dn + 1) / 2;
+  if (!f->staged && (p0 != 0 || p1 != (v.n_dn + 1) / 2)) return fail(HUB_ERR_STATE, "pass 1: partial range");
+  if (p1 <= p0) return HUB_OK;
   int rc = prof_mark(h, HUB_PROF_UP, true, s);
   if (rc) return rc;
   if (f->staged) {
     count_launch(h);
     const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
-    const int grid = (int)std::min<int64_t>((v.n_dn + 1) / 2, (int64_t)num_sms());
+    const int grid = (int)std::min<int64_t>(p1 - p0, (int64_t)num_sms());
     const size_t smem = up_smem(f);
 #define HUB_UP(C, E)                                                                                      \
   do {                                                                                                    \
     HUB_CUDA(cudaFuncSetAttribute(k_up<C, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage)); \
-    k_up<C, E><<<grid, threads, smem, s>>>(v, x, z);                                                     \
+    k_up<C, E><<<grid, threads, smem, s>>>(v, x, z, p0, p1);                                             \
   } while (0)
     if (f->col16) {
       if (h->has_eps) HUB_UP(uint16_t, true); else HUB_UP(uint16_t, false);
@@ -1230,13 +1272,106 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
   count_launch(h, 2);
   k_max_exp<<<G, 256, 0, s>>>(D, x, f->d_emax);
-  k_f64_to_df<<<row_grid(h), 256, 0, s>>>(h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->slot_row, f->xdf);
+  k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->slot_row,
+                                          f->xdf);
   HUB_LAUNCH_CHECK();
   if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
   if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s))) return rc;
   count_launch(h);
-  k_unpermute<<<row_grid(h), 512, 0, s>>>(h->count[1], h->count[0], f->ld, f->zdf, f->slot_of, f->d_emax, G, y);
+  k_unpermute<<<row_grid(h), 512, 0, s>>>(0, h->count[1], h->count[0], f->ld, f->zdf, f->slot_of, f->d_emax, G,
+                                          y);
   HUB_LAUNCH_CHECK();
+  return HUB_OK;
+}
+
+// hub_apply_host on the fast path with staged rows.  The input arrives in row chunks on a copy
+// stream while the compute stream converts each chunk and runs pass 1 on its row pairs; after
+// pass 2 the output goes back in row chunks while later chunks are un-permuted.  The
+// power-of-two scale of the conversion is taken from the first chunk's largest exponent; if
+// the whole vector's largest exponent is larger, conversion and pass 1 are redone with it, so
+// the result is bit for bit that of hub_apply.  xd, yd: the handle's FP64 device buffers.
+constexpr int kHostChunks = 8;
+
+int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd, double *yd, cudaStream_t s) {
+  FastState *f = fast_of(h);
+  if (!f || !f->built) return fail(HUB_ERR_STATE, "fast apply: not built");
+  const int64_t n_up = h->count[0], n_dn = h->count[1];
+  if (!f->staged || n_dn < 2 * kHostChunks) {   // one piece: copy in, apply, copy out
+    HUB_CUDA(cudaMemcpyAsync(xd, x_host, sizeof(double) * n_up * n_dn, cudaMemcpyHostToDevice, s));
+    int rc = fast_apply_f64(h, xd, yd, s);
+    if (rc) return rc;
+    HUB_CUDA(cudaMemcpyAsync(y_host, yd, sizeof(double) * n_up * n_dn, cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    return HUB_OK;
+  }
+  const int64_t Dp = n_dn * 2 * f->ld;
+  int rc;
+  if ((rc = ensure_vec(&f->xdf, Dp, "apply scratch x")) || (rc = ensure_vec(&f->zdf, Dp, "apply scratch z")))
+    return rc;
+  const int G = grid_vec();
+  if (!f->d_emax_chunks &&
+      (!dev_alloc((void **)&f->d_emax_chunks, sizeof(int) * G * kHostChunks, "exponent partials") ||
+       !dev_alloc((void **)&f->d_flag, sizeof(int), "scale flag")))
+    return HUB_ERR_OOM;
+  if (!f->h_flag) HUB_CUDA(cudaMallocHost((void **)&f->h_flag, sizeof(int)));
+  if (!f->copy_stream) HUB_CUDA(cudaStreamCreateWithFlags(&f->copy_stream, cudaStreamNonBlocking));
+  while ((int)f->events.size() < 2 * kHostChunks + 2) {
+    cudaEvent_t e;
+    HUB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    f->events.push_back(e);
+  }
+  cudaStream_t sc = f->copy_stream;
+  cudaEvent_t *ev_in = f->events.data(), *ev_out = ev_in + kHostChunks, ev_start = ev_in[2 * kHostChunks],
+              ev_end = ev_in[2 * kHostChunks + 1];
+  // row chunks with even boundaries, so that no pass-1 row pair straddles two chunks
+  const int64_t per = ((n_dn + kHostChunks - 1) / kHostChunks + 1) & ~(int64_t)1;
+  int nc = 0;
+  int64_t b[kHostChunks + 1];
+  for (int c = 0; c <= kHostChunks; ++c) b[c] = std::min<int64_t>((int64_t)c * per, n_dn);
+  while (nc < kHostChunks && b[nc + 1] > b[nc]) ++nc;
+  HUB_CUDA(cudaEventRecord(ev_start, s));
+  HUB_CUDA(cudaStreamWaitEvent(sc, ev_start, 0));
+  for (int c = 0; c < nc; ++c) {
+    HUB_CUDA(cudaMemcpyAsync(xd + b[c] * n_up, x_host + b[c] * n_up, sizeof(double) * (b[c + 1] - b[c]) * n_up,
+                             cudaMemcpyHostToDevice, sc));
+    HUB_CUDA(cudaEventRecord(ev_in[c], sc));
+  }
+  int *emax = f->d_emax_chunks;
+  const int rg = (int)std::min<int64_t>(per, (int64_t)num_sms() * 8);
+  for (int c = 0; c < nc; ++c) {
+    HUB_CUDA(cudaStreamWaitEvent(s, ev_in[c], 0));
+    count_launch(h, 2);
+    k_max_exp<<<G, 256, 0, s>>>((b[c + 1] - b[c]) * n_up, xd + b[c] * n_up, emax + c * G);
+    k_f64_to_df<<<rg, 256, 0, s>>>(b[c], b[c + 1], n_up, f->ld, xd, emax, G, f->slot_row, f->xdf);
+    HUB_LAUNCH_CHECK();
+    if ((rc = run_up(h, f, f->xdf, f->zdf, s, b[c] / 2, (b[c + 1] + 1) / 2))) return rc;
+  }
+  count_launch(h);
+  k_shift_check<<<1, 256, 0, s>>>(emax, nc * G, G, f->d_flag);
+  HUB_LAUNCH_CHECK();
+  HUB_CUDA(cudaMemcpyAsync(f->h_flag, f->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
+  HUB_CUDA(cudaStreamSynchronize(s));
+  int nblk = G;
+  if (*f->h_flag) {   // the largest exponent lies outside the first chunk: redo with the global one
+    nblk = nc * G;
+    count_launch(h);
+    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, n_dn, n_up, f->ld, xd, emax, nblk, f->slot_row, f->xdf);
+    HUB_LAUNCH_CHECK();
+    if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
+  }
+  if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s))) return rc;
+  for (int c = 0; c < nc; ++c) {
+    count_launch(h);
+    k_unpermute<<<rg, 512, 0, s>>>(b[c], b[c + 1], n_up, f->ld, f->zdf, f->slot_of, emax, nblk, yd);
+    HUB_LAUNCH_CHECK();
+    HUB_CUDA(cudaEventRecord(ev_out[c], s));
+    HUB_CUDA(cudaStreamWaitEvent(sc, ev_out[c], 0));
+    HUB_CUDA(cudaMemcpyAsync(y_host + b[c] * n_up, yd + b[c] * n_up, sizeof(double) * (b[c + 1] - b[c]) * n_up,
+                             cudaMemcpyDeviceToHost, sc));
+  }
+  HUB_CUDA(cudaEventRecord(ev_end, sc));
+  HUB_CUDA(cudaStreamWaitEvent(s, ev_end, 0));
+  HUB_CUDA(cudaStreamSynchronize(s));
   return HUB_OK;
 }
 
@@ -1282,7 +1417,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   // r_1 = x0 as double-float (no scaling), scal[1] = beta_0 = |x0|, scal[2] = 0
   auto start = [&](float *r) -> int {
     count_launch(h, 3);
-    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(h->count[1], h->count[0], f->ld, x0, nullptr, 0, f->slot_row, r);
+    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, h->count[1], h->count[0], f->ld, x0, nullptr, 0, f->slot_row, r);
     k_df_norm2<<<G, 256, 0, s>>>(Q, r, P);
     HUB_LAUNCH_CHECK();
     int rc2 = reduce_partials(P, G, scal + 1, 1, s);

@@ -145,6 +145,7 @@ bool fast_eligible(const hub_ctx *h);
 int fast_build(hub_ctx *h);
 void fast_release(hub_ctx *h);
 int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s);
+int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd, double *yd, cudaStream_t s);
 int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out, int *iters,
                  cudaStream_t s);
 int fast_check_error(hub_ctx *h);

@@ -442,6 +442,37 @@ def test_apply_host_buffers(hub):
         m.close()
 
 
+@pytest.mark.parametrize("case", ["max_in_first_chunk", "max_in_last_chunk", "odd_rows"])
+def test_apply_host_pipelined(hub, case):
+    """hub_apply_host on the fast path overlaps the copies with the passes in row chunks, with
+    the conversion scale taken from the first chunk and redone when a later chunk holds a
+    larger exponent: the result equals hub_apply bit for bit and the oracle within the
+    per-entry bound (pinned host buffers)."""
+    if case == "odd_rows":
+        M, nu, nd = 11, 5, 3                       # count_dn = C(11, 3) = 165 rows: odd tail pair
+    else:
+        M, nu, nd = 12, 6, 6                       # 924 x 924
+    bonds = W.ring_bonds(M)
+    m = hub.Hubbard(M, nu, nd, bonds, 1.0, 4.0)
+    om = O.Model(M, bonds, 1.0, 4.0)
+    try:
+        x = W.normal(17, m.D)
+        n_up = m.count_up
+        if case == "max_in_first_chunk":
+            x[: 2 * n_up] *= 64.0
+        elif case == "max_in_last_chunk":
+            x[-2 * n_up:] *= 1e6
+        xh = torch.from_numpy(x).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        hub.hub_apply_host(m.h, xh, yh)
+        yd = m.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+        assert np.array_equal(yh.numpy(), yd)
+        B = O.basis(M, nu, nd)
+        assert_entrywise(yh.numpy(), O.apply(om, B, x), abs_bound(om, B, x))
+    finally:
+        m.close()
+
+
 # --------------------------------------------------------------------------- autograd
 
 def test_autograd_apply(hub):
