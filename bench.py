@@ -461,6 +461,21 @@ def run_gpu(a):
         rl = m.ground(x0, maxit=a.lanczos_iters, tol=0.0)
         torch.cuda.synchronize()
         lanczos = {"E0": rl["E0"], "iterations": rl["iters"], "wall_s": time.perf_counter() - t0}
+        # time to |E0_j - E0_{j-1}| < 1e-12 for the three interaction strengths of the 4x4
+        # configuration (same lattice and start vector)
+        if a.workload == "4x4" and rank == 0:
+            conv = {}
+            for Uc in (2.0, 4.0, 8.0):
+                wc = workload(Uc, a.workload)
+                mc = hub.Hubbard(wc["M"], wc["n_up"], wc["n_dn"], wc["bonds"], wc["t"], wc["U"], wc["eps"])
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                rc_ = mc.ground(x0, maxit=1000, tol=1e-12)
+                torch.cuda.synchronize()
+                conv[f"U={Uc:g}"] = {"E0": rc_["E0"], "iterations": rc_["iters"],
+                                     "wall_s": time.perf_counter() - t0, "converged": rc_["status"] == 0}
+                mc.close()
+            lanczos["to_tol_1e-12"] = conv
 
     # end-to-end: the host-buffer apply through the C ABI (H2D + apply + D2H each step)
     e2e = None
