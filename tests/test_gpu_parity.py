@@ -609,3 +609,33 @@ def test_equal_spin_counts_share_tables(hub, M, n):
     for x, y in zip(a, b):
         assert np.array_equal(np.asarray(x), np.asarray(y))
     m.close()
+
+
+# ---------------------------------------- 32-bit column tables (a spin count above 65536)
+
+@pytest.mark.parametrize("nu,nd", [pytest.param(2, 10, marks=pytest.mark.slow), (10, 1)])
+def test_apply_wide_sectors(hub, nu, nd):
+    """M = 20 with C(20, 10) = 184,756 states of one spin, more than 16-bit column indices
+    hold: (2, 10) runs pass 1 on staged rows of 190 columns with 32-bit schedule words and
+    pass 2 with 32-bit strip rows; (10, 1) runs pass 1 on the transposed matrix (rows of
+    184,756 columns do not fit in shared memory).  Sampled rows against the oracle (whose
+    two-spin basis scan makes the first case slow)."""
+    M = 20
+    bonds = np.array([tuple(b) for b in W.ring_bonds(M).tolist()] + [(0, 10), (3, 17), (5, 12)], dtype=np.int32)
+    m = hub.Hubbard(M, nu, nd, bonds, 1.0, 3.0)
+    om = O.Model(M, bonds, 1.0, 3.0)
+    try:
+        B = O.basis(M, nu, nd)
+        x = W.normal(23, B.shape[0])
+        y = m.apply(torch.from_numpy(x).cuda()).cpu().numpy()
+        D = B.shape[0]
+        for r0 in (0, D // 2 + 5, D - 2000):
+            rows = (r0, min(D, r0 + 2000))
+            assert_entrywise(y[rows[0]:rows[1]], O.apply(om, B, x, rows=rows), abs_bound(om, B, x, rows=rows))
+        if D < 5_000_000:
+            # and a short Lanczos run agrees with the oracle's on the same start vector
+            r = m.ground(torch.from_numpy(x).cuda(), maxit=12, tol=0.0)
+            ro = O.lanczos(om, B, x, maxit=12, fixed_iters=True)
+            assert abs(r["E0"] - ro["E0"]) < 1e-10 * abs(ro["E0"])
+    finally:
+        m.close()
