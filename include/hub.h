@@ -144,7 +144,8 @@ int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host, int cap, 
  * eig_host (ascending) and, if resid_host != NULL, the residual estimate
  * |beta_{k-1} s_{k-1}| of each (s the normalised eigenvector of T): values whose estimate
  * is not small have not converged.  A single start vector resolves each eigenvalue once,
- * whatever its multiplicity.  1 <= maxit <= 10000; blocks until done; host outputs.
+ * whatever its multiplicity.  1 <= maxit <= 3000 (the host eigenvalue step is O(maxit^2));
+ * blocks until done; host outputs.
  */
 int hub_lanczos_spectrum(hub_t h, const double *x0_dev, int maxit, int n_eig, double *eig_host, double *resid_host,
                          int *n_found, void *stream);

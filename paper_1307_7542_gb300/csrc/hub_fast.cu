@@ -1292,6 +1292,9 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
 // the result is bit for bit that of hub_apply.  xd, yd: the handle's FP64 device buffers.
 constexpr int kHostChunks = 8;
 
+static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double *y_host, double *xd, double *yd,
+                         cudaStream_t s, const int64_t *b, int nc, int64_t per);
+
 int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd, double *yd, cudaStream_t s) {
   FastState *f = fast_of(h);
   if (!f || !f->built) return fail(HUB_ERR_STATE, "fast apply: not built");
@@ -1309,10 +1312,9 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
   if ((rc = ensure_vec(&f->xdf, Dp, "apply scratch x")) || (rc = ensure_vec(&f->zdf, Dp, "apply scratch z")))
     return rc;
   const int G = grid_vec();
-  if (!f->d_emax_chunks &&
-      (!dev_alloc((void **)&f->d_emax_chunks, sizeof(int) * G * kHostChunks, "exponent partials") ||
-       !dev_alloc((void **)&f->d_flag, sizeof(int), "scale flag")))
+  if (!f->d_emax_chunks && !dev_alloc((void **)&f->d_emax_chunks, sizeof(int) * G * kHostChunks, "exponent partials"))
     return HUB_ERR_OOM;
+  if (!f->d_flag && !dev_alloc((void **)&f->d_flag, sizeof(int), "scale flag")) return HUB_ERR_OOM;
   if (!f->h_flag) HUB_CUDA(cudaMallocHost((void **)&f->h_flag, sizeof(int)));
   if (!f->copy_stream) HUB_CUDA(cudaStreamCreateWithFlags(&f->copy_stream, cudaStreamNonBlocking));
   while ((int)f->events.size() < 2 * kHostChunks + 2) {
@@ -1321,8 +1323,7 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
     f->events.push_back(e);
   }
   cudaStream_t sc = f->copy_stream;
-  cudaEvent_t *ev_in = f->events.data(), *ev_out = ev_in + kHostChunks, ev_start = ev_in[2 * kHostChunks],
-              ev_end = ev_in[2 * kHostChunks + 1];
+  const cudaEvent_t ev_start = f->events[2 * kHostChunks];
   // row chunks with even boundaries, so that no pass-1 row pair straddles two chunks
   const int64_t per = ((n_dn + kHostChunks - 1) / kHostChunks + 1) & ~(int64_t)1;
   int nc = 0;
@@ -1331,6 +1332,22 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
   while (nc < kHostChunks && b[nc + 1] > b[nc]) ++nc;
   HUB_CUDA(cudaEventRecord(ev_start, s));
   HUB_CUDA(cudaStreamWaitEvent(sc, ev_start, 0));
+  rc = pipeline_host(h, f, x_host, y_host, xd, yd, s, b, nc, per);
+  if (rc) {   // no copy into or out of the caller's buffers may outlive the call
+    cudaStreamSynchronize(sc);
+    cudaStreamSynchronize(s);
+  }
+  return rc;
+}
+
+// The chunked copies and passes of fast_apply_host (b: chunk row bounds, nc chunks).
+static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double *y_host, double *xd, double *yd,
+                         cudaStream_t s, const int64_t *b, int nc, int64_t per) {
+  const int64_t n_up = h->count[0], n_dn = h->count[1];
+  const int G = grid_vec();
+  int rc;
+  cudaStream_t sc = f->copy_stream;
+  cudaEvent_t *ev_in = f->events.data(), *ev_out = ev_in + kHostChunks, ev_end = ev_in[2 * kHostChunks + 1];
   for (int c = 0; c < nc; ++c) {
     HUB_CUDA(cudaMemcpyAsync(xd + b[c] * n_up, x_host + b[c] * n_up, sizeof(double) * (b[c + 1] - b[c]) * n_up,
                              cudaMemcpyHostToDevice, sc));

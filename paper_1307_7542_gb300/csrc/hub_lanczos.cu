@@ -398,7 +398,7 @@ extern "C" int hub_lanczos_coeffs(hub_t h, double *alpha_host, double *beta_host
 extern "C" int hub_lanczos_spectrum(hub_t h, const double *x0_dev, int maxit, int n_eig, double *eig_host,
                                     double *resid_host, int *n_found, void *stream) {
   if (!h) return fail(HUB_ERR_ARG, "hub_lanczos_spectrum: NULL handle");
-  if (n_eig < 1 || !eig_host || !n_found || maxit < 1 || maxit > 10000)
+  if (n_eig < 1 || !eig_host || !n_found || maxit < 1 || maxit > 3000)
     return fail(HUB_ERR_ARG, "hub_lanczos_spectrum: bad argument");
   double E0 = 0.0;
   int it = 0;
