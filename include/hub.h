@@ -151,6 +151,16 @@ int hub_lanczos_spectrum(hub_t h, const double *x0_dev, int maxit, int n_eig, do
                          int *n_found, void *stream);
 
 /*
+ * Eigenvector of a low-lying excited state (Sec. IV): maxit steps of the plain recurrence
+ * from x0_dev (NULL: the seeded start vector), then the second pass of hub_lanczos_ground
+ * forms the normalised Ritz vector psi_dev (device, count_up * count_dn) for the eigenvalue
+ * of T nearest `target` (e.g. one returned by hub_lanczos_spectrum with the same x0 and
+ * maxit); *ritz_host receives that eigenvalue.  1 <= maxit <= 3000; blocks until done.
+ */
+int hub_lanczos_ritz(hub_t h, const double *x0_dev, int maxit, double target, double *psi_dev, double *ritz_host,
+                     void *stream);
+
+/*
  * One-particle Green's function at zero temperature (Sec. VII, Eq. count8):
  *   G_s(p, z) = <psi0| c_ps (z + E0 - H)^-1 c+_ps |psi0> + <psi0| c+_ps (z - E0 + H)^-1 c_ps |psi0>,
  * each term a continued fraction from the Lanczos recurrence started at c+_ps psi0 or

@@ -1518,7 +1518,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
 
   if (psi_out) {
     // second pass with the stored coefficients: psi = sum_j v_j q_j = sum_j v_j r_j / beta_{j-1}
-    std::vector<double> vv = tridiag_vector(h->alpha.data(), h->beta.data(), k, E);
+    std::vector<double> vv = tridiag_vector(h->alpha.data(), h->beta.data(), k, psi_eigenvalue(h, E));
     if ((rc = ensure_vec(&f->psi, Dp, "ground-state vector"))) return rc;
     rp = f->lz[0];
     rcur = f->lz[1];

@@ -102,6 +102,10 @@ struct hub_ctx {
 
   // |x0| of the last Lanczos run (the continued fraction of the Green's function needs it)
   double start_norm = 0.0;
+  // second Lanczos pass: expand the eigenvector of T for the eigenvalue nearest psi_target
+  // instead of the lowest one (hub_lanczos_ritz); psi_value records the value used
+  bool psi_at_target = false;
+  double psi_target = 0.0, psi_value = 0.0;
   // source index and sign per state of this handle's sector for hub_ladder
   int32_t *ladder_map = nullptr;
   int64_t ladder_cap = 0;
@@ -149,6 +153,9 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
 int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out, int *iters,
                  cudaStream_t s);
 int fast_check_error(hub_ctx *h);
+// Eigenvalue of the last run's T whose eigenvector the second Lanczos pass expands (E0, or the
+// one nearest h->psi_target); also stored in h->psi_value.
+double psi_eigenvalue(hub_ctx *h, double E0);
 inline bool use_fast(const hub_ctx *h) { return h->mode == HUB_MODE_AUTO && h->fast && fast_eligible(h); }
 
 // Event pair around a launch of the given kind (no-op unless profiling).

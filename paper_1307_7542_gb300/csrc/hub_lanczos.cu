@@ -245,6 +245,19 @@ std::vector<double> tridiag_all(const double *a, const double *b, int k) {
   return ev;
 }
 
+double psi_eigenvalue(hub_ctx *h, double E0) {
+  double v = E0;
+  const int k = (int)h->alpha.size();
+  if (h->psi_at_target && k > 0) {
+    const std::vector<double> ev = tridiag_all(h->alpha.data(), h->beta.data(), k);
+    v = ev[0];
+    for (double e : ev)
+      if (fabs(e - h->psi_target) < fabs(v - h->psi_target)) v = e;
+  }
+  h->psi_value = v;
+  return v;
+}
+
 static int ensure_workspace(hub_ctx *h, int64_t D) {
   for (int k = 0; k < 3; ++k)
     if (!h->work[k] && !dev_alloc((void **)&h->work[k], sizeof(double) * D, "Lanczos vector")) return HUB_ERR_OOM;
@@ -347,7 +360,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
 
   if (psi_dev) {
     // second pass: psi = sum_j v_j q_j with v the lowest eigenvector of T_k
-    std::vector<double> v = tridiag_vector(h->alpha.data(), h->beta.data(), k, E);
+    std::vector<double> v = tridiag_vector(h->alpha.data(), h->beta.data(), k, psi_eigenvalue(h, E));
     qp = h->work[0];
     q = h->work[1];
     w = h->work[2];
@@ -439,5 +452,21 @@ extern "C" int hub_lanczos_spectrum(hub_t h, const double *x0_dev, int maxit, in
     }
   }
   *n_found = n;
+  return HUB_OK;
+}
+
+extern "C" int hub_lanczos_ritz(hub_t h, const double *x0_dev, int maxit, double target, double *psi_dev,
+                                double *ritz_host, void *stream) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_lanczos_ritz: NULL handle");
+  if (!psi_dev || !ritz_host || maxit < 1 || maxit > 3000 || !std::isfinite(target))
+    return fail(HUB_ERR_ARG, "hub_lanczos_ritz: bad argument");
+  h->psi_at_target = true;
+  h->psi_target = target;
+  double E0 = 0.0;
+  int it = 0;
+  const int rc = hub_lanczos_ground(h, x0_dev, maxit, 0.0, &E0, psi_dev, &it, stream);
+  h->psi_at_target = false;
+  if (rc < 0) return rc;
+  *ritz_host = h->psi_value;
   return HUB_OK;
 }

@@ -43,6 +43,7 @@ SIGNATURES = {
     "hub_lanczos_ground": (_i, [_p, _p, _i, _d, ctypes.POINTER(_d), _p, ctypes.POINTER(_i), _p]),
     "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
     "hub_lanczos_spectrum": (_i, [_p, _p, _i, _i, _p, _p, ctypes.POINTER(_i), _p]),
+    "hub_lanczos_ritz": (_i, [_p, _p, _i, _d, _p, ctypes.POINTER(_d), _p]),
     "hub_ladder": (_i, [_p, _p, _i, _i, _i, _p, _p, _p]),
     "hub_green_coeffs": (_i, [_p, _p, _i, _p, _p, ctypes.POINTER(_d), ctypes.POINTER(_i), _p]),
     "hub_green_eval": (_i, [_i, _p, _p, _d, _d, _i, _i, _p, _p, _p, _p]),
@@ -188,6 +189,13 @@ def hub_lanczos_spectrum(h, x0, maxit, n_eig, stream=None):
     _check(lib().hub_lanczos_spectrum(h, _ptr(x0), maxit, n_eig, _ptr(e), _ptr(r), ctypes.byref(n),
                                       _stream(stream)))
     return e[: n.value], r[: n.value]
+
+
+def hub_lanczos_ritz(h, x0, maxit, target, psi, stream=None):
+    """Normalised Ritz vector (into psi) for the eigenvalue of T nearest target; returns that value."""
+    v = _d()
+    _check(lib().hub_lanczos_ritz(h, _ptr(x0), maxit, target, _ptr(psi), ctypes.byref(v), _stream(stream)))
+    return v.value
 
 
 def hub_ladder(h_from, h_to, site, spin, create, x, y, stream=None):

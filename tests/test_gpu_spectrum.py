@@ -77,3 +77,53 @@ def test_spectrum_4x4_full_size(hub):
     assert abs(e[0] - g["E0"]) < 1e-10 * abs(g["E0"])
     assert np.all(np.diff(e) > 0)
     assert r[0] < 1e-4
+
+
+def _ritz_checks(hub, m, x0, maxit, levels, ref_vals, ref_vecs):
+    for i in levels:
+        psi = torch.empty(m.D, dtype=torch.float64, device="cuda")
+        theta = hub.hub_lanczos_ritz(m.h, x0, maxit, float(ref_vals[i]), psi)
+        assert abs(theta - ref_vals[i]) < 1e-9 * max(1.0, abs(ref_vals[i]))
+        p = psi.cpu().numpy()
+        assert abs(np.linalg.norm(p) - 1.0) < 1e-12
+        assert 1.0 - abs(float(p @ ref_vecs[:, i])) < 1e-8, i
+        r = (m.apply(psi) - theta * psi).norm().item()
+        assert r < 1e-6, (i, r)
+
+
+def test_ritz_vectors_disordered_fp64_path(hub):
+    """Excited-state eigenvectors (Sec. IV) on the FP64 path: the Ritz vectors of the second
+    and third levels of a disordered 7-site chain, (3,2), match the dense eigenvectors."""
+    M, nu, nd = 7, 3, 2
+    bonds = W.chain_bonds(M)
+    r = W.uniform(31, 3 * M)
+    t = 1.0 + 0.3 * (r[: M - 1] - 0.5)
+    U, eps = 2.0 + 4.0 * r[M: 2 * M], 0.4 * (r[2 * M:] - 0.5)
+    om = O.Model(M, bonds, t, U, eps)
+    w, V = np.linalg.eigh(O.dense_fock(om, nu, nd))
+    assert min(w[2] - w[1], w[1] - w[0], w[3] - w[2]) > 1e-3
+    m = hub.Hubbard(M, nu, nd, bonds, t, U, eps)
+    x0 = torch.from_numpy(W.normal(4, m.D)).cuda()
+    _ritz_checks(hub, m, x0, 150, [0, 1, 2], w, V)
+    m.close()
+
+
+def test_ritz_vectors_chain8_fast_path(hub):
+    """Excited-state eigenvectors on the double-float path: open chain M = 8, (4,4), U = 4;
+    the two lowest levels against ARPACK eigenvectors of the oracle's apply."""
+    from scipy.sparse.linalg import LinearOperator, eigsh
+    M = 8
+    bonds = W.chain_bonds(M)
+    om = O.Model(M, bonds, 1.0, 4.0)
+    B = O.basis(M, 4, 4)
+    op = LinearOperator((B.size, B.size), matvec=lambda v: O.apply(om, B, np.ascontiguousarray(v, dtype=np.float64)),
+                        dtype=np.float64)
+    w, V = eigsh(op, k=6, which="SA", tol=1e-14, v0=W.normal(3, B.size))
+    order = np.argsort(w)
+    w, V = w[order], V[:, order]
+    levels = [i for i in range(2) if min(abs(w[i] - w[j]) for j in range(len(w)) if j != i) > 1e-3]
+    assert levels
+    m = hub.Hubbard(M, 4, 4, bonds, 1.0, 4.0)
+    x0 = torch.from_numpy(W.normal(2, m.D)).cuda()
+    _ritz_checks(hub, m, x0, 200, levels, w, V)
+    m.close()
