@@ -34,7 +34,7 @@ SMEM_PEAK_TBS = 28.7          # shared-memory load bandwidth, conflict-free, all
 # DRAM bytes (read + write) per element of X from one ncu capture of the same kernels on the
 # 4x4 (6,6) sector (profiles/k_up_k_dn_4x4_sector66.md); the per-element traffic does not depend
 # on the sector, so a launch's traffic is this times D
-NCU_DRAM_BYTES_PER_ELEMENT = {"k_up": 0.982509e9 / 64128064, "k_dn": 2.137257e9 / 64128064}
+NCU_DRAM_BYTES_PER_ELEMENT = {"k_up": 0.981464e9 / 64128064, "k_dn": 2.136734e9 / 64128064}
 STAGE_MAX_COLS = 14076        # rows up to this length are staged in shared memory by pass 1
 
 
