@@ -55,6 +55,9 @@ extern "C" {
 #define HUB_MODE_AUTO 0   /* fast double-float path when t and U are uniform, else FP64 */
 #define HUB_MODE_FP64 1   /* always the native FP64 kernels                              */
 
+#define HUB_SYM_NONE 0    /* the full sector (N_up, N_dn)                              */
+#define HUB_SYM_K0 1      /* its k = 0 subspace under the translation i -> i-1 mod M   */
+
 #define HUB_PROF_APPLY 0  /* a whole product H x (both passes on the fast path)       */
 #define HUB_PROF_UP 1     /* fast path pass 1: spin-up hops + diagonal                 */
 #define HUB_PROF_DN 2     /* fast path pass 2: spin-down hops + epilogue               */
@@ -266,6 +269,45 @@ int hub_grad_noalloc(hub_t h, const double *psi_dev, double *dE_dt_host, double 
  */
 int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_dev, double *xbar_dev,
                   double *tbar_host, double *Ubar_host, double *epsbar_host, void *stream);
+
+/*
+ * Translation symmetry (Sec. V): restrict the handle to the k = 0 subspace of the
+ * translation T c+_{i sigma} T^-1 = c+_{i-1 sigma} (site 0 -> site M-1; the direction of the
+ * paper's Tables I and II), about M times smaller than the sector.
+ *   - Requires hub_hopping and hub_set_U first, a bond set that T maps onto itself with equal
+ *     t (a ring, a ring with further-neighbour bonds, ...), uniform U and uniform eps;
+ *     otherwise HUB_ERR_ARG.  HUB_ERR_OOM if one k = 0 vector would not fit on the device.
+ *   - Layout ("row form"): the up strings are grouped into T-cycles; the smallest member of
+ *     each is its representative R_i (i = 0 .. rows-1, ascending; hub_k0_reps gives them and
+ *     their periods P_i).  A k = 0 state Psi is stored as the rows x cols FP64 array
+ *         X[i * cols + r] = sqrt(P_i) * Psi(R_i, d_r),   cols = count_dn,
+ *     d_r the down string of rank r; the plain dot product of two such arrays is the inner
+ *     product of the states.  Rows with P_i < M hold tied entries (a cycle of T^P_i within
+ *     the row); hub_k0_project enforces the ties, and entries of cycles with no k = 0 state
+ *     are zero.  dim (hub_k0_dims) is the number of independent entries, the dimension of
+ *     the k = 0 space.
+ *   - While it is active, vectors of hub_apply, hub_apply_host, hub_lanczos_ground,
+ *     hub_lanczos_spectrum, hub_lanczos_ritz and hub_green_coeffs are row-form arrays of
+ *     length rows * cols; start vectors are projected; products always return projected
+ *     arrays.  hub_grad, hub_grad_noalloc, hub_apply_vjp and hub_ladder return
+ *     HUB_ERR_STATE.  hub_hopping and hub_set_U return the handle to the full sector.
+ *   - Changing the symmetry frees the handle's Lanczos workspace (it is sized per layout).
+ *   - Blocks until the tables are built.  HUB_SYM_NONE returns to the full sector.
+ */
+int hub_set_symmetry(hub_t h, int sym);
+
+/* Row-form shape and dimension of the k = 0 space.  HUB_ERR_STATE outside it. */
+int hub_k0_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim);
+
+/* Up representatives R_i and periods P_i of the rows (host arrays of length rows). */
+int hub_k0_reps(hub_t h, uint32_t *rep_host, int32_t *period_host);
+
+/*
+ * y_dev = the row-form array x_dev with the ties of the short rows enforced (the
+ * orthogonal projection onto the k = 0 space in row form); x_dev == y_dev is allowed,
+ * other overlaps are HUB_ERR_ARG.  Enqueued on stream.
+ */
+int hub_k0_project(hub_t h, const double *x_dev, double *y_dev, void *stream);
 
 /*
  * Arithmetic path (no counterpart in the paper).  HUB_MODE_AUTO (default) runs products

@@ -94,6 +94,7 @@ int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
 static int apply_kernels(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   const Ham H = h->view();
   if (H.n_up == 0 || H.n_dn == 0) return HUB_OK;
+  if (h->k0) return k0_apply(h, x, y, s);
   if (use_fast(h)) return fast_apply_f64(h, x, y, s);
   count_launch(h);
   const size_t smem = stage_bytes(H);
@@ -128,7 +129,7 @@ extern "C" int hub_apply(hub_t h, const double *x_dev, double *y_dev, void *stre
   int rc = check_ready(h, "hub_apply");
   if (rc) return rc;
   if (!x_dev || !y_dev) return fail(HUB_ERR_ARG, "hub_apply: NULL vector");
-  const int64_t D = h->count[0] * h->count[1];
+  const int64_t D = vec_len(h);
   if (x_dev < y_dev + D && y_dev < x_dev + D) return fail(HUB_ERR_ARG, "hub_apply: x and y overlap");
   return apply_launch(h, x_dev, y_dev, (cudaStream_t)stream);
 }
@@ -137,7 +138,7 @@ extern "C" int hub_apply_host(hub_t h, const double *x_host, double *y_host, voi
   int rc = check_ready(h, "hub_apply_host");
   if (rc) return rc;
   if (!x_host || !y_host) return fail(HUB_ERR_ARG, "hub_apply_host: NULL vector");
-  const int64_t D = h->count[0] * h->count[1];
+  const int64_t D = vec_len(h);
   if (!h->hx) {
     if (!dev_alloc((void **)&h->hx, sizeof(double) * D, "host-apply input") ||
         !dev_alloc((void **)&h->hy, sizeof(double) * D, "host-apply output")) {

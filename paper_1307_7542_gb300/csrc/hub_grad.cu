@@ -138,6 +138,7 @@ extern "C" int hub_grad(hub_t h, const double *psi_dev, double *dE_dt_host, doub
                         double *dE_deps_host, void *stream) {
   int rc = ready(h, "hub_grad");
   if (rc) return rc;
+  if (h->k0) return fail(HUB_ERR_STATE, "hub_grad: not available in the k = 0 sector (hub_set_symmetry)");
   if (!psi_dev) return fail(HUB_ERR_ARG, "hub_grad: psi is NULL");
   return bilinear(h, psi_dev, psi_dev, dE_dt_host, dE_dU_host, dE_deps_host, (cudaStream_t)stream);
 }
@@ -146,6 +147,7 @@ extern "C" int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_de
                              double *tbar_host, double *Ubar_host, double *epsbar_host, void *stream) {
   int rc = ready(h, "hub_apply_vjp");
   if (rc) return rc;
+  if (h->k0) return fail(HUB_ERR_STATE, "hub_apply_vjp: not available in the k = 0 sector (hub_set_symmetry)");
   if (!ybar_dev || (!x_dev && (tbar_host || Ubar_host || epsbar_host)))
     return fail(HUB_ERR_ARG, "hub_apply_vjp: NULL vector");
   cudaStream_t s = (cudaStream_t)stream;
@@ -199,6 +201,7 @@ extern "C" int hub_grad_noalloc(hub_t h, const double *psi_dev, double *dE_dt_ho
                                 double *dE_deps_host, void *stream) {
   int rc = ready(h, "hub_grad_noalloc");
   if (rc) return rc;
+  if (h->k0) return fail(HUB_ERR_STATE, "hub_grad_noalloc: not available in the k = 0 sector (hub_set_symmetry)");
   if (!psi_dev) return fail(HUB_ERR_ARG, "hub_grad_noalloc: psi is NULL");
   const int n_par = h->n_bonds + 2 * h->M;
   if (n_par > kNoAllocMaxParams)

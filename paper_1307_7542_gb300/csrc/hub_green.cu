@@ -76,6 +76,7 @@ extern "C" int hub_ladder(hub_t from, hub_t to, int site, int spin, int create, 
                           double *y_dev, void *stream) {
   if (!from || !to) return fail(HUB_ERR_ARG, "hub_ladder: NULL handle");
   if (from->M != to->M) return fail(HUB_ERR_ARG, "hub_ladder: the two handles have different M");
+  if (from->k0 || to->k0) return fail(HUB_ERR_STATE, "hub_ladder: not available in the k = 0 sector (hub_set_symmetry)");
   if (site < 0 || site >= from->M) return fail(HUB_ERR_ARG, "hub_ladder: site out of range");
   if (spin != HUB_SPIN_UP && spin != HUB_SPIN_DN) return fail(HUB_ERR_ARG, "hub_ladder: bad spin");
   if (!x_dev || !y_dev) return fail(HUB_ERR_ARG, "hub_ladder: NULL vector");

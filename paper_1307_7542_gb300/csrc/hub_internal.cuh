@@ -44,6 +44,7 @@ struct SpinCSR {
 };
 
 struct FastState;   // fast-path tables and scratch (hub_fast.cu)
+struct K0State;     // k = 0 translation-sector tables (hub_k0.cu)
 
 // Read-only view of everything a kernel needs, passed by value.
 struct Ham {
@@ -121,6 +122,10 @@ struct hub_ctx {
   hub::FastState *fast = nullptr;
   int mode = 0;                        // HUB_MODE_AUTO or HUB_MODE_FP64
 
+  // k = 0 sector of the translation i -> i-1 mod M (hub_set_symmetry); vectors are then in
+  // row form, rows x cols (hub_k0.cu)
+  hub::K0State *k0 = nullptr;
+
   hub::Ham view() const;
 };
 
@@ -156,7 +161,16 @@ int fast_check_error(hub_ctx *h);
 // Eigenvalue of the last run's T whose eigenvector the second Lanczos pass expands (E0, or the
 // one nearest h->psi_target); also stored in h->psi_value.
 double psi_eigenvalue(hub_ctx *h, double E0);
-inline bool use_fast(const hub_ctx *h) { return h->mode == HUB_MODE_AUTO && h->fast && fast_eligible(h); }
+inline bool use_fast(const hub_ctx *h) {
+  return h->mode == HUB_MODE_AUTO && h->fast && !h->k0 && fast_eligible(h);
+}
+
+// k = 0 sector (hub_k0.cu).
+int64_t vec_len(const hub_ctx *h);   // length of a state vector in the handle's current layout
+int k0_apply(hub_ctx *h, const double *x, double *y, cudaStream_t s);
+int k0_project_inplace(hub_ctx *h, double *x, cudaStream_t s);
+void k0_leave(hub_ctx *h);           // back to the full sector, vectors sized for it dropped
+void k0_release(hub_ctx *h);
 
 // Event pair around a launch of the given kind (no-op unless profiling).
 int prof_mark(hub_ctx *h, int kind, bool begin, cudaStream_t s);

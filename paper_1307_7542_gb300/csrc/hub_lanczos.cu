@@ -258,6 +258,15 @@ double psi_eigenvalue(hub_ctx *h, double E0) {
   return v;
 }
 
+// In the k = 0 sector the start vector is projected onto the sector (ties of the short rows)
+// in w, which then stands for it.
+static int k0_start(hub_ctx *h, const double **x0, double *w, cudaStream_t s) {
+  if (!h->k0) return HUB_OK;
+  if (*x0 != w) HUB_CUDA(cudaMemcpyAsync(w, *x0, sizeof(double) * vec_len(h), cudaMemcpyDeviceToDevice, s));
+  *x0 = w;
+  return k0_project_inplace(h, w, s);
+}
+
 static int ensure_workspace(hub_ctx *h, int64_t D) {
   for (int k = 0; k < 3; ++k)
     if (!h->work[k] && !dev_alloc((void **)&h->work[k], sizeof(double) * D, "Lanczos vector")) return HUB_ERR_OOM;
@@ -276,7 +285,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
   if (rc) return rc;
   if (!E0) return fail(HUB_ERR_ARG, "hub_lanczos_ground: E0 is NULL");
   if (maxit < 1) return fail(HUB_ERR_ARG, "hub_lanczos_ground: maxit < 1");
-  const int64_t D = h->count[0] * h->count[1];
+  const int64_t D = vec_len(h);
   if (D == 0) return fail(HUB_ERR_ARG, "hub_lanczos_ground: empty sector");
   if (use_fast(h)) {
     if (!x0_dev) {
@@ -302,6 +311,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
     HUB_LAUNCH_CHECK();
     x0 = w;
   }
+  if ((rc = k0_start(h, &x0, w, s))) return rc;
   count_launch(h, x0_dev ? 3 : 4);   // [splitmix], dot, reduce, copy_scaled
   k_dot<<<G, T, 0, s>>>(D, x0, x0, P);
   HUB_LAUNCH_CHECK();
@@ -370,6 +380,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
       HUB_LAUNCH_CHECK();
       xs = w;
     }
+    if ((rc = k0_start(h, &xs, w, s))) return rc;
     k_copy_scaled<<<G, T, 0, s>>>(D, q, xs, scal + 3);
     HUB_CUDA(cudaMemsetAsync(qp, 0, sizeof(double) * D, s));
     HUB_CUDA(cudaMemsetAsync(psi_dev, 0, sizeof(double) * D, s));

@@ -444,6 +444,7 @@ extern "C" int hub_hopping(hub_t h, int n_bonds, const int32_t *bonds_host, cons
     bt.j[b] = (uint8_t)j;
     bt.t[b] = t_host[b];
   }
+  k0_leave(h);
   h->have_hop = false;
   h->n_bonds = n_bonds;
   h->bonds.assign(bonds_host, bonds_host + 2 * n_bonds);
@@ -502,6 +503,7 @@ extern "C" int hub_set_U(hub_t h, int n_U, const double *U_host) {
     h->U[i] = U_host[i];
     if (U_host[i] != U_host[0]) uni = false;
   }
+  k0_leave(h);
   h->uniform_U = uni;
   h->U0 = U_host[0];
   h->have_U = true;
@@ -552,6 +554,7 @@ extern "C" void hub_free(hub_t h) {
   dev_free(h->hx);
   dev_free(h->hy);
   fast_release(h);
+  k0_release(h);
   for (int k = 0; k < 3; ++k) {
     for (cudaEvent_t e : h->ev_start[k]) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_end[k]) cudaEventDestroy(e);

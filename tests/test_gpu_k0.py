@@ -1,0 +1,245 @@
+"""GPU parity of the k = 0 translation sector (Sec. V) through the C ABI.
+
+The oracle builds the k = 0 Bloch states of the paper's combined representatives in the full
+two-spin basis and applies the full H (oracle/hub_oracle_k0.py).  The library works in row
+form, X[i, d] = sqrt(P_i) Psi(R_i, d); the tests sample the oracle's translation-invariant
+vectors on the rows of the up representatives to compare.  Integer data (representatives,
+periods, dimension) bit for bit; products per entry within 1e-13 (|H||Psi|); energies within
+1e-10 relative.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from helpers import assert_entrywise
+from oracle import hub_oracle as O
+from oracle import hub_oracle_k0 as K
+from paper_1307_7542_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def hub(cuda_ok):
+    import __graft_entry__
+    __graft_entry__.build()
+    from paper_1307_7542_gb300 import hub as H
+    return H
+
+
+def ring(M, nnn=False):
+    b = [(i, (i + 1) % M) for i in range(M)]
+    if nnn:
+        b += [(i, (i + 2) % M) for i in range(M)]
+    return np.array(b, dtype=np.int32)
+
+
+# (M, N_up, N_dn, next-nearest bonds, t, U, eps)
+CASES = [
+    (4, 2, 1, False, 1.0, 4.0, 0.0),
+    (4, 2, 0, False, 1.0, 4.0, 0.0),     # a cycle with no k = 0 state
+    (6, 3, 3, False, 1.0, 4.0, 0.0),
+    (6, 4, 2, False, 0.7, 2.5, 0.3),     # short rows and cycles with no k = 0 state
+    (6, 3, 3, True, 1.0, 4.0, -0.2),
+    (7, 3, 4, False, 1.0, 3.0, 0.0),
+    (8, 4, 4, False, 1.0, 4.0, 0.0),
+    (8, 4, 2, True, 0.9, 6.0, 0.1),
+    (9, 3, 3, False, 1.0, 8.0, 0.0),
+    (10, 5, 5, False, 1.0, 4.0, 0.0),
+    (12, 6, 6, False, 1.0, 4.0, 0.0),    # 924 columns: four 256-column tiles, ragged tail
+    (12, 4, 5, True, 1.1, 2.0, 0.05),
+    (6, 0, 2, False, 1.0, 4.0, 0.0),     # one row of period 1
+    (5, 5, 2, False, 1.0, 4.0, 0.0),     # full up filling
+]
+
+
+def _models(hub, M, nu, nd, nnn, t, U, eps):
+    bonds = ring(M, nnn)
+    om = O.Model(M, bonds, t, U, eps)
+    m = hub.Hubbard(M, nu, nd, bonds, t, U, np.full(M, eps) if eps else None)
+    m.set_symmetry(hub.HUB_SYM_K0)
+    return om, m
+
+
+@pytest.mark.parametrize("M,nu,nd,nnn,t,U,eps", CASES)
+def test_k0_tables_bitexact(hub, M, nu, nd, nnn, t, U, eps):
+    """Rows, columns and dimension of the k = 0 space; the up representatives and their
+    periods equal the oracle's cycle enumeration, bit for bit."""
+    om, m = _models(hub, M, nu, nd, nnn, t, U, eps)
+    tb = K.spin_tables(M, nu)
+    is_rep = tb["state"] == tb["rep"]
+    reps, per = m.k0_reps()
+    m.close()
+    assert np.array_equal(reps.astype(np.uint64), tb["state"][is_rep])
+    assert np.array_equal(per.astype(np.int64), tb["period"][is_rep])
+    assert (m.k0_rows, m.k0_cols) == (int(is_rep.sum()), math.comb(M, nd))
+    assert m.k0_dim == K.k0_dimension(M, nu, nd)
+
+
+@pytest.mark.parametrize("M,nu,nd,nnn,t,U,eps", CASES)
+def test_k0_apply_parity(hub, M, nu, nd, nnn, t, U, eps):
+    """H on random k = 0 states: the library's row-form product equals the oracle's full
+    two-spin product sampled on the representative rows, per entry within 1e-13 |H||Psi|."""
+    om, m = _models(hub, M, nu, nd, nnn, t, U, eps)
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix(M, nu, nd, B)
+    for seed in (1, 2):
+        psi = np.asarray(V @ W.normal(seed, V.shape[1]))
+        X, _, _ = K.row_form(M, nu, nd, B, psi)
+        Yref, _, _ = K.row_form(M, nu, nd, B, O.apply(om, B, psi))
+        bound, _, _ = K.row_form(M, nu, nd, B, O.apply(om, B, np.abs(psi), absolute=True))
+        y = m.apply(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
+        assert_entrywise(y, Yref.ravel(), bound.ravel())
+    m.close()
+
+
+@pytest.mark.parametrize("M,nu,nd", [(4, 2, 0), (6, 4, 2), (8, 4, 2), (8, 4, 4), (9, 3, 3)])
+def test_k0_projection(hub, M, nu, nd):
+    """hub_k0_project is the orthogonal projection onto the k = 0 space in row form: it
+    keeps row-form k = 0 states, is idempotent bit for bit, leaves x - Px orthogonal to the
+    k = 0 states, and its trace (projecting every unit array) is the k = 0 dimension."""
+    om, m = _models(hub, M, nu, nd, False, 1.0, 4.0, 0.0)
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix(M, nu, nd, B)
+    X, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ W.normal(5, V.shape[1])))
+    px = m.k0_project(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
+    assert np.max(np.abs(px - X.ravel())) < 1e-14 * np.max(np.abs(X))
+    x = torch.from_numpy(W.normal(6, m.D)).cuda()
+    p1 = m.k0_project(x)
+    p2 = m.k0_project(p1.clone())
+    assert torch.equal(p1, p2)
+    r = (x - p1).cpu().numpy()
+    for seed in (7, 8):
+        Z, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ W.normal(seed, V.shape[1])))
+        assert abs(float(r @ Z.ravel())) < 1e-13 * np.linalg.norm(r) * np.linalg.norm(Z)
+    eye = torch.eye(m.D, dtype=torch.float64, device="cuda")
+    tr = sum(float(m.k0_project(eye[k].contiguous())[k]) for k in range(m.D))
+    assert abs(tr - K.k0_dimension(M, nu, nd)) < 1e-12 * m.D
+    m.close()
+
+
+@pytest.mark.parametrize("M,nu,nd,nnn,t,U,eps", [c for c in CASES if c[0] <= 10])
+def test_k0_ground_energy(hub, M, nu, nd, nnn, t, U, eps):
+    """Lowest k = 0 eigenvalue by the library's Lanczos in the k = 0 sector equals the lowest
+    eigenvalue of V^T H V, within 1e-10 relative; the row-form ground state matches the
+    oracle's eigenvector sampled on the rows (when that level is simple)."""
+    om, m = _models(hub, M, nu, nd, nnn, t, U, eps)
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix(M, nu, nd, B)
+    w, Z = np.linalg.eigh(K.k0_matrix(om, B, V))
+    g = m.ground(None, maxit=min(400, 3 * m.k0_dim + 5), tol=1e-13, want_psi=True)
+    assert abs(g["E0"] - w[0]) < 1e-10 * max(1.0, abs(w[0]))
+    if w.size > 1 and w[1] - w[0] > 1e-6:
+        ref, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ Z[:, 0]))
+        p = g["psi"].cpu().numpy()
+        assert 1.0 - abs(float(p @ ref.ravel())) < 1e-9
+    m.close()
+
+
+@pytest.mark.parametrize("M,nu,nd,nnn", [(8, 4, 4, False), (6, 4, 2, False), (9, 3, 3, True)])
+def test_k0_spectrum(hub, M, nu, nd, nnn):
+    """hub_lanczos_spectrum in the k = 0 sector: the lowest distinct k = 0 eigenvalues."""
+    om, m = _models(hub, M, nu, nd, nnn, 1.0, 4.0, 0.0)
+    B = O.basis(M, nu, nd)
+    w = np.linalg.eigvalsh(K.k0_matrix(om, B, K.bloch_matrix(M, nu, nd, B)))
+    ref = []
+    for x in w:
+        if not ref or x - ref[-1] > 1e-8:
+            ref.append(x)
+    n = min(4, len(ref))
+    e, _ = hub.hub_lanczos_spectrum(m.h, None, min(3000, 4 * m.k0_dim + 20), n)
+    m.close()
+    assert np.max(np.abs(e[:n] - np.array(ref[:n]))) < 1e-9 * max(1.0, abs(ref[0]))
+
+
+def test_k0_hermitian_and_free_ring_at_M14(hub):
+    """M = 14, (7, 7): U = 0 k = 0 ground energy equals the best momentum-0 filling of the
+    one-particle levels; at U = 4 the product is symmetric on projected random arrays."""
+    M = 14
+    bonds = ring(M)
+    m = hub.Hubbard(M, 7, 7, bonds, 1.0, 0.0)
+    m.set_symmetry(hub.HUB_SYM_K0)
+    g = m.ground(None, maxit=300, tol=1e-13)
+    ref = K.ring_free_k0_levels(M, 7, 7)[0]
+    assert abs(g["E0"] - ref) < 1e-10 * abs(ref)
+    m.set_params(1.0, 4.0)
+    m.set_symmetry(hub.HUB_SYM_K0)
+    a = m.k0_project(torch.from_numpy(W.normal(1, m.D)).cuda())
+    b = m.k0_project(torch.from_numpy(W.normal(2, m.D)).cuda())
+    lhs, rhs = float(a @ m.apply(b)), float(m.apply(a) @ b)
+    assert abs(lhs - rhs) < 1e-12 * (float(a.norm()) * float(m.apply(b).norm()))
+    m.close()
+
+
+def test_k0_table4_M14(hub):
+    """Table IV: the 14-site ring at half filling, U = 4, t = 1.  The ground state lies at
+    k = 0 (seven electrons of each spin); the k = 0 Lanczos energy equals the printed value
+    within 5e-10 and the full-sector energy of the library within 1e-10 relative."""
+    M = 14
+    from conftest import golden
+    printed = {int(r[0]): float(r[2]) for r in golden("table4_E0.txt")}[M]
+    m = hub.Hubbard(M, 7, 7, ring(M), 1.0, 4.0)
+    full = m.ground(None, maxit=400, tol=1e-13)["E0"]
+    m.set_symmetry(hub.HUB_SYM_K0)
+    assert m.k0_dim * 14 >= m.count_up * m.count_dn
+    k0 = m.ground(None, maxit=400, tol=1e-13)["E0"]
+    m.set_symmetry(hub.HUB_SYM_NONE)
+    again = m.ground(None, maxit=400, tol=1e-13)["E0"]
+    m.close()
+    assert abs(k0 - printed) < 5e-10
+    assert abs(k0 - full) < 1e-10 * abs(full)
+    assert again == full
+
+
+@pytest.mark.slow
+def test_k0_M16_variational(hub):
+    """M = 16, (8, 8), U = 4: the k = 0 energy is not below the full-sector energy (a
+    subspace), and the 16-fold smaller space reaches it when the ground state lies there."""
+    M = 16
+    m = hub.Hubbard(M, 8, 8, ring(M), 1.0, 4.0)
+    full = m.ground(None, maxit=400, tol=1e-12)["E0"]
+    m.set_symmetry(hub.HUB_SYM_K0)
+    k0 = m.ground(None, maxit=400, tol=1e-12)["E0"]
+    m.close()
+    assert k0 >= full - 1e-10 * abs(full)
+
+
+def test_k0_errors(hub):
+    """Refusals: bonds not invariant under T, site-dependent U or eps; calls that have no
+    k = 0 form; the k = 0 queries outside the sector.  New parameters leave the sector."""
+    M = 6
+    m = hub.Hubbard(M, 3, 3, W.chain_bonds(M), 1.0, 4.0)          # open chain
+    with pytest.raises(hub.HubError) as e:
+        m.set_symmetry(hub.HUB_SYM_K0)
+    assert e.value.code == hub.HUB_ERR_ARG
+    with pytest.raises(hub.HubError) as e:
+        hub.hub_k0_dims(m.h)
+    assert e.value.code == hub.HUB_ERR_STATE
+    m.set_params(np.ones(M - 1), 4.0)
+    m.close()
+    m = hub.Hubbard(M, 3, 3, ring(M), 1.0, np.arange(M, dtype=np.float64))
+    with pytest.raises(hub.HubError) as e:
+        m.set_symmetry(hub.HUB_SYM_K0)
+    assert e.value.code == hub.HUB_ERR_ARG
+    m.set_params(1.0, 4.0, np.linspace(0, 1, M))
+    with pytest.raises(hub.HubError) as e:
+        m.set_symmetry(hub.HUB_SYM_K0)
+    assert e.value.code == hub.HUB_ERR_ARG
+    m.set_params(1.0, 4.0)
+    m.set_symmetry(hub.HUB_SYM_K0)
+    psi = torch.zeros(m.D, dtype=torch.float64, device="cuda")
+    with pytest.raises(hub.HubError) as e:
+        m.grad(psi)
+    assert e.value.code == hub.HUB_ERR_STATE
+    with pytest.raises(hub.HubError) as e:
+        hub.hub_set_symmetry(m.h, 7)
+    assert e.value.code == hub.HUB_ERR_ARG
+    m.set_params(1.0, 5.0)                                     # leaves the k = 0 sector
+    assert m.D == m.count_up * m.count_dn
+    with pytest.raises(hub.HubError) as e:
+        hub.hub_k0_dims(m.h)
+    assert e.value.code == hub.HUB_ERR_STATE
+    m.close()
