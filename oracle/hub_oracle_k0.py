@@ -26,6 +26,11 @@ Everything here follows the definitions of Sec. V, written out plainly:
                         two-spin apply of ``hub_oracle`` (the plain definition; the
                         paper's Algorithms III-V build the same matrix another way).
 
+The paper implements k = 0 only.  Every function that depends on the momentum also takes
+``omega`` = e^{ik} = -1 for k = pi, the other momentum with real Bloch states (M even):
+a(k) = P^-1/2 sum_r e^{-ikr} T^r |a>, which vanishes unless e^{-ikP} times the closing
+sign of the orbit is +1.
+
 Readings taken where the paper is silent or its formula is garbled:
 
 1. Eq. count6 subtracts, for a period z, the strings whose period is a proper divisor i
@@ -163,12 +168,13 @@ def spin_reps(M: int, N: int):
     return bits[order], per[order], eb[order]
 
 
-def combined_reps(M: int, n_up: int, n_dn: int) -> dict:
+def combined_reps(M: int, n_up: int, n_dn: int, omega: int = 1) -> dict:
     """Two-spin representatives |r_up> T^n |r_dn>, n = 0 .. hcf(P_up, P_dn) - 1 (Eq.
     count7), ordered as Table I: up representative, then down representative, then n.
     Per entry: up bits, down representative bits, n, down bits of T^n r_dn and the sign of
     T^n |r_dn> = sign |bits>, the orbit length P = lcm(P_up, P_dn) and `null` (reading 2):
-    T^P of the signed two-spin state is minus itself."""
+    T^P of the signed two-spin state is minus itself (for k = 0; omega^P times that sign is
+    -1 in general)."""
     ub, up_, _ = spin_reps(M, n_up)
     db, dp_, _ = spin_reps(M, n_dn)
     rows = []
@@ -198,13 +204,15 @@ def combined_reps(M: int, n_up: int, n_dn: int) -> dict:
         cd, sd = translate(M, cd, n_dn)
         sg = sg * su * sd
         closing = np.where(period == k, sg, closing)
+    phase = np.where(period % 2 == 1, float(omega), 1.0)
     return {"up": up, "dn_rep": dn_rep, "n": n, "dn": dn, "sign": sign, "period": period,
-            "null": closing < 0}
+            "null": closing * phase < 0}
 
 
-def k0_dimension(M: int, n_up: int, n_dn: int) -> int:
-    """Number of k = 0 states: combined representatives whose Bloch sum does not vanish."""
-    return int(np.count_nonzero(~combined_reps(M, n_up, n_dn)["null"]))
+def k0_dimension(M: int, n_up: int, n_dn: int, omega: int = 1) -> int:
+    """Number of k = 0 (omega = -1: k = pi) states: combined representatives whose Bloch sum
+    does not vanish."""
+    return int(np.count_nonzero(~combined_reps(M, n_up, n_dn, omega)["null"]))
 
 
 def _index(B: np.ndarray, I: np.ndarray) -> np.ndarray:
@@ -213,14 +221,14 @@ def _index(B: np.ndarray, I: np.ndarray) -> np.ndarray:
     return idx
 
 
-def bloch_matrix(M: int, n_up: int, n_dn: int, B: np.ndarray | None = None):
-    """Sparse V (D x D0): column j = P^-1/2 sum_{r<P} T^r |b_j> for the j-th non-null
-    combined representative b_j = sign |up, dn> (Sec. V, k = 0), rows in the two-spin
-    basis B of Eq. 6 (I = I_up + 2^M I_dn ascending)."""
+def bloch_matrix(M: int, n_up: int, n_dn: int, B: np.ndarray | None = None, omega: int = 1):
+    """Sparse V (D x D0): column j = P^-1/2 sum_{r<P} omega^r T^r |b_j> for the j-th non-null
+    combined representative b_j = sign |up, dn> (Sec. V; omega = 1 is k = 0, -1 is k = pi),
+    rows in the two-spin basis B of Eq. 6 (I = I_up + 2^M I_dn ascending)."""
     import scipy.sparse as sp
     if B is None:
         B = O.basis(M, n_up, n_dn)
-    cr = combined_reps(M, n_up, n_dn)
+    cr = combined_reps(M, n_up, n_dn, omega)
     keep = ~cr["null"]
     up, dn, sg, P = cr["up"][keep], cr["dn"][keep], cr["sign"][keep], cr["period"][keep]
     D0 = up.shape[0]
@@ -234,7 +242,7 @@ def bloch_matrix(M: int, n_up: int, n_dn: int, B: np.ndarray | None = None):
         vals.append((sg / np.sqrt(P))[live])
         up, su = translate(M, up, n_up)
         dn, sd = translate(M, dn, n_dn)
-        sg = sg * su * sd
+        sg = sg * su * sd * float(omega)
     V = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                       shape=(B.shape[0], D0))
     return V
@@ -250,17 +258,18 @@ def translation_matrix(M: int, n_up: int, n_dn: int, B: np.ndarray):
     return sp.csr_matrix((su * sd, (dst, np.arange(B.shape[0]))), shape=(B.shape[0], B.shape[0]))
 
 
-def character_dimension(M: int, n_up: int, n_dn: int, B: np.ndarray) -> int:
-    """dim of the k = 0 space as the multiplicity of eigenvalue 1 of T: (1/M) sum_r tr T^r,
-    each trace the signed count of basis states that T^r maps to themselves."""
+def character_dimension(M: int, n_up: int, n_dn: int, B: np.ndarray, omega: int = 1) -> int:
+    """dim of the sector as the multiplicity of the eigenvalue omega of T:
+    (1/M) sum_r omega^-r tr T^r, each trace the signed count of basis states that T^r maps to
+    themselves."""
     up, dn = O.spin_parts(M, B)
     cu, cd, sg = up.copy(), dn.copy(), np.ones(B.shape[0])
     total = float(B.shape[0])                            # r = 0
-    for _ in range(1, M):
+    for r in range(1, M):
         cu, su = translate(M, cu, n_up)
         cd, sd = translate(M, cd, n_dn)
         sg = sg * su * sd
-        total += float(np.sum(sg[(cu == up) & (cd == dn)]))
+        total += float(omega) ** r * float(np.sum(sg[(cu == up) & (cd == dn)]))
     val = total / M
     assert abs(val - round(val)) < 1e-9
     return int(round(val))
@@ -281,15 +290,17 @@ def k0_matrix(model: O.Model, B: np.ndarray, V) -> np.ndarray:
     return np.asarray(V.T @ HV)
 
 
-def ring_free_k0_levels(M: int, n_up: int, n_dn: int, t: float = 1.0) -> np.ndarray:
-    """U = 0 nearest-neighbour ring: every k = 0 eigenvalue, sorted.  One-particle
-    states of momentum 2 pi m / M have energy -2 t cos(2 pi m / M); a product state lies
-    in the k = 0 sector when the momenta of all electrons add to 0 modulo 2 pi."""
+def ring_free_k0_levels(M: int, n_up: int, n_dn: int, t: float = 1.0, omega: int = 1) -> np.ndarray:
+    """U = 0 nearest-neighbour ring: every eigenvalue of the k = 0 (omega = -1: k = pi)
+    sector, sorted.  One-particle states of momentum 2 pi m / M have energy
+    -2 t cos(2 pi m / M); a product state lies in the sector when the momenta of all
+    electrons add to 0 (pi) modulo 2 pi."""
     from itertools import combinations
+    target = 0 if omega == 1 else M // 2
     e = -2.0 * t * np.cos(2.0 * np.pi * np.arange(M) / M)
     ups = [(sum(c) % M, sum(e[list(c)])) for c in combinations(range(M), n_up)]
     dns = [(sum(c) % M, sum(e[list(c)])) for c in combinations(range(M), n_dn)]
-    out = [eu + ed for ku, eu in ups for kd, ed in dns if (ku + kd) % M == 0]
+    out = [eu + ed for ku, eu in ups for kd, ed in dns if (ku + kd) % M == target]
     return np.sort(np.array(out))
 
 

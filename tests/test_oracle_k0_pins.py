@@ -2,7 +2,8 @@
 and what the mathematics fixes: Tables I and II, brute-force counts of representatives,
 the character formula for the dimension of the k = 0 space, the complete U = 0 spectrum
 from one-particle momenta, and the spectrum of H on the range of the projector
-(1/M) sum_r T^r built from the brute-force translation matrix."""
+(1/M) sum_r T^r built from the brute-force translation matrix.  The same pins hold the
+k = pi sector (omega = e^{ik} = -1, even M) of the oracle."""
 import os
 from itertools import product
 
@@ -77,6 +78,21 @@ SECTORS = [(4, 2, 1), (4, 2, 2), (4, 2, 0), (5, 2, 3), (6, 3, 3), (6, 2, 1), (6,
            (8, 4, 2), (8, 6, 2), (9, 3, 3), (6, 6, 6), (6, 0, 0), (6, 2, 0)]
 
 
+@pytest.mark.parametrize("M,nu,nd", [s for s in SECTORS if s[0] % 2 == 0])
+def test_k_pi_dimension_and_invariance(M, nu, nd):
+    """k = pi: dim = (1/M) sum_r (-1)^r tr T^r, the Bloch columns are orthonormal and
+    T V = -V."""
+    B = O.basis(M, nu, nd)
+    assert K.k0_dimension(M, nu, nd, -1) == K.character_dimension(M, nu, nd, B, -1)
+    V = K.bloch_matrix(M, nu, nd, B, -1)
+    assert V.shape[1] == K.k0_dimension(M, nu, nd, -1)
+    if V.shape[1] == 0:
+        return
+    assert abs((V.T @ V).toarray() - np.eye(V.shape[1])).max() < 1e-14
+    T = K.translation_matrix(M, nu, nd, B)
+    assert abs(T @ V + V).max() == 0.0
+
+
 @pytest.mark.parametrize("M,nu,nd", SECTORS)
 def test_dimension_is_the_character_count(M, nu, nd):
     """dim k = 0 = (1/M) sum_r tr T^r (brute force on the full basis); the Bloch columns
@@ -95,29 +111,32 @@ def test_dimension_is_the_character_count(M, nu, nd):
         assert not K.combined_reps(M, nu, nd)["null"].any()
 
 
-@pytest.mark.parametrize("M,nu,nd", [(6, 3, 3), (6, 2, 1), (6, 4, 2), (5, 2, 3), (8, 4, 2), (7, 3, 2)])
-def test_free_ring_k0_spectrum(M, nu, nd):
-    """U = 0: every eigenvalue of H in the k = 0 basis is a sum of one-particle energies
-    -2t cos(2 pi m / M) whose momenta add to 0 mod 2 pi, and all such sums appear."""
+@pytest.mark.parametrize("M,nu,nd,omega", [(6, 3, 3, 1), (6, 2, 1, 1), (6, 4, 2, 1), (5, 2, 3, 1), (8, 4, 2, 1),
+                                         (7, 3, 2, 1), (6, 3, 3, -1), (6, 4, 2, -1), (8, 4, 4, -1), (4, 2, 0, -1)])
+def test_free_ring_k0_spectrum(M, nu, nd, omega):
+    """U = 0: every eigenvalue of H in the k = 0 (k = pi) basis is a sum of one-particle
+    energies -2t cos(2 pi m / M) whose momenta add to 0 (pi) mod 2 pi, and all such sums
+    appear."""
     m = O.Model(M, ring(M), 1.0, 0.0)
     B = O.basis(M, nu, nd)
-    w = np.linalg.eigvalsh(K.k0_matrix(m, B, K.bloch_matrix(M, nu, nd, B)))
-    ref = K.ring_free_k0_levels(M, nu, nd)
+    w = np.linalg.eigvalsh(K.k0_matrix(m, B, K.bloch_matrix(M, nu, nd, B, omega)))
+    ref = K.ring_free_k0_levels(M, nu, nd, omega=omega)
     assert w.shape == ref.shape
     assert np.max(np.abs(w - ref)) < 1e-12
 
 
-@pytest.mark.parametrize("M,nu,nd,nnn", [(6, 3, 2, False), (6, 4, 2, False), (5, 2, 2, False), (6, 3, 3, True),
-                                         (7, 3, 2, True)])
-def test_projector_route(M, nu, nd, nnn):
+@pytest.mark.parametrize("M,nu,nd,nnn,omega", [(6, 3, 2, False, 1), (6, 4, 2, False, 1), (5, 2, 2, False, 1),
+                                               (6, 3, 3, True, 1), (7, 3, 2, True, 1), (6, 3, 2, False, -1),
+                                               (6, 3, 3, True, -1)])
+def test_projector_route(M, nu, nd, nnn, omega):
     """U = 4, eps = 0.3 (nearest- and next-nearest-neighbour rings): the spectrum of V^T H V
-    equals that of H on the range of (1/M) sum_r T^r, computed from the dense Jordan-Wigner
-    Hamiltonian and the brute-force translation matrix."""
+    equals that of H on the range of (1/M) sum_r omega^r T^r, computed from the dense
+    Jordan-Wigner Hamiltonian and the brute-force translation matrix."""
     m = O.Model(M, ring(M, nnn), 1.0, 4.0, 0.3)
     B = O.basis(M, nu, nd)
-    w = np.linalg.eigvalsh(K.k0_matrix(m, B, K.bloch_matrix(M, nu, nd, B)))
+    w = np.linalg.eigvalsh(K.k0_matrix(m, B, K.bloch_matrix(M, nu, nd, B, omega)))
     T = K.translation_matrix(M, nu, nd, B).toarray()
-    P = sum(np.linalg.matrix_power(T, r) for r in range(M)) / M
+    P = sum(float(omega) ** r * np.linalg.matrix_power(T, r) for r in range(M)) / M
     ev, Q = np.linalg.eigh(P)
     Q = Q[:, ev > 0.5]
     w2 = np.linalg.eigvalsh(Q.T @ O.dense_fock(m, nu, nd) @ Q)
