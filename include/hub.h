@@ -57,6 +57,7 @@ extern "C" {
 
 #define HUB_SYM_NONE 0    /* the full sector (N_up, N_dn)                              */
 #define HUB_SYM_K0 1      /* its k = 0 subspace under the translation i -> i-1 mod M   */
+#define HUB_SYM_KPI 2     /* its k = pi subspace (T eigenvalue -1; M even)             */
 
 #define HUB_PROF_APPLY 0  /* a whole product H x (both passes on the fast path)       */
 #define HUB_PROF_UP 1     /* fast path pass 1: spin-up hops + diagonal                 */
@@ -273,18 +274,21 @@ int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_dev, double *
 /*
  * Translation symmetry (Sec. V): restrict the handle to the k = 0 subspace of the
  * translation T c+_{i sigma} T^-1 = c+_{i-1 sigma} (site 0 -> site M-1; the direction of the
- * paper's Tables I and II), about M times smaller than the sector.
+ * paper's Tables I and II), about M times smaller than the sector.  HUB_SYM_KPI selects the
+ * k = pi subspace instead (T Psi = -Psi; an extension beyond the paper's k = 0, the other
+ * momentum whose Bloch states are real; M must be even, else HUB_ERR_ARG).  Everything
+ * below holds for both, with "k = 0" read as the selected momentum.
  *   - Requires hub_hopping and hub_set_U first, a bond set that T maps onto itself with equal
  *     t (a ring, a ring with further-neighbour bonds, ...), uniform U and uniform eps;
  *     otherwise HUB_ERR_ARG.  HUB_ERR_OOM if one k = 0 vector would not fit on the device.
  *   - Layout ("row form"): the up strings are grouped into T-cycles; the smallest member of
- *     each is its representative R_i (i = 0 .. rows-1, ascending; hub_k0_reps gives them and
+ *     each is its representative R_i (i = 0 .. rows-1, ascending; hub_k_reps gives them and
  *     their periods P_i).  A k = 0 state Psi is stored as the rows x cols FP64 array
  *         X[i * cols + r] = sqrt(P_i) * Psi(R_i, d_r),   cols = count_dn,
  *     d_r the down string of rank r; the plain dot product of two such arrays is the inner
  *     product of the states.  Rows with P_i < M hold tied entries (a cycle of T^P_i within
- *     the row); hub_k0_project enforces the ties, and entries of cycles with no k = 0 state
- *     are zero.  dim (hub_k0_dims) is the number of independent entries, the dimension of
+ *     the row); hub_k_project enforces the ties, and entries of cycles with no k = 0 state
+ *     are zero.  dim (hub_k_dims) is the number of independent entries, the dimension of
  *     the k = 0 space.
  *   - While it is active, vectors of hub_apply, hub_apply_host, hub_lanczos_ground,
  *     hub_lanczos_spectrum, hub_lanczos_ritz and hub_green_coeffs are row-form arrays of
@@ -296,18 +300,18 @@ int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_dev, double *
  */
 int hub_set_symmetry(hub_t h, int sym);
 
-/* Row-form shape and dimension of the k = 0 space.  HUB_ERR_STATE outside it. */
-int hub_k0_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim);
+/* Row-form shape and dimension of the momentum sector.  HUB_ERR_STATE outside one. */
+int hub_k_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim);
 
 /* Up representatives R_i and periods P_i of the rows (host arrays of length rows). */
-int hub_k0_reps(hub_t h, uint32_t *rep_host, int32_t *period_host);
+int hub_k_reps(hub_t h, uint32_t *rep_host, int32_t *period_host);
 
 /*
  * y_dev = the row-form array x_dev with the ties of the short rows enforced (the
  * orthogonal projection onto the k = 0 space in row form); x_dev == y_dev is allowed,
  * other overlaps are HUB_ERR_ARG.  Enqueued on stream.
  */
-int hub_k0_project(hub_t h, const double *x_dev, double *y_dev, void *stream);
+int hub_k_project(hub_t h, const double *x_dev, double *y_dev, void *stream);
 
 /*
  * Arithmetic path (no counterpart in the paper).  HUB_MODE_AUTO (default) runs products

@@ -19,6 +19,10 @@
 // product and every start vector is projected onto them, with each cycle's average summed
 // in one fixed order so that the tied entries agree bit for bit.
 //
+// The k = pi sector (T Psi = -Psi, M even) uses the same layout: every relation
+// Psi(T^t c) = tau Psi(c) of the k = 0 sector gains the factor (-1)^t, so the up-hop
+// coefficients take (-1)^t and the closing sign of a short row b_i becomes (-1)^P_i b_i.
+//
 // Product in row form (Sec. V with Eq. 11): for (i, d)
 //     Y = (U popc(R_i & d) + eps (N_up + N_dn)) X[i, d]                diagonal
 //       + sum_d' H_dn[d, d'] X[i, d']                                    down hops, in-row
@@ -47,7 +51,8 @@ struct K0State {
   std::vector<int32_t> per_h;
   uint32_t *rep = nullptr;      // [rows] up representatives, ascending
   int32_t *per = nullptr;       // [rows] their periods
-  int32_t *eb = nullptr;        // [rows] sign of T^P_i on R_i
+  int32_t *eb = nullptr;        // [rows] sign of T^P_i on R_i, times omega^P_i
+  int omega = 1;                // e^{ik}: 1 for k = 0, -1 for k = pi
   int32_t *uh_ptr = nullptr;    // [rows + 1] up-hop list of each row
   int32_t *uh_row = nullptr;    // [n_uh] target row i'
   int32_t *uh_t = nullptr;      // [n_uh] translation t
@@ -301,11 +306,12 @@ static int check_invariant(const hub_ctx *h) {
   return HUB_OK;
 }
 
-static int k0_build(hub_ctx *h) {
+static int k0_build(hub_ctx *h, int omega) {
   const int M = h->M, Nu = h->N[0], Nd = h->N[1];
   K0State *k = new (std::nothrow) K0State();
   if (!k) return fail(HUB_ERR_OOM, "hub_set_symmetry: host allocation failed");
   h->k0 = k;
+  k->omega = omega;
   k->cols = h->count[1];
   k->diag0 = (h->eps.empty() ? 0.0 : h->eps[0]) * (double)(Nu + Nd);
 
@@ -336,7 +342,7 @@ static int k0_build(hub_ctx *h) {
         }
         reps.push_back(x);
         per.push_back(P);
-        eb.push_back(sg);
+        eb.push_back((omega < 0 && (P & 1)) ? -sg : sg);
       }
       if (Nu == 0) break;
       const uint64_t lo = u & (~u + 1), r = u + lo;   // next string with Nu bits (Gosper)
@@ -383,6 +389,7 @@ static int k0_build(hub_ctx *h) {
       if (cur != u2) return fail(HUB_ERR_CUDA, "hub_set_symmetry: translation not found");
       uh_row.push_back(i2);
       uh_t.push_back(t);
+      if (omega < 0 && (t & 1)) sg = -sg;
       uh_val.push_back(val * sg * std::sqrt((double)per[i] / (double)per[i2]));
     }
     uh_ptr.push_back((int32_t)uh_row.size());
@@ -471,7 +478,8 @@ using namespace hub;
 
 extern "C" int hub_set_symmetry(hub_t h, int sym) {
   if (!h) return fail(HUB_ERR_ARG, "hub_set_symmetry: NULL handle");
-  if (sym != HUB_SYM_NONE && sym != HUB_SYM_K0) return fail(HUB_ERR_ARG, "hub_set_symmetry: unknown symmetry");
+  if (sym != HUB_SYM_NONE && sym != HUB_SYM_K0 && sym != HUB_SYM_KPI)
+    return fail(HUB_ERR_ARG, "hub_set_symmetry: unknown symmetry");
   if (sym == HUB_SYM_NONE) {
     k0_leave(h);
     return HUB_OK;
@@ -479,25 +487,26 @@ extern "C" int hub_set_symmetry(hub_t h, int sym) {
   int rc = ready(h, "hub_set_symmetry");
   if (rc) return rc;
   if ((rc = check_invariant(h))) return rc;
+  if (sym == HUB_SYM_KPI && (h->M & 1)) return fail(HUB_ERR_ARG, "hub_set_symmetry: k = pi needs an even M");
   k0_release(h);
   release_vectors(h);
-  rc = k0_build(h);
+  rc = k0_build(h, sym == HUB_SYM_KPI ? -1 : 1);
   if (rc) k0_release(h);
   return rc;
 }
 
-extern "C" int hub_k0_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim) {
-  if (!h) return fail(HUB_ERR_ARG, "hub_k0_dims: NULL handle");
-  if (!h->k0) return fail(HUB_ERR_STATE, "hub_k0_dims: call hub_set_symmetry(h, HUB_SYM_K0) first");
+extern "C" int hub_k_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_k_dims: NULL handle");
+  if (!h->k0) return fail(HUB_ERR_STATE, "hub_k_dims: no momentum sector is active (hub_set_symmetry)");
   if (rows) *rows = h->k0->rows;
   if (cols) *cols = h->k0->cols;
   if (dim) *dim = h->k0->dim;
   return HUB_OK;
 }
 
-extern "C" int hub_k0_reps(hub_t h, uint32_t *rep_host, int32_t *period_host) {
-  if (!h) return fail(HUB_ERR_ARG, "hub_k0_reps: NULL handle");
-  if (!h->k0) return fail(HUB_ERR_STATE, "hub_k0_reps: call hub_set_symmetry(h, HUB_SYM_K0) first");
+extern "C" int hub_k_reps(hub_t h, uint32_t *rep_host, int32_t *period_host) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_k_reps: NULL handle");
+  if (!h->k0) return fail(HUB_ERR_STATE, "hub_k_reps: no momentum sector is active (hub_set_symmetry)");
   const K0State *k = h->k0;
   for (int64_t i = 0; i < k->rows; ++i) {
     if (rep_host) rep_host[i] = k->rep_h[i];
@@ -506,13 +515,13 @@ extern "C" int hub_k0_reps(hub_t h, uint32_t *rep_host, int32_t *period_host) {
   return HUB_OK;
 }
 
-extern "C" int hub_k0_project(hub_t h, const double *x_dev, double *y_dev, void *stream) {
-  if (!h) return fail(HUB_ERR_ARG, "hub_k0_project: NULL handle");
-  if (!h->k0) return fail(HUB_ERR_STATE, "hub_k0_project: call hub_set_symmetry(h, HUB_SYM_K0) first");
-  if (!x_dev || !y_dev) return fail(HUB_ERR_ARG, "hub_k0_project: NULL vector");
+extern "C" int hub_k_project(hub_t h, const double *x_dev, double *y_dev, void *stream) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_k_project: NULL handle");
+  if (!h->k0) return fail(HUB_ERR_STATE, "hub_k_project: no momentum sector is active (hub_set_symmetry)");
+  if (!x_dev || !y_dev) return fail(HUB_ERR_ARG, "hub_k_project: NULL vector");
   const int64_t D = vec_len(h);
   if (x_dev != y_dev && x_dev < y_dev + D && y_dev < x_dev + D)
-    return fail(HUB_ERR_ARG, "hub_k0_project: x and y overlap without being equal");
+    return fail(HUB_ERR_ARG, "hub_k_project: x and y overlap without being equal");
   cudaStream_t s = (cudaStream_t)stream;
   if (x_dev != y_dev && D) HUB_CUDA(cudaMemcpyAsync(y_dev, x_dev, sizeof(double) * D, cudaMemcpyDeviceToDevice, s));
   return k0_project_inplace(h, y_dev, s);

@@ -28,6 +28,7 @@ HUB_ERR_STATE = -5
 HUB_ERR_TIMEOUT = -6
 HUB_SYM_NONE = 0
 HUB_SYM_K0 = 1
+HUB_SYM_KPI = 2
 
 # (name, restype, argtypes) of every exported entry point.
 _i, _i64, _d, _p = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p
@@ -54,9 +55,9 @@ SIGNATURES = {
     "hub_grad_noalloc": (_i, [_p, _p, _p, _p, _p, _p]),
     "hub_batch_ground": (_i, [_i, _i, _p, _i, _p, _p, _p, _i, _p, _p, _p, _i, _d, _p, _p, _p, _p]),
     "hub_set_symmetry": (_i, [_p, _i]),
-    "hub_k0_dims": (_i, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
-    "hub_k0_reps": (_i, [_p, _p, _p]),
-    "hub_k0_project": (_i, [_p, _p, _p, _p]),
+    "hub_k_dims": (_i, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
+    "hub_k_reps": (_i, [_p, _p, _p]),
+    "hub_k_project": (_i, [_p, _p, _p, _p]),
     "hub_set_mode": (_i, [_p, _i]),
     "hub_check": (_i, [_p]),
     "hub_profile": (_i, [_p, _i]),
@@ -284,21 +285,21 @@ def hub_set_symmetry(h, sym):
     _check(lib().hub_set_symmetry(h, sym))
 
 
-def hub_k0_dims(h):
+def hub_k_dims(h):
     r, c, d = _i64(), _i64(), _i64()
-    _check(lib().hub_k0_dims(h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(d)))
+    _check(lib().hub_k_dims(h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(d)))
     return r.value, c.value, d.value
 
 
-def hub_k0_reps(h, rows):
+def hub_k_reps(h, rows):
     reps = np.empty(rows, dtype=np.uint32)
     per = np.empty(rows, dtype=np.int32)
-    _check(lib().hub_k0_reps(h, reps.ctypes.data, per.ctypes.data))
+    _check(lib().hub_k_reps(h, reps.ctypes.data, per.ctypes.data))
     return reps, per
 
 
-def hub_k0_project(h, x, y, stream=None):
-    _check(lib().hub_k0_project(h, _ptr(x), _ptr(y), _stream(stream)))
+def hub_k_project(h, x, y, stream=None):
+    _check(lib().hub_k_project(h, _ptr(x), _ptr(y), _stream(stream)))
 
 
 def hub_set_mode(h, mode):
@@ -343,23 +344,24 @@ class Hubbard:
         self.D = self.count_up * self.count_dn      # new parameters leave the k = 0 sector
 
     def set_symmetry(self, sym):
-        """HUB_SYM_K0: work in the k = 0 sector of the translation i -> i-1 mod M (Sec. V);
-        vectors are then k0_rows x k0_cols arrays in row form.  HUB_SYM_NONE: full sector."""
+        """HUB_SYM_K0 / HUB_SYM_KPI: work in the k = 0 / k = pi sector of the translation
+        i -> i-1 mod M (Sec. V); vectors are then k_rows x k_cols arrays in row form.
+        HUB_SYM_NONE: the full sector."""
         hub_set_symmetry(self.h, sym)
-        if sym == HUB_SYM_K0:
-            self.k0_rows, self.k0_cols, self.k0_dim = hub_k0_dims(self.h)
-            self.D = self.k0_rows * self.k0_cols
+        if sym in (HUB_SYM_K0, HUB_SYM_KPI):
+            self.k_rows, self.k_cols, self.k_dim = hub_k_dims(self.h)
+            self.D = self.k_rows * self.k_cols
         else:
             self.D = self.count_up * self.count_dn
 
-    def k0_reps(self):
-        return hub_k0_reps(self.h, self.k0_rows)
+    def k_reps(self):
+        return hub_k_reps(self.h, self.k_rows)
 
-    def k0_project(self, x, y=None, stream=None):
+    def k_project(self, x, y=None, stream=None):
         import torch
         if y is None:
             y = torch.empty_like(x)
-        hub_k0_project(self.h, x, y, stream)
+        hub_k_project(self.h, x, y, stream)
         return y
 
     @property

@@ -56,36 +56,51 @@ CASES = [
 ]
 
 
-def _models(hub, M, nu, nd, nnn, t, U, eps):
+# (case, omega): k = 0 for every case, k = pi (omega = -1) for the even rings
+SECTOR_CASES = [(c, 1) for c in CASES] + [(c, -1) for c in CASES if c[0] % 2 == 0]
+
+
+def _ids(sc):
+    (M, nu, nd, nnn, *_), om = sc
+    return f"M{M}-{nu}-{nd}{'-nnn' if nnn else ''}-{'k0' if om == 1 else 'kpi'}"
+
+
+def _models(hub, M, nu, nd, nnn, t, U, eps, omega=1):
     bonds = ring(M, nnn)
     om = O.Model(M, bonds, t, U, eps)
     m = hub.Hubbard(M, nu, nd, bonds, t, U, np.full(M, eps) if eps else None)
-    m.set_symmetry(hub.HUB_SYM_K0)
+    m.set_symmetry(hub.HUB_SYM_K0 if omega == 1 else hub.HUB_SYM_KPI)
     return om, m
 
 
-@pytest.mark.parametrize("M,nu,nd,nnn,t,U,eps", CASES)
-def test_k0_tables_bitexact(hub, M, nu, nd, nnn, t, U, eps):
-    """Rows, columns and dimension of the k = 0 space; the up representatives and their
-    periods equal the oracle's cycle enumeration, bit for bit."""
-    om, m = _models(hub, M, nu, nd, nnn, t, U, eps)
+@pytest.mark.parametrize("sc", SECTOR_CASES, ids=_ids)
+def test_k0_tables_bitexact(hub, sc):
+    """Rows, columns and dimension of the k = 0 (k = pi) space; the up representatives and
+    their periods equal the oracle's cycle enumeration, bit for bit."""
+    (M, nu, nd, nnn, t, U, eps), omega = sc
+    om, m = _models(hub, M, nu, nd, nnn, t, U, eps, omega)
     tb = K.spin_tables(M, nu)
     is_rep = tb["state"] == tb["rep"]
-    reps, per = m.k0_reps()
+    reps, per = m.k_reps()
     m.close()
     assert np.array_equal(reps.astype(np.uint64), tb["state"][is_rep])
     assert np.array_equal(per.astype(np.int64), tb["period"][is_rep])
-    assert (m.k0_rows, m.k0_cols) == (int(is_rep.sum()), math.comb(M, nd))
-    assert m.k0_dim == K.k0_dimension(M, nu, nd)
+    assert (m.k_rows, m.k_cols) == (int(is_rep.sum()), math.comb(M, nd))
+    assert m.k_dim == K.k0_dimension(M, nu, nd, omega)
 
 
-@pytest.mark.parametrize("M,nu,nd,nnn,t,U,eps", CASES)
-def test_k0_apply_parity(hub, M, nu, nd, nnn, t, U, eps):
-    """H on random k = 0 states: the library's row-form product equals the oracle's full
-    two-spin product sampled on the representative rows, per entry within 1e-13 |H||Psi|."""
-    om, m = _models(hub, M, nu, nd, nnn, t, U, eps)
+@pytest.mark.parametrize("sc", SECTOR_CASES, ids=_ids)
+def test_k0_apply_parity(hub, sc):
+    """H on random k = 0 (k = pi) states: the library's row-form product equals the oracle's
+    full two-spin product sampled on the representative rows, per entry within
+    1e-13 |H||Psi|."""
+    (M, nu, nd, nnn, t, U, eps), omega = sc
+    om, m = _models(hub, M, nu, nd, nnn, t, U, eps, omega)
     B = O.basis(M, nu, nd)
-    V = K.bloch_matrix(M, nu, nd, B)
+    V = K.bloch_matrix(M, nu, nd, B, omega)
+    if V.shape[1] == 0:
+        m.close()
+        return
     for seed in (1, 2):
         psi = np.asarray(V @ W.normal(seed, V.shape[1]))
         X, _, _ = K.row_form(M, nu, nd, B, psi)
@@ -96,41 +111,46 @@ def test_k0_apply_parity(hub, M, nu, nd, nnn, t, U, eps):
     m.close()
 
 
-@pytest.mark.parametrize("M,nu,nd", [(4, 2, 0), (6, 4, 2), (8, 4, 2), (8, 4, 4), (9, 3, 3)])
-def test_k0_projection(hub, M, nu, nd):
-    """hub_k0_project is the orthogonal projection onto the k = 0 space in row form: it
-    keeps row-form k = 0 states, is idempotent bit for bit, leaves x - Px orthogonal to the
-    k = 0 states, and its trace (projecting every unit array) is the k = 0 dimension."""
-    om, m = _models(hub, M, nu, nd, False, 1.0, 4.0, 0.0)
+@pytest.mark.parametrize("M,nu,nd,omega", [(4, 2, 0, 1), (6, 4, 2, 1), (8, 4, 2, 1), (8, 4, 4, 1), (9, 3, 3, 1),
+                                         (4, 2, 0, -1), (6, 4, 2, -1), (8, 4, 4, -1), (6, 2, 1, -1)])
+def test_k0_projection(hub, M, nu, nd, omega):
+    """hub_k_project is the orthogonal projection onto the sector in row form: it keeps
+    row-form states of the sector, is idempotent bit for bit, leaves x - Px orthogonal to the
+    sector, and its trace (projecting every unit array) is the sector's dimension."""
+    om, m = _models(hub, M, nu, nd, False, 1.0, 4.0, 0.0, omega)
     B = O.basis(M, nu, nd)
-    V = K.bloch_matrix(M, nu, nd, B)
+    V = K.bloch_matrix(M, nu, nd, B, omega)
     X, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ W.normal(5, V.shape[1])))
-    px = m.k0_project(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
+    px = m.k_project(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
     assert np.max(np.abs(px - X.ravel())) < 1e-14 * np.max(np.abs(X))
     x = torch.from_numpy(W.normal(6, m.D)).cuda()
-    p1 = m.k0_project(x)
-    p2 = m.k0_project(p1.clone())
+    p1 = m.k_project(x)
+    p2 = m.k_project(p1.clone())
     assert torch.equal(p1, p2)
     r = (x - p1).cpu().numpy()
     for seed in (7, 8):
         Z, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ W.normal(seed, V.shape[1])))
         assert abs(float(r @ Z.ravel())) < 1e-13 * np.linalg.norm(r) * np.linalg.norm(Z)
     eye = torch.eye(m.D, dtype=torch.float64, device="cuda")
-    tr = sum(float(m.k0_project(eye[k].contiguous())[k]) for k in range(m.D))
-    assert abs(tr - K.k0_dimension(M, nu, nd)) < 1e-12 * m.D
+    tr = sum(float(m.k_project(eye[k].contiguous())[k]) for k in range(m.D))
+    assert abs(tr - K.k0_dimension(M, nu, nd, omega)) < 1e-12 * m.D
     m.close()
 
 
-@pytest.mark.parametrize("M,nu,nd,nnn,t,U,eps", [c for c in CASES if c[0] <= 10])
-def test_k0_ground_energy(hub, M, nu, nd, nnn, t, U, eps):
-    """Lowest k = 0 eigenvalue by the library's Lanczos in the k = 0 sector equals the lowest
+@pytest.mark.parametrize("sc", [c for c in SECTOR_CASES if c[0][0] <= 10], ids=_ids)
+def test_k0_ground_energy(hub, sc):
+    """Lowest eigenvalue of the sector by the library's Lanczos in it equals the lowest
     eigenvalue of V^T H V, within 1e-10 relative; the row-form ground state matches the
     oracle's eigenvector sampled on the rows (when that level is simple)."""
-    om, m = _models(hub, M, nu, nd, nnn, t, U, eps)
+    (M, nu, nd, nnn, t, U, eps), omega = sc
+    om, m = _models(hub, M, nu, nd, nnn, t, U, eps, omega)
     B = O.basis(M, nu, nd)
-    V = K.bloch_matrix(M, nu, nd, B)
+    V = K.bloch_matrix(M, nu, nd, B, omega)
+    if V.shape[1] == 0:
+        m.close()
+        return
     w, Z = np.linalg.eigh(K.k0_matrix(om, B, V))
-    g = m.ground(None, maxit=min(400, 3 * m.k0_dim + 5), tol=1e-13, want_psi=True)
+    g = m.ground(None, maxit=min(400, 3 * m.k_dim + 5), tol=1e-13, want_psi=True)
     assert abs(g["E0"] - w[0]) < 1e-10 * max(1.0, abs(w[0]))
     if w.size > 1 and w[1] - w[0] > 1e-6:
         ref, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ Z[:, 0]))
@@ -139,18 +159,19 @@ def test_k0_ground_energy(hub, M, nu, nd, nnn, t, U, eps):
     m.close()
 
 
-@pytest.mark.parametrize("M,nu,nd,nnn", [(8, 4, 4, False), (6, 4, 2, False), (9, 3, 3, True)])
-def test_k0_spectrum(hub, M, nu, nd, nnn):
-    """hub_lanczos_spectrum in the k = 0 sector: the lowest distinct k = 0 eigenvalues."""
-    om, m = _models(hub, M, nu, nd, nnn, 1.0, 4.0, 0.0)
+@pytest.mark.parametrize("M,nu,nd,nnn,omega", [(8, 4, 4, False, 1), (6, 4, 2, False, 1), (9, 3, 3, True, 1),
+                                               (8, 4, 4, False, -1), (8, 3, 4, True, -1)])
+def test_k0_spectrum(hub, M, nu, nd, nnn, omega):
+    """hub_lanczos_spectrum in a momentum sector: its lowest distinct eigenvalues."""
+    om, m = _models(hub, M, nu, nd, nnn, 1.0, 4.0, 0.0, omega)
     B = O.basis(M, nu, nd)
-    w = np.linalg.eigvalsh(K.k0_matrix(om, B, K.bloch_matrix(M, nu, nd, B)))
+    w = np.linalg.eigvalsh(K.k0_matrix(om, B, K.bloch_matrix(M, nu, nd, B, omega)))
     ref = []
     for x in w:
         if not ref or x - ref[-1] > 1e-8:
             ref.append(x)
     n = min(4, len(ref))
-    e, _ = hub.hub_lanczos_spectrum(m.h, None, min(3000, 4 * m.k0_dim + 20), n)
+    e, _ = hub.hub_lanczos_spectrum(m.h, None, min(3000, 4 * m.k_dim + 20), n)
     m.close()
     assert np.max(np.abs(e[:n] - np.array(ref[:n]))) < 1e-9 * max(1.0, abs(ref[0]))
 
@@ -167,8 +188,8 @@ def test_k0_hermitian_and_free_ring_at_M14(hub):
     assert abs(g["E0"] - ref) < 1e-10 * abs(ref)
     m.set_params(1.0, 4.0)
     m.set_symmetry(hub.HUB_SYM_K0)
-    a = m.k0_project(torch.from_numpy(W.normal(1, m.D)).cuda())
-    b = m.k0_project(torch.from_numpy(W.normal(2, m.D)).cuda())
+    a = m.k_project(torch.from_numpy(W.normal(1, m.D)).cuda())
+    b = m.k_project(torch.from_numpy(W.normal(2, m.D)).cuda())
     lhs, rhs = float(a @ m.apply(b)), float(m.apply(a) @ b)
     assert abs(lhs - rhs) < 1e-12 * (float(a.norm()) * float(m.apply(b).norm()))
     m.close()
@@ -184,7 +205,7 @@ def test_k0_table4_M14(hub):
     m = hub.Hubbard(M, 7, 7, ring(M), 1.0, 4.0)
     full = m.ground(None, maxit=400, tol=1e-13)["E0"]
     m.set_symmetry(hub.HUB_SYM_K0)
-    assert m.k0_dim * 14 >= m.count_up * m.count_dn
+    assert m.k_dim * 14 >= m.count_up * m.count_dn
     k0 = m.ground(None, maxit=400, tol=1e-13)["E0"]
     m.set_symmetry(hub.HUB_SYM_NONE)
     again = m.ground(None, maxit=400, tol=1e-13)["E0"]
@@ -196,15 +217,20 @@ def test_k0_table4_M14(hub):
 
 @pytest.mark.slow
 def test_k0_M16_variational(hub):
-    """M = 16, (8, 8), U = 4: the k = 0 energy is not below the full-sector energy (a
-    subspace), and the 16-fold smaller space reaches it when the ground state lies there."""
+    """M = 16, (8, 8), U = 4: the k = 0 and k = pi energies are not below the full-sector
+    energy (subspaces); with eight electrons of each spin the ground state lies at k = pi,
+    where the 16-fold smaller space reaches the full-sector energy (Table IV)."""
     M = 16
     m = hub.Hubbard(M, 8, 8, ring(M), 1.0, 4.0)
     full = m.ground(None, maxit=400, tol=1e-12)["E0"]
     m.set_symmetry(hub.HUB_SYM_K0)
     k0 = m.ground(None, maxit=400, tol=1e-12)["E0"]
+    m.set_symmetry(hub.HUB_SYM_KPI)
+    kpi = m.ground(None, maxit=400, tol=1e-12)["E0"]
     m.close()
     assert k0 >= full - 1e-10 * abs(full)
+    assert kpi >= full - 1e-10 * abs(full)
+    assert abs(kpi - full) < 1e-10 * abs(full)
 
 
 def test_k0_errors(hub):
@@ -216,7 +242,7 @@ def test_k0_errors(hub):
         m.set_symmetry(hub.HUB_SYM_K0)
     assert e.value.code == hub.HUB_ERR_ARG
     with pytest.raises(hub.HubError) as e:
-        hub.hub_k0_dims(m.h)
+        hub.hub_k_dims(m.h)
     assert e.value.code == hub.HUB_ERR_STATE
     m.set_params(np.ones(M - 1), 4.0)
     m.close()
@@ -237,9 +263,12 @@ def test_k0_errors(hub):
     with pytest.raises(hub.HubError) as e:
         hub.hub_set_symmetry(m.h, 7)
     assert e.value.code == hub.HUB_ERR_ARG
+    with pytest.raises(hub.HubError) as e:
+        hub.Hubbard(5, 2, 2, ring(5), 1.0, 4.0).set_symmetry(hub.HUB_SYM_KPI)   # odd M
+    assert e.value.code == hub.HUB_ERR_ARG
     m.set_params(1.0, 5.0)                                     # leaves the k = 0 sector
     assert m.D == m.count_up * m.count_dn
     with pytest.raises(hub.HubError) as e:
-        hub.hub_k0_dims(m.h)
+        hub.hub_k_dims(m.h)
     assert e.value.code == hub.HUB_ERR_STATE
     m.close()
