@@ -235,8 +235,8 @@ def combine_ranks(elapsed_ms, steps, world, device):
 
 def extras(hub, W, torch):
     """Measurements beside the headline: batched vs one-at-a-time impurity solves, adjoint
-    gradients vs finite differences, the 3x6 bandwidth-stress Lanczos step and the 4x4
-    zero-temperature Green's function."""
+    gradients vs finite differences, the 3x6 bandwidth-stress Lanczos step, the 4x4
+    zero-temperature Green's function and the momentum sectors of the 16- and 20-site rings."""
     import numpy as np
     out = {}
     # (1) AIM star M=8: 81 sectors x 64 parameter sets, one persistent launch
@@ -351,6 +351,25 @@ def extras(hub, W, torch):
                         "ground_state_s": t_gs, "ground_state_iters": r0["iters"], "E0": r0["E0"],
                         "terms": stages, "sum_rule_norm2_total": sum(norms),
                         "total_s": t_gs + sum(v_["coeffs_s"] + v_["ladder_ms"] / 1000 for v_ in stages.values())}
+    # (5) momentum sectors of the Hubbard ring (Sec. V), half filling, U = 4: at M = 16 the
+    # full sector against its k = pi subspace, where the ground state lies, each to
+    # |dE0| < 1e-12; at M = 20 products in the k = pi subspace (the full sector would need
+    # 273 GB per vector).  FP64 multiply-adds per element: the hops of both spins,
+    # 2 * (2 M C(M-2, N-1) / C(M, N)), plus the diagonal.
+    from paper_1307_7542_gb300 import ring as R
+    full16 = R.run(16, 8, 8, "full", maxit=400, tol=1e-12, applies=5)
+    kpi16 = R.run(16, 8, 8, "kpi", maxit=400, tol=1e-12, applies=20)
+    kpi20 = R.run(20, 10, 10, "kpi", maxit=0, applies=3)
+    for r in (kpi16, kpi20):
+        M, N = r["M"], r["n_up"]
+        fma = 2 * (2 * M * math.comb(M - 2, N - 1) / math.comb(M, N)) + 1
+        r["fp64_fma_per_element"] = fma
+        r["fp64_issue_frac"] = fma * r["vector_len"] / (r["apply_ms"] / 1000) / FP64_INSTR_PEAK
+    out["ring_momentum"] = {"workload": "Hubbard ring, half filling, t=1, U=4; k = pi subspace of the "
+                                        "translation (T eigenvalue -1) against the full sector",
+                            "M16_full": full16, "M16_kpi": kpi16, "M20_kpi": kpi20,
+                            "M16_E0_diff": abs(kpi16["E0"] - full16["E0"]),
+                            "M16_speedup_time_to_tol": full16["lanczos_s"] / kpi16["lanczos_s"]}
     return out
 
 
