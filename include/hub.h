@@ -52,7 +52,8 @@ extern "C" {
 #define HUB_SPIN_UP 0
 #define HUB_SPIN_DN 1
 
-#define HUB_MODE_AUTO 0   /* fast double-float path when t and U are uniform, else FP64 */
+#define HUB_MODE_AUTO 0   /* fast double-float path when t and U are uniform, else FP64;
+                             in a momentum sector: integer-pipe sums when t is uniform   */
 #define HUB_MODE_FP64 1   /* always the native FP64 kernels                              */
 
 #define HUB_SYM_NONE 0    /* the full sector (N_up, N_dn)                              */
@@ -281,15 +282,19 @@ int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_dev, double *
  *   - Requires hub_hopping and hub_set_U first, a bond set that T maps onto itself with equal
  *     t (a ring, a ring with further-neighbour bonds, ...), uniform U and uniform eps;
  *     otherwise HUB_ERR_ARG.  HUB_ERR_OOM if one k = 0 vector would not fit on the device.
- *   - Layout ("row form"): the up strings are grouped into T-cycles; the smallest member of
- *     each is its representative R_i (i = 0 .. rows-1, ascending; hub_k_reps gives them and
- *     their periods P_i).  A k = 0 state Psi is stored as the rows x cols FP64 array
- *         X[i * cols + r] = sqrt(P_i) * Psi(R_i, d_r),   cols = count_dn,
- *     d_r the down string of rank r; the plain dot product of two such arrays is the inner
- *     product of the states.  Rows with P_i < M hold tied entries (a cycle of T^P_i within
- *     the row); hub_k_project enforces the ties, and entries of cycles with no k = 0 state
- *     are zero.  dim (hub_k_dims) is the number of independent entries, the dimension of
- *     the k = 0 space.
+ *   - Layout ("row form", the order of the paper's Table I): the strings of each spin are
+ *     grouped into T-cycles; the smallest member of a cycle is its representative.  Rows:
+ *     the up representatives R_i (i = 0 .. rows-1, ascending; hub_k_reps gives them and
+ *     their periods P_i).  Columns: the down representatives R_j ascending, each followed by
+ *     its translations, column c = (j, n) for n = 0 .. P_j - 1 (hub_k_columns gives the
+ *     string d_c of T^n R_j and the sign s_c with T^n |R_j> = s_c |d_c>); cols = count_dn.
+ *     A state Psi of the sector is stored as the rows x cols FP64 array
+ *         X[i * cols + c] = sqrt(P_i) * s_c * Psi(R_i, d_c),
+ *     and the plain dot product of two such arrays is the inner product of the states.
+ *     Rows with P_i < M hold tied entries (a cycle of T^P_i within each column block);
+ *     hub_k_project enforces the ties, and entries of cycles with no state in the sector are
+ *     zero.  dim (hub_k_dims) is the number of independent entries, the dimension of the
+ *     sector.
  *   - While it is active, vectors of hub_apply, hub_apply_host, hub_lanczos_ground,
  *     hub_lanczos_spectrum, hub_lanczos_ritz and hub_green_coeffs are row-form arrays of
  *     length rows * cols; start vectors are projected; products always return projected
@@ -305,6 +310,9 @@ int hub_k_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim);
 
 /* Up representatives R_i and periods P_i of the rows (host arrays of length rows). */
 int hub_k_reps(hub_t h, uint32_t *rep_host, int32_t *period_host);
+
+/* Down string d_c and sign s_c of every column (host arrays of length cols). */
+int hub_k_columns(hub_t h, uint32_t *dn_host, int32_t *sign_host);
 
 /*
  * y_dev = the row-form array x_dev with the ties of the short rows enforced (the

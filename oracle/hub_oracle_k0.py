@@ -317,3 +317,35 @@ def row_form(M: int, n_up: int, n_dn: int, B: np.ndarray, psi: np.ndarray):
     I = reps[:, None] + (S_dn[None, :] << np.uint64(M))
     X = psi[_index(B, I.ravel())].reshape(reps.shape[0], S_dn.shape[0]) * np.sqrt(per)[:, None]
     return X, reps, per
+
+
+def rep_columns(M: int, N: int):
+    """Column order of Table I for one spin: representatives R_j ascending, then the
+    translations n = 0 .. P_j - 1; per column the string d = T^n R_j and the sign s with
+    T^n |R_j> = s |d>.  Returns (d_bits, sign)."""
+    tb = spin_tables(M, N)
+    is_rep = tb["state"] == tb["rep"]
+    reps, per = tb["state"][is_rep], tb["period"][is_rep]
+    bits, sign = [], []
+    for R, P in zip(reps.tolist(), per.tolist()):
+        d, s = np.array([R], dtype=np.uint64), np.ones(1)
+        for _ in range(P):
+            bits.append(int(d[0]))
+            sign.append(float(s[0]))
+            d, si = translate(M, d, N)
+            s = s * si
+    return np.array(bits, dtype=np.uint64), np.array(sign)
+
+
+def row_form_rep(M: int, n_up: int, n_dn: int, B: np.ndarray, psi: np.ndarray):
+    """A translation-invariant two-spin vector psi on the rows of the up representatives
+    with the columns of Table I's order: X[i, c] = sqrt(P_i) <R_i (x) T^n R_j | psi>
+    = sqrt(P_i) s_c psi(R_i, d_c) for column c = (R_j, n) of ``rep_columns``.  Returns
+    (X, reps, periods)."""
+    tb = spin_tables(M, n_up)
+    is_rep = tb["state"] == tb["rep"]
+    reps, per = tb["state"][is_rep], tb["period"][is_rep]
+    d_bits, sign = rep_columns(M, n_dn)
+    I = reps[:, None] + (d_bits[None, :] << np.uint64(M))
+    X = psi[_index(B, I.ravel())].reshape(reps.shape[0], d_bits.shape[0])
+    return X * np.sqrt(per)[:, None] * sign[None, :], reps, per

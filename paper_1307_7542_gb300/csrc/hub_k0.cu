@@ -1,35 +1,46 @@
-// hub_k0.cu -- the k = 0 sector of a translation-invariant chain (Sec. V).
+// hub_k0.cu -- momentum sectors (k = 0 and k = pi) of a translation-invariant chain (Sec. V).
 //
 // T moves every electron one site down the chain, T c+_i T^-1 = c+_{i-1} (site 0 to site
 // M-1), the direction of Tables I and II.  On a spin string x with N electrons (sites in
 // ascending order) one step is the rotation x -> (x >> 1) | (x & 1) << (M-1) with sign
-// (-1)^(N-1) when site 0 was occupied; after t steps the sign is (-1)^((N-1) c) with c the
-// electrons of x on sites 0 .. t-1.
+// (-1)^(N-1) when site 0 was occupied.  A string's cycle under T has a period P (a divisor of
+// M); its smallest member is the representative R, and T^P |R> = b |R> with b = +-1.
 //
-// Layout ("row form").  The up strings fall into translation cycles; the smallest member of
-// a cycle is its representative R_i (Sec. V), i = 0 .. rows-1 in ascending order, with
-// period P_i.  A k = 0 vector Psi of the full two-spin space is determined by its values on
-// the pairs (R_i, d), d any down string, and is stored as
-//     X[i * cols + r] = sqrt(P_i) * Psi(R_i, d_r),   cols = count_dn, r the rank of d_r,
-// so that the Euclidean inner product of two such arrays equals that of the two-spin
-// vectors.  When P_i = M every pair (R_i, d) lies in a different cycle of T and row i is
-// free.  When P_i < M, T^P_i maps row i to itself (T^P_i |R_i> = b_i |R_i>), and the
-// entries of one T^P_i-cycle of the row are tied together; a cycle whose closing sign is -1
-// has no k = 0 state and is zero.  The library keeps those few rows consistent: every
-// product and every start vector is projected onto them, with each cycle's average summed
-// in one fixed order so that the tied entries agree bit for bit.
+// Layout ("row form", the order of Table I).  Rows: the up representatives R_i, ascending,
+// periods P_i.  Columns: the down representatives R_j, ascending, each followed by its
+// translations: column c = (j, n), n = 0 .. P_j - 1, stands for the signed state T^n |R_j>.
+// A state Psi of the sector (T Psi = omega Psi, omega = 1 for k = 0, -1 for k = pi) is stored as
+//     X[i * cols + c] = sqrt(P_i) <R_i (x) T^n R_j | Psi>,        cols = count_dn,
+// and the plain dot product of two such arrays equals the inner product of the states.  When
+// P_i = M every column of row i belongs to a different cycle of T and the row is free.  When
+// P_i < M, T^P_i maps row i into itself and ties the entries n, n + P_i, ... of each column
+// block; a cycle whose closing sign is -1 has no state in the sector and is zero.  The
+// library keeps those few rows consistent: every product and every start vector is
+// projected onto them, each cycle's average summed in one fixed order so that tied entries
+// agree bit for bit.
 //
-// The k = pi sector (T Psi = -Psi, M even) uses the same layout: every relation
-// Psi(T^t c) = tau Psi(c) of the k = 0 sector gains the factor (-1)^t, so the up-hop
-// coefficients take (-1)^t and the closing sign of a short row b_i becomes (-1)^P_i b_i.
+// Product (Sec. V with Eq. 11): for entry (i, c), c = (j, n), d the string of T^n R_j,
+//     Y = (U popc(R_i & d) + eps (N_up + N_dn)) X[i, c]                           diagonal
+//       + sum_c' H_dn[d, d'] s_c s_c' X[i, c']                                      down hops
+//       + sum_{u'} H_up[R_i, u'] s omega^t sqrt(P_i / P_i') b_j^w X[i', (j, n - t mod P_j)]
+// where s_c is the sign of T^n |R_j> relative to |d>, T^t |R_i'> = s |u'> (R_i' the
+// representative of u', t < P_i'), and w counts the wraps of n - t below zero.  An up hop is
+// thus a cyclic shift inside each column block of another row: the gathers of consecutive
+// columns are consecutive words.  The up-hop list of each row (i', t, coefficient) and the
+// down hopping matrix in this column order are built on the host.
 //
-// Product in row form (Sec. V with Eq. 11): for (i, d)
-//     Y = (U popc(R_i & d) + eps (N_up + N_dn)) X[i, d]                diagonal
-//       + sum_d' H_dn[d, d'] X[i, d']                                    down hops, in-row
-//       + sum_{u'} H_up[R_i, u'] s sqrt(P_i / P_i') s_e X[i', e]          up hops
-// where T^t |R_i'> = s |u'> (R_i' the representative of u', t < P_i') and e = T^-t d with
-// T^t |e> = s_e |d>.  The up-hop list of each row (i', t, coefficient) is built on the host;
-// the (rank of T^-t d, s_e) table for all t < M and all down strings on the device.
+// Integer accumulation.  GB300 issues FP64 at about 1/70 of its FP32 and integer rates, and
+// the product above is about 22 FP64 multiply-adds per entry.  With uniform t every hop term
+// is -t times +-x, so the entry is diag x + (-t) S with S a signed sum of gathered values.
+// S is formed in 64-bit fixed point on the integer pipe: the point sits at the largest
+// exponent among the entry's own terms (the accumulator is shifted down whenever a larger one
+// arrives), each term's 53-bit significand shifted in with s0 guard bits, s0 chosen so that
+// no sum of the entry's terms can overflow.  The only rounding is the truncation of each
+// aligned term, below 2^-(52+s0) of the largest term, far inside the 1e-13 (|H||x|)_n bound;
+// one int64 -> FP64 conversion and two FP64 multiply-adds finish the entry.  Hops whose
+// coefficient is not +-t (rows of period P_i < M and hops into them, factor
+// sqrt(P_i / P_i')) stay in FP64.  HUB_MODE_FP64 selects a kernel with FP64 multiply-adds
+// throughout (also used when t is not uniform).
 #include <algorithm>
 #include <cmath>
 #include <map>
@@ -44,25 +55,37 @@ namespace hub {
 int ready(const hub_ctx *h, const char *who);
 
 constexpr int kK0Threads = 256;
+// uh_t word: translation t in bits 0-7; integer path: the hop's coefficient is +-t (bit 8),
+// and its sign relative to -t (bit 9)
+constexpr int kHopUnit = 1 << 8, kHopNeg = 1 << 9;
+// column word: n in bits 0-7, P_j in bits 8-15, b_j = -1 in bit 16
+constexpr uint32_t kColNegB = 1u << 16;
 
 struct K0State {
   int64_t rows = 0, cols = 0, dim = 0;
-  std::vector<uint32_t> rep_h;
-  std::vector<int32_t> per_h;
+  std::vector<uint32_t> rep_h, col_bits_h;
+  std::vector<int32_t> per_h, col_sign_h;
   uint32_t *rep = nullptr;      // [rows] up representatives, ascending
   int32_t *per = nullptr;       // [rows] their periods
   int32_t *eb = nullptr;        // [rows] sign of T^P_i on R_i, times omega^P_i
-  int omega = 1;                // e^{ik}: 1 for k = 0, -1 for k = pi
   int32_t *uh_ptr = nullptr;    // [rows + 1] up-hop list of each row
   int32_t *uh_row = nullptr;    // [n_uh] target row i'
-  int32_t *uh_t = nullptr;      // [n_uh] translation t
-  double *uh_val = nullptr;     // [n_uh] H_up[R_i, u'] s sqrt(P_i / P_i')
-  uint32_t *rot = nullptr;      // [M * cols] rank of T^-t d | (s_e = -1) << 31
+  int32_t *uh_t = nullptr;      // [n_uh] translation t and flags
+  double *uh_val = nullptr;     // [n_uh] H_up[R_i, u'] s omega^t sqrt(P_i / P_i')
+  uint32_t *cinfo = nullptr;    // [cols] n | P_j << 8 | (b_j < 0) << 16
+  uint32_t *cbits = nullptr;    // [cols] down string of the column
+  int32_t *krp = nullptr;       // [cols + 1] down hopping matrix in column order
+  uint32_t *kscol = nullptr;    // [nnz] column | (sign of JW s_c s_c') << 31
+  double *kval = nullptr;       // [nnz] -t_b JW s_c s_c'
   int32_t *short_rows = nullptr;   // rows with P_i < M
   int n_short = 0;
   double *scratch = nullptr;    // [n_short * cols]
   unsigned long long *d_count = nullptr;
   double diag0 = 0.0;           // eps (N_up + N_dn) for uniform eps
+  int omega = 1;                // e^{ik}: 1 for k = 0, -1 for k = pi
+  int fix = 0;                  // integer accumulation of the +-t hops (uniform t)
+  int s0 = 0;                   // guard bits of the fixed-point terms
+  double mt = 0.0;              // -t
 };
 
 struct K0View {
@@ -72,16 +95,17 @@ struct K0View {
   const int32_t *per, *eb;
   const int32_t *uh_ptr, *uh_row, *uh_t;
   const double *uh_val;
-  const uint32_t *rot;
-  const int32_t *rp_dn, *col_dn;
-  const double *val_dn;
-  const uint32_t *basis_dn;
+  const uint32_t *cinfo, *cbits;
+  const int32_t *krp;
+  const uint32_t *kscol;
+  const double *kval;
   double U0, diag0;
+  int s0;
+  double mt;
 };
 
 static K0View k0_view(const hub_ctx *h) {
   const K0State *k = h->k0;
-  const Ham H = h->view();
   K0View v{};
   v.M = h->M;
   v.rows = k->rows;
@@ -93,13 +117,15 @@ static K0View k0_view(const hub_ctx *h) {
   v.uh_row = k->uh_row;
   v.uh_t = k->uh_t;
   v.uh_val = k->uh_val;
-  v.rot = k->rot;
-  v.rp_dn = H.rp_dn;
-  v.col_dn = H.col_dn;
-  v.val_dn = H.val_dn;
-  v.basis_dn = H.basis_dn;
+  v.cinfo = k->cinfo;
+  v.cbits = k->cbits;
+  v.krp = k->krp;
+  v.kscol = k->kscol;
+  v.kval = k->kval;
   v.U0 = h->U0;
   v.diag0 = k->diag0;
+  v.s0 = k->s0;
+  v.mt = k->mt;
   return v;
 }
 
@@ -107,93 +133,231 @@ static K0View k0_view(const hub_ctx *h) {
 // Device side
 // ---------------------------------------------------------------------------------------
 
-// (rank of e = T^-t d, s_e) for every t < M and every down string d of rank r.
-__global__ void k_k0_rot(int M, int N, int64_t cols, const uint32_t *__restrict__ basis,
-                         const uint64_t *__restrict__ C, uint32_t *__restrict__ rot) {
-  const uint32_t mask = (uint32_t)((1ull << M) - 1);
-  const int64_t n = (int64_t)M * cols;
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int t = (int)(k / cols);
-    const uint32_t d = basis[k - (int64_t)t * cols];
-    const uint32_t e = t ? (((d << t) | (d >> (M - t))) & mask) : d;
-    const int c = __popc(e & (uint32_t)((1ull << t) - 1));
-    const bool neg = ((N - 1) & 1) && (c & 1);
-    rot[k] = rank_of(e, C) | (neg ? 0x80000000u : 0u);
+// Column of (j, n - t mod P_j) for column c = (j, n) with word ci, and whether the shift
+// picks up b_j an odd number of times (n - t wrapped below zero an odd number of times).
+__device__ __forceinline__ uint32_t k0_shift(uint32_t c, uint32_t ci, int t, bool *flip) {
+  const int n = (int)(ci & 0xff), P = (int)((ci >> 8) & 0xff);
+  int m = n - t, q = 0;
+  for (int it = 0; m < 0 && it < 256; ++it) {   // n - t > -M, P >= 1: at most M - 1 steps
+    m += P;
+    ++q;
   }
+  *flip = (ci & kColNegB) && (q & 1);
+  return c - (uint32_t)n + (uint32_t)m;
 }
 
-// Member g of the T^P-cycle of column r in a row with period P and closing sign b:
-// position of T^-(gP) d and the sign beta with Psi(R, d) = beta Psi(R, T^-(gP) d).
-__device__ __forceinline__ uint32_t k0_member(const K0View &K, int P, int b, int g, int64_t r, int *sign) {
-  const uint32_t w = __ldg(K.rot + (int64_t)(g * P) * K.cols + r);
-  int s = (w >> 31) ? -1 : 1;
-  if (b < 0 && (g & 1)) s = -s;
+// Member g of the T^P-cycle of column c in a row with period P and closing sign b (times
+// omega^P): its column and the sign beta with X[i, c] = beta X[i, member].
+__device__ __forceinline__ uint32_t k0_member(const K0View &K, int P, int b, int g, uint32_t c, int *sign) {
+  const uint32_t ci = __ldg(K.cinfo + c);
+  const int n = (int)(ci & 0xff), Pj = (int)((ci >> 8) & 0xff);
+  const int v = n + g * P, q = v / Pj, m = v - q * Pj;
+  int s = (b < 0 && (g & 1)) ? -1 : 1;
+  if ((ci & kColNegB) && (q & 1)) s = -s;
   *sign = s;
-  return w & 0x7fffffffu;
+  return c - (uint32_t)n + (uint32_t)m;
 }
 
-// Row value of the product at (i, r) before the projection of short rows.
-__device__ __forceinline__ double k0_row_value(const K0View &K, int64_t i, int64_t r, const double *__restrict__ x) {
+// Row value of the product at (i, c) before the projection of short rows, FP64 throughout.
+__device__ __forceinline__ double k0_row_value(const K0View &K, int64_t i, int64_t c, const double *__restrict__ x) {
   const double *xi = x + i * K.cols;
-  double acc = fma(K.U0, (double)__popc(__ldg(K.rep + i) & __ldg(K.basis_dn + r)), K.diag0) * xi[r];
-  const int k0 = __ldg(K.rp_dn + r), k1 = __ldg(K.rp_dn + r + 1);
-  for (int k = k0; k < k1; ++k) acc = fma(__ldg(K.val_dn + k), xi[__ldg(K.col_dn + k)], acc);
+  double acc = fma(K.U0, (double)__popc(__ldg(K.rep + i) & __ldg(K.cbits + c)), K.diag0) * xi[c];
+  const int k0 = __ldg(K.krp + c), k1 = __ldg(K.krp + c + 1);
+  int k = k0;
+  for (; k + 4 <= k1; k += 4) {          // four gathers in flight before the multiply-adds
+    uint32_t w[4];
+    double v[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = __ldg(K.kscol + k + j);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) v[j] = xi[w[j] & 0x7fffffffu];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc = fma(__ldg(K.kval + k + j), v[j], acc);
+  }
+  for (; k < k1; ++k) acc = fma(__ldg(K.kval + k), xi[__ldg(K.kscol + k) & 0x7fffffffu], acc);
+  const uint32_t ci = __ldg(K.cinfo + c);
   const int h0 = __ldg(K.uh_ptr + i), h1 = __ldg(K.uh_ptr + i + 1);
-  for (int k = h0; k < h1; ++k) {
-    const uint32_t w = __ldg(K.rot + (int64_t)__ldg(K.uh_t + k) * K.cols + r);
-    const double c = __ldg(K.uh_val + k);
-    acc = fma((w >> 31) ? -c : c, x[(int64_t)__ldg(K.uh_row + k) * K.cols + (w & 0x7fffffffu)], acc);
+  for (k = h0; k < h1; ++k) {
+    bool flip;
+    const uint32_t c2 = k0_shift((uint32_t)c, ci, __ldg(K.uh_t + k) & 0xff, &flip);
+    const double cf = __ldg(K.uh_val + k);
+    acc = fma(flip ? -cf : cf, x[(int64_t)__ldg(K.uh_row + k) * K.cols + c2], acc);
   }
   return acc;
 }
 
-// Projection of a short row onto its tied cycles at column r: the cycle's average, summed
-// from its smallest-rank member in the order g = 0, 1, ..., times the sign relating r to
-// that member; 0 for a cycle that closes with sign -1.  value(pos) gives the unprojected
-// entry of the row at column pos.
-template <class F>
-__device__ __forceinline__ double k0_projected(const K0View &K, int64_t i, int64_t r, F value) {
-  const int P = __ldg(K.per + i), b = __ldg(K.eb + i), G = K.M / P;
-  int64_t c = r;
-  int cs = 1;
-  for (int g = 1; g < G; ++g) {
-    int s;
-    const int64_t pos = k0_member(K, P, b, g, r, &s);
-    if (pos == r && s < 0) return 0.0;
-    if (pos < c) {
-      c = pos;
-      cs = s;
+// Signed sum of FP64 values in 64-bit fixed point (see the integer accumulation above).
+struct FixSum {
+  long long acc;
+  int e;      // largest biased exponent so far (0: no nonzero term yet)
+  int bad;    // an Inf or NaN term was seen
+};
+
+// Four terms at once: one rescale to the largest of their exponents, then four aligned adds.
+__device__ __forceinline__ void fix_add4(FixSum &f, const double (&x)[4], const bool (&neg)[4], int s0) {
+  int ek[4];
+  unsigned long long m[4];
+  int emax = f.e;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[j]);
+    ek[j] = (int)((b >> 52) & 0x7ff);
+    m[j] = b & 0x000fffffffffffffull;
+    if (ek[j] == 0x7ff) {
+      f.bad = 1;
+      ek[j] = 0;
+      m[j] = 0;
+    } else if (ek[j] == 0) {
+      ek[j] = m[j] ? 1 : 0;                 // subnormal: exponent of 2^-1022, no implicit bit
+    } else {
+      m[j] |= 0x0010000000000000ull;
+    }
+    emax = max(emax, ek[j]);
+  }
+  if (emax > f.e) {
+    const int d = emax - f.e;
+    f.acc = d >= 63 ? (f.acc < 0 ? -1ll : 0ll) : (f.acc >> d);
+    f.e = emax;
+  }
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    const int sh = f.e - ek[j];
+    const long long v = sh >= 62 ? 0ll : (long long)((m[j] << s0) >> sh);
+    const bool sgn = (((unsigned long long)__double_as_longlong(x[j]) >> 63) != 0) != neg[j];
+    f.acc += sgn ? -v : v;
+  }
+}
+
+__device__ __forceinline__ void fix_add(FixSum &f, double x, bool neg, int s0) {
+  const double xs[4] = {x, 0.0, 0.0, 0.0};
+  const bool ns[4] = {neg, false, false, false};
+  fix_add4(f, xs, ns, s0);
+}
+
+__device__ __forceinline__ double fix_value(const FixSum &f, int s0) {
+  if (f.bad) return __longlong_as_double(0x7ff8000000000000ll);
+  if (f.acc == 0) return 0.0;
+  return ldexp((double)f.acc, f.e - 1075 - s0);
+}
+
+// Row value on the integer path: diag x + (-t) S + (hops with other coefficients, FP64).
+__device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, int64_t c,
+                                                    const double *__restrict__ x) {
+  const double *xi = x + i * K.cols;
+  FixSum f{0ll, 0, 0};
+  double side = 0.0;
+  const int k0 = __ldg(K.krp + c), k1 = __ldg(K.krp + c + 1);
+  int k = k0;
+  for (; k + 4 <= k1; k += 4) {          // four gathers in flight before any arithmetic
+    uint32_t w[4];
+    double v[4];
+    bool ng[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) w[j] = __ldg(K.kscol + k + j);
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      v[j] = xi[w[j] & 0x7fffffffu];
+      ng[j] = (w[j] >> 31) != 0;
+    }
+    fix_add4(f, v, ng, K.s0);
+  }
+  for (; k < k1; ++k) {
+    const uint32_t w = __ldg(K.kscol + k);
+    fix_add(f, xi[w & 0x7fffffffu], (w >> 31) != 0, K.s0);
+  }
+  const uint32_t ci = __ldg(K.cinfo + c);
+  const int h0 = __ldg(K.uh_ptr + i), h1 = __ldg(K.uh_ptr + i + 1);
+  for (k = h0; k + 4 <= h1; k += 4) {
+    int tw[4];
+    double v[4];
+    bool fl[4], ng[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      tw[j] = __ldg(K.uh_t + k + j);
+      const uint32_t c2 = k0_shift((uint32_t)c, ci, tw[j] & 0xff, &fl[j]);
+      v[j] = x[(int64_t)__ldg(K.uh_row + k + j) * K.cols + c2];
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      ng[j] = fl[j] != ((tw[j] & kHopNeg) != 0);
+      if (!(tw[j] & kHopUnit)) {
+        const double cf = __ldg(K.uh_val + k + j);
+        side = fma(fl[j] ? -cf : cf, v[j], side);
+        v[j] = 0.0;
+      }
+    }
+    fix_add4(f, v, ng, K.s0);
+  }
+  for (; k < h1; ++k) {
+    const int tw = __ldg(K.uh_t + k);
+    bool flip;
+    const uint32_t c2 = k0_shift((uint32_t)c, ci, tw & 0xff, &flip);
+    const double v = x[(int64_t)__ldg(K.uh_row + k) * K.cols + c2];
+    if (tw & kHopUnit) {
+      fix_add(f, v, flip != ((tw & kHopNeg) != 0), K.s0);
+    } else {
+      const double cf = __ldg(K.uh_val + k);
+      side = fma(flip ? -cf : cf, v, side);
     }
   }
-  double sum = value(c);
+  const double diag = fma(K.U0, (double)__popc(__ldg(K.rep + i) & __ldg(K.cbits + c)), K.diag0);
+  return fma(diag, xi[c], fma(K.mt, fix_value(f, K.s0), side));
+}
+
+template <bool kFix>
+__device__ __forceinline__ double k0_value(const K0View &K, int64_t i, int64_t c, const double *__restrict__ x) {
+  if (kFix) return k0_row_value_fix(K, i, c, x);
+  return k0_row_value(K, i, c, x);
+}
+
+// Projection of a short row onto its tied cycles at column c: the cycle's average, summed
+// from its smallest member in the order g = 0, 1, ..., times the sign relating c to that
+// member; 0 for a cycle that closes with sign -1.  value(col) gives the unprojected entry of
+// the row at a column.
+template <class F>
+__device__ __forceinline__ double k0_projected(const K0View &K, int64_t i, int64_t c, F value) {
+  const int P = __ldg(K.per + i), b = __ldg(K.eb + i), G = K.M / P;
+  uint32_t least = (uint32_t)c;
+  int ls = 1;
   for (int g = 1; g < G; ++g) {
     int s;
-    const int64_t pos = k0_member(K, P, b, g, c, &s);
-    const double v = value(pos);
+    const uint32_t pos = k0_member(K, P, b, g, (uint32_t)c, &s);
+    if (pos == (uint32_t)c && s < 0) return 0.0;
+    if (pos < least) {
+      least = pos;
+      ls = s;
+    }
+  }
+  double sum = value((int64_t)least);
+  for (int g = 1; g < G; ++g) {
+    int s;
+    const uint32_t pos = k0_member(K, P, b, g, least, &s);
+    const double v = value((int64_t)pos);
     sum += s < 0 ? -v : v;
   }
   const double avg = sum / (double)G;
-  return cs < 0 ? -avg : avg;
+  return ls < 0 ? -avg : avg;
 }
 
+template <bool kFix>
 __global__ void __launch_bounds__(kK0Threads) k_k0_apply(K0View K, const double *__restrict__ x,
                                                          double *__restrict__ y) {
   const int64_t chunks = (K.cols + kK0Threads - 1) / kK0Threads;
   const int64_t tiles = K.rows * chunks;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
     const int64_t i = tile / chunks;
-    const int64_t r = (tile - i * chunks) * kK0Threads + threadIdx.x;
-    if (r >= K.cols) continue;
+    const int64_t c = (tile - i * chunks) * kK0Threads + threadIdx.x;
+    if (c >= K.cols) continue;
     double v;
     if (__ldg(K.per + i) == K.M)
-      v = k0_row_value(K, i, r, x);
+      v = k0_value<kFix>(K, i, c, x);
     else
-      v = k0_projected(K, i, r, [&](int64_t pos) { return k0_row_value(K, i, pos, x); });
-    y[i * K.cols + r] = v;
+      v = k0_projected(K, i, c, [&](int64_t col) { return k0_value<kFix>(K, i, col, x); });
+    y[i * K.cols + c] = v;
   }
 }
 
-// scratch[s, r] = x[short_rows[s], r]
+// scratch[s, c] = x[short_rows[s], c]
 __global__ void k_k0_gather_short(int64_t cols, int n_short, const int32_t *__restrict__ short_rows,
                                   const double *__restrict__ x, double *__restrict__ scratch) {
   const int64_t n = (int64_t)n_short * cols;
@@ -203,34 +367,34 @@ __global__ void k_k0_gather_short(int64_t cols, int n_short, const int32_t *__re
   }
 }
 
-// y[short_rows[s], r] = projection of scratch row s at r
+// y[short_rows[s], c] = projection of scratch row s at c
 __global__ void k_k0_project_short(K0View K, int n_short, const int32_t *__restrict__ short_rows,
                                    const double *__restrict__ scratch, double *__restrict__ y) {
   const int64_t n = (int64_t)n_short * K.cols;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = k / K.cols, r = k - s * K.cols;
+    const int64_t s = k / K.cols, c = k - s * K.cols;
     const double *src = scratch + s * K.cols;
     const int64_t i = short_rows[s];
-    y[i * K.cols + r] = k0_projected(K, i, r, [&](int64_t pos) { return src[pos]; });
+    y[i * K.cols + c] = k0_projected(K, i, c, [&](int64_t col) { return src[col]; });
   }
 }
 
-// Number of k = 0 states in the short rows: columns that are the smallest member of a
-// cycle that does not close with sign -1.
+// Number of states of the sector in the short rows: columns that are the smallest member of
+// a cycle that does not close with sign -1.
 __global__ void k_k0_count_short(K0View K, int n_short, const int32_t *__restrict__ short_rows,
                                  unsigned long long *__restrict__ count) {
   const int64_t n = (int64_t)n_short * K.cols;
   unsigned long long mine = 0;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
-    const int64_t s = k / K.cols, r = k - s * K.cols;
+    const int64_t s = k / K.cols, c = k - s * K.cols;
     const int64_t i = short_rows[s];
     const int P = K.per[i], b = K.eb[i], G = K.M / P;
     bool least = true, null = false;
     for (int g = 1; g < G; ++g) {
       int sg;
-      const int64_t pos = k0_member(K, P, b, g, r, &sg);
-      if (pos < r) least = false;
-      if (pos == r && sg < 0) null = true;
+      const uint32_t pos = k0_member(K, P, b, g, (uint32_t)c, &sg);
+      if (pos < (uint32_t)c) least = false;
+      if (pos == (uint32_t)c && sg < 0) null = true;
     }
     if (least && !null) ++mine;
   }
@@ -245,6 +409,44 @@ __global__ void k_k0_count_short(K0View K, int n_short, const int32_t *__restric
 static inline uint32_t step_T(uint32_t x, int M) { return (x >> 1) | ((x & 1u) << (M - 1)); }
 static inline int step_sign(uint32_t x, int N) { return ((x & 1u) && ((N - 1) & 1)) ? -1 : 1; }
 
+// All M-bit strings with N ones, ascending (Gosper's successor).
+static std::vector<uint32_t> strings_of(int M, int N) {
+  std::vector<uint32_t> out;
+  const uint64_t limit = 1ull << M;
+  uint64_t u = N == 0 ? 0 : (1ull << N) - 1;
+  while (u < limit) {
+    out.push_back((uint32_t)u);
+    if (N == 0) break;
+    const uint64_t lo = u & (~u + 1), r = u + lo;
+    u = (((r ^ u) >> 2) / lo) | r;
+  }
+  return out;
+}
+
+// Cycle data of string x: is it the smallest member, its period, and the closing sign of
+// T^P on it.
+static void cycle_of(uint32_t x, int M, int N, bool *is_rep, int *P, int *b) {
+  uint32_t c = x;
+  bool least = true;
+  *P = M;
+  for (int s = 1; s <= M; ++s) {
+    c = step_T(c, M);
+    if (c == x) {
+      *P = s;
+      break;
+    }
+    if (c < x) least = false;
+  }
+  int sg = 1;
+  uint32_t y = x;
+  for (int s = 0; s < *P; ++s) {
+    sg *= step_sign(y, N);
+    y = step_T(y, M);
+  }
+  *is_rep = least;
+  *b = sg;
+}
+
 void k0_release(hub_ctx *h) {
   K0State *k = h->k0;
   if (!k) return;
@@ -255,7 +457,11 @@ void k0_release(hub_ctx *h) {
   dev_free(k->uh_row);
   dev_free(k->uh_t);
   dev_free(k->uh_val);
-  dev_free(k->rot);
+  dev_free(k->cinfo);
+  dev_free(k->cbits);
+  dev_free(k->krp);
+  dev_free(k->kscol);
+  dev_free(k->kval);
   dev_free(k->short_rows);
   dev_free(k->scratch);
   dev_free(k->d_count);
@@ -306,6 +512,12 @@ static int check_invariant(const hub_ctx *h) {
   return HUB_OK;
 }
 
+template <class T>
+static bool upload(T **dst, const std::vector<T> &src, const char *what) {
+  if (!dev_alloc((void **)dst, sizeof(T) * std::max<size_t>(src.size(), 1), what)) return false;
+  return src.empty() || cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+}
+
 static int k0_build(hub_ctx *h, int omega) {
   const int M = h->M, Nu = h->N[0], Nd = h->N[1];
   K0State *k = new (std::nothrow) K0State();
@@ -315,51 +527,37 @@ static int k0_build(hub_ctx *h, int omega) {
   k->cols = h->count[1];
   k->diag0 = (h->eps.empty() ? 0.0 : h->eps[0]) * (double)(Nu + Nd);
 
-  // up representatives (smallest member of each cycle), ascending, with periods and signs
+  // rows: up representatives, ascending, with periods and closing signs (times omega^P)
   std::vector<uint32_t> reps;
   std::vector<int32_t> per, eb;
-  {
-    const uint64_t limit = 1ull << M;
-    uint64_t u = Nu == 0 ? 0 : (1ull << Nu) - 1;
-    while (u < limit) {
-      const uint32_t x = (uint32_t)u;
-      uint32_t c = x, least = x;
-      int P = M;
-      for (int s = 1; s <= M; ++s) {
-        c = step_T(c, M);
-        if (c == x) {
-          P = s;
-          break;
-        }
-        least = std::min(least, c);
-      }
-      if (least == x) {
-        int sg = 1;
-        uint32_t y = x;
-        for (int s = 0; s < P; ++s) {
-          sg *= step_sign(y, Nu);
-          y = step_T(y, M);
-        }
-        reps.push_back(x);
-        per.push_back(P);
-        eb.push_back((omega < 0 && (P & 1)) ? -sg : sg);
-      }
-      if (Nu == 0) break;
-      const uint64_t lo = u & (~u + 1), r = u + lo;   // next string with Nu bits (Gosper)
-      u = (((r ^ u) >> 2) / lo) | r;
-    }
+  for (uint32_t x : strings_of(M, Nu)) {
+    bool is_rep;
+    int P, b;
+    cycle_of(x, M, Nu, &is_rep, &P, &b);
+    if (!is_rep) continue;
+    reps.push_back(x);
+    per.push_back(P);
+    eb.push_back((omega < 0 && (P & 1)) ? -b : b);
   }
   k->rows = (int64_t)reps.size();
   k->rep_h = reps;
   k->per_h = per;
 
-  // size check before any large allocation
   size_t free_b = 0, total_b = 0;
   HUB_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  const double row_form_bytes = 8.0 * (double)k->rows * (double)k->cols;
-  if (row_form_bytes > (double)free_b) return fail(HUB_ERR_OOM, "hub_set_symmetry: one k = 0 vector does not fit");
+  if (8.0 * (double)k->rows * (double)k->cols > (double)free_b)
+    return fail(HUB_ERR_OOM, "hub_set_symmetry: one vector of the sector does not fit");
 
-  // up-hop lists
+  // integer accumulation: uniform nonzero t and room for every entry's terms (at most one per
+  // bond and spin) with at least one guard bit: terms * 2^(53 + s0) < 2^63
+  const Ham Hv = h->view();
+  int terms_log2 = 0;
+  while ((1 << terms_log2) < 2 * std::max(h->n_bonds, 1)) ++terms_log2;
+  k->s0 = 10 - terms_log2;
+  k->mt = -Hv.t0;
+  k->fix = (Hv.uniform_t && Hv.t0 != 0.0 && k->s0 >= 1) ? 1 : 0;
+
+  // up-hop lists: hopped string u', its representative R_i' and t with T^t |R_i'> = s |u'>
   std::vector<int32_t> uh_ptr(1, 0), uh_row, uh_t;
   std::vector<double> uh_val;
   for (size_t i = 0; i < reps.size(); ++i) {
@@ -387,9 +585,14 @@ static int k0_build(hub_ctx *h, int omega) {
         ++t;
       }
       if (cur != u2) return fail(HUB_ERR_CUDA, "hub_set_symmetry: translation not found");
-      uh_row.push_back(i2);
-      uh_t.push_back(t);
       if (omega < 0 && (t & 1)) sg = -sg;
+      int tw = t;
+      if (per[i] == per[i2] && k->fix) {
+        tw |= kHopUnit;
+        if (val * sg / k->mt < 0) tw |= kHopNeg;
+      }
+      uh_row.push_back(i2);
+      uh_t.push_back(tw);
       uh_val.push_back(val * sg * std::sqrt((double)per[i] / (double)per[i2]));
     }
     uh_ptr.push_back((int32_t)uh_row.size());
@@ -399,46 +602,79 @@ static int k0_build(hub_ctx *h, int omega) {
     if (per[i] < M) shorts.push_back((int32_t)i);
   k->n_short = (int)shorts.size();
 
-  const size_t n_uh = std::max<size_t>(uh_row.size(), 1);
-  const int64_t nrot = (int64_t)M * k->cols;
-  if (!dev_alloc((void **)&k->rep, sizeof(uint32_t) * std::max<int64_t>(k->rows, 1), "k = 0 representatives") ||
-      !dev_alloc((void **)&k->per, sizeof(int32_t) * std::max<int64_t>(k->rows, 1), "k = 0 periods") ||
-      !dev_alloc((void **)&k->eb, sizeof(int32_t) * std::max<int64_t>(k->rows, 1), "k = 0 signs") ||
-      !dev_alloc((void **)&k->uh_ptr, sizeof(int32_t) * (k->rows + 1), "k = 0 up hops") ||
-      !dev_alloc((void **)&k->uh_row, sizeof(int32_t) * n_uh, "k = 0 up hops") ||
-      !dev_alloc((void **)&k->uh_t, sizeof(int32_t) * n_uh, "k = 0 up hops") ||
-      !dev_alloc((void **)&k->uh_val, sizeof(double) * n_uh, "k = 0 up hops") ||
-      !dev_alloc((void **)&k->rot, sizeof(uint32_t) * std::max<int64_t>(nrot, 1), "k = 0 translation table") ||
-      !dev_alloc((void **)&k->short_rows, sizeof(int32_t) * std::max<size_t>(shorts.size(), 1), "k = 0 short rows") ||
-      !dev_alloc((void **)&k->scratch, sizeof(double) * std::max<int64_t>(k->n_short * k->cols, 1), "k = 0 scratch") ||
-      !dev_alloc((void **)&k->d_count, sizeof(unsigned long long), "k = 0 counter"))
-    return HUB_ERR_OOM;
-  if (k->rows) {
-    HUB_CUDA(cudaMemcpy(k->rep, reps.data(), sizeof(uint32_t) * k->rows, cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(k->per, per.data(), sizeof(int32_t) * k->rows, cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(k->eb, eb.data(), sizeof(int32_t) * k->rows, cudaMemcpyHostToDevice));
+  // columns in the order of Table I: down representatives ascending, then n = 0 .. P_j - 1
+  const std::vector<uint32_t> dn = strings_of(M, Nd);
+  if ((int64_t)dn.size() != k->cols) return fail(HUB_ERR_CUDA, "hub_set_symmetry: down basis size mismatch");
+  std::vector<uint32_t> cinfo, cbits;
+  std::vector<int32_t> csign, pos(dn.size(), -1);
+  for (uint32_t x : dn) {
+    bool is_rep;
+    int P, b;
+    cycle_of(x, M, Nd, &is_rep, &P, &b);
+    if (!is_rep) continue;
+    uint32_t d = x;
+    int s = 1;
+    for (int n = 0; n < P; ++n) {
+      const size_t r = (size_t)(std::lower_bound(dn.begin(), dn.end(), d) - dn.begin());
+      pos[r] = (int32_t)cbits.size();
+      cinfo.push_back((uint32_t)n | ((uint32_t)P << 8) | (b < 0 ? kColNegB : 0u));
+      cbits.push_back(d);
+      csign.push_back(s);
+      s *= step_sign(d, Nd);
+      d = step_T(d, M);
+    }
   }
-  HUB_CUDA(cudaMemcpy(k->uh_ptr, uh_ptr.data(), sizeof(int32_t) * (k->rows + 1), cudaMemcpyHostToDevice));
-  if (!uh_row.empty()) {
-    HUB_CUDA(cudaMemcpy(k->uh_row, uh_row.data(), sizeof(int32_t) * uh_row.size(), cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(k->uh_t, uh_t.data(), sizeof(int32_t) * uh_t.size(), cudaMemcpyHostToDevice));
-    HUB_CUDA(cudaMemcpy(k->uh_val, uh_val.data(), sizeof(double) * uh_val.size(), cudaMemcpyHostToDevice));
+  if ((int64_t)cbits.size() != k->cols || std::find(pos.begin(), pos.end(), -1) != pos.end())
+    return fail(HUB_ERR_CUDA, "hub_set_symmetry: column order incomplete");
+  k->col_bits_h = cbits;
+  k->col_sign_h = csign;
+
+  // the down hopping matrix of a2 relabelled to this column order, signs s_c s_c' folded in
+  const SpinCSR &cd = h->csr[h->shared ? 0 : 1];
+  std::vector<int32_t> rp(k->cols + 1), col(std::max<int64_t>(cd.nnz, 1));
+  std::vector<uint32_t> scol(std::max<int64_t>(cd.nnz, 1));
+  std::vector<double> val(std::max<int64_t>(cd.nnz, 1));
+  HUB_CUDA(cudaMemcpy(rp.data(), cd.rowptr, sizeof(int32_t) * (k->cols + 1), cudaMemcpyDeviceToHost));
+  if (cd.nnz) {
+    HUB_CUDA(cudaMemcpy(col.data(), cd.col, sizeof(int32_t) * cd.nnz, cudaMemcpyDeviceToHost));
+    HUB_CUDA(cudaMemcpy(scol.data(), cd.scol, sizeof(uint32_t) * cd.nnz, cudaMemcpyDeviceToHost));
+    HUB_CUDA(cudaMemcpy(val.data(), cd.val, sizeof(double) * cd.nnz, cudaMemcpyDeviceToHost));
   }
-  if (!shorts.empty())
-    HUB_CUDA(cudaMemcpy(k->short_rows, shorts.data(), sizeof(int32_t) * shorts.size(), cudaMemcpyHostToDevice));
-  const int sms = num_sms();
-  if (nrot > 0) {
-    k_k0_rot<<<(int)std::min<int64_t>((nrot + 255) / 256, (int64_t)sms * 32), 256>>>(M, Nd, k->cols, h->basis[1],
-                                                                                   h->binom, k->rot);
-    HUB_LAUNCH_CHECK();
+  std::vector<int32_t> krp(1, 0);
+  std::vector<uint32_t> kscol;
+  std::vector<double> kval;
+  kscol.reserve(std::max<int64_t>(cd.nnz, 1));
+  kval.reserve(std::max<int64_t>(cd.nnz, 1));
+  for (int64_t c = 0; c < k->cols; ++c) {
+    const size_t r = (size_t)(std::lower_bound(dn.begin(), dn.end(), cbits[c]) - dn.begin());
+    for (int32_t e = rp[r]; e < rp[r + 1]; ++e) {
+      const int32_t c2 = pos[col[e]];
+      const int sg = csign[c] * csign[c2];
+      const bool neg = ((scol[e] >> 31) != 0) != (sg < 0);
+      kscol.push_back((uint32_t)c2 | (neg ? 0x80000000u : 0u));
+      kval.push_back(val[e] * sg);
+    }
+    krp.push_back((int32_t)kscol.size());
   }
+
+  if (!upload(&k->rep, reps, "sector representatives") || !upload(&k->per, per, "sector periods") ||
+      !upload(&k->eb, eb, "sector signs") || !upload(&k->uh_ptr, uh_ptr, "sector up hops") ||
+      !upload(&k->uh_row, uh_row, "sector up hops") || !upload(&k->uh_t, uh_t, "sector up hops") ||
+      !upload(&k->uh_val, uh_val, "sector up hops") || !upload(&k->cinfo, cinfo, "sector columns") ||
+      !upload(&k->cbits, cbits, "sector columns") || !upload(&k->krp, krp, "sector down hops") ||
+      !upload(&k->kscol, kscol, "sector down hops") || !upload(&k->kval, kval, "sector down hops") ||
+      !upload(&k->short_rows, shorts, "sector short rows") ||
+      !dev_alloc((void **)&k->scratch, sizeof(double) * std::max<int64_t>(k->n_short * k->cols, 1), "sector scratch") ||
+      !dev_alloc((void **)&k->d_count, sizeof(unsigned long long), "sector counter"))
+    return fail(HUB_ERR_OOM, std::string("hub_set_symmetry: ") + hub_last_error());
+
   // dimension: free rows count fully, short rows by their cycles
   k->dim = (k->rows - k->n_short) * k->cols;
   if (k->n_short && k->cols) {
     HUB_CUDA(cudaMemset(k->d_count, 0, sizeof(unsigned long long)));
     const int64_t n = (int64_t)k->n_short * k->cols;
-    k_k0_count_short<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)sms * 32), 256>>>(k0_view(h), k->n_short,
-                                                                                       k->short_rows, k->d_count);
+    k_k0_count_short<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 32), 256>>>(
+        k0_view(h), k->n_short, k->short_rows, k->d_count);
     HUB_LAUNCH_CHECK();
     unsigned long long c = 0;
     HUB_CUDA(cudaMemcpy(&c, k->d_count, sizeof(c), cudaMemcpyDeviceToHost));
@@ -454,7 +690,10 @@ int k0_apply(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   const int64_t tiles = k->rows * ((k->cols + kK0Threads - 1) / kK0Threads);
   const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 16);
   count_launch(h);
-  k_k0_apply<<<grid, kK0Threads, 0, s>>>(k0_view(h), x, y);
+  if (k->fix && h->mode == HUB_MODE_AUTO)
+    k_k0_apply<true><<<grid, kK0Threads, 0, s>>>(k0_view(h), x, y);
+  else
+    k_k0_apply<false><<<grid, kK0Threads, 0, s>>>(k0_view(h), x, y);
   HUB_LAUNCH_CHECK();
   return HUB_OK;
 }
@@ -511,6 +750,17 @@ extern "C" int hub_k_reps(hub_t h, uint32_t *rep_host, int32_t *period_host) {
   for (int64_t i = 0; i < k->rows; ++i) {
     if (rep_host) rep_host[i] = k->rep_h[i];
     if (period_host) period_host[i] = k->per_h[i];
+  }
+  return HUB_OK;
+}
+
+extern "C" int hub_k_columns(hub_t h, uint32_t *dn_host, int32_t *sign_host) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_k_columns: NULL handle");
+  if (!h->k0) return fail(HUB_ERR_STATE, "hub_k_columns: no momentum sector is active (hub_set_symmetry)");
+  const K0State *k = h->k0;
+  for (int64_t c = 0; c < k->cols; ++c) {
+    if (dn_host) dn_host[c] = k->col_bits_h[c];
+    if (sign_host) sign_host[c] = k->col_sign_h[c];
   }
   return HUB_OK;
 }

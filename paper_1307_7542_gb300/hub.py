@@ -57,6 +57,7 @@ SIGNATURES = {
     "hub_set_symmetry": (_i, [_p, _i]),
     "hub_k_dims": (_i, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "hub_k_reps": (_i, [_p, _p, _p]),
+    "hub_k_columns": (_i, [_p, _p, _p]),
     "hub_k_project": (_i, [_p, _p, _p, _p]),
     "hub_set_mode": (_i, [_p, _i]),
     "hub_check": (_i, [_p]),
@@ -298,6 +299,13 @@ def hub_k_reps(h, rows):
     return reps, per
 
 
+def hub_k_columns(h, cols):
+    bits = np.empty(cols, dtype=np.uint32)
+    sign = np.empty(cols, dtype=np.int32)
+    _check(lib().hub_k_columns(h, bits.ctypes.data, sign.ctypes.data))
+    return bits, sign
+
+
 def hub_k_project(h, x, y, stream=None):
     _check(lib().hub_k_project(h, _ptr(x), _ptr(y), _stream(stream)))
 
@@ -356,6 +364,9 @@ class Hubbard:
 
     def k_reps(self):
         return hub_k_reps(self.h, self.k_rows)
+
+    def k_columns(self):
+        return hub_k_columns(self.h, self.k_cols)
 
     def k_project(self, x, y=None, stream=None):
         import torch

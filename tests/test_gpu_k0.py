@@ -2,8 +2,9 @@
 
 The oracle builds the k = 0 Bloch states of the paper's combined representatives in the full
 two-spin basis and applies the full H (oracle/hub_oracle_k0.py).  The library works in row
-form, X[i, d] = sqrt(P_i) Psi(R_i, d); the tests sample the oracle's translation-invariant
-vectors on the rows of the up representatives to compare.  Integer data (representatives,
+form with the columns of Table I, X[i, (j, n)] = sqrt(P_i) <R_i (x) T^n R_j | Psi>; the tests
+sample the oracle's translation-invariant vectors on the rows of the up representatives in
+that column order (oracle ``row_form_rep``) to compare.  Integer data (representatives,
 periods, dimension) bit for bit; products per entry within 1e-13 (|H||Psi|); energies within
 1e-10 relative.
 """
@@ -53,7 +54,15 @@ CASES = [
     (12, 4, 5, True, 1.1, 2.0, 0.05),
     (6, 0, 2, False, 1.0, 4.0, 0.0),     # one row of period 1
     (5, 5, 2, False, 1.0, 4.0, 0.0),     # full up filling
+    (8, 4, 3, True, (1.0, 0.6), 4.0, 0.0),   # two hopping amplitudes: the FP64 kernel
 ]
+
+
+def _t(M, nnn, t):
+    """Per-bond t: a scalar for every bond, or (nearest, next-nearest)."""
+    if np.ndim(t) == 0:
+        return float(t)
+    return np.r_[np.full(M, t[0]), np.full(M, t[1])] if nnn else np.full(M, t[0])
 
 
 # (case, omega): k = 0 for every case, k = pi (omega = -1) for the even rings
@@ -67,6 +76,7 @@ def _ids(sc):
 
 def _models(hub, M, nu, nd, nnn, t, U, eps, omega=1):
     bonds = ring(M, nnn)
+    t = _t(M, nnn, t)
     om = O.Model(M, bonds, t, U, eps)
     m = hub.Hubbard(M, nu, nd, bonds, t, U, np.full(M, eps) if eps else None)
     m.set_symmetry(hub.HUB_SYM_K0 if omega == 1 else hub.HUB_SYM_KPI)
@@ -87,6 +97,11 @@ def test_k0_tables_bitexact(hub, sc):
     assert np.array_equal(per.astype(np.int64), tb["period"][is_rep])
     assert (m.k_rows, m.k_cols) == (int(is_rep.sum()), math.comb(M, nd))
     assert m.k_dim == K.k0_dimension(M, nu, nd, omega)
+    bits, sign = K.rep_columns(M, nd)
+    om, m = _models(hub, M, nu, nd, nnn, t, U, eps, omega)
+    cb, cs = m.k_columns()
+    m.close()
+    assert np.array_equal(cb.astype(np.uint64), bits) and np.array_equal(cs, sign.astype(np.int32))
 
 
 @pytest.mark.parametrize("sc", SECTOR_CASES, ids=_ids)
@@ -103,12 +118,54 @@ def test_k0_apply_parity(hub, sc):
         return
     for seed in (1, 2):
         psi = np.asarray(V @ W.normal(seed, V.shape[1]))
-        X, _, _ = K.row_form(M, nu, nd, B, psi)
-        Yref, _, _ = K.row_form(M, nu, nd, B, O.apply(om, B, psi))
-        bound, _, _ = K.row_form(M, nu, nd, B, O.apply(om, B, np.abs(psi), absolute=True))
+        X, _, _ = K.row_form_rep(M, nu, nd, B, psi)
+        Yref, _, _ = K.row_form_rep(M, nu, nd, B, O.apply(om, B, psi))
+        bound, _, _ = K.row_form_rep(M, nu, nd, B, O.apply(om, B, np.abs(psi), absolute=True))
         y = m.apply(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
-        assert_entrywise(y, Yref.ravel(), bound.ravel())
+        assert_entrywise(y, Yref.ravel(), np.abs(bound).ravel())
     m.close()
+
+
+@pytest.mark.parametrize("M,nu,nd,nnn,omega", [(6, 4, 2, False, 1), (8, 4, 4, True, 1), (8, 4, 4, False, -1),
+                                               (10, 5, 4, False, 1)])
+def test_k0_apply_wide_range(hub, M, nu, nd, nnn, omega):
+    """Integer-pipe sums on vectors spanning 10^-300 .. 10^300 with zeros and subnormal
+    entries: per entry within 1e-13 |H||Psi| of the oracle."""
+    om, m = _models(hub, M, nu, nd, nnn, 1.0, 4.0, 0.0, omega)
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix(M, nu, nd, B, omega)
+    n = V.shape[1]
+    phi = W.normal(11, n) * 10.0 ** W.uniform(12, n, -300.0, 300.0)
+    phi[W.uniform(13, n) < 0.2] = 0.0
+    phi[:3] = [5e-321, -2e-310, 1e-308]
+    psi = np.asarray(V @ phi)
+    X, _, _ = K.row_form_rep(M, nu, nd, B, psi)
+    Yref, _, _ = K.row_form_rep(M, nu, nd, B, O.apply(om, B, psi))
+    bound, _, _ = K.row_form_rep(M, nu, nd, B, O.apply(om, B, np.abs(psi), absolute=True))
+    y = m.apply(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
+    m.close()
+    assert_entrywise(y, Yref.ravel(), np.abs(bound).ravel())
+
+
+@pytest.mark.parametrize("M,omega", [(14, 1), (16, -1)])
+def test_k0_integer_path_matches_fp64_kernel(hub, M, omega):
+    """Full-size rings: the integer-pipe product (default) against the FP64 kernel
+    (HUB_MODE_FP64) on the same projected random array, per entry within 1e-13 of the
+    entry's |H||x| scale, and the same Lanczos energy to 1e-12."""
+    m = hub.Hubbard(M, M // 2, M // 2, ring(M), 1.0, 4.0)
+    m.set_symmetry(hub.HUB_SYM_K0 if omega == 1 else hub.HUB_SYM_KPI)
+    x = m.k_project(torch.from_numpy(W.normal(3, m.D)).cuda())
+    y_int = m.apply(x)
+    e_int = m.ground(None, maxit=300, tol=1e-12)["E0"]
+    hub.hub_set_mode(m.h, hub.HUB_MODE_FP64)
+    y_f64 = m.apply(x)
+    e_f64 = m.ground(None, maxit=300, tol=1e-12)["E0"]
+    scale = m.apply(x.abs())          # >= the |H||x| scale entrywise only up to signs of H
+    m.close()
+    err = (y_int - y_f64).abs()
+    bound = 1e-13 * (scale.abs() + 4.0 * M * x.abs().max())
+    assert bool((err <= bound).all())
+    assert abs(e_int - e_f64) < 1e-12 * abs(e_f64)
 
 
 @pytest.mark.parametrize("M,nu,nd,omega", [(4, 2, 0, 1), (6, 4, 2, 1), (8, 4, 2, 1), (8, 4, 4, 1), (9, 3, 3, 1),
@@ -120,7 +177,7 @@ def test_k0_projection(hub, M, nu, nd, omega):
     om, m = _models(hub, M, nu, nd, False, 1.0, 4.0, 0.0, omega)
     B = O.basis(M, nu, nd)
     V = K.bloch_matrix(M, nu, nd, B, omega)
-    X, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ W.normal(5, V.shape[1])))
+    X, _, _ = K.row_form_rep(M, nu, nd, B, np.asarray(V @ W.normal(5, V.shape[1])))
     px = m.k_project(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
     assert np.max(np.abs(px - X.ravel())) < 1e-14 * np.max(np.abs(X))
     x = torch.from_numpy(W.normal(6, m.D)).cuda()
@@ -129,7 +186,7 @@ def test_k0_projection(hub, M, nu, nd, omega):
     assert torch.equal(p1, p2)
     r = (x - p1).cpu().numpy()
     for seed in (7, 8):
-        Z, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ W.normal(seed, V.shape[1])))
+        Z, _, _ = K.row_form_rep(M, nu, nd, B, np.asarray(V @ W.normal(seed, V.shape[1])))
         assert abs(float(r @ Z.ravel())) < 1e-13 * np.linalg.norm(r) * np.linalg.norm(Z)
     eye = torch.eye(m.D, dtype=torch.float64, device="cuda")
     tr = sum(float(m.k_project(eye[k].contiguous())[k]) for k in range(m.D))
@@ -153,7 +210,7 @@ def test_k0_ground_energy(hub, sc):
     g = m.ground(None, maxit=min(400, 3 * m.k_dim + 5), tol=1e-13, want_psi=True)
     assert abs(g["E0"] - w[0]) < 1e-10 * max(1.0, abs(w[0]))
     if w.size > 1 and w[1] - w[0] > 1e-6:
-        ref, _, _ = K.row_form(M, nu, nd, B, np.asarray(V @ Z[:, 0]))
+        ref, _, _ = K.row_form_rep(M, nu, nd, B, np.asarray(V @ Z[:, 0]))
         p = g["psi"].cpu().numpy()
         assert 1.0 - abs(float(p @ ref.ravel())) < 1e-9
     m.close()
