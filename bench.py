@@ -354,7 +354,7 @@ def extras(hub, W, torch):
     # (5) momentum sectors of the Hubbard ring (Sec. V), half filling, U = 4: at M = 16 the
     # full sector against its k = pi subspace, where the ground state lies, each to
     # |dE0| < 1e-12; at M = 20 products in the k = pi subspace (the full sector would need
-    # 273 GB per vector).  FP64 multiply-adds per element: the hops of both spins,
+    # 273 GB per vector).  Terms per element: the hops of both spins,
     # 2 * (2 M C(M-2, N-1) / C(M, N)), plus the diagonal.
     from paper_1307_7542_gb300 import ring as R
     full16 = R.run(16, 8, 8, "full", maxit=400, tol=1e-12, applies=5)
@@ -362,9 +362,10 @@ def extras(hub, W, torch):
     kpi20 = R.run(20, 10, 10, "kpi", maxit=0, applies=3)
     for r in (kpi16, kpi20):
         M, N = r["M"], r["n_up"]
-        fma = 2 * (2 * M * math.comb(M - 2, N - 1) / math.comb(M, N)) + 1
-        r["fp64_fma_per_element"] = fma
-        r["fp64_issue_frac"] = fma * r["vector_len"] / (r["apply_ms"] / 1000) / FP64_INSTR_PEAK
+        terms = 2 * (2 * M * math.comb(M - 2, N - 1) / math.comb(M, N)) + 1
+        r["terms_per_element"] = terms
+        r["terms_per_s"] = terms * r["vector_len"] / (r["apply_ms"] / 1000)
+        r["as_fp64_fma_frac_of_fp64_issue"] = r["terms_per_s"] / FP64_INSTR_PEAK
     out["ring_momentum"] = {"workload": "Hubbard ring, half filling, t=1, U=4; k = pi subspace of the "
                                         "translation (T eigenvalue -1) against the full sector",
                             "M16_full": full16, "M16_kpi": kpi16, "M20_kpi": kpi20,

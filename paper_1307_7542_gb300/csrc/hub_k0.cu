@@ -88,7 +88,10 @@ struct K0State {
   double mt = 0.0;              // -t
 };
 
+constexpr int kDiagTab = 32;   // U n + eps (N_up + N_dn) for n = 0 .. 31 doubly occupied sites
+
 struct K0View {
+  double diag_tab[kDiagTab];
   int M;
   int64_t rows, cols;
   const uint32_t *rep;
@@ -124,6 +127,7 @@ static K0View k0_view(const hub_ctx *h) {
   v.kval = k->kval;
   v.U0 = h->U0;
   v.diag0 = k->diag0;
+  for (int n = 0; n < kDiagTab; ++n) v.diag_tab[n] = h->U0 * (double)n + k->diag0;
   v.s0 = k->s0;
   v.mt = k->mt;
   return v;
@@ -161,7 +165,7 @@ __device__ __forceinline__ uint32_t k0_member(const K0View &K, int P, int b, int
 // Row value of the product at (i, c) before the projection of short rows, FP64 throughout.
 __device__ __forceinline__ double k0_row_value(const K0View &K, int64_t i, int64_t c, const double *__restrict__ x) {
   const double *xi = x + i * K.cols;
-  double acc = fma(K.U0, (double)__popc(__ldg(K.rep + i) & __ldg(K.cbits + c)), K.diag0) * xi[c];
+  double acc = K.diag_tab[__popc(__ldg(K.rep + i) & __ldg(K.cbits + c))] * xi[c];
   const int k0 = __ldg(K.krp + c), k1 = __ldg(K.krp + c + 1);
   int k = k0;
   for (; k + 4 <= k1; k += 4) {          // four gathers in flight before the multiply-adds
@@ -234,10 +238,15 @@ __device__ __forceinline__ void fix_add(FixSum &f, double x, bool neg, int s0) {
   fix_add4(f, xs, ns, s0);
 }
 
+// acc * 2^(e - 1075 - s0): the power of two is built from its exponent bits, in two factors
+// when it lies below the normal range (e near the bottom of the exponent range).
 __device__ __forceinline__ double fix_value(const FixSum &f, int s0) {
   if (f.bad) return __longlong_as_double(0x7ff8000000000000ll);
-  if (f.acc == 0) return 0.0;
-  return ldexp((double)f.acc, f.e - 1075 - s0);
+  const int n = f.e - 1075 - s0;   // >= -1085 and <= 971
+  const int n1 = n < -1022 ? -1022 : n, n2 = n - n1;
+  const double p1 = __longlong_as_double((long long)(n1 + 1023) << 52);
+  const double p2 = __longlong_as_double((long long)(n2 + 1023) << 52);
+  return (double)f.acc * p1 * p2;
 }
 
 // Row value on the integer path: diag x + (-t) S + (hops with other coefficients, FP64).
@@ -300,7 +309,7 @@ __device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, i
       side = fma(flip ? -cf : cf, v, side);
     }
   }
-  const double diag = fma(K.U0, (double)__popc(__ldg(K.rep + i) & __ldg(K.cbits + c)), K.diag0);
+  const double diag = K.diag_tab[__popc(__ldg(K.rep + i) & __ldg(K.cbits + c))];
   return fma(diag, xi[c], fma(K.mt, fix_value(f, K.s0), side));
 }
 
