@@ -353,13 +353,13 @@ def extras(hub, W, torch):
                         "total_s": t_gs + sum(v_["coeffs_s"] + v_["ladder_ms"] / 1000 for v_ in stages.values())}
     # (5) momentum sectors of the Hubbard ring (Sec. V), half filling, U = 4: at M = 16 the
     # full sector against its k = pi subspace, where the ground state lies, each to
-    # |dE0| < 1e-12; at M = 20 products in the k = pi subspace (the full sector would need
-    # 273 GB per vector).  Terms per element: the hops of both spins,
+    # |dE0| < 1e-12; at M = 20 the k = pi ground state and products (the full sector would
+    # need 273 GB per vector).  Terms per element: the hops of both spins,
     # 2 * (2 M C(M-2, N-1) / C(M, N)), plus the diagonal.
     from paper_1307_7542_gb300 import ring as R
     full16 = R.run(16, 8, 8, "full", maxit=400, tol=1e-12, applies=5)
     kpi16 = R.run(16, 8, 8, "kpi", maxit=400, tol=1e-12, applies=20)
-    kpi20 = R.run(20, 10, 10, "kpi", maxit=0, applies=3)
+    kpi20 = R.run(20, 10, 10, "kpi", maxit=300, tol=1e-12, applies=3)
     for r in (kpi16, kpi20):
         M, N = r["M"], r["n_up"]
         terms = 2 * (2 * M * math.comb(M - 2, N - 1) / math.comb(M, N)) + 1

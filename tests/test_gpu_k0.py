@@ -329,3 +329,28 @@ def test_k0_errors(hub):
         hub.hub_k_dims(m.h)
     assert e.value.code == hub.HUB_ERR_STATE
     m.close()
+
+
+def test_k_sector_host_apply_and_ritz(hub):
+    """Inside a momentum sector: hub_apply_host (host arrays) equals hub_apply, and
+    hub_lanczos_ritz returns the eigenvector (row form) and value of the lowest simple excited
+    k = 0 level."""
+    M, nu, nd = 8, 4, 4
+    om, m = _models(hub, M, nu, nd, False, 1.0, 4.0, 0.0, 1)
+    x = m.k_project(torch.from_numpy(W.normal(9, m.D)).cuda())
+    y_dev = m.apply(x).cpu().numpy()
+    xh = x.cpu().numpy().copy()
+    yh = np.empty_like(xh)
+    hub.hub_apply_host(m.h, xh, yh)
+    assert np.array_equal(yh, y_dev)
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix(M, nu, nd, B)
+    w, Z = np.linalg.eigh(K.k0_matrix(om, B, V))
+    lvl = next(l for l in range(1, w.size - 1) if min(w[l] - w[l - 1], w[l + 1] - w[l]) > 1e-3)
+    assert lvl <= 4
+    psi = torch.empty(m.D, dtype=torch.float64, device="cuda")
+    theta = hub.hub_lanczos_ritz(m.h, None, 200, float(w[lvl]), psi)
+    ref, _, _ = K.row_form_rep(M, nu, nd, B, np.asarray(V @ Z[:, lvl]))
+    m.close()
+    assert abs(theta - w[lvl]) < 1e-9 * abs(w[lvl])
+    assert 1.0 - abs(float(psi.cpu().numpy() @ ref.ravel())) < 1e-8
