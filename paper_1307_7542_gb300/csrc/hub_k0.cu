@@ -521,10 +521,12 @@ static int check_invariant(const hub_ctx *h) {
   return HUB_OK;
 }
 
+// Device copy of a host table: HUB_ERR_OOM if the allocation fails, HUB_ERR_CUDA if the copy does.
 template <class T>
-static bool upload(T **dst, const std::vector<T> &src, const char *what) {
-  if (!dev_alloc((void **)dst, sizeof(T) * std::max<size_t>(src.size(), 1), what)) return false;
-  return src.empty() || cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice) == cudaSuccess;
+static int upload(T **dst, const std::vector<T> &src, const char *what) {
+  if (!dev_alloc((void **)dst, sizeof(T) * std::max<size_t>(src.size(), 1), what)) return HUB_ERR_OOM;
+  if (!src.empty()) HUB_CUDA(cudaMemcpy(*dst, src.data(), sizeof(T) * src.size(), cudaMemcpyHostToDevice));
+  return HUB_OK;
 }
 
 static int k0_build(hub_ctx *h, int omega) {
@@ -666,16 +668,18 @@ static int k0_build(hub_ctx *h, int omega) {
     krp.push_back((int32_t)kscol.size());
   }
 
-  if (!upload(&k->rep, reps, "sector representatives") || !upload(&k->per, per, "sector periods") ||
-      !upload(&k->eb, eb, "sector signs") || !upload(&k->uh_ptr, uh_ptr, "sector up hops") ||
-      !upload(&k->uh_row, uh_row, "sector up hops") || !upload(&k->uh_t, uh_t, "sector up hops") ||
-      !upload(&k->uh_val, uh_val, "sector up hops") || !upload(&k->cinfo, cinfo, "sector columns") ||
-      !upload(&k->cbits, cbits, "sector columns") || !upload(&k->krp, krp, "sector down hops") ||
-      !upload(&k->kscol, kscol, "sector down hops") || !upload(&k->kval, kval, "sector down hops") ||
-      !upload(&k->short_rows, shorts, "sector short rows") ||
-      !dev_alloc((void **)&k->scratch, sizeof(double) * std::max<int64_t>(k->n_short * k->cols, 1), "sector scratch") ||
+  int rc = HUB_OK;
+  if ((rc = upload(&k->rep, reps, "sector representatives")) || (rc = upload(&k->per, per, "sector periods")) ||
+      (rc = upload(&k->eb, eb, "sector signs")) || (rc = upload(&k->uh_ptr, uh_ptr, "sector up hops")) ||
+      (rc = upload(&k->uh_row, uh_row, "sector up hops")) || (rc = upload(&k->uh_t, uh_t, "sector up hops")) ||
+      (rc = upload(&k->uh_val, uh_val, "sector up hops")) || (rc = upload(&k->cinfo, cinfo, "sector columns")) ||
+      (rc = upload(&k->cbits, cbits, "sector columns")) || (rc = upload(&k->krp, krp, "sector down hops")) ||
+      (rc = upload(&k->kscol, kscol, "sector down hops")) || (rc = upload(&k->kval, kval, "sector down hops")) ||
+      (rc = upload(&k->short_rows, shorts, "sector short rows")))
+    return rc;
+  if (!dev_alloc((void **)&k->scratch, sizeof(double) * std::max<int64_t>(k->n_short * k->cols, 1), "sector scratch") ||
       !dev_alloc((void **)&k->d_count, sizeof(unsigned long long), "sector counter"))
-    return fail(HUB_ERR_OOM, std::string("hub_set_symmetry: ") + hub_last_error());
+    return HUB_ERR_OOM;
 
   // dimension: free rows count fully, short rows by their cycles
   k->dim = (k->rows - k->n_short) * k->cols;
