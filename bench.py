@@ -236,7 +236,8 @@ def combine_ranks(elapsed_ms, steps, world, device):
 def extras(hub, W, torch):
     """Measurements beside the headline: batched vs one-at-a-time impurity solves, adjoint
     gradients vs finite differences, the 3x6 bandwidth-stress Lanczos step, the 4x4
-    zero-temperature Green's function and the momentum sectors of the 16- and 20-site rings."""
+    zero-temperature Green's function, the 8-site ring's E0 wall time and the momentum sectors
+    of the 16- and 20-site rings."""
     import numpy as np
     out = {}
     # (1) AIM star M=8: 81 sectors x 64 parameter sets, one persistent launch
@@ -366,6 +367,36 @@ def extras(hub, W, torch):
         r["terms_per_element"] = terms
         r["terms_per_s"] = terms * r["vector_len"] / (r["apply_ms"] / 1000)
         r["as_fp64_fma_frac_of_fp64_issue"] = r["terms_per_s"] / FP64_INSTR_PEAK
+    # (6) the 8-site ring at half filling (D = 4900), E0 to |dE0| < 1e-12 from a seed-0 normal
+    # start vector: latency-bound; through hub_lanczos_ground (one host read-back of alpha and
+    # beta per iteration) and as a single job of the persistent batched solver (one launch; it
+    # draws its own start vector)
+    bonds8 = np.array([(i, (i + 1) % 8) for i in range(8)], dtype=np.int32)
+    m8 = hub.Hubbard(8, 4, 4, bonds8, 1.0, 4.0)
+    x8 = torch.from_numpy(W.normal(0, m8.D)).cuda()
+    m8.ground(x8, maxit=300, tol=1e-12)
+    reps8 = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r8 = m8.ground(x8, maxit=300, tol=1e-12)
+        torch.cuda.synchronize()
+        reps8.append(time.perf_counter() - t0)
+    m8.close()
+    one = lambda a: np.asarray(a, dtype=np.float64).reshape(1, -1)
+    hub.hub_batch_ground(8, bonds8, one(np.ones(8)), one(np.full(8, 4.0)), one(np.zeros(8)),
+                         np.array([4]), np.array([4]), np.array([0]), maxit=300, tol=1e-12)
+    reps_b = []
+    for _ in range(5):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        Eb, itb, _ = hub.hub_batch_ground(8, bonds8, one(np.ones(8)), one(np.full(8, 4.0)), one(np.zeros(8)),
+                                          np.array([4]), np.array([4]), np.array([0]), maxit=300, tol=1e-12)
+        reps_b.append(time.perf_counter() - t0)
+    out["ring8"] = {"workload": "ring M=8, (4,4), D=4900, t=1, U=4, to |dE0| < 1e-12",
+                    "E0": r8["E0"], "iterations": r8["iters"], "lanczos_ground_ms": 1000 * min(reps8),
+                    "batched_single_job_E0": float(Eb[0]), "batched_single_job_iterations": int(itb[0]),
+                    "batched_single_job_ms": 1000 * min(reps_b)}
     out["ring_momentum"] = {"workload": "Hubbard ring, half filling, t=1, U=4; k = pi subspace of the "
                                         "translation (T eigenvalue -1) against the full sector",
                             "M16_full": full16, "M16_kpi": kpi16, "M20_kpi": kpi20,
