@@ -482,6 +482,14 @@ __global__ void k_coeffs(double *__restrict__ scal, float2 *__restrict__ coef) {
 }
 
 // scal[i] = v for the given slots (stream-ordered host -> device scalar writes)
+// beta_prev <- beta_cur, beta_cur <- beta_j (scal[2], scal[1], scal[3]) without a host value,
+// so that a captured iteration needs no per-iteration arguments.
+__global__ void k_rotate_beta(double *__restrict__ scal) {
+  const double b_cur = scal[1];
+  scal[1] = scal[3];
+  scal[2] = b_cur;
+}
+
 __global__ void k_set_scal(double *__restrict__ scal, int i0, double v0, int i1, double v1, int i2, double v2) {
   if (i0 >= 0) scal[i0] = v0;
   if (i1 >= 0) scal[i1] = v1;
@@ -849,6 +857,13 @@ struct FastState {
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> events;
   int *d_emax_chunks = nullptr, *d_flag = nullptr, *h_flag = nullptr;
+  // CUDA graphs of one Lanczos iteration (first pass), one per rotation of the three
+  // vectors, captured on graph_stream and replayed on the caller's stream; lz_graph_key holds
+  // the operands they were captured with
+  cudaStream_t graph_stream = nullptr;
+  cudaGraphExec_t lz_graph[3] = {nullptr, nullptr, nullptr};
+  std::vector<unsigned char> lz_graph_key;
+  bool lz_graph_failed = false;
 };
 
 static FastState *fast_of(const hub_ctx *h) { return h->fast; }
@@ -874,6 +889,9 @@ void fast_release(hub_ctx *h) {
   if (f->h_flag) cudaFreeHost(f->h_flag);
   for (cudaEvent_t e : f->events) cudaEventDestroy(e);
   if (f->copy_stream) cudaStreamDestroy(f->copy_stream);
+  for (int k = 0; k < 3; ++k)
+    if (f->lz_graph[k]) cudaGraphExecDestroy(f->lz_graph[k]);
+  if (f->graph_stream) cudaStreamDestroy(f->graph_stream);
   dev_free(f->coef);
   dev_free(f->sl_add);
   dev_free(f->sl_sub);
@@ -1410,6 +1428,67 @@ int fast_check_error(hub_ctx *h) {
 // scal: [0] alpha_j, [1] beta_cur = |r_j|, [2] beta_prev = |r_{j-1}| (0 at the start),
 // [3] beta_j, [5] |psi|, [6] 1/beta_cur.
 // ---------------------------------------------------------------------------------------
+// Captures `iteration` once per rotation of the three Lanczos vectors (graphs replayed in
+// turn on the caller's stream) unless the cached graphs were captured with the same operands.
+// Returns false, with the CUDA error state cleared, if capture is not possible; the caller
+// then launches each kernel itself.
+template <class F>
+static bool lz_graphs(hub_ctx *h, FastState *f, float *v0, float *v1, float *v2, F &iteration) {
+  if (f->lz_graph_failed) return false;
+  std::vector<unsigned char> key;
+  auto add = [&](const void *p, size_t n) {
+    const unsigned char *b = (const unsigned char *)p;
+    key.insert(key.end(), b, b + n);
+  };
+  const FastView v = fast_view(h, f);
+  const Side S = side_dn(h, f);
+  const void *ptrs[9] = {v0, v1, v2, f->zdf, h->partials, h->d_scal, h->h_scal, f->coef, f->d_err};
+  add(&v, sizeof(v));
+  add(&S.n_rows, sizeof(S.n_rows));
+  add(&S.ld, sizeof(S.ld));
+  add(ptrs, sizeof(ptrs));
+  add(&h->partials_n, sizeof(h->partials_n));
+  if (f->lz_graph[0] && key == f->lz_graph_key) return true;
+  for (int k = 0; k < 3; ++k)
+    if (f->lz_graph[k]) {
+      cudaGraphExecDestroy(f->lz_graph[k]);
+      f->lz_graph[k] = nullptr;
+    }
+  if (!f->graph_stream && cudaStreamCreateWithFlags(&f->graph_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    f->graph_stream = nullptr;
+    f->lz_graph_failed = true;
+    cudaGetLastError();
+    return false;
+  }
+  float *r[3] = {v0, v1, v2};
+  bool ok = true;
+  for (int k = 0; k < 3 && ok; ++k) {
+    if (cudaStreamBeginCapture(f->graph_stream, cudaStreamCaptureModeRelaxed) != cudaSuccess) {
+      ok = false;
+      break;
+    }
+    const int rc = iteration(r[k % 3], r[(k + 1) % 3], r[(k + 2) % 3], f->graph_stream);
+    cudaGraph_t g = nullptr;
+    const cudaError_t e = cudaStreamEndCapture(f->graph_stream, &g);
+    ok = rc == HUB_OK && e == cudaSuccess && g != nullptr &&
+         cudaGraphInstantiate(&f->lz_graph[k], g, 0) == cudaSuccess;
+    if (g) cudaGraphDestroy(g);
+  }
+  if (!ok) {
+    for (int k = 0; k < 3; ++k)
+      if (f->lz_graph[k]) {
+        cudaGraphExecDestroy(f->lz_graph[k]);
+        f->lz_graph[k] = nullptr;
+      }
+    f->lz_graph_failed = true;
+    cudaGetLastError();
+    set_error("");
+    return false;
+  }
+  f->lz_graph_key = key;
+  return true;
+}
+
 int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out,
                  int *iters, cudaStream_t s) {
   FastState *f = fast_of(h);
@@ -1444,26 +1523,45 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   };
   // one step of the recurrence: w = H q_j - beta_prev q_{j-1}, alpha partials, then (with
   // alpha in scal[0]) r_{j+1} = w - alpha q_j in place and |r_{j+1}|^2 partials
-  auto step_apply = [&](float *rp, float *rcur, float *w) -> int {
+  auto step_apply = [&](float *rp, float *rcur, float *w, cudaStream_t st) -> int {
     count_launch(h);
-    k_coeffs<<<1, 1, 0, s>>>(scal, coef);
+    k_coeffs<<<1, 1, 0, st>>>(scal, coef);
     HUB_LAUNCH_CHECK();
-    int rc2 = prof_mark(h, HUB_PROF_APPLY, true, s);
+    int rc2 = prof_mark(h, HUB_PROF_APPLY, true, st);
     if (rc2) return rc2;
-    if ((rc2 = run_up(h, f, rcur, f->zdf, s))) return rc2;
+    if ((rc2 = run_up(h, f, rcur, f->zdf, st))) return rc2;
     LzArgs L{rcur, rp, coef, scal + 6, P};
-    if ((rc2 = run_dn(h, f, 1, rcur, f->zdf, w, L, s))) return rc2;
-    return prof_mark(h, HUB_PROF_APPLY, false, s);
+    if ((rc2 = run_dn(h, f, 1, rcur, f->zdf, w, L, st))) return rc2;
+    return prof_mark(h, HUB_PROF_APPLY, false, st);
   };
-  auto step_update = [&](float *rcur, float *w) -> int {
+  auto step_update = [&](float *rcur, float *w, cudaStream_t st) -> int {
     count_launch(h, 2);
-    k_coeffs<<<1, 1, 0, s>>>(scal, coef);
-    k_df_update<<<G, 256, 0, s>>>(Q, w, rcur, coef, P);
+    k_coeffs<<<1, 1, 0, st>>>(scal, coef);
+    k_df_update<<<G, 256, 0, st>>>(Q, w, rcur, coef, P);
+    HUB_LAUNCH_CHECK();
+    return HUB_OK;
+  };
+  // a whole first-pass iteration: alpha_j and beta_j into the pinned host scalars, then the
+  // device-side rotation of the betas
+  auto iteration = [&](float *rp, float *rcur, float *w, cudaStream_t st) -> int {
+    int rc2;
+    if ((rc2 = step_apply(rp, rcur, w, st))) return rc2;
+    if ((rc2 = reduce_partials_2stage(P, (int)n_dn_blocks, P + std::max<int64_t>(n_dn_blocks, G), kTmp, scal + 0, 0,
+                                      st)))
+      return rc2;
+    if ((rc2 = step_update(rcur, w, st))) return rc2;
+    if ((rc2 = reduce_partials(P, G, scal + 3, 1, st))) return rc2;      // beta_j
+    HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
+    count_launch(h);
+    k_rotate_beta<<<1, 1, 0, st>>>(scal);
     HUB_LAUNCH_CHECK();
     return HUB_OK;
   };
 
   float *rp = f->lz[0], *rcur = f->lz[1], *w = f->lz[2];
+  // Replay captured iterations unless profiling (event pairs per launch) is on; rows that
+  // take the transposed pass 1 allocate on first use and are not captured.
+  const bool graphs = !h->prof && f->staged && lz_graphs(h, f, rp, rcur, w, iteration);
   if ((rc = start(rcur))) return rc;
   HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float) * Dp, s));
   HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
@@ -1471,20 +1569,17 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   h->start_norm = h->h_scal[1];
   if (!(h->h_scal[1] > 0.0) || !std::isfinite(h->h_scal[1]))
     return fail(HUB_ERR_ARG, "hub_lanczos_ground: start vector is zero or not finite");
-  double b_cur = h->h_scal[1];
 
   h->alpha.clear();
   h->beta.clear();
   double E = 0.0, E_prev = 0.0;
   int status = HUB_ERR_NOCONV;
   for (int j = 0; j < maxit; ++j) {
-    if ((rc = step_apply(rp, rcur, w))) return rc;
-    if ((rc = reduce_partials_2stage(P, (int)n_dn_blocks, P + std::max<int64_t>(n_dn_blocks, G), kTmp, scal + 0, 0,
-                                     s)))
+    if (graphs) {
+      HUB_CUDA(cudaGraphLaunch(f->lz_graph[j % 3], s));
+    } else if ((rc = iteration(rp, rcur, w, s))) {
       return rc;
-    if ((rc = step_update(rcur, w))) return rc;
-    if ((rc = reduce_partials(P, G, scal + 3, 1, s))) return rc;      // beta_j
-    HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, s));
+    }
     HUB_CUDA(cudaStreamSynchronize(s));
     const double a = h->h_scal[0], b = h->h_scal[3];
     if (!std::isfinite(a) || !std::isfinite(b)) return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha/beta");
@@ -1500,11 +1595,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
       status = HUB_CONVERGED_BREAKDOWN;
       break;
     }
-    // rotate: beta_prev <- beta_cur, beta_cur <- beta_j; r_{j-1} <- r_j <- r_{j+1}
-    count_launch(h);
-    k_set_scal<<<1, 1, 0, s>>>(scal, 1, b, 2, b_cur, -1, 0.0);
-    HUB_LAUNCH_CHECK();
-    b_cur = b;
+    // r_{j-1} <- r_j <- r_{j+1} (the betas rotated on the device)
     float *t0 = rp;
     rp = rcur;
     rcur = w;
@@ -1526,21 +1617,20 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
     if ((rc = start(rcur))) return rc;
     HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float) * Dp, s));
     HUB_CUDA(cudaMemsetAsync(f->psi, 0, sizeof(float) * Dp, s));
-    double bc = b_cur;
     HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
     HUB_CUDA(cudaStreamSynchronize(s));
-    bc = h->h_scal[1];
+    double bc = h->h_scal[1];
     for (int j = 0; j < k; ++j) {
       count_launch(h, 2);
       k_psi_coef<<<1, 1, 0, s>>>(scal, vv[j], coef);
       k_df_axpy<<<G, 256, 0, s>>>(Q, coef, 3, rcur, f->psi);
       HUB_LAUNCH_CHECK();
       if (j + 1 == k) break;
-      if ((rc = step_apply(rp, rcur, w))) return rc;
+      if ((rc = step_apply(rp, rcur, w, s))) return rc;
       count_launch(h);
       k_set_scal<<<1, 1, 0, s>>>(scal, 0, h->alpha[j], -1, 0.0, -1, 0.0);
       HUB_LAUNCH_CHECK();
-      if ((rc = step_update(rcur, w))) return rc;
+      if ((rc = step_update(rcur, w, s))) return rc;
       count_launch(h);
       k_set_scal<<<1, 1, 0, s>>>(scal, 1, h->beta[j], 2, bc, -1, 0.0);
       HUB_LAUNCH_CHECK();

@@ -639,3 +639,32 @@ def test_apply_wide_sectors(hub, nu, nd):
             assert abs(r["E0"] - ro["E0"]) < 1e-10 * abs(ro["E0"])
     finally:
         m.close()
+
+
+def test_lanczos_graph_replay_matches_direct_launches(hub):
+    """The fast Lanczos replays each iteration as a captured CUDA graph unless profiling is on;
+    both give bit-identical alpha and beta, the cached graphs are reused for a second run and
+    recaptured after new parameters (U), matching a fresh handle with those parameters."""
+    M = 8
+    bonds = W.ring_bonds(M)
+    m = hub.Hubbard(M, 4, 4, bonds, 1.0, 4.0)
+    x0 = torch.from_numpy(W.normal(0, m.D)).cuda()
+    runs = []
+    for prof in (False, False, True):
+        hub.hub_profile(m.h, prof)
+        r = m.ground(x0, maxit=40, tol=0.0)
+        runs.append((r["E0"],) + tuple(np.array(c) for c in hub.hub_lanczos_coeffs(m.h)))
+    hub.hub_profile(m.h, False)
+    for k in (1, 2):
+        assert runs[k][0] == runs[0][0]
+        assert np.array_equal(runs[k][1], runs[0][1]) and np.array_equal(runs[k][2], runs[0][2])
+    m.set_params(1.0, 6.0)
+    e6 = m.ground(x0, maxit=40, tol=0.0)["E0"]
+    a6 = hub.hub_lanczos_coeffs(m.h)[0]
+    m.close()
+    fresh = hub.Hubbard(M, 4, 4, bonds, 1.0, 6.0)
+    hub.hub_profile(fresh.h, True)
+    ef = fresh.ground(x0, maxit=40, tol=0.0)["E0"]
+    af = hub.hub_lanczos_coeffs(fresh.h)[0]
+    fresh.close()
+    assert e6 == ef and np.array_equal(a6, af)
