@@ -538,6 +538,13 @@ static int k0_build(hub_ctx *h, int omega) {
   k->cols = h->count[1];
   k->diag0 = (h->eps.empty() ? 0.0 : h->eps[0]) * (double)(Nu + Nd);
 
+  // every cycle has at most M members, so rows >= count_up / M: refuse before enumerating
+  // when even that many rows of one vector cannot fit
+  size_t free_b = 0, total_b = 0;
+  HUB_CUDA(cudaMemGetInfo(&free_b, &total_b));
+  if (8.0 * ((double)h->count[0] / M) * (double)k->cols > (double)free_b)
+    return fail(HUB_ERR_OOM, "hub_set_symmetry: one vector of the sector does not fit");
+
   // rows: up representatives, ascending, with periods and closing signs (times omega^P)
   std::vector<uint32_t> reps;
   std::vector<int32_t> per, eb;
@@ -554,8 +561,6 @@ static int k0_build(hub_ctx *h, int omega) {
   k->rep_h = reps;
   k->per_h = per;
 
-  size_t free_b = 0, total_b = 0;
-  HUB_CUDA(cudaMemGetInfo(&free_b, &total_b));
   if (8.0 * (double)k->rows * (double)k->cols > (double)free_b)
     return fail(HUB_ERR_OOM, "hub_set_symmetry: one vector of the sector does not fit");
 
