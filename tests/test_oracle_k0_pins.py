@@ -186,3 +186,30 @@ def test_k0_ground_state_M10_half_filling():
     x0 = np.random.default_rng(0).standard_normal(B.shape[0])
     E0 = O.lanczos(m, B, x0, maxit=300, tol=1e-13)["E0"]
     assert abs(w[0] - E0) < 1e-10
+
+
+def test_rep_columns_follow_table2():
+    """Column order of Table I for one spin: each representative followed by its
+    translations, with the phases of Table II (M = 4, N = 2: 0011, 1001(-), 1100, 0110,
+    0101, 1010(-)); for other sizes a bijection onto all strings."""
+    bits, sign = K.rep_columns(4, 2)
+    rows = _rows("k0_table2_M4_N2.txt")
+    assert [format(int(b), "04b") for b in bits] == [r[0] for r in rows]
+    assert [int(x) for x in sign] == [int(r[4]) for r in rows]
+    for M, N in [(6, 3), (8, 4), (9, 3), (6, 0), (5, 5), (10, 4)]:
+        b, s = K.rep_columns(M, N)
+        assert np.array_equal(np.sort(b), K.spin_strings(M, N))
+        assert set(np.unique(s).tolist()) <= {-1.0, 1.0}
+
+
+@pytest.mark.parametrize("M,nu,nd,omega", [(6, 4, 2, 1), (8, 4, 3, 1), (6, 3, 3, -1)])
+def test_row_form_rep_is_an_isometry(M, nu, nd, omega):
+    """X[i, (j, n)] = sqrt(P_i) <R_i (x) T^n R_j | psi> keeps the norm and the inner products
+    of states of the sector."""
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix(M, nu, nd, B, omega)
+    rng = np.random.default_rng(7)
+    a, b = (np.asarray(V @ rng.standard_normal(V.shape[1])) for _ in range(2))
+    Xa, _, _ = K.row_form_rep(M, nu, nd, B, a)
+    Xb, _, _ = K.row_form_rep(M, nu, nd, B, b)
+    assert abs(float(np.sum(Xa * Xb)) - float(a @ b)) < 1e-12 * np.linalg.norm(a) * np.linalg.norm(b)
