@@ -349,3 +349,143 @@ def row_form_rep(M: int, n_up: int, n_dn: int, B: np.ndarray, psi: np.ndarray):
     I = reps[:, None] + (d_bits[None, :] << np.uint64(M))
     X = psi[_index(B, I.ravel())].reshape(reps.shape[0], d_bits.shape[0])
     return X * np.sqrt(per)[:, None] * sign[None, :], reps, per
+
+
+# --------------------------------------------------------------------------------------
+# Several commuting translations (a torus): the same construction for the abelian group G
+# generated by site permutations, with a real character chi (chi(generator) = +-1).  Sec. V
+# treats the chain (one generator, T); the definitions carry over unchanged: a state of the
+# sector satisfies g Psi = chi(g) Psi for all g in G, and the Bloch state of a two-spin
+# configuration r is sum_g chi(g) g |r>, normalised (zero when the sum cancels).
+# --------------------------------------------------------------------------------------
+
+def permute(x: int, N: int, perm) -> tuple:
+    """g|x> = sign |x'> for the site permutation g: c+_i -> c+_perm[i], creation operators in
+    ascending site order before and after: sign = parity of the reordering of the images."""
+    sites = [i for i in range(len(perm)) if (x >> i) & 1]
+    images = [perm[i] for i in sites]
+    inv = sum(1 for a in range(len(images)) for b in range(a + 1, len(images)) if images[a] > images[b])
+    y = 0
+    for i in images:
+        y |= 1 << i
+    return y, (-1.0 if inv & 1 else 1.0)
+
+
+def site_group(gens) -> list:
+    """All elements of the group generated by the site permutations gens, as tuples, each with
+    the exponents of the generators of one word reaching it (breadth-first from the identity)."""
+    M = len(gens[0])
+    ident = tuple(range(M))
+    seen = {ident: (0,) * len(gens)}
+    order = [ident]
+    k = 0
+    while k < len(order):
+        p = order[k]
+        k += 1
+        for a, g in enumerate(gens):
+            q = tuple(g[p[i]] for i in range(M))          # apply p, then g
+            if q not in seen:
+                e = list(seen[p])
+                e[a] += 1
+                seen[q] = tuple(e)
+                order.append(q)
+    return [(p, seen[p]) for p in order]
+
+
+def group_character(elements, chars) -> list:
+    """chi of every element from the generators' values (+-1), product over a word; raises if
+    the values do not define a character (chi(p q) != chi(p) chi(q) for some pair)."""
+    out = []
+    for p, e in elements:
+        c = 1.0
+        for ch, n in zip(chars, e):
+            c *= float(ch) ** n
+        out.append(c)
+    pos = {p: k for k, (p, _) in enumerate(elements)}
+    for a, (p, _) in enumerate(elements):
+        for b, (q, _) in enumerate(elements):
+            pq = tuple(q[p[i]] for i in range(len(p)))
+            if out[pos[pq]] != out[a] * out[b]:
+                raise ValueError("the generator values do not define a character of the group")
+    return out
+
+
+def _act_two_spin(M, I, n_up, n_dn, perm):
+    up, dn = int(I) & ((1 << M) - 1), int(I) >> M
+    u2, su = permute(up, n_up, perm)
+    d2, sd = permute(dn, n_dn, perm)
+    return u2 + (d2 << M), su * sd
+
+
+def bloch_matrix_group(M: int, n_up: int, n_dn: int, B: np.ndarray, gens, chars):
+    """Sparse V: one column per orbit of two-spin configurations whose Bloch sum
+    sum_g chi(g) g |r> (r the smallest configuration of the orbit) does not cancel, normalised;
+    columns ordered by r.  Small sectors only (pure Python)."""
+    import scipy.sparse as sp
+    els = site_group(gens)
+    chi = group_character(els, chars)
+    index = {int(v): k for k, v in enumerate(B.tolist())}
+    done = np.zeros(B.shape[0], dtype=bool)
+    rows, cols, vals = [], [], []
+    col = 0
+    for k in range(B.shape[0]):
+        if done[k]:
+            continue
+        acc = {}
+        for (p, _), c in zip(els, chi):
+            I2, s = _act_two_spin(M, B[k], n_up, n_dn, p)
+            j = index[I2]
+            done[j] = True
+            acc[j] = acc.get(j, 0.0) + c * s
+        nz = {j: v for j, v in acc.items() if abs(v) > 1e-12}
+        if not nz:
+            continue
+        nrm = np.sqrt(sum(v * v for v in nz.values()))
+        for j, v in sorted(nz.items()):
+            rows.append(j)
+            cols.append(col)
+            vals.append(v / nrm)
+        col += 1
+    return sp.csr_matrix((vals, (rows, cols)), shape=(B.shape[0], col))
+
+
+def character_dimension_group(M: int, n_up: int, n_dn: int, B: np.ndarray, gens, chars) -> int:
+    """Multiplicity of the character chi: (1/|G|) sum_g chi(g) tr(g), each trace the signed
+    count of configurations that g maps to themselves (brute force)."""
+    els = site_group(gens)
+    chi = group_character(els, chars)
+    total = 0.0
+    for (p, _), c in zip(els, chi):
+        tr = 0.0
+        for I in B.tolist():
+            I2, s = _act_two_spin(M, I, n_up, n_dn, p)
+            if I2 == I:
+                tr += s
+        total += c * tr
+    val = total / len(els)
+    assert abs(val - round(val)) < 1e-9
+    return int(round(val))
+
+
+def torus_translations(Lx: int, Ly: int):
+    """The two translations of the Lx x Ly torus (site x + Lx y), each moving every electron
+    one site down its axis: (x, y) -> (x - 1, y) and (x, y) -> (x, y - 1)."""
+    tx = [((x - 1) % Lx) + Lx * y for y in range(Ly) for x in range(Lx)]
+    ty = [x + Lx * ((y - 1) % Ly) for y in range(Ly) for x in range(Lx)]
+    return [tx, ty]
+
+
+def torus_free_levels(Lx: int, Ly: int, n_up: int, n_dn: int, kx_pi: bool, ky_pi: bool, t: float = 1.0):
+    """U = 0 nearest-neighbour torus (Lx, Ly >= 3): every eigenvalue of the sector whose total
+    momentum is (pi if kx_pi else 0, pi if ky_pi else 0), sorted.  One-particle states of
+    momentum (2 pi mx / Lx, 2 pi my / Ly) have energy -2t (cos kx + cos ky)."""
+    from itertools import combinations
+    ks = [(mx, my) for my in range(Ly) for mx in range(Lx)]
+    e = np.array([-2.0 * t * (np.cos(2 * np.pi * mx / Lx) + np.cos(2 * np.pi * my / Ly)) for mx, my in ks])
+    tx, ty = (Lx // 2 if kx_pi else 0), (Ly // 2 if ky_pi else 0)
+    ups = [(sum(ks[i][0] for i in c) % Lx, sum(ks[i][1] for i in c) % Ly, sum(e[list(c)])) for c in
+           combinations(range(len(ks)), n_up)]
+    dns = [(sum(ks[i][0] for i in c) % Lx, sum(ks[i][1] for i in c) % Ly, sum(e[list(c)])) for c in
+           combinations(range(len(ks)), n_dn)]
+    out = [eu + ed for ax, ay, eu in ups for bx, by, ed in dns if (ax + bx) % Lx == tx and (ay + by) % Ly == ty]
+    return np.sort(np.array(out))

@@ -213,3 +213,60 @@ def test_row_form_rep_is_an_isometry(M, nu, nd, omega):
     Xa, _, _ = K.row_form_rep(M, nu, nd, B, a)
     Xb, _, _ = K.row_form_rep(M, nu, nd, B, b)
     assert abs(float(np.sum(Xa * Xb)) - float(a @ b)) < 1e-12 * np.linalg.norm(a) * np.linalg.norm(b)
+
+
+# ------------------------------------------------------------------ several translations (torus)
+
+def torus_bonds(Lx, Ly):
+    b = set()
+    for y in range(Ly):
+        for x in range(Lx):
+            s = x + Lx * y
+            for dx, dy in ((1, 0), (0, 1)):
+                s2 = (x + dx) % Lx + Lx * ((y + dy) % Ly)
+                b.add((min(s, s2), max(s, s2)))
+    return sorted(b)
+
+
+@pytest.mark.parametrize("M,nu,nd,omega", [(6, 3, 3, 1), (6, 4, 2, 1), (6, 3, 3, -1), (6, 4, 2, -1), (5, 2, 2, 1)])
+def test_group_construction_equals_chain(M, nu, nd, omega):
+    """One generator (the chain's T): the group construction spans the same space as the
+    chain construction (equal projectors V V^T)."""
+    B = O.basis(M, nu, nd)
+    Vg = K.bloch_matrix_group(M, nu, nd, B, [[(i - 1) % M for i in range(M)]], [omega])
+    V = K.bloch_matrix(M, nu, nd, B, omega)
+    assert Vg.shape[1] == V.shape[1]
+    assert abs((Vg @ Vg.T - V @ V.T)).max() < 1e-13
+
+
+@pytest.mark.parametrize("Lx,Ly,nu,nd", [(3, 3, 2, 2), (3, 3, 3, 2), (4, 3, 2, 2), (4, 3, 3, 1)])
+def test_torus_free_spectrum_and_dimension(Lx, Ly, nu, nd):
+    """Torus translations, every real character: dimension = (1/|G|) sum_g chi(g) tr g by brute
+    force, Bloch columns orthonormal and invariant (g V = chi(g) V), and at U = 0 the complete
+    spectrum equals the sums of one-particle energies -2t (cos kx + cos ky) with total momentum
+    of the character."""
+    M = Lx * Ly
+    gens = K.torus_translations(Lx, Ly)
+    B = O.basis(M, nu, nd)
+    m = O.Model(M, torus_bonds(Lx, Ly), 1.0, 0.0)
+    for cx in ([1, -1] if Lx % 2 == 0 else [1]):
+        for cy in ([1, -1] if Ly % 2 == 0 else [1]):
+            V = K.bloch_matrix_group(M, nu, nd, B, gens, [cx, cy])
+            assert V.shape[1] == K.character_dimension_group(M, nu, nd, B, gens, [cx, cy])
+            assert abs((V.T @ V).toarray() - np.eye(V.shape[1])).max() < 1e-13
+            for g, c in zip(gens, (cx, cy)):
+                P = np.zeros((B.shape[0], B.shape[0]))
+                idx = {int(v): k for k, v in enumerate(B.tolist())}
+                for k, I in enumerate(B.tolist()):
+                    I2, s = K._act_two_spin(M, I, nu, nd, g)
+                    P[idx[I2], k] = s
+                assert abs(P @ V.toarray() - c * V.toarray()).max() < 1e-13
+            w = np.linalg.eigvalsh(K.k0_matrix(m, B, V))
+            ref = K.torus_free_levels(Lx, Ly, nu, nd, cx < 0, cy < 0)
+            assert w.shape == ref.shape and np.max(np.abs(w - ref)) < 1e-12
+
+
+def test_group_character_must_be_consistent():
+    """-1 on a generator of odd order is no character: refused."""
+    with pytest.raises(ValueError):
+        K.group_character(K.site_group([[(i - 1) % 5 for i in range(5)]]), [-1])
