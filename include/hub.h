@@ -305,6 +305,26 @@ int hub_apply_vjp(hub_t h, const double *ybar_dev, const double *x_dev, double *
  */
 int hub_set_symmetry(hub_t h, int sym);
 
+/*
+ * Several commuting translations (a torus and the like): restrict the handle to the sector
+ * g Psi = chi(g) Psi of the abelian group G generated by n_gen site permutations (perm_host,
+ * n_gen x M: generator a moves site i to perm_host[a * M + i]) with real character values
+ * char_host[a] = +1 or -1 on the generators (k = 0 or pi along each).  Sec. V's construction
+ * with G in place of the powers of T; hub_set_symmetry(h, HUB_SYM_K0 / HUB_SYM_KPI) is the
+ * case n_gen = 1, perm = (i -> i-1 mod M).
+ *   - HUB_ERR_ARG unless: every generator is a permutation of the sites that maps the bonds
+ *     onto bonds with equal t; the generators commute; G has at most 64 elements; the
+ *     values define a character (-1 on a generator of odd order does not); U and eps are
+ *     uniform.  1 <= n_gen <= 8.
+ *   - Layout and everything else as for hub_set_symmetry, with orbits of G in place of
+ *     T-cycles: rows the up representatives (smallest member of each orbit) with their orbit
+ *     sizes P_i (hub_k_reps), columns each down representative followed by its images under
+ *     the coset representatives of its stabiliser (the smallest element of each coset, the
+ *     elements numbered breadth-first from the identity over the generators in order;
+ *     hub_k_columns), X[i * cols + c] = sqrt(P_i) * s_c * Psi(R_i, d_c).
+ */
+int hub_set_translations(hub_t h, int n_gen, const int32_t *perm_host, const int32_t *char_host);
+
 /* Row-form shape and dimension of the momentum sector.  HUB_ERR_STATE outside one. */
 int hub_k_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim);
 

@@ -489,3 +489,58 @@ def torus_free_levels(Lx: int, Ly: int, n_up: int, n_dn: int, kx_pi: bool, ky_pi
            combinations(range(len(ks)), n_dn)]
     out = [eu + ed for ax, ay, eu in ups for bx, by, ed in dns if (ax + bx) % Lx == tx and (ay + by) % Ly == ty]
     return np.sort(np.array(out))
+
+
+def group_orbit(M: int, N: int, x: int, gens):
+    """(smallest image, stabiliser as [(element index, sign)]) of string x under the group
+    generated by gens (elements in the breadth-first order of ``site_group``)."""
+    els = site_group(gens)
+    least, stab = x, []
+    for k, (p, _) in enumerate(els):
+        y, s = permute(x, N, p)
+        least = min(least, y)
+        if y == x:
+            stab.append((k, s))
+    return least, stab
+
+
+def group_columns(M: int, N: int, gens):
+    """Column order of Table I for a group: representatives ascending, each followed by the
+    images c_k |R> for the coset representatives c_k of its stabiliser (smallest element index
+    of each coset, in element order).  Returns (strings, signs)."""
+    els = site_group(gens)
+    g = len(els)
+    pos = {p: k for k, (p, _) in enumerate(els)}
+    bits, sign = [], []
+    for x in spin_strings(M, N).tolist():
+        least, stab = group_orbit(M, N, x, gens)
+        if least != x:
+            continue
+        covered = [False] * g
+        for e in range(g):
+            if covered[e]:
+                continue
+            for h, _ in stab:
+                pe, ph = els[e][0], els[h][0]
+                covered[pos[tuple(ph[pe[i]] for i in range(M))]] = True
+            y, s = permute(x, N, els[e][0])
+            bits.append(y)
+            sign.append(s)
+    return np.array(bits, dtype=np.uint64), np.array(sign)
+
+
+def row_form_group(M: int, n_up: int, n_dn: int, B: np.ndarray, psi: np.ndarray, gens):
+    """X[i, c] = sqrt(P_i) s_c psi(R_i, d_c): rows the up representatives (ascending, P_i the
+    orbit sizes), columns as ``group_columns``.  Returns (X, reps, orbit sizes)."""
+    g = len(site_group(gens))
+    reps, per = [], []
+    for x in spin_strings(M, n_up).tolist():
+        least, stab = group_orbit(M, n_up, x, gens)
+        if least == x:
+            reps.append(x)
+            per.append(g // len(stab))
+    d_bits, sign = group_columns(M, n_dn, gens)
+    reps = np.array(reps, dtype=np.uint64)
+    I = reps[:, None] + (d_bits[None, :] << np.uint64(M))
+    X = psi[_index(B, I.ravel())].reshape(reps.shape[0], d_bits.shape[0])
+    return X * np.sqrt(np.array(per, dtype=np.float64))[:, None] * sign[None, :], reps, np.array(per)

@@ -1,33 +1,40 @@
-// hub_k0.cu -- momentum sectors (k = 0 and k = pi) of a translation-invariant chain (Sec. V).
+// hub_k0.cu -- momentum sectors of translation-invariant lattices (Sec. V).
 //
-// T moves every electron one site down the chain, T c+_i T^-1 = c+_{i-1} (site 0 to site
-// M-1), the direction of Tables I and II.  On a spin string x with N electrons (sites in
-// ascending order) one step is the rotation x -> (x >> 1) | (x & 1) << (M-1) with sign
-// (-1)^(N-1) when site 0 was occupied.  A string's cycle under T has a period P (a divisor of
-// M); its smallest member is the representative R, and T^P |R> = b |R> with b = +-1.
+// Sec. V reduces the chain by its translation T c+_i T^-1 = c+_{i-1} (site 0 to site M-1, the
+// direction of Tables I and II) to the k = 0 space.  The same construction holds for any
+// abelian group G of site permutations that leaves H unchanged (the two translations of a
+// torus, ...) and any real character chi of G (chi(g) = +-1; for the chain k = 0 and k = pi):
+// the sector is {Psi : g Psi = chi(g) Psi for all g}.  An element g acts on a spin string x as
+// g|x> = sign |x'>, x' the permuted sites and sign the parity of reordering the images of the
+// occupied sites (creation operators in ascending site order).  A string's orbit has
+// |G| / |S| members (S its stabiliser, on which g|x> = sigma(g)|x>); its smallest member is
+// the representative.
 //
 // Layout ("row form", the order of Table I).  Rows: the up representatives R_i, ascending,
-// periods P_i.  Columns: the down representatives R_j, ascending, each followed by its
-// translations: column c = (j, n), n = 0 .. P_j - 1, stands for the signed state T^n |R_j>.
-// A state Psi of the sector (T Psi = omega Psi, omega = 1 for k = 0, -1 for k = pi) is stored as
-//     X[i * cols + c] = sqrt(P_i) <R_i (x) T^n R_j | Psi>,        cols = count_dn,
+// orbit sizes P_i.  Columns: the down representatives R_j, ascending, each followed by the
+// rest of its orbit: column c = (j, k) stands for the signed state c_k |R_j>, c_0 = 1, c_k the
+// smallest element of the k-th coset of S_j.  A state of the sector is stored as
+//     X[i * cols + c] = sqrt(P_i) <R_i (x) c_k R_j | Psi>,        cols = count_dn,
 // and the plain dot product of two such arrays equals the inner product of the states.  When
-// P_i = M every column of row i belongs to a different cycle of T and the row is free.  When
-// P_i < M, T^P_i maps row i into itself and ties the entries n, n + P_i, ... of each column
-// block; a cycle whose closing sign is -1 has no state in the sector and is zero.  The
-// library keeps those few rows consistent: every product and every start vector is
-// projected onto them, each cycle's average summed in one fixed order so that tied entries
-// agree bit for bit.
+// S_i is trivial every column of row i belongs to a different orbit and the row is free.
+// Otherwise the elements h of S_i tie the entries of each column block, X[i, (j, k)] =
+// chi(h) sigma_i(h) sigma' X[i, (j, k')] with h c_k = c_k' h' (h' in S_j, sigma' = sigma_j(h'));
+// an orbit that meets itself with sign -1 has no state in the sector and is zero.  The
+// library keeps those few rows consistent: every product and every start vector is projected
+// onto them, each orbit's average summed in one fixed order so that tied entries agree bit
+// for bit.  How an element moves the members of a block depends only on the block's
+// stabiliser and its signs (its "type"): one small table per type, tab[e][k] = (k', sigma')
+// with e c_k = c_k' h', sigma' = sigma_j(h').  For the chain a block is a cycle of period P_j
+// and the table is the cyclic shift k -> k - t mod P_j.
 //
-// Product (Sec. V with Eq. 11): for entry (i, c), c = (j, n), d the string of T^n R_j,
+// Product (Sec. V with Eq. 11): for entry (i, c), c = (j, k), d the string of c_k R_j,
 //     Y = (U popc(R_i & d) + eps (N_up + N_dn)) X[i, c]                           diagonal
 //       + sum_c' H_dn[d, d'] s_c s_c' X[i, c']                                      down hops
-//       + sum_{u'} H_up[R_i, u'] s omega^t sqrt(P_i / P_i') b_j^w X[i', (j, n - t mod P_j)]
-// where s_c is the sign of T^n |R_j> relative to |d>, T^t |R_i'> = s |u'> (R_i' the
-// representative of u', t < P_i'), and w counts the wraps of n - t below zero.  An up hop is
-// thus a cyclic shift inside each column block of another row: the gathers of consecutive
-// columns are consecutive words.  The up-hop list of each row (i', t, coefficient) and the
-// down hopping matrix in this column order are built on the host.
+//       + sum_{u'} H_up[R_i, u'] s chi(g) sqrt(P_i / P_i') sigma' X[i', (j, k')]      up hops
+// where s_c is the sign of c_k |R_j> relative to |d>, g |R_i'> = s |u'> (R_i' the
+// representative of u'), and (k', sigma') = tab_j[g^-1][k].  The up-hop list of each row
+// (i', g^-1, coefficient), the tables and the down hopping matrix in this column order are
+// built on the host.
 //
 // Integer accumulation.  GB300 issues FP64 at about 1/70 of its FP32 and integer rates, and
 // the product above is about 22 FP64 multiply-adds per entry.  With uniform t every hop term
@@ -38,7 +45,7 @@
 // no sum of the entry's terms can overflow.  The only rounding is the truncation of each
 // aligned term, below 2^-(52+s0) of the largest term, far inside the 1e-13 (|H||x|)_n bound;
 // one int64 -> FP64 conversion and two FP64 multiply-adds finish the entry.  Hops whose
-// coefficient is not +-t (rows of period P_i < M and hops into them, factor
+// coefficient is not +-t (rows with a nontrivial stabiliser and hops into them, factor
 // sqrt(P_i / P_i')) stay in FP64.  HUB_MODE_FP64 selects a kernel with FP64 multiply-adds
 // throughout (also used when t is not uniform).
 #include <algorithm>
@@ -55,34 +62,38 @@ namespace hub {
 int ready(const hub_ctx *h, const char *who);
 
 constexpr int kK0Threads = 256;
-// uh_t word: translation t in bits 0-7; integer path: the hop's coefficient is +-t (bit 8),
+constexpr int kMaxGroup = 64;   // elements of the symmetry group
+// uh_t word: element g^-1 in bits 0-7; integer path: the hop's coefficient is +-t (bit 8),
 // and its sign relative to -t (bit 9)
 constexpr int kHopUnit = 1 << 8, kHopNeg = 1 << 9;
-// column word: n in bits 0-7, P_j in bits 8-15, b_j = -1 in bit 16
-constexpr uint32_t kColNegB = 1u << 16;
+// column word: k in bits 0-7, block type in bits 8-15
+// table entry: k' in bits 0-7, sigma' = -1 in bit 15
 
 struct K0State {
   int64_t rows = 0, cols = 0, dim = 0;
+  int g = 0;                    // group order
   std::vector<uint32_t> rep_h, col_bits_h;
   std::vector<int32_t> per_h, col_sign_h;
   uint32_t *rep = nullptr;      // [rows] up representatives, ascending
-  int32_t *per = nullptr;       // [rows] their periods
-  int32_t *eb = nullptr;        // [rows] sign of T^P_i on R_i, times omega^P_i
+  int32_t *per = nullptr;       // [rows] orbit sizes
+  int32_t *st_ptr = nullptr;    // [rows + 1] stabiliser list of each row (identity left out)
+  int32_t *st = nullptr;        // element | (chi(h) sigma_i(h) = -1) << 8
   int32_t *uh_ptr = nullptr;    // [rows + 1] up-hop list of each row
   int32_t *uh_row = nullptr;    // [n_uh] target row i'
-  int32_t *uh_t = nullptr;      // [n_uh] translation t and flags
-  double *uh_val = nullptr;     // [n_uh] H_up[R_i, u'] s omega^t sqrt(P_i / P_i')
-  uint32_t *cinfo = nullptr;    // [cols] n | P_j << 8 | (b_j < 0) << 16
+  int32_t *uh_t = nullptr;      // [n_uh] element g^-1 and flags
+  double *uh_val = nullptr;     // [n_uh] H_up[R_i, u'] s chi(g) sqrt(P_i / P_i')
+  uint32_t *cinfo = nullptr;    // [cols] k | type << 8
   uint32_t *cbits = nullptr;    // [cols] down string of the column
+  int32_t *tab_off = nullptr;   // [types] start of each type's table; its block size follows
+  uint16_t *tab = nullptr;      // tables, [e][k] per type
   int32_t *krp = nullptr;       // [cols + 1] down hopping matrix in column order
   uint32_t *kscol = nullptr;    // [nnz] column | (sign of JW s_c s_c') << 31
   double *kval = nullptr;       // [nnz] -t_b JW s_c s_c'
-  int32_t *short_rows = nullptr;   // rows with P_i < M
+  int32_t *short_rows = nullptr;   // rows with a nontrivial stabiliser
   int n_short = 0;
   double *scratch = nullptr;    // [n_short * cols]
   unsigned long long *d_count = nullptr;
   double diag0 = 0.0;           // eps (N_up + N_dn) for uniform eps
-  int omega = 1;                // e^{ik}: 1 for k = 0, -1 for k = pi
   int fix = 0;                  // integer accumulation of the +-t hops (uniform t)
   int s0 = 0;                   // guard bits of the fixed-point terms
   double mt = 0.0;              // -t
@@ -92,17 +103,18 @@ constexpr int kDiagTab = 32;   // U n + eps (N_up + N_dn) for n = 0 .. 31 doubly
 
 struct K0View {
   double diag_tab[kDiagTab];
-  int M;
   int64_t rows, cols;
   const uint32_t *rep;
-  const int32_t *per, *eb;
+  const int32_t *per, *st_ptr, *st;
   const int32_t *uh_ptr, *uh_row, *uh_t;
   const double *uh_val;
   const uint32_t *cinfo, *cbits;
+  const int32_t *tab_off;
+  const uint16_t *tab;
   const int32_t *krp;
   const uint32_t *kscol;
   const double *kval;
-  double U0, diag0;
+  int g;
   int s0;
   double mt;
 };
@@ -110,24 +122,25 @@ struct K0View {
 static K0View k0_view(const hub_ctx *h) {
   const K0State *k = h->k0;
   K0View v{};
-  v.M = h->M;
+  for (int n = 0; n < kDiagTab; ++n) v.diag_tab[n] = h->U0 * (double)n + k->diag0;
   v.rows = k->rows;
   v.cols = k->cols;
   v.rep = k->rep;
   v.per = k->per;
-  v.eb = k->eb;
+  v.st_ptr = k->st_ptr;
+  v.st = k->st;
   v.uh_ptr = k->uh_ptr;
   v.uh_row = k->uh_row;
   v.uh_t = k->uh_t;
   v.uh_val = k->uh_val;
   v.cinfo = k->cinfo;
   v.cbits = k->cbits;
+  v.tab_off = k->tab_off;
+  v.tab = k->tab;
   v.krp = k->krp;
   v.kscol = k->kscol;
   v.kval = k->kval;
-  v.U0 = h->U0;
-  v.diag0 = k->diag0;
-  for (int n = 0; n < kDiagTab; ++n) v.diag_tab[n] = h->U0 * (double)n + k->diag0;
+  v.g = k->g;
   v.s0 = k->s0;
   v.mt = k->mt;
   return v;
@@ -137,29 +150,14 @@ static K0View k0_view(const hub_ctx *h) {
 // Device side
 // ---------------------------------------------------------------------------------------
 
-// Column of (j, n - t mod P_j) for column c = (j, n) with word ci, and whether the shift
-// picks up b_j an odd number of times (n - t wrapped below zero an odd number of times).
-__device__ __forceinline__ uint32_t k0_shift(uint32_t c, uint32_t ci, int t, bool *flip) {
-  const int n = (int)(ci & 0xff), P = (int)((ci >> 8) & 0xff);
-  int m = n - t, q = 0;
-  for (int it = 0; m < 0 && it < 256; ++it) {   // n - t > -M, P >= 1: at most M - 1 steps
-    m += P;
-    ++q;
-  }
-  *flip = (ci & kColNegB) && (q & 1);
-  return c - (uint32_t)n + (uint32_t)m;
-}
-
-// Member g of the T^P-cycle of column c in a row with period P and closing sign b (times
-// omega^P): its column and the sign beta with X[i, c] = beta X[i, member].
-__device__ __forceinline__ uint32_t k0_member(const K0View &K, int P, int b, int g, uint32_t c, int *sign) {
-  const uint32_t ci = __ldg(K.cinfo + c);
-  const int n = (int)(ci & 0xff), Pj = (int)((ci >> 8) & 0xff);
-  const int v = n + g * P, q = v / Pj, m = v - q * Pj;
-  int s = (b < 0 && (g & 1)) ? -1 : 1;
-  if ((ci & kColNegB) && (q & 1)) s = -s;
-  *sign = s;
-  return c - (uint32_t)n + (uint32_t)m;
+// Where element e moves column c = (j, k) inside its block: the column of c_k' with
+// e c_k = c_k' h', and whether sigma_j(h') = -1.
+__device__ __forceinline__ uint32_t k0_move(const K0View &K, uint32_t c, uint32_t ci, int e, bool *flip) {
+  const int k = (int)(ci & 0xff), type = (int)((ci >> 8) & 0xff);
+  const int off = __ldg(K.tab_off + 2 * type), bs = __ldg(K.tab_off + 2 * type + 1);
+  const uint32_t w = __ldg(K.tab + off + e * bs + k);
+  *flip = (w & 0x8000u) != 0;
+  return c - (uint32_t)k + (w & 0xffu);
 }
 
 // Row value of the product at (i, c) before the projection of short rows, FP64 throughout.
@@ -183,7 +181,7 @@ __device__ __forceinline__ double k0_row_value(const K0View &K, int64_t i, int64
   const int h0 = __ldg(K.uh_ptr + i), h1 = __ldg(K.uh_ptr + i + 1);
   for (k = h0; k < h1; ++k) {
     bool flip;
-    const uint32_t c2 = k0_shift((uint32_t)c, ci, __ldg(K.uh_t + k) & 0xff, &flip);
+    const uint32_t c2 = k0_move(K, (uint32_t)c, ci, __ldg(K.uh_t + k) & 0xff, &flip);
     const double cf = __ldg(K.uh_val + k);
     acc = fma(flip ? -cf : cf, x[(int64_t)__ldg(K.uh_row + k) * K.cols + c2], acc);
   }
@@ -283,7 +281,7 @@ __device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, i
 #pragma unroll
     for (int j = 0; j < 4; ++j) {
       tw[j] = __ldg(K.uh_t + k + j);
-      const uint32_t c2 = k0_shift((uint32_t)c, ci, tw[j] & 0xff, &fl[j]);
+      const uint32_t c2 = k0_move(K, (uint32_t)c, ci, tw[j] & 0xff, &fl[j]);
       v[j] = x[(int64_t)__ldg(K.uh_row + k + j) * K.cols + c2];
     }
 #pragma unroll
@@ -300,7 +298,7 @@ __device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, i
   for (; k < h1; ++k) {
     const int tw = __ldg(K.uh_t + k);
     bool flip;
-    const uint32_t c2 = k0_shift((uint32_t)c, ci, tw & 0xff, &flip);
+    const uint32_t c2 = k0_move(K, (uint32_t)c, ci, tw & 0xff, &flip);
     const double v = x[(int64_t)__ldg(K.uh_row + k) * K.cols + c2];
     if (tw & kHopUnit) {
       fix_add(f, v, flip != ((tw & kHopNeg) != 0), K.s0);
@@ -319,32 +317,42 @@ __device__ __forceinline__ double k0_value(const K0View &K, int64_t i, int64_t c
   return k0_row_value(K, i, c, x);
 }
 
-// Projection of a short row onto its tied cycles at column c: the cycle's average, summed
-// from its smallest member in the order g = 0, 1, ..., times the sign relating c to that
-// member; 0 for a cycle that closes with sign -1.  value(col) gives the unprojected entry of
-// the row at a column.
+// Member of the orbit of column c under the stabiliser entry s of row i: its column and the
+// sign beta with X[i, c] = beta X[i, member].
+__device__ __forceinline__ uint32_t k0_member(const K0View &K, int s, uint32_t c, int *sign) {
+  const int w = __ldg(K.st + s);
+  bool flip;
+  const uint32_t pos = k0_move(K, c, __ldg(K.cinfo + c), w & 0xff, &flip);
+  *sign = (((w >> 8) & 1) != 0) != flip ? -1 : 1;
+  return pos;
+}
+
+// Projection of a short row onto its tied orbits at column c: the orbit's average, summed
+// from its smallest member in stabiliser order, times the sign relating c to that member; 0
+// for an orbit that meets itself with sign -1.  value(col) gives the unprojected entry of the
+// row at a column.
 template <class F>
 __device__ __forceinline__ double k0_projected(const K0View &K, int64_t i, int64_t c, F value) {
-  const int P = __ldg(K.per + i), b = __ldg(K.eb + i), G = K.M / P;
+  const int s0 = __ldg(K.st_ptr + i), s1 = __ldg(K.st_ptr + i + 1);
   uint32_t least = (uint32_t)c;
   int ls = 1;
-  for (int g = 1; g < G; ++g) {
-    int s;
-    const uint32_t pos = k0_member(K, P, b, g, (uint32_t)c, &s);
-    if (pos == (uint32_t)c && s < 0) return 0.0;
+  for (int s = s0; s < s1; ++s) {
+    int sg;
+    const uint32_t pos = k0_member(K, s, (uint32_t)c, &sg);
+    if (pos == (uint32_t)c && sg < 0) return 0.0;
     if (pos < least) {
       least = pos;
-      ls = s;
+      ls = sg;
     }
   }
   double sum = value((int64_t)least);
-  for (int g = 1; g < G; ++g) {
-    int s;
-    const uint32_t pos = k0_member(K, P, b, g, least, &s);
+  for (int s = s0; s < s1; ++s) {
+    int sg;
+    const uint32_t pos = k0_member(K, s, least, &sg);
     const double v = value((int64_t)pos);
-    sum += s < 0 ? -v : v;
+    sum += sg < 0 ? -v : v;
   }
-  const double avg = sum / (double)G;
+  const double avg = sum / (double)(s1 - s0 + 1);
   return ls < 0 ? -avg : avg;
 }
 
@@ -358,7 +366,7 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_apply(K0View K, const double 
     const int64_t c = (tile - i * chunks) * kK0Threads + threadIdx.x;
     if (c >= K.cols) continue;
     double v;
-    if (__ldg(K.per + i) == K.M)
+    if (__ldg(K.st_ptr + i) == __ldg(K.st_ptr + i + 1))
       v = k0_value<kFix>(K, i, c, x);
     else
       v = k0_projected(K, i, c, [&](int64_t col) { return k0_value<kFix>(K, i, col, x); });
@@ -389,7 +397,7 @@ __global__ void k_k0_project_short(K0View K, int n_short, const int32_t *__restr
 }
 
 // Number of states of the sector in the short rows: columns that are the smallest member of
-// a cycle that does not close with sign -1.
+// an orbit that does not meet itself with sign -1.
 __global__ void k_k0_count_short(K0View K, int n_short, const int32_t *__restrict__ short_rows,
                                  unsigned long long *__restrict__ count) {
   const int64_t n = (int64_t)n_short * K.cols;
@@ -397,11 +405,10 @@ __global__ void k_k0_count_short(K0View K, int n_short, const int32_t *__restric
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
     const int64_t s = k / K.cols, c = k - s * K.cols;
     const int64_t i = short_rows[s];
-    const int P = K.per[i], b = K.eb[i], G = K.M / P;
     bool least = true, null = false;
-    for (int g = 1; g < G; ++g) {
+    for (int e = K.st_ptr[i]; e < K.st_ptr[i + 1]; ++e) {
       int sg;
-      const uint32_t pos = k0_member(K, P, b, g, (uint32_t)c, &sg);
+      const uint32_t pos = k0_member(K, e, (uint32_t)c, &sg);
       if (pos < (uint32_t)c) least = false;
       if (pos == (uint32_t)c && sg < 0) null = true;
     }
@@ -415,8 +422,72 @@ __global__ void k_k0_count_short(K0View K, int n_short, const int32_t *__restric
 // Host side
 // ---------------------------------------------------------------------------------------
 
-static inline uint32_t step_T(uint32_t x, int M) { return (x >> 1) | ((x & 1u) << (M - 1)); }
-static inline int step_sign(uint32_t x, int N) { return ((x & 1u) && ((N - 1) & 1)) ? -1 : 1; }
+// The symmetry group: elements as site permutations (site i -> perm[e][i]), element 0 the
+// identity, with the character, the product table and the inverses.
+struct Group {
+  int M = 0, g = 0;
+  std::vector<std::vector<int>> perm;
+  std::vector<int> chi;
+  std::vector<int> mul;   // [a * g + b]: apply a, then b
+  std::vector<int> inv;
+};
+
+// e|x> = sign |x'>: x' the permuted occupation, sign the parity of the images of the occupied
+// sites taken in ascending site order.
+static uint32_t act(const Group &G, int e, uint32_t x, int *sign) {
+  uint32_t seen = 0;
+  int inversions = 0;
+  for (uint32_t b = x; b; b &= b - 1) {
+    const int p = G.perm[e][__builtin_ctz(b)];
+    inversions += popc32(seen >> (p + 1));
+    seen |= 1u << p;
+  }
+  *sign = (inversions & 1) ? -1 : 1;
+  return seen;
+}
+
+// Closure of the generators (breadth-first from the identity), character by words, then the
+// checks that make the construction valid: commuting elements and chi a homomorphism.
+static int make_group(int M, int n_gen, const int32_t *perms, const int32_t *chars, Group *G) {
+  G->M = M;
+  std::map<std::vector<int>, int> index;
+  std::vector<int> ident(M);
+  for (int i = 0; i < M; ++i) ident[i] = i;
+  G->perm.push_back(ident);
+  G->chi.push_back(1);
+  index[ident] = 0;
+  for (size_t k = 0; k < G->perm.size(); ++k) {
+    for (int a = 0; a < n_gen; ++a) {
+      std::vector<int> q(M);
+      for (int i = 0; i < M; ++i) q[i] = perms[a * M + G->perm[k][i]];
+      if (index.count(q)) continue;
+      if ((int)G->perm.size() >= kMaxGroup) return fail(HUB_ERR_ARG, "hub_set_translations: the group has more than 64 elements");
+      index[q] = (int)G->perm.size();
+      G->perm.push_back(q);
+      G->chi.push_back(G->chi[k] * chars[a]);
+    }
+  }
+  const int g = G->g = (int)G->perm.size();
+  G->mul.assign((size_t)g * g, 0);
+  G->inv.assign(g, -1);
+  for (int a = 0; a < g; ++a)
+    for (int b = 0; b < g; ++b) {
+      std::vector<int> r(M);
+      for (int i = 0; i < M; ++i) r[i] = G->perm[b][G->perm[a][i]];
+      const int p = index.at(r);
+      G->mul[(size_t)a * g + b] = p;
+      if (p == 0) G->inv[a] = b;
+    }
+  for (int a = 0; a < g; ++a)
+    for (int b = 0; b < g; ++b) {
+      if (G->mul[(size_t)a * g + b] != G->mul[(size_t)b * g + a])
+        return fail(HUB_ERR_ARG, "hub_set_translations: the permutations do not commute");
+      if (G->chi[G->mul[(size_t)a * g + b]] != G->chi[a] * G->chi[b])
+        return fail(HUB_ERR_ARG, "hub_set_translations: the signs do not define a character of the group "
+                                 "(e.g. -1 on a permutation of odd order)");
+    }
+  return HUB_OK;
+}
 
 // All M-bit strings with N ones, ascending (Gosper's successor).
 static std::vector<uint32_t> strings_of(int M, int N) {
@@ -432,28 +503,27 @@ static std::vector<uint32_t> strings_of(int M, int N) {
   return out;
 }
 
-// Cycle data of string x: is it the smallest member, its period, and the closing sign of
-// T^P on it.
-static void cycle_of(uint32_t x, int M, int N, bool *is_rep, int *P, int *b) {
-  uint32_t c = x;
-  bool least = true;
-  *P = M;
-  for (int s = 1; s <= M; ++s) {
-    c = step_T(c, M);
-    if (c == x) {
-      *P = s;
-      break;
+// Orbit data of string x: smallest image, the first element reaching it with its sign, and
+// the stabiliser as (element, sign) pairs.
+struct OrbitOf {
+  uint32_t least;
+  int e_least, s_least;
+  std::vector<std::pair<int, int>> stab;
+};
+
+static OrbitOf orbit_of(const Group &G, uint32_t x) {
+  OrbitOf o{x, 0, 1, {}};
+  for (int e = 0; e < G.g; ++e) {
+    int s;
+    const uint32_t y = act(G, e, x, &s);
+    if (y < o.least) {
+      o.least = y;
+      o.e_least = e;
+      o.s_least = s;
     }
-    if (c < x) least = false;
+    if (y == x) o.stab.push_back({e, s});
   }
-  int sg = 1;
-  uint32_t y = x;
-  for (int s = 0; s < *P; ++s) {
-    sg *= step_sign(y, N);
-    y = step_T(y, M);
-  }
-  *is_rep = least;
-  *b = sg;
+  return o;
 }
 
 void k0_release(hub_ctx *h) {
@@ -461,13 +531,16 @@ void k0_release(hub_ctx *h) {
   if (!k) return;
   dev_free(k->rep);
   dev_free(k->per);
-  dev_free(k->eb);
+  dev_free(k->st_ptr);
+  dev_free(k->st);
   dev_free(k->uh_ptr);
   dev_free(k->uh_row);
   dev_free(k->uh_t);
   dev_free(k->uh_val);
   dev_free(k->cinfo);
   dev_free(k->cbits);
+  dev_free(k->tab_off);
+  dev_free(k->tab);
   dev_free(k->krp);
   dev_free(k->kscol);
   dev_free(k->kval);
@@ -500,23 +573,23 @@ int64_t vec_len(const hub_ctx *h) {
   return h->count[0] * h->count[1];
 }
 
-// H must commute with T: every bond moved one site down is a bond with the same t, and U and
-// eps are the same on every site.
-static int check_invariant(const hub_ctx *h) {
-  const int M = h->M;
+// H must commute with every generator: each bond moved by it is a bond with the same t, and U
+// and eps are the same on every site.
+static int check_invariant(const hub_ctx *h, int n_gen, const int32_t *perms) {
   std::map<std::pair<int, int>, double> bonds;
   for (int b = 0; b < h->n_bonds; ++b) {
     const int i = h->bonds[2 * b], j = h->bonds[2 * b + 1];
     bonds[{std::min(i, j), std::max(i, j)}] = h->t[b];
   }
-  for (int b = 0; b < h->n_bonds; ++b) {
-    const int i = (h->bonds[2 * b] + M - 1) % M, j = (h->bonds[2 * b + 1] + M - 1) % M;
-    const auto it = bonds.find({std::min(i, j), std::max(i, j)});
-    if (it == bonds.end() || it->second != h->t[b])
-      return fail(HUB_ERR_ARG, "hub_set_symmetry: the bonds are not invariant under the translation i -> i-1 mod M");
-  }
+  for (int a = 0; a < n_gen; ++a)
+    for (int b = 0; b < h->n_bonds; ++b) {
+      const int i = perms[a * h->M + h->bonds[2 * b]], j = perms[a * h->M + h->bonds[2 * b + 1]];
+      const auto it = bonds.find({std::min(i, j), std::max(i, j)});
+      if (it == bonds.end() || it->second != h->t[b])
+        return fail(HUB_ERR_ARG, "hub_set_symmetry: the bonds are not invariant under the translations");
+    }
   if (!h->uniform_U) return fail(HUB_ERR_ARG, "hub_set_symmetry: U differs between sites");
-  for (int i = 1; i < M; ++i)
+  for (int i = 1; i < h->M; ++i)
     if (h->eps[i] != h->eps[0]) return fail(HUB_ERR_ARG, "hub_set_symmetry: eps differs between sites");
   return HUB_OK;
 }
@@ -529,38 +602,37 @@ static int upload(T **dst, const std::vector<T> &src, const char *what) {
   return HUB_OK;
 }
 
-static int k0_build(hub_ctx *h, int omega) {
-  const int M = h->M, Nu = h->N[0], Nd = h->N[1];
+static int k0_build(hub_ctx *h, const Group &G) {
+  const int M = h->M, Nu = h->N[0], Nd = h->N[1], g = G.g;
   K0State *k = new (std::nothrow) K0State();
   if (!k) return fail(HUB_ERR_OOM, "hub_set_symmetry: host allocation failed");
   h->k0 = k;
-  k->omega = omega;
+  k->g = g;
   k->cols = h->count[1];
   k->diag0 = (h->eps.empty() ? 0.0 : h->eps[0]) * (double)(Nu + Nd);
 
-  // every cycle has at most M members, so rows >= count_up / M: refuse before enumerating
+  // every orbit has at most |G| members, so rows >= count_up / |G|: refuse before enumerating
   // when even that many rows of one vector cannot fit
   size_t free_b = 0, total_b = 0;
   HUB_CUDA(cudaMemGetInfo(&free_b, &total_b));
-  if (8.0 * ((double)h->count[0] / M) * (double)k->cols > (double)free_b)
+  if (8.0 * ((double)h->count[0] / g) * (double)k->cols > (double)free_b)
     return fail(HUB_ERR_OOM, "hub_set_symmetry: one vector of the sector does not fit");
 
-  // rows: up representatives, ascending, with periods and closing signs (times omega^P)
+  // rows: up representatives, ascending, orbit sizes, stabiliser lists
   std::vector<uint32_t> reps;
-  std::vector<int32_t> per, eb;
+  std::vector<int32_t> per, st_ptr(1, 0), st;
   for (uint32_t x : strings_of(M, Nu)) {
-    bool is_rep;
-    int P, b;
-    cycle_of(x, M, Nu, &is_rep, &P, &b);
-    if (!is_rep) continue;
+    const OrbitOf o = orbit_of(G, x);
+    if (o.least != x) continue;
     reps.push_back(x);
-    per.push_back(P);
-    eb.push_back((omega < 0 && (P & 1)) ? -b : b);
+    per.push_back(g / (int)o.stab.size());
+    for (const auto &hs : o.stab)
+      if (hs.first != 0) st.push_back(hs.first | ((G.chi[hs.first] * hs.second < 0) ? (1 << 8) : 0));
+    st_ptr.push_back((int32_t)st.size());
   }
   k->rows = (int64_t)reps.size();
   k->rep_h = reps;
   k->per_h = per;
-
   if (8.0 * (double)k->rows * (double)k->cols > (double)free_b)
     return fail(HUB_ERR_OOM, "hub_set_symmetry: one vector of the sector does not fit");
 
@@ -573,7 +645,8 @@ static int k0_build(hub_ctx *h, int omega) {
   k->mt = -Hv.t0;
   k->fix = (Hv.uniform_t && Hv.t0 != 0.0 && k->s0 >= 1) ? 1 : 0;
 
-  // up-hop lists: hopped string u', its representative R_i' and t with T^t |R_i'> = s |u'>
+  // up-hop lists: hopped string u', its representative R_i' and the first element e0 with
+  // e0 |u'> = s |R_i'>, so that g = e0^-1 maps R_i' to s u' and the gather moves by g^-1 = e0
   std::vector<int32_t> uh_ptr(1, 0), uh_row, uh_t;
   std::vector<double> uh_val;
   for (size_t i = 0; i < reps.size(); ++i) {
@@ -585,59 +658,84 @@ static int k0_build(hub_ctx *h, int omega) {
       const int lo = std::min(a, c), hi = std::max(a, c);
       const uint32_t between = ((1u << hi) - 1u) & ~((2u << lo) - 1u);
       const double val = -h->t[b] * ((popc32(R & between) & 1) ? -1.0 : 1.0);
-      uint32_t least = u2, cur = u2;
-      for (int s = 1; s < M; ++s) {
-        cur = step_T(cur, M);
-        least = std::min(least, cur);
-      }
-      const auto it = std::lower_bound(reps.begin(), reps.end(), least);
-      if (it == reps.end() || *it != least) return fail(HUB_ERR_CUDA, "hub_set_symmetry: representative not found");
+      const OrbitOf o = orbit_of(G, u2);
+      const auto it = std::lower_bound(reps.begin(), reps.end(), o.least);
+      if (it == reps.end() || *it != o.least) return fail(HUB_ERR_CUDA, "hub_set_symmetry: representative not found");
       const int i2 = (int)(it - reps.begin());
-      int t = 0, sg = 1;
-      cur = least;
-      while (cur != u2 && t < per[i2]) {
-        sg *= step_sign(cur, Nu);
-        cur = step_T(cur, M);
-        ++t;
-      }
-      if (cur != u2) return fail(HUB_ERR_CUDA, "hub_set_symmetry: translation not found");
-      if (omega < 0 && (t & 1)) sg = -sg;
-      int tw = t;
+      const int e0 = o.e_least, s = o.s_least;
+      const double cf = val * s * G.chi[G.inv[e0]];
+      int tw = e0;
       if (per[i] == per[i2] && k->fix) {
         tw |= kHopUnit;
-        if (val * sg / k->mt < 0) tw |= kHopNeg;
+        if (cf / k->mt < 0) tw |= kHopNeg;
       }
       uh_row.push_back(i2);
       uh_t.push_back(tw);
-      uh_val.push_back(val * sg * std::sqrt((double)per[i] / (double)per[i2]));
+      uh_val.push_back(cf * std::sqrt((double)per[i] / (double)per[i2]));
     }
     uh_ptr.push_back((int32_t)uh_row.size());
   }
   std::vector<int32_t> shorts;
   for (size_t i = 0; i < reps.size(); ++i)
-    if (per[i] < M) shorts.push_back((int32_t)i);
+    if (st_ptr[i + 1] > st_ptr[i]) shorts.push_back((int32_t)i);
   k->n_short = (int)shorts.size();
 
-  // columns in the order of Table I: down representatives ascending, then n = 0 .. P_j - 1
+  // columns in the order of Table I: down representatives ascending, each followed by the
+  // rest of its orbit (coset representatives c_k, smallest element first); one move table per
+  // stabiliser type
   const std::vector<uint32_t> dn = strings_of(M, Nd);
   if ((int64_t)dn.size() != k->cols) return fail(HUB_ERR_CUDA, "hub_set_symmetry: down basis size mismatch");
+  std::map<std::vector<std::pair<int, int>>, int> types;
+  std::vector<int32_t> tab_off;
+  std::vector<uint16_t> tab;
+  std::vector<std::vector<int>> cos_rep;   // per type: c_k
   std::vector<uint32_t> cinfo, cbits;
   std::vector<int32_t> csign, pos(dn.size(), -1);
   for (uint32_t x : dn) {
-    bool is_rep;
-    int P, b;
-    cycle_of(x, M, Nd, &is_rep, &P, &b);
-    if (!is_rep) continue;
-    uint32_t d = x;
-    int s = 1;
-    for (int n = 0; n < P; ++n) {
+    const OrbitOf o = orbit_of(G, x);
+    if (o.least != x) continue;
+    int type;
+    const auto ti = types.find(o.stab);
+    if (ti != types.end()) {
+      type = ti->second;
+    } else {
+      type = (int)cos_rep.size();
+      if (type > 255) return fail(HUB_ERR_ARG, "hub_set_symmetry: too many stabiliser types");
+      types[o.stab] = type;
+      std::vector<int> coset_of(g, -1), hof(g, -1), reps_k;
+      std::vector<int> sig(g, 0);
+      for (const auto &hs : o.stab) sig[hs.first] = hs.second;
+      for (int e = 0; e < g; ++e) {
+        if (coset_of[e] >= 0) continue;
+        const int kk = (int)reps_k.size();
+        reps_k.push_back(e);
+        for (const auto &hs : o.stab) {
+          const int p = G.mul[(size_t)e * g + hs.first];
+          coset_of[p] = kk;
+          hof[p] = hs.first;
+        }
+      }
+      const int nb = (int)reps_k.size();
+      tab_off.push_back((int32_t)tab.size());
+      tab_off.push_back(nb);
+      for (int e = 0; e < g; ++e)
+        for (int kk = 0; kk < nb; ++kk) {
+          const int p = G.mul[(size_t)reps_k[kk] * g + e];
+          tab.push_back((uint16_t)(coset_of[p] | (sig[hof[p]] < 0 ? 0x8000 : 0)));
+        }
+      cos_rep.push_back(reps_k);
+    }
+    const std::vector<int> &ck = cos_rep[type];
+    for (size_t kk = 0; kk < ck.size(); ++kk) {
+      int s;
+      const uint32_t d = act(G, ck[kk], x, &s);
       const size_t r = (size_t)(std::lower_bound(dn.begin(), dn.end(), d) - dn.begin());
+      if (r >= dn.size() || dn[r] != d || pos[r] >= 0)
+        return fail(HUB_ERR_CUDA, "hub_set_symmetry: column order inconsistent");
       pos[r] = (int32_t)cbits.size();
-      cinfo.push_back((uint32_t)n | ((uint32_t)P << 8) | (b < 0 ? kColNegB : 0u));
+      cinfo.push_back((uint32_t)kk | ((uint32_t)type << 8));
       cbits.push_back(d);
       csign.push_back(s);
-      s *= step_sign(d, Nd);
-      d = step_T(d, M);
     }
   }
   if ((int64_t)cbits.size() != k->cols || std::find(pos.begin(), pos.end(), -1) != pos.end())
@@ -674,19 +772,20 @@ static int k0_build(hub_ctx *h, int omega) {
   }
 
   int rc = HUB_OK;
-  if ((rc = upload(&k->rep, reps, "sector representatives")) || (rc = upload(&k->per, per, "sector periods")) ||
-      (rc = upload(&k->eb, eb, "sector signs")) || (rc = upload(&k->uh_ptr, uh_ptr, "sector up hops")) ||
-      (rc = upload(&k->uh_row, uh_row, "sector up hops")) || (rc = upload(&k->uh_t, uh_t, "sector up hops")) ||
-      (rc = upload(&k->uh_val, uh_val, "sector up hops")) || (rc = upload(&k->cinfo, cinfo, "sector columns")) ||
-      (rc = upload(&k->cbits, cbits, "sector columns")) || (rc = upload(&k->krp, krp, "sector down hops")) ||
-      (rc = upload(&k->kscol, kscol, "sector down hops")) || (rc = upload(&k->kval, kval, "sector down hops")) ||
-      (rc = upload(&k->short_rows, shorts, "sector short rows")))
+  if ((rc = upload(&k->rep, reps, "sector representatives")) || (rc = upload(&k->per, per, "sector orbits")) ||
+      (rc = upload(&k->st_ptr, st_ptr, "sector stabilisers")) || (rc = upload(&k->st, st, "sector stabilisers")) ||
+      (rc = upload(&k->uh_ptr, uh_ptr, "sector up hops")) || (rc = upload(&k->uh_row, uh_row, "sector up hops")) ||
+      (rc = upload(&k->uh_t, uh_t, "sector up hops")) || (rc = upload(&k->uh_val, uh_val, "sector up hops")) ||
+      (rc = upload(&k->cinfo, cinfo, "sector columns")) || (rc = upload(&k->cbits, cbits, "sector columns")) ||
+      (rc = upload(&k->tab_off, tab_off, "sector move tables")) || (rc = upload(&k->tab, tab, "sector move tables")) ||
+      (rc = upload(&k->krp, krp, "sector down hops")) || (rc = upload(&k->kscol, kscol, "sector down hops")) ||
+      (rc = upload(&k->kval, kval, "sector down hops")) || (rc = upload(&k->short_rows, shorts, "sector short rows")))
     return rc;
   if (!dev_alloc((void **)&k->scratch, sizeof(double) * std::max<int64_t>(k->n_short * k->cols, 1), "sector scratch") ||
       !dev_alloc((void **)&k->d_count, sizeof(unsigned long long), "sector counter"))
     return HUB_ERR_OOM;
 
-  // dimension: free rows count fully, short rows by their cycles
+  // dimension: free rows count fully, short rows by their orbits
   k->dim = (k->rows - k->n_short) * k->cols;
   if (k->n_short && k->cols) {
     HUB_CUDA(cudaMemset(k->d_count, 0, sizeof(unsigned long long)));
@@ -729,6 +828,30 @@ int k0_project_inplace(hub_ctx *h, double *x, cudaStream_t s) {
   return HUB_OK;
 }
 
+// Validate the generators, build the group and the tables of its sector.
+static int set_translations(hub_t h, int n_gen, const int32_t *perms, const int32_t *chars, const char *who) {
+  int rc = ready(h, who);
+  if (rc) return rc;
+  const int M = h->M;
+  if (n_gen < 1 || n_gen > 8 || !perms || !chars) return fail(HUB_ERR_ARG, std::string(who) + ": bad argument");
+  for (int a = 0; a < n_gen; ++a) {
+    std::vector<int> hit(M, 0);
+    for (int i = 0; i < M; ++i) {
+      const int p = perms[a * M + i];
+      if (p < 0 || p >= M || hit[p]++) return fail(HUB_ERR_ARG, std::string(who) + ": a generator is not a permutation of the sites");
+    }
+    if (chars[a] != 1 && chars[a] != -1) return fail(HUB_ERR_ARG, std::string(who) + ": characters must be +1 or -1");
+  }
+  if ((rc = check_invariant(h, n_gen, perms))) return rc;
+  Group G;
+  if ((rc = make_group(M, n_gen, perms, chars, &G))) return rc;
+  k0_release(h);
+  release_vectors(h);
+  rc = k0_build(h, G);
+  if (rc) k0_release(h);
+  return rc;
+}
+
 }  // namespace hub
 
 using namespace hub;
@@ -741,15 +864,16 @@ extern "C" int hub_set_symmetry(hub_t h, int sym) {
     k0_leave(h);
     return HUB_OK;
   }
-  int rc = ready(h, "hub_set_symmetry");
-  if (rc) return rc;
-  if ((rc = check_invariant(h))) return rc;
   if (sym == HUB_SYM_KPI && (h->M & 1)) return fail(HUB_ERR_ARG, "hub_set_symmetry: k = pi needs an even M");
-  k0_release(h);
-  release_vectors(h);
-  rc = k0_build(h, sym == HUB_SYM_KPI ? -1 : 1);
-  if (rc) k0_release(h);
-  return rc;
+  std::vector<int32_t> perm(h->M);
+  for (int i = 0; i < h->M; ++i) perm[i] = (i + h->M - 1) % h->M;   // T: site i -> i - 1
+  const int32_t chi = sym == HUB_SYM_KPI ? -1 : 1;
+  return set_translations(h, 1, perm.data(), &chi, "hub_set_symmetry");
+}
+
+extern "C" int hub_set_translations(hub_t h, int n_gen, const int32_t *perm_host, const int32_t *char_host) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_set_translations: NULL handle");
+  return set_translations(h, n_gen, perm_host, char_host, "hub_set_translations");
 }
 
 extern "C" int hub_k_dims(hub_t h, int64_t *rows, int64_t *cols, int64_t *dim) {

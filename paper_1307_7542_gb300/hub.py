@@ -55,6 +55,7 @@ SIGNATURES = {
     "hub_grad_noalloc": (_i, [_p, _p, _p, _p, _p, _p]),
     "hub_batch_ground": (_i, [_i, _i, _p, _i, _p, _p, _p, _i, _p, _p, _p, _i, _d, _p, _p, _p, _p]),
     "hub_set_symmetry": (_i, [_p, _i]),
+    "hub_set_translations": (_i, [_p, _i, _p, _p]),
     "hub_k_dims": (_i, [_p, ctypes.POINTER(_i64), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "hub_k_reps": (_i, [_p, _p, _p]),
     "hub_k_columns": (_i, [_p, _p, _p]),
@@ -286,6 +287,13 @@ def hub_set_symmetry(h, sym):
     _check(lib().hub_set_symmetry(h, sym))
 
 
+def hub_set_translations(h, perms, chars):
+    perms = np.ascontiguousarray(np.asarray(perms, dtype=np.int32))
+    chars = np.ascontiguousarray(np.asarray(chars, dtype=np.int32).reshape(-1))
+    assert perms.ndim == 2 and perms.shape[0] == chars.shape[0]
+    _check(lib().hub_set_translations(h, perms.shape[0], _ptr(perms), _ptr(chars)))
+
+
 def hub_k_dims(h):
     r, c, d = _i64(), _i64(), _i64()
     _check(lib().hub_k_dims(h, ctypes.byref(r), ctypes.byref(c), ctypes.byref(d)))
@@ -361,6 +369,13 @@ class Hubbard:
             self.D = self.k_rows * self.k_cols
         else:
             self.D = self.count_up * self.count_dn
+
+    def set_translations(self, perms, chars):
+        """The sector g Psi = chi(g) Psi of the group generated by the site permutations
+        perms (chi = +-1 on each); vectors then in row form, k_rows x k_cols."""
+        hub_set_translations(self.h, perms, chars)
+        self.k_rows, self.k_cols, self.k_dim = hub_k_dims(self.h)
+        self.D = self.k_rows * self.k_cols
 
     def k_reps(self):
         return hub_k_reps(self.h, self.k_rows)

@@ -354,3 +354,95 @@ def test_k_sector_host_apply_and_ritz(hub):
     m.close()
     assert abs(theta - w[lvl]) < 1e-9 * abs(w[lvl])
     assert 1.0 - abs(float(psi.cpu().numpy() @ ref.ravel())) < 1e-8
+
+
+# ------------------------------------------------------------------ several translations (torus)
+
+def torus_bonds(Lx, Ly):
+    b = set()
+    for y in range(Ly):
+        for x in range(Lx):
+            s = x + Lx * y
+            for dx, dy in ((1, 0), (0, 1)):
+                s2 = (x + dx) % Lx + Lx * ((y + dy) % Ly)
+                b.add((min(s, s2), max(s, s2)))
+    return np.array(sorted(b), dtype=np.int32)
+
+
+# (Lx, Ly, N_up, N_dn, characters, t, U, eps)
+TORUS = [
+    (3, 3, 2, 2, (1, 1), 1.0, 4.0, 0.0),
+    (3, 3, 3, 2, (1, 1), 0.8, 2.0, 0.1),
+    (4, 2, 3, 3, (-1, 1), 1.0, 4.0, 0.0),
+    (4, 2, 4, 2, (-1, -1), 1.0, 3.0, 0.0),     # stabilisers with sign -1, empty orbits
+    (4, 2, 2, 2, (1, -1), 0.7, 5.0, -0.2),
+    (2, 2, 2, 2, (-1, 1), 1.0, 4.0, 0.0),
+    (4, 3, 3, 3, (-1, 1), 1.0, 4.0, 0.0),       # 220 x 220 strings: several column tiles
+]
+
+
+@pytest.mark.parametrize("case", TORUS, ids=lambda c: f"{c[0]}x{c[1]}-{c[2]}-{c[3]}-{c[4]}")
+def test_torus_sector_parity(hub, case):
+    """Momentum sectors of the torus (hub_set_translations): representatives, orbit sizes,
+    columns and dimension bit-exact against the oracle's group construction; products of
+    random states of the sector per entry within 1e-13 |H||Psi|; the lowest eigenvalue of the
+    sector by the library's Lanczos against dense V^T H V."""
+    Lx, Ly, nu, nd, chars, t, U, eps = case
+    M = Lx * Ly
+    gens = K.torus_translations(Lx, Ly)
+    bonds = torus_bonds(Lx, Ly)
+    om = O.Model(M, bonds, t, U, eps)
+    m = hub.Hubbard(M, nu, nd, bonds, t, U, np.full(M, eps) if eps else None)
+    m.set_translations(gens, chars)
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix_group(M, nu, nd, B, gens, list(chars))
+    assert m.k_dim == V.shape[1]
+    X0, reps, per = K.row_form_group(M, nu, nd, B, np.zeros(B.shape[0]), gens)
+    r, p = m.k_reps()
+    assert np.array_equal(r.astype(np.uint64), reps) and np.array_equal(p.astype(np.int64), per)
+    cb, cs = m.k_columns()
+    ob, osg = K.group_columns(M, nd, gens)
+    assert np.array_equal(cb.astype(np.uint64), ob) and np.array_equal(cs, osg.astype(np.int32))
+    for seed in (1, 2):
+        psi = np.asarray(V @ W.normal(seed, V.shape[1]))
+        X, _, _ = K.row_form_group(M, nu, nd, B, psi, gens)
+        Yref, _, _ = K.row_form_group(M, nu, nd, B, O.apply(om, B, psi), gens)
+        bound, _, _ = K.row_form_group(M, nu, nd, B, O.apply(om, B, np.abs(psi), absolute=True), gens)
+        y = m.apply(torch.from_numpy(X.ravel()).cuda()).cpu().numpy()
+        assert_entrywise(y, Yref.ravel(), np.abs(bound).ravel())
+    w = np.linalg.eigvalsh(K.k0_matrix(om, B, V))
+    g = m.ground(None, maxit=min(400, 3 * m.k_dim + 5), tol=1e-13)
+    m.close()
+    assert abs(g["E0"] - w[0]) < 1e-10 * max(1.0, abs(w[0]))
+
+
+def test_torus_translation_errors(hub):
+    """Refusals: a generator that is not a permutation, one that does not map bonds onto
+    bonds, non-commuting generators, -1 on a generator of odd order."""
+    M = 9
+    gens = K.torus_translations(3, 3)
+    m = hub.Hubbard(M, 2, 2, torus_bonds(3, 3), 1.0, 4.0)
+    for perms, chars in [([[0] * M], [1]), ([list(range(1, M)) + [0]], [1]), (gens, [-1, 1]),
+                         ([gens[0], [1, 0, 2, 4, 3, 5, 7, 6, 8]], [1, 1])]:
+        with pytest.raises(hub.HubError) as e:
+            m.set_translations(perms, chars)
+        assert e.value.code == hub.HUB_ERR_ARG
+    m.close()
+
+
+@pytest.mark.slow
+def test_torus_4x4_sectors_reach_the_ground_state(hub):
+    """4x4 torus, half filling, U = 4: the four real-momentum sectors (each about 16 times
+    smaller than the sector) lie above the full-sector E0, and the lowest of them equals it."""
+    w = W.square4x4(4.0)
+    m = hub.Hubbard(16, 8, 8, w["bonds"], w["t"], w["U"], w["eps"])
+    full = m.ground(None, maxit=400, tol=1e-12)["E0"]
+    gens = K.torus_translations(4, 4)
+    energies = []
+    for chars in ((1, 1), (-1, 1), (1, -1), (-1, -1)):
+        m.set_translations(gens, chars)
+        assert 0.9 * m.count_up * m.count_dn <= 16 * m.k_dim <= 1.1 * m.count_up * m.count_dn
+        energies.append(m.ground(None, maxit=400, tol=1e-12)["E0"])
+    m.close()
+    assert min(energies) >= full - 1e-10 * abs(full)
+    assert abs(min(energies) - full) < 1e-10 * abs(full)

@@ -270,3 +270,24 @@ def test_group_character_must_be_consistent():
     """-1 on a generator of odd order is no character: refused."""
     with pytest.raises(ValueError):
         K.group_character(K.site_group([[(i - 1) % 5 for i in range(5)]]), [-1])
+
+
+def test_group_columns_reduce_to_the_chain_and_cover_the_strings():
+    """One generator: group_columns is the chain's column order with its signs; tori: every
+    string once; row_form_group preserves inner products."""
+    for M, N in [(4, 2), (6, 3), (8, 4), (6, 0)]:
+        b1, s1 = K.rep_columns(M, N)
+        b2, s2 = K.group_columns(M, N, [[(i - 1) % M for i in range(M)]])
+        assert np.array_equal(b1, b2) and np.array_equal(s1, s2)
+    for Lx, Ly, N in [(3, 3, 2), (4, 2, 3), (3, 3, 4)]:
+        b, s = K.group_columns(Lx * Ly, N, K.torus_translations(Lx, Ly))
+        assert np.array_equal(np.sort(b), K.spin_strings(Lx * Ly, N))
+    M, nu, nd = 8, 3, 3
+    gens = K.torus_translations(4, 2)
+    B = O.basis(M, nu, nd)
+    V = K.bloch_matrix_group(M, nu, nd, B, gens, [-1, 1])
+    rng = np.random.default_rng(5)
+    a, b = (np.asarray(V @ rng.standard_normal(V.shape[1])) for _ in range(2))
+    Xa, _, _ = K.row_form_group(M, nu, nd, B, a, gens)
+    Xb, _, _ = K.row_form_group(M, nu, nd, B, b, gens)
+    assert abs(float(np.sum(Xa * Xb)) - float(a @ b)) < 1e-12 * np.linalg.norm(a) * np.linalg.norm(b)
