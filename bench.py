@@ -236,8 +236,8 @@ def combine_ranks(elapsed_ms, steps, world, device):
 def extras(hub, W, torch):
     """Measurements beside the headline: batched vs one-at-a-time impurity solves, adjoint
     gradients vs finite differences, the 3x6 bandwidth-stress Lanczos step, the 4x4
-    zero-temperature Green's function, the 8-site ring's E0 wall time and the momentum sectors
-    of the 16- and 20-site rings."""
+    zero-temperature Green's function, the 8-site ring's E0 wall time, the momentum sectors
+    of the 16- and 20-site rings and of the 4x4 torus."""
     import numpy as np
     out = {}
     # (1) AIM star M=8: 81 sectors x 64 parameter sets, one persistent launch
@@ -397,6 +397,16 @@ def extras(hub, W, torch):
                     "E0": r8["E0"], "iterations": r8["iters"], "lanczos_ground_ms": 1000 * min(reps8),
                     "batched_single_job_E0": float(Eb[0]), "batched_single_job_iterations": int(itb[0]),
                     "batched_single_job_ms": 1000 * min(reps_b)}
+    # (7) the 4x4 torus (the benchmark lattice) in its four real-momentum sectors of the two
+    # translations, U = 4, each to |dE0| < 1e-12; the lowest is the full sector's ground state
+    tor = {}
+    for kx, ky in (("0", "0"), ("pi", "0"), ("0", "pi"), ("pi", "pi")):
+        tor[f"k=({kx},{ky})"] = R.run(16, 8, 8, "k", maxit=400, tol=1e-12, applies=10, torus=(4, 4), k=(kx, ky))
+    low = min(tor.values(), key=lambda r: r["E0"])
+    out["torus_4x4_momentum"] = {"workload": "4x4 PBC (8,8), t=1, U=4: sectors of the two translations",
+                                 "sectors": tor, "lowest_sector": [k_ for k_, v_ in tor.items() if v_ is low][0],
+                                 "lowest_E0": low["E0"],
+                                 "all_sectors_lanczos_s": sum(v_["lanczos_s"] for v_ in tor.values())}
     out["ring_momentum"] = {"workload": "Hubbard ring, half filling, t=1, U=4; k = pi subspace of the "
                                         "translation (T eigenvalue -1) against the full sector",
                             "M16_full": full16, "M16_kpi": kpi16, "M20_kpi": kpi20,
