@@ -291,3 +291,28 @@ def test_group_columns_reduce_to_the_chain_and_cover_the_strings():
     Xa, _, _ = K.row_form_group(M, nu, nd, B, a, gens)
     Xb, _, _ = K.row_form_group(M, nu, nd, B, b, gens)
     assert abs(float(np.sum(Xa * Xb)) - float(a @ b)) < 1e-12 * np.linalg.norm(a) * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("Lx,Ly,nu,nd,chars", [(3, 2, 3, 3, (1, 1)), (3, 2, 3, 2, (1, -1)), (2, 3, 2, 2, (-1, 1)),
+                                               (2, 3, 3, 3, (-1, 1)), (2, 3, 3, 2, (1, 1))])
+def test_group_projector_route_torus_6_sites(Lx, Ly, nu, nd, chars):
+    """3 x 2 and 2 x 3 tori (a length-2 direction carries one bond per pair), U = 4,
+    eps = 0.3: the spectrum of V^T H V for each real character equals that of H on the range
+    of (1/|G|) sum_g chi(g) g, from the dense Jordan-Wigner Hamiltonian and brute-force g."""
+    M = Lx * Ly
+    gens = K.torus_translations(Lx, Ly)
+    m = O.Model(M, torus_bonds(Lx, Ly), 1.0, 4.0, 0.3)
+    B = O.basis(M, nu, nd)
+    w = np.linalg.eigvalsh(K.k0_matrix(m, B, K.bloch_matrix_group(M, nu, nd, B, gens, list(chars))))
+    els = K.site_group(gens)
+    chi = K.group_character(els, list(chars))
+    idx = {int(v): k for k, v in enumerate(B.tolist())}
+    P = np.zeros((B.shape[0], B.shape[0]))
+    for (p, _), c in zip(els, chi):
+        for k, I in enumerate(B.tolist()):
+            I2, s = K._act_two_spin(M, I, nu, nd, p)
+            P[idx[I2], k] += c * s / len(els)
+    ev, Q = np.linalg.eigh((P + P.T) / 2)
+    Q = Q[:, ev > 0.5]
+    w2 = np.linalg.eigvalsh(Q.T @ O.dense_fock(m, nu, nd) @ Q)
+    assert w.shape == w2.shape and np.max(np.abs(w - w2)) < 1e-12
