@@ -62,3 +62,70 @@ def test_no_gpu_returns_error_code(libpath):
     with pytest.raises(hub.HubError) as e:
         hub.hub_basis(4, 2, 2)
     assert e.value.code < 0
+
+
+def test_null_handles_are_refused(libpath):
+    """Every entry point that takes a handle refuses NULL with HUB_ERR_ARG and a message,
+    before any device work (host logic, no GPU needed)."""
+    from paper_1307_7542_gb300 import hub
+    import ctypes
+    L = hub.lib()
+    i64 = ctypes.c_int64()
+    d = ctypes.c_double()
+    n = ctypes.c_int()
+    buf = (ctypes.c_int32 * 8)()
+    calls = {
+        "hub_dims": lambda: L.hub_dims(None, ctypes.byref(i64), ctypes.byref(i64)),
+        "hub_hopping": lambda: L.hub_hopping(None, 0, None, None, None),
+        "hub_set_U": lambda: L.hub_set_U(None, 1, None),
+        "hub_apply": lambda: L.hub_apply(None, None, None, None),
+        "hub_apply_host": lambda: L.hub_apply_host(None, None, None, None),
+        "hub_lanczos_ground": lambda: L.hub_lanczos_ground(None, None, 10, 0.0, ctypes.byref(d), None,
+                                                           ctypes.byref(n), None),
+        "hub_lanczos_coeffs": lambda: L.hub_lanczos_coeffs(None, None, None, 0, ctypes.byref(n)),
+        "hub_lanczos_spectrum": lambda: L.hub_lanczos_spectrum(None, None, 10, 1, None, None, ctypes.byref(n), None),
+        "hub_lanczos_ritz": lambda: L.hub_lanczos_ritz(None, None, 10, 0.0, None, ctypes.byref(d), None),
+        "hub_green_coeffs": lambda: L.hub_green_coeffs(None, None, 1, None, None, ctypes.byref(d), ctypes.byref(n), None),
+        "hub_ladder": lambda: L.hub_ladder(None, None, 0, 0, 1, None, None, None),
+        "hub_grad": lambda: L.hub_grad(None, None, None, None, None, None),
+        "hub_grad_noalloc": lambda: L.hub_grad_noalloc(None, None, None, None, None, None),
+        "hub_apply_vjp": lambda: L.hub_apply_vjp(None, None, None, None, None, None, None, None),
+        "hub_set_symmetry": lambda: L.hub_set_symmetry(None, 1),
+        "hub_set_translations": lambda: L.hub_set_translations(None, 1, buf, buf),
+        "hub_k_dims": lambda: L.hub_k_dims(None, None, None, None),
+        "hub_k_reps": lambda: L.hub_k_reps(None, None, None),
+        "hub_k_columns": lambda: L.hub_k_columns(None, None, None),
+        "hub_k_project": lambda: L.hub_k_project(None, None, None, None),
+        "hub_set_mode": lambda: L.hub_set_mode(None, 0),
+        "hub_check": lambda: L.hub_check(None),
+        "hub_profile": lambda: L.hub_profile(None, 1),
+        "hub_profile_read": lambda: L.hub_profile_read(None, 0, None, None, None),
+        "hub_csr_info": lambda: L.hub_csr_info(None, 0, None, None),
+        "hub_get_csr": lambda: L.hub_get_csr(None, 0, None, None, None),
+        "hub_get_basis": lambda: L.hub_get_basis(None, 0, None),
+    }
+    for name, call in calls.items():
+        assert call() == hub.HUB_ERR_ARG, name
+        assert L.hub_last_error(), name
+    L.hub_free(None)
+
+
+def test_green_eval_is_the_continued_fraction(libpath):
+    """hub_green_eval (host code) equals the oracle's continued fraction on random coefficients,
+    particle and hole terms, at points on and off the real axis; k = 0 gives 0; bad arguments
+    are refused."""
+    import numpy as np
+    from oracle import hub_oracle as O
+    from paper_1307_7542_gb300 import hub
+    rng = np.random.default_rng(11)
+    for k in (1, 2, 7, 40):
+        a = rng.uniform(-3, 3, k)
+        b = rng.uniform(0.1, 2.0, k)
+        z = rng.uniform(-8, 8, 25) + 1j * rng.uniform(0.01, 1.0, 25)
+        for sign in (1, -1):
+            g = hub.hub_green_eval(a, b, 0.7, -1.3, sign, z)
+            ref = O.continued_fraction(a, b, 0.7, -1.3, sign, z)
+            assert np.max(np.abs(g - ref) / np.abs(ref)) < 1e-13
+    assert np.all(hub.hub_green_eval(np.zeros(0), np.zeros(0), 1.0, 0.0, 1, np.array([1.0 + 1j])) == 0)
+    with pytest.raises(hub.HubError):
+        hub.hub_green_eval(np.ones(3), np.ones(3), 1.0, 0.0, 2, np.array([1.0 + 1j]))
