@@ -31,6 +31,13 @@ The paper implements k = 0 only.  Every function that depends on the momentum al
 a(k) = P^-1/2 sum_r e^{-ikr} T^r |a>, which vanishes unless e^{-ikP} times the closing
 sign of the orbit is +1.
 
+Several commuting translations (a torus): ``permute`` (a site permutation on one spin string
+with its fermion sign), ``site_group`` (closure of the generators), ``group_character``,
+``bloch_matrix_group`` (columns sum_g chi(g) g |r>, normalised), ``character_dimension_group``,
+``torus_translations`` and ``torus_free_levels`` (U = 0 levels of a momentum sector), and the
+test helpers ``group_orbit``, ``group_columns``, ``row_form_group`` that sample states of a
+sector in the column order of Table I.
+
 Readings taken where the paper is silent or its formula is garbled:
 
 1. Eq. count6 subtracts, for a period z, the strings whose period is a proper divisor i
