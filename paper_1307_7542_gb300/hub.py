@@ -29,6 +29,8 @@ HUB_ERR_TIMEOUT = -6
 HUB_SYM_NONE = 0
 HUB_SYM_K0 = 1
 HUB_SYM_KPI = 2
+HUB_SPIN_UP = 0
+HUB_SPIN_DN = 1
 
 # (name, restype, argtypes) of every exported entry point.
 _i, _i64, _d, _p = ctypes.c_int, ctypes.c_int64, ctypes.c_double, ctypes.c_void_p

@@ -129,3 +129,14 @@ def test_green_eval_is_the_continued_fraction(libpath):
     assert np.all(hub.hub_green_eval(np.zeros(0), np.zeros(0), 1.0, 0.0, 1, np.array([1.0 + 1j])) == 0)
     with pytest.raises(hub.HubError):
         hub.hub_green_eval(np.ones(3), np.ones(3), 1.0, 0.0, 2, np.array([1.0 + 1j]))
+
+
+def test_binding_constants_match_the_header():
+    """Every #define HUB_* of include/hub.h exists in the binding with the same value."""
+    from paper_1307_7542_gb300 import hub
+    src = open(HEADER).read()
+    defs = dict(re.findall(r"#define\s+(HUB_[A-Z0-9_]+)\s+\(?(-?\d+)\)?", src))
+    assert len(defs) >= 15
+    for name, val in defs.items():
+        assert hasattr(hub, name), name
+        assert getattr(hub, name) == int(val), name
