@@ -21,7 +21,8 @@
  *     message for the calling thread's last failure.
  *   - Pointers named *_dev are device pointers owned by the caller, pointers named
  *     *_host are host pointers owned by the caller.  Vectors are FP64, dense, of length
- *     D = count_up * count_dn, 8-byte aligned.
+ *     D = count_up * count_dn, 8-byte aligned (rows * cols, the row form, while a momentum
+ *     sector is active: hub_set_symmetry, hub_set_translations).
  *   - stream is a cudaStream_t passed as void* (NULL = the legacy default stream).
  *     Calls that take a stream enqueue work on it and may return before it finishes,
  *     except where stated.  Set-up calls (hub_basis, hub_hopping, hub_set_U) run on
