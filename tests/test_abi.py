@@ -140,3 +140,17 @@ def test_binding_constants_match_the_header():
     for name, val in defs.items():
         assert hasattr(hub, name), name
         assert getattr(hub, name) == int(val), name
+
+
+def test_plain_c_caller(libpath, tmp_path):
+    """tests/c_abi_check.c, compiled with gcc against include/hub.h and the library, runs the
+    device-free calls and checks them (refusals, the continued fraction by hand)."""
+    exe = str(tmp_path / "c_abi_check")
+    libdir = os.path.dirname(libpath)
+    lib = os.path.basename(libpath)[3:-3]
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", os.path.join(ROOT, "tests", "c_abi_check.c"),
+                        "-I", os.path.join(ROOT, "include"), "-L", libdir, f"-l{lib}",
+                        f"-Wl,-rpath,{libdir}", "-lm", "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
