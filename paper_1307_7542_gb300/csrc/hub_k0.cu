@@ -55,6 +55,7 @@
 #include <utility>
 #include <vector>
 
+#include "hub_group.h"
 #include "hub_internal.cuh"
 
 namespace hub {
@@ -62,7 +63,6 @@ namespace hub {
 int ready(const hub_ctx *h, const char *who);
 
 constexpr int kK0Threads = 256;
-constexpr int kMaxGroup = 64;   // elements of the symmetry group
 // uh_t word: element g^-1 in bits 0-7; integer path: the hop's coefficient is +-t (bit 8),
 // and its sign relative to -t (bit 9)
 constexpr int kHopUnit = 1 << 8, kHopNeg = 1 << 9;
@@ -422,110 +422,6 @@ __global__ void k_k0_count_short(K0View K, int n_short, const int32_t *__restric
 // Host side
 // ---------------------------------------------------------------------------------------
 
-// The symmetry group: elements as site permutations (site i -> perm[e][i]), element 0 the
-// identity, with the character, the product table and the inverses.
-struct Group {
-  int M = 0, g = 0;
-  std::vector<std::vector<int>> perm;
-  std::vector<int> chi;
-  std::vector<int> mul;   // [a * g + b]: apply a, then b
-  std::vector<int> inv;
-};
-
-// e|x> = sign |x'>: x' the permuted occupation, sign the parity of the images of the occupied
-// sites taken in ascending site order.
-static uint32_t act(const Group &G, int e, uint32_t x, int *sign) {
-  uint32_t seen = 0;
-  int inversions = 0;
-  for (uint32_t b = x; b; b &= b - 1) {
-    const int p = G.perm[e][__builtin_ctz(b)];
-    inversions += popc32(seen >> (p + 1));
-    seen |= 1u << p;
-  }
-  *sign = (inversions & 1) ? -1 : 1;
-  return seen;
-}
-
-// Closure of the generators (breadth-first from the identity), character by words, then the
-// checks that make the construction valid: commuting elements and chi a homomorphism.
-static int make_group(int M, int n_gen, const int32_t *perms, const int32_t *chars, Group *G) {
-  G->M = M;
-  std::map<std::vector<int>, int> index;
-  std::vector<int> ident(M);
-  for (int i = 0; i < M; ++i) ident[i] = i;
-  G->perm.push_back(ident);
-  G->chi.push_back(1);
-  index[ident] = 0;
-  for (size_t k = 0; k < G->perm.size(); ++k) {
-    for (int a = 0; a < n_gen; ++a) {
-      std::vector<int> q(M);
-      for (int i = 0; i < M; ++i) q[i] = perms[a * M + G->perm[k][i]];
-      if (index.count(q)) continue;
-      if ((int)G->perm.size() >= kMaxGroup) return fail(HUB_ERR_ARG, "hub_set_translations: the group has more than 64 elements");
-      index[q] = (int)G->perm.size();
-      G->perm.push_back(q);
-      G->chi.push_back(G->chi[k] * chars[a]);
-    }
-  }
-  const int g = G->g = (int)G->perm.size();
-  G->mul.assign((size_t)g * g, 0);
-  G->inv.assign(g, -1);
-  for (int a = 0; a < g; ++a)
-    for (int b = 0; b < g; ++b) {
-      std::vector<int> r(M);
-      for (int i = 0; i < M; ++i) r[i] = G->perm[b][G->perm[a][i]];
-      const int p = index.at(r);
-      G->mul[(size_t)a * g + b] = p;
-      if (p == 0) G->inv[a] = b;
-    }
-  for (int a = 0; a < g; ++a)
-    for (int b = 0; b < g; ++b) {
-      if (G->mul[(size_t)a * g + b] != G->mul[(size_t)b * g + a])
-        return fail(HUB_ERR_ARG, "hub_set_translations: the permutations do not commute");
-      if (G->chi[G->mul[(size_t)a * g + b]] != G->chi[a] * G->chi[b])
-        return fail(HUB_ERR_ARG, "hub_set_translations: the signs do not define a character of the group "
-                                 "(e.g. -1 on a permutation of odd order)");
-    }
-  return HUB_OK;
-}
-
-// All M-bit strings with N ones, ascending (Gosper's successor).
-static std::vector<uint32_t> strings_of(int M, int N) {
-  std::vector<uint32_t> out;
-  const uint64_t limit = 1ull << M;
-  uint64_t u = N == 0 ? 0 : (1ull << N) - 1;
-  while (u < limit) {
-    out.push_back((uint32_t)u);
-    if (N == 0) break;
-    const uint64_t lo = u & (~u + 1), r = u + lo;
-    u = (((r ^ u) >> 2) / lo) | r;
-  }
-  return out;
-}
-
-// Orbit data of string x: smallest image, the first element reaching it with its sign, and
-// the stabiliser as (element, sign) pairs.
-struct OrbitOf {
-  uint32_t least;
-  int e_least, s_least;
-  std::vector<std::pair<int, int>> stab;
-};
-
-static OrbitOf orbit_of(const Group &G, uint32_t x) {
-  OrbitOf o{x, 0, 1, {}};
-  for (int e = 0; e < G.g; ++e) {
-    int s;
-    const uint32_t y = act(G, e, x, &s);
-    if (y < o.least) {
-      o.least = y;
-      o.e_least = e;
-      o.s_least = s;
-    }
-    if (y == x) o.stab.push_back({e, s});
-  }
-  return o;
-}
-
 void k0_release(hub_ctx *h) {
   K0State *k = h->k0;
   if (!k) return;
@@ -680,66 +576,16 @@ static int k0_build(hub_ctx *h, const Group &G) {
     if (st_ptr[i + 1] > st_ptr[i]) shorts.push_back((int32_t)i);
   k->n_short = (int)shorts.size();
 
-  // columns in the order of Table I: down representatives ascending, each followed by the
-  // rest of its orbit (coset representatives c_k, smallest element first); one move table per
-  // stabiliser type
+  // columns in the order of Table I (down representatives ascending, each followed by the rest
+  // of its orbit) and one move table per stabiliser type
   const std::vector<uint32_t> dn = strings_of(M, Nd);
   if ((int64_t)dn.size() != k->cols) return fail(HUB_ERR_CUDA, "hub_set_symmetry: down basis size mismatch");
-  std::map<std::vector<std::pair<int, int>>, int> types;
-  std::vector<int32_t> tab_off;
-  std::vector<uint16_t> tab;
-  std::vector<std::vector<int>> cos_rep;   // per type: c_k
-  std::vector<uint32_t> cinfo, cbits;
-  std::vector<int32_t> csign, pos(dn.size(), -1);
-  for (uint32_t x : dn) {
-    const OrbitOf o = orbit_of(G, x);
-    if (o.least != x) continue;
-    int type;
-    const auto ti = types.find(o.stab);
-    if (ti != types.end()) {
-      type = ti->second;
-    } else {
-      type = (int)cos_rep.size();
-      if (type > 255) return fail(HUB_ERR_ARG, "hub_set_symmetry: too many stabiliser types");
-      types[o.stab] = type;
-      std::vector<int> coset_of(g, -1), hof(g, -1), reps_k;
-      std::vector<int> sig(g, 0);
-      for (const auto &hs : o.stab) sig[hs.first] = hs.second;
-      for (int e = 0; e < g; ++e) {
-        if (coset_of[e] >= 0) continue;
-        const int kk = (int)reps_k.size();
-        reps_k.push_back(e);
-        for (const auto &hs : o.stab) {
-          const int p = G.mul[(size_t)e * g + hs.first];
-          coset_of[p] = kk;
-          hof[p] = hs.first;
-        }
-      }
-      const int nb = (int)reps_k.size();
-      tab_off.push_back((int32_t)tab.size());
-      tab_off.push_back(nb);
-      for (int e = 0; e < g; ++e)
-        for (int kk = 0; kk < nb; ++kk) {
-          const int p = G.mul[(size_t)reps_k[kk] * g + e];
-          tab.push_back((uint16_t)(coset_of[p] | (sig[hof[p]] < 0 ? 0x8000 : 0)));
-        }
-      cos_rep.push_back(reps_k);
-    }
-    const std::vector<int> &ck = cos_rep[type];
-    for (size_t kk = 0; kk < ck.size(); ++kk) {
-      int s;
-      const uint32_t d = act(G, ck[kk], x, &s);
-      const size_t r = (size_t)(std::lower_bound(dn.begin(), dn.end(), d) - dn.begin());
-      if (r >= dn.size() || dn[r] != d || pos[r] >= 0)
-        return fail(HUB_ERR_CUDA, "hub_set_symmetry: column order inconsistent");
-      pos[r] = (int32_t)cbits.size();
-      cinfo.push_back((uint32_t)kk | ((uint32_t)type << 8));
-      cbits.push_back(d);
-      csign.push_back(s);
-    }
-  }
-  if ((int64_t)cbits.size() != k->cols || std::find(pos.begin(), pos.end(), -1) != pos.end())
-    return fail(HUB_ERR_CUDA, "hub_set_symmetry: column order incomplete");
+  Columns C;
+  std::string cerr;
+  if (build_columns(G, dn, &C, &cerr)) return fail(HUB_ERR_ARG, "hub_set_symmetry: " + cerr);
+  const std::vector<uint32_t> &cinfo = C.cinfo, &cbits = C.cbits;
+  const std::vector<int32_t> &csign = C.csign, &pos = C.pos, &tab_off = C.tab_off;
+  const std::vector<uint16_t> &tab = C.tab;
   k->col_bits_h = cbits;
   k->col_sign_h = csign;
 
@@ -844,7 +690,8 @@ static int set_translations(hub_t h, int n_gen, const int32_t *perms, const int3
   }
   if ((rc = check_invariant(h, n_gen, perms))) return rc;
   Group G;
-  if ((rc = make_group(M, n_gen, perms, chars, &G))) return rc;
+  std::string err;
+  if (make_group(M, n_gen, perms, chars, &G, &err)) return fail(HUB_ERR_ARG, std::string(who) + ": " + err);
   k0_release(h);
   release_vectors(h);
   rc = k0_build(h, G);

@@ -154,3 +154,16 @@ def test_plain_c_caller(libpath, tmp_path):
     assert r.returncode == 0, r.stderr
     r = subprocess.run([exe], capture_output=True, text=True)
     assert r.returncode == 0, r.stdout + r.stderr
+
+
+def test_group_construction_host_checks(tmp_path):
+    """tests/cpp_group_check.cpp (g++, csrc/hub_group.h): the momentum-sector group closure and
+    refusals, the action on spin strings as a representation with fermion signs, orbits and
+    stabilisers, and every move-table entry against the action."""
+    exe = str(tmp_path / "cpp_group_check")
+    r = subprocess.run(["g++", "-std=c++17", "-O1", "-Wall", "-Werror", "-I",
+                        os.path.join(ROOT, "paper_1307_7542_gb300", "csrc"),
+                        os.path.join(ROOT, "tests", "cpp_group_check.cpp"), "-o", exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+    r = subprocess.run([exe], capture_output=True, text=True)
+    assert r.returncode == 0, r.stdout + r.stderr
