@@ -417,3 +417,27 @@ def test_lanczos_spectrum_matches_arpack():
     ref = _distinct(w)[:5]
     got = O.lanczos_spectrum(m, B, W.normal(2, B.size), maxit=400, n_eig=5)
     assert np.max(np.abs(got - ref)) < 1e-9 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("M,nu,nd", [(6, 3, 3), (6, 4, 5), (7, 5, 4), (5, 1, 4), (6, 6, 2)])
+def test_diagonal_by_site_lists(M, nu, nd):
+    """Sec. III.B and Algorithm II's route to the diagonal: per-site U_i counted over the list of
+    sites occupied by both spins (site lists, no bit operations), plus eps_i times the
+    occupations; when N_up + N_dn > M every state has at least N_up + N_dn - M doubly occupied
+    sites, the baseline of Algorithm II, and the excess equals the sites empty for both spins."""
+    rng = np.random.default_rng(M * 10 + nu)
+    U = rng.uniform(1.0, 5.0, M)
+    eps = rng.uniform(-0.5, 0.5, M)
+    m = O.Model(M, W.ring_bonds(M), 1.0, U, eps)
+    B = O.basis(M, nu, nd)
+    d = O.diagonal(m, B)
+    up, dn = O.spin_parts(M, B)
+    for k in range(B.shape[0]):
+        su = [i for i in range(M) if (int(up[k]) >> i) & 1]
+        sd = [i for i in range(M) if (int(dn[k]) >> i) & 1]
+        both = [i for i in su if i in sd]
+        ref = sum(U[i] for i in both) + sum(eps[i] for i in su) + sum(eps[i] for i in sd)
+        assert abs(d[k] - ref) < 1e-13
+        if nu + nd > M:
+            empty = [i for i in range(M) if i not in su and i not in sd]
+            assert len(both) == nu + nd - M + len(empty)
