@@ -48,13 +48,14 @@ extern "C" {
 #define HUB_ERR_CUDA (-3)         /* a CUDA runtime call failed                             */
 #define HUB_ERR_NOCONV (-4)       /* Lanczos hit maxit before |dE0| < tol (E0 still set)    */
 #define HUB_ERR_STATE (-5)        /* call order: e.g. hub_apply before hub_hopping           */
-#define HUB_ERR_TIMEOUT (-6)      /* a device-side bounded wait gave up (batched solver)    */
+#define HUB_ERR_TIMEOUT (-6)      /* a device-side bounded wait gave up                      */
 
 #define HUB_SPIN_UP 0
 #define HUB_SPIN_DN 1
 
-#define HUB_MODE_AUTO 0   /* fast double-float path when t and U are uniform, else FP64;
-                             in a momentum sector: integer-pipe sums when t is uniform   */
+#define HUB_MODE_AUTO 0   /* fast double-float path when t and U are uniform (window and
+                             bound: see hub_apply), else FP64; in a momentum sector:
+                             integer-pipe sums when t is uniform                         */
 #define HUB_MODE_FP64 1   /* always the native FP64 kernels                              */
 
 #define HUB_SYM_NONE 0    /* the full sector (N_up, N_dn)                              */
@@ -110,13 +111,25 @@ int hub_get_csr(hub_t h, int spin, int32_t *rowptr_host, int32_t *cols_host, dou
  * y = H x (Sec. IV.A, Eq. 11, applied matrix-free as X H_up^T + H_dn X + diag o X;
  * Sec. III.B for the diagonal, evaluated from popcount(I_up & I_dn) on the fly).
  * x_dev and y_dev must not overlap.  Requires hub_hopping and hub_set_U.
+ *
+ * Accuracy: every entry satisfies |y_n - (Hx)_n| <= 1e-13 (|H||x|)_n, |H| the entrywise
+ * absolute matrix.  The native FP64 kernel (HUB_MODE_FP64; non-uniform t or U) does
+ * this with FP64 multiply-adds.  In HUB_MODE_AUTO with uniform t and U the product runs
+ * in double-float arithmetic (pairs of FP32 numbers, 48 significant bits; compensated
+ * sums) with a worst-case error of about 12 * 2^-48 (|H||x|)_n = 4.3e-14 (|H||x|)_n.
+ * That bound needs a window, checked on the device for every call: the largest |x_n| in
+ * [2^-823, 2^877], every nonzero |x_n| at least 2^-80 times the largest (no FP64
+ * subnormals, infinities or NaN), and |t|, |U| and every |eps_i| either 0 or in
+ * [2^-16, 2^16] (t != 0).  A vector or model outside it is multiplied by the FP64 kernel
+ * instead, on the same stream and with no host synchronisation, so every call meets the
+ * bound.
  */
 int hub_apply(hub_t h, const double *x_dev, double *y_dev, void *stream);
 
 /*
  * The same product on host buffers: copies x_host to the device, applies H, copies the
  * result to y_host, and returns when y_host is complete.  Uses two device vectors the
- * handle allocates on first use.
+ * handle allocates on first use.  Accuracy, window and routing as for hub_apply.
  */
 int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream);
 
@@ -130,6 +143,11 @@ int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream);
  * HUB_ERR_NOCONV, *E0 still set).  If psi_dev != NULL the recurrence is run a second
  * time to form the normalised ground-state vector.  Blocks until done; *E0 and *iters
  * are host pointers (iters may be NULL).  Workspace: three device vectors.
+ * In HUB_MODE_AUTO with uniform t and U (and t, U, eps in hub_apply's parameter range)
+ * the Lanczos vectors are held in double-float form: x0 is scaled by a power of two so
+ * that its largest entry lies in [1, 2), and components smaller than about 2^-126 times
+ * the largest entry of a Lanczos vector are flushed.  Neither changes E0 at the 1e-10
+ * level; HUB_MODE_FP64 keeps every vector in FP64.
  */
 int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, double *E0,
                        double *psi_dev, int *iters, void *stream);
@@ -253,9 +271,10 @@ int hub_grad(hub_t h, const double *psi_dev, double *dE_dt_host, double *dE_dU_h
  * The caller still owns psi and the host output arrays; the handle's own tables were
  * allocated when it was built.
  *   - Limit: n_bonds + 2*M <= 160; larger models return HUB_ERR_ARG (use hub_grad).
- *   - The handle's device must be the current device.  The first call on a device looks
- *     up the array's device address (cudaGetSymbolAddress); make that first call before
- *     any stream capture.
+ *   - The handle's device must be the current device.  Every call looks up the array's
+ *     device address there (cudaGetSymbolAddress); the first call on a device may also
+ *     load the library's device code on it, which places the array.  Make that first call
+ *     before any stream capture.
  *   - All calls share the one array: calls that overlap on the GPU (two streams, two
  *     threads, two handles) race and give wrong results.  Every value a call reads from
  *     the array is written earlier in the same call, so nothing needs clearing.
@@ -346,8 +365,10 @@ int hub_k_project(hub_t h, const double *x_dev, double *y_dev, void *stream);
  * Arithmetic path (no counterpart in the paper).  HUB_MODE_AUTO (default) runs products
  * with uniform t and U on the fast path: vectors held as pairs of FP32 numbers (about 48
  * significant bits), sums by error-free transformations on the FP32 pipe, because the
- * FP64 unit of this GPU issues about 1/70 of the FP32 rate.  Inputs and outputs of every
- * entry point stay FP64.  HUB_MODE_FP64 forces the native FP64 kernels.
+ * FP64 unit of this GPU issues about 1/70 of the FP32 rate.  Its per-entry error is at
+ * most about 4.3e-14 (|H||x|)_n inside the window stated at hub_apply, and inputs outside
+ * the window go to the FP64 kernel, so both modes meet 1e-13 (|H||x|)_n.  Inputs and
+ * outputs of every entry point stay FP64.  HUB_MODE_FP64 forces the native FP64 kernels.
  */
 int hub_set_mode(hub_t h, int mode);
 
@@ -357,6 +378,16 @@ int hub_set_mode(hub_t h, int mode);
  * HUB_ERR_CUDA on a CUDA error, else HUB_OK.  hub_lanczos_ground checks this itself.
  */
 int hub_check(hub_t h);
+
+/*
+ * Test hook (no counterpart in the paper; off by default).  While enabled, every CTA of the
+ * fast path's first pass, once the bulk copies of its first row pair have landed, takes the
+ * exit a given-up bounded wait takes: it sets the handle's device error flag and returns
+ * without computing.  No wait runs out and no copy is left in flight; the hook exists so
+ * that the error path (hub_check and hub_lanczos_ground returning HUB_ERR_TIMEOUT) can be
+ * exercised.  Results computed while it is enabled are meaningless.
+ */
+int hub_test_fail_waits(hub_t h, int enable);
 
 /*
  * Measurement hooks (no counterpart in the paper).  hub_profile(h, 1) resets the counters

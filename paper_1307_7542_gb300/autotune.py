@@ -3,11 +3,14 @@
 The fast apply (csrc/hub_fast.cu) and the batched solver (csrc/hub_batch.cu) take their launch
 shapes from compile-time knobs:
 
-* ``HUB_DN_LANE_COLS`` -- columns a pass-2 lane owns (2: 64-bit loads, 4 or 8: 128-bit loads);
-* ``HUB_DN_BATCH``     -- strip rows whose loads pass 2 issues together;
+* ``HUB_DN_LANE_COLS`` -- columns a pass-2 lane owns (2: 64-bit loads, 4: 128-bit loads);
+* ``HUB_DN_BATCH``     -- strip rows whose loads pass 2 issues together (2 or 4);
 * ``HUB_DN_MINB``      -- resident pass-2 CTAs per SM the register allocation aims for;
 * ``HUB_BANK_CAP``     -- distinct columns per shared-memory bank and step in the pass-1
   schedule (k > 0 fixed, 0 adaptive, -k adaptive capped at k);
+* ``HUB_FUSED_UPDATE`` -- 1: the Lanczos update r_j = w - c r_{j-1} is formed by pass 1 while
+  it stages the rows; 0: a separate vector pass before pass 1;
+* ``HUB_UPD_Q``        -- column quads per thread whose loads the fused update issues together;
 * ``HUB_BATCH_THREADS`` -- threads per CTA of the batched persistent solver.
 
 For each candidate setting this module builds one copy of the library, times on the GPU what
@@ -34,14 +37,16 @@ TUNE_DIR = os.path.join(PKG, "_build", "tune")
 TUNED = os.path.join(PKG, "tuned.json")
 
 APPLY_SPACE = {
-    "HUB_DN_LANE_COLS": [2, 4, 8],
-    "HUB_DN_BATCH": [1, 2, 3],
-    "HUB_DN_MINB": [4, 5, 6],
+    "HUB_DN_LANE_COLS": [2, 4],
+    "HUB_DN_BATCH": [2, 4],
+    "HUB_DN_MINB": [3, 4, 5, 6],
     "HUB_BANK_CAP": [2, 3, 0, -2],
+    "HUB_FUSED_UPDATE": [1, 0],
+    "HUB_UPD_Q": [1, 2],
 }
 BATCH_SPACE = {"HUB_BATCH_THREADS": [256, 512, 1024]}
-DEFAULTS = {"HUB_DN_LANE_COLS": 4, "HUB_DN_BATCH": 2, "HUB_DN_MINB": 5, "HUB_BANK_CAP": 2,
-            "HUB_BATCH_THREADS": 512}
+DEFAULTS = {"HUB_DN_LANE_COLS": 4, "HUB_DN_BATCH": 2, "HUB_DN_MINB": 4, "HUB_BANK_CAP": 2,
+            "HUB_FUSED_UPDATE": 1, "HUB_UPD_Q": 1, "HUB_BATCH_THREADS": 256}
 MARGIN = 0.01
 
 

@@ -28,9 +28,13 @@ __device__ __forceinline__ double diag_of(const Ham &H, uint32_t Iu, uint32_t Id
   return v;
 }
 
+// gate: null, or a device flag; the kernel does nothing while gate[0] is 0 (the fast path
+// passes its out-of-window flag, so that this kernel multiplies exactly the vectors the
+// double-float kernels cannot).
 template <bool kStage>
 __global__ void __launch_bounds__(512) k_apply_f64(const Ham H, const double *__restrict__ x,
-                                                   double *__restrict__ y) {
+                                                   double *__restrict__ y, const int *__restrict__ gate) {
+  if (gate && gate[0] == 0) return;
   extern __shared__ double xs[];
   const int64_t nu = H.n_up, nd = H.n_dn;
   for (int64_t d = blockIdx.x; d < nd; d += gridDim.x) {
@@ -96,6 +100,11 @@ static int apply_kernels(hub_ctx *h, const double *x, double *y, cudaStream_t s)
   if (H.n_up == 0 || H.n_dn == 0) return HUB_OK;
   if (h->k0) return k0_apply(h, x, y, s);
   if (use_fast(h)) return fast_apply_f64(h, x, y, s);
+  return f64_apply(h, x, y, nullptr, s);
+}
+
+int f64_apply(hub_ctx *h, const double *x, double *y, const int *gate, cudaStream_t s) {
+  const Ham H = h->view();
   count_launch(h);
   const size_t smem = stage_bytes(H);
   const int threads = H.n_up >= 512 ? 512 : (H.n_up >= 128 ? 256 : 64);
@@ -104,9 +113,9 @@ static int apply_kernels(hub_ctx *h, const double *x, double *y, cudaStream_t s)
   if (grid > cap) grid = cap;
   if (smem <= 200 * 1024) {
     HUB_CUDA(cudaFuncSetAttribute(k_apply_f64<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
-    k_apply_f64<true><<<(int)grid, threads, smem, s>>>(H, x, y);
+    k_apply_f64<true><<<(int)grid, threads, smem, s>>>(H, x, y, gate);
   } else {
-    k_apply_f64<false><<<(int)grid, threads, 0, s>>>(H, x, y);
+    k_apply_f64<false><<<(int)grid, threads, 0, s>>>(H, x, y, gate);
   }
   HUB_LAUNCH_CHECK();
   return HUB_OK;
@@ -186,6 +195,12 @@ extern "C" int hub_profile_read(hub_t h, int kind, double *ms, int64_t *launches
 extern "C" int hub_set_mode(hub_t h, int mode) {
   if (!h || (mode != HUB_MODE_AUTO && mode != HUB_MODE_FP64)) return fail(HUB_ERR_ARG, "hub_set_mode: bad argument");
   h->mode = mode;
+  return HUB_OK;
+}
+
+extern "C" int hub_test_fail_waits(hub_t h, int enable) {
+  if (!h) return fail(HUB_ERR_ARG, "hub_test_fail_waits: NULL handle");
+  h->fail_waits = enable != 0;
   return HUB_OK;
 }
 

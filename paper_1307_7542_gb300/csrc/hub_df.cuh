@@ -30,7 +30,8 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 }
 
 // Accumulator: the exact sum of the high parts is kept as H plus the rounding errors,
-// which go to L together with the low parts.
+// which go to L together with the low parts (used for the long dot products of Lanczos;
+// the hopping sums of the product use the compensated DfSum4 below).
 struct DfAcc {
   float H, L;
 };
@@ -110,6 +111,9 @@ __device__ __forceinline__ f2x sub2(f2x a, f2x b) {
 
 __device__ __forceinline__ f2x bcast2(float a) { return pk2(a, a); }
 
+// sign bits of both lanes (XOR negates both exactly)
+constexpr f2x kSign2 = 0x8000000080000000ull;
+
 struct DfAcc2 {
   f2x H, L;   // high parts (exact running sums) and low parts + TwoSum errors, per lane
 };
@@ -131,6 +135,110 @@ __device__ __forceinline__ void acc2_sub(DfAcc2 &a, f2x vh, f2x vl) {
   const f2x e = sub2(sub2(a.H, sub2(s, bb)), add2(vh, bb));
   a.H = s;
   a.L = add2(sub2(a.L, vl), e);
+}
+
+// ---------------------------------------------------------------------------------------
+// Compensated paired sum for the hopping terms of the product (sums of +-v, v = vh + vl a
+// normalised double-float, |vl| <= u |vh|, u = 2^-24).  Per term:
+//   (H, e) = TwoSum(H, vh)     H: the FP32 running sum of the high parts, e its exact error
+//   (L, f) = TwoSum(L, e)      the errors summed exactly as well ...
+//   C += f                     ... up to the plain sum of their own errors
+//   V[j] += vl                 low parts, plainly, in four accumulators used in turn
+// so that H + L + C_exact + sum_j V_j_exact is the exact sum.  Error over F terms (A =
+// sum |v|): each e is at most u A, so |L| <= F u A and |f| <= F u^2 A, and C's roundings
+// add at most F^3 u^3 A / 2 (1e-3 u^2 A for F = 32); accumulator V[j] adds n_j - 1
+// roundings of at most u sum |vl| over its n_j terms, i.e. at most (max_j n_j - 1) u^2 A.
+// The closing steps (V into L by TwoSum, then H + L + C) round once more, by at most
+// u^2 |H + L| + u |C|.  The plain form (e and vl summed in one FP32 word) can reach
+// F^2 u^2 A, far above the product's tolerance (1e-13 A ~ 28 u^2 A); this one costs 14
+// packed instructions per term against 8.
+// ---------------------------------------------------------------------------------------
+struct DfSum4 {
+  f2x H, L, C, V[4];
+};
+
+// (s, err) = TwoSum(a, b) per lane
+__device__ __forceinline__ void two_sum2(f2x a, f2x b, f2x &s, f2x &err) {
+  s = add2(a, b);
+  const f2x bb = sub2(s, a);
+  err = add2(sub2(a, sub2(s, bb)), sub2(b, bb));
+}
+// (s, err) = TwoSum(a, -b) per lane, written with subtractions
+__device__ __forceinline__ void two_diff2(f2x a, f2x b, f2x &s, f2x &err) {
+  s = sub2(a, b);
+  const f2x bb = sub2(s, a);
+  err = sub2(sub2(a, sub2(s, bb)), add2(b, bb));
+}
+
+// a += v, low part into V[j] (j a compile-time constant after unrolling, so that V stays
+// in registers)
+__device__ __forceinline__ void sum4_add(DfSum4 &a, f2x vh, f2x vl, int j) {
+  f2x e, f;
+  two_sum2(a.H, vh, a.H, e);
+  two_sum2(a.L, e, a.L, f);
+  a.C = add2(a.C, f);
+  a.V[j & 3] = add2(a.V[j & 3], vl);
+}
+// a -= v (negation is exact: the same steps on -v)
+__device__ __forceinline__ void sum4_sub(DfSum4 &a, f2x vh, f2x vl, int j) {
+  f2x e, f;
+  two_diff2(a.H, vh, a.H, e);
+  two_sum2(a.L, e, a.L, f);
+  a.C = add2(a.C, f);
+  a.V[j & 3] = sub2(a.V[j & 3], vl);
+}
+// Normalised (hi, lo) per lane of the sum.
+__device__ __forceinline__ void sum4_norm(const DfSum4 &a, f2x &h, f2x &l) {
+  f2x L = a.L, C = a.C, f;
+#pragma unroll
+  for (int j = 0; j < 4; ++j) {
+    two_sum2(L, a.V[j], L, f);
+    C = add2(C, f);
+  }
+  f2x s, e;
+  two_sum2(a.H, L, s, e);
+  two_sum2(s, add2(e, C), h, l);
+}
+
+// The same sum with the low parts of two terms added together first (one rounding of at
+// most u |vl_a + vl_b|) and the pair sums going to two accumulators in turn: per pair the
+// same instruction count as DfSum4, three registers pairs fewer.  A row of F_add + F_sub
+// terms puts at most ceil(F_add/4) + ceil(F_sub/4) pair sums (or single last terms) into
+// one accumulator.
+struct DfSumP {
+  f2x H, L, C, V[2];
+};
+
+__device__ __forceinline__ void sump_hi(DfSumP &a, f2x vh, bool add) {
+  f2x e, f;
+  if (add)
+    two_sum2(a.H, vh, a.H, e);
+  else
+    two_diff2(a.H, vh, a.H, e);
+  two_sum2(a.L, e, a.L, f);
+  a.C = add2(a.C, f);
+}
+// a += va + vb (add) or a -= va + vb, the pair's low parts into V[j]
+__device__ __forceinline__ void sump_pair(DfSumP &a, f2x vha, f2x vla, f2x vhb, f2x vlb, bool add, int j) {
+  sump_hi(a, vha, add);
+  sump_hi(a, vhb, add);
+  const f2x v = add2(vla, vlb);
+  a.V[j & 1] = add ? add2(a.V[j & 1], v) : sub2(a.V[j & 1], v);
+}
+__device__ __forceinline__ void sump_one(DfSumP &a, f2x vh, f2x vl, bool add, int j) {
+  sump_hi(a, vh, add);
+  a.V[j & 1] = add ? add2(a.V[j & 1], vl) : sub2(a.V[j & 1], vl);
+}
+__device__ __forceinline__ void sump_norm(const DfSumP &a, f2x &h, f2x &l) {
+  f2x L = a.L, C = a.C, f;
+#pragma unroll
+  for (int j = 0; j < 2; ++j) {
+    two_sum2(L, a.V[j], L, f);
+    C = add2(C, f);
+  }
+  f2x s, e;
+  two_sum2(a.H, L, s, e);
+  two_sum2(s, add2(e, C), h, l);
 }
 
 // Normalised (hi, lo) per lane of a paired accumulator.

@@ -112,11 +112,10 @@ struct FastView {
   uint32_t idle_word;                // a column word whose entries are all idle steps
   const int32_t *slot_row;           // spin-up rank held by slot k
   const uint32_t *basis_up_slot;     // spin-up strings in slot order
-  const float2 *eps_up, *eps_dn;     // per-state site energies (double-float; up: slot order) or null
-  float2 t;                          // uniform hopping t (double-float)
-  int t_is_one;
-  float2 Utab[32];                   // U * k for k = popcount(I_up & I_dn)
+  int t_neg;                         // the kernels apply H / |t|: hopping sign(t), diagonal U k / |t|
+  float2 Utab[32];                   // (U / |t|) k for k = popcount(I_up & I_dn)
   int *err;                          // device error flag (bounded waits)
+  int fail_waits;                    // test hook: take the given-up-wait exit once the copies landed
 };
 
 template <typename Col>
@@ -142,60 +141,131 @@ __global__ void k_split_csr(int64_t n, const int32_t *__restrict__ rp, const uin
   }
 }
 
-// basis and site energies of the spin-up states in slot order
+// basis of the spin-up states in slot order
 __global__ void k_to_slots(int64_t n, const int32_t *__restrict__ slot_row, const uint32_t *__restrict__ basis,
-                           uint32_t *__restrict__ basis_slot, const float2 *__restrict__ eps, float2 *__restrict__ eps_slot) {
-  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+                           uint32_t *__restrict__ basis_slot) {
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x)
     basis_slot[k] = basis[slot_row[k]];
-    if (eps) eps_slot[k] = eps[slot_row[k]];
-  }
-}
-
-__global__ void k_eps_df(int64_t n, const double *__restrict__ e, float2 *__restrict__ out) {
-  for (int64_t r = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; r < n; r += (int64_t)gridDim.x * blockDim.x)
-    out[r] = f64_to_df(e[r], 0);
 }
 
 // ---------------------------------------------------------------------------------------
 // Conversions between the ABI's FP64 layout (row length n_up, rank order) and the planar
 // double-float layout (slot order), with a power-of-two scale.
 // ---------------------------------------------------------------------------------------
-// partials[block] = max biased FP64 exponent of |x| over the block's elements
-__global__ void k_max_exp(int64_t D, const double *__restrict__ x, int *__restrict__ partials) {
-  int m = 0;
+// The fast path holds a vector as double-floats scaled by 2^-shift, max |x| 2^-shift in
+// [1, 2).  Its per-entry error bound (about 20 u^2 (|H||x|)_n, u = 2^-24) needs every
+// term, product and sum it forms to keep 48 bits, i.e. FP32 low parts above the FP32
+// subnormal range: with nonzero |x| 2^-shift >= 2^-80 and a diagonal coefficient U / |t|
+// of 0 or in [2^-16, 2^16] (fast_eligible), every nonzero product is at least 2^-96, its
+// low part at least 2^-120.  The scaled results must also map back into the FP64 range.
+// The window:
+// the largest biased FP64 exponent in [kExpLo, kExpHi] and every nonzero entry's exponent
+// at most kExpSpan below it; FP64 subnormals, infinities and NaN are outside.  A vector
+// outside the window is multiplied by the FP64 kernel instead.
+constexpr int kExpSpan = 80, kExpLo = 200, kExpHi = 1900;
+
+// partials[block] = largest biased FP64 exponent of the block's elements (2047 for inf or
+// NaN), partials[nblk + block] = smallest biased exponent among its nonzero elements (0 for
+// an FP64 subnormal, 2048 if all are zero); nblk = gridDim.x
+__global__ void k_exp_range(int64_t D, const double *__restrict__ x, int *__restrict__ partials) {
+  int m = 0, n = 2048;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < D; k += (int64_t)gridDim.x * blockDim.x) {
-    const uint32_t hi = (uint32_t)((uint64_t)__double_as_longlong(x[k]) >> 32);
-    m = max(m, (int)((hi >> 20) & 0x7ffu));
+    const uint64_t b = (uint64_t)__double_as_longlong(x[k]);
+    const int e = (int)((b >> 52) & 0x7ffu);
+    m = max(m, e);
+    if (b << 1) n = min(n, e);
   }
-  for (int o = 16; o > 0; o >>= 1) m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
-  __shared__ int ws[32];
-  if ((threadIdx.x & 31) == 0) ws[threadIdx.x >> 5] = m;
+  for (int o = 16; o > 0; o >>= 1) {
+    m = max(m, __shfl_xor_sync(0xffffffffu, m, o));
+    n = min(n, __shfl_xor_sync(0xffffffffu, n, o));
+  }
+  __shared__ int wm[32], wn[32];
+  if ((threadIdx.x & 31) == 0) {
+    wm[threadIdx.x >> 5] = m;
+    wn[threadIdx.x >> 5] = n;
+  }
   __syncthreads();
   if (threadIdx.x < 32) {
-    int v = threadIdx.x < (blockDim.x >> 5) ? ws[threadIdx.x] : 0;
-    for (int o = 16; o > 0; o >>= 1) v = max(v, __shfl_xor_sync(0xffffffffu, v, o));
-    if (threadIdx.x == 0) partials[blockIdx.x] = v;
+    const bool in = threadIdx.x < (blockDim.x >> 5);
+    int a = in ? wm[threadIdx.x] : 0, c = in ? wn[threadIdx.x] : 2048;
+    for (int o = 16; o > 0; o >>= 1) {
+      a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+      c = min(c, __shfl_xor_sync(0xffffffffu, c, o));
+    }
+    if (threadIdx.x == 0) {
+      partials[blockIdx.x] = a;
+      partials[gridDim.x + blockIdx.x] = c;
+    }
   }
 }
 
-// shift such that max |x| 2^-shift lies in [1, 2) (0 for a zero vector); block-uniform call
-__device__ __forceinline__ int block_shift(const int *__restrict__ emax, int nblk) {
-  __shared__ int s_shift;
-  if (threadIdx.x == 0) {
-    int m = 0;
-    for (int k = 0; k < nblk; ++k) m = max(m, emax[k]);
-    s_shift = m == 0 ? 0 : m - 1023;
+// Range of partials[0 .. nblk) (stride: nblk to the minima, as k_exp_range writes them;
+// n_sets such sets back to back).
+__device__ __forceinline__ void range_of(const int *__restrict__ p, int nblk, int n_sets, int &emax, int &emin) {
+  int a = 0, c = 2048;
+  for (int s = 0; s < n_sets; ++s)
+    for (int k = threadIdx.x; k < nblk; k += blockDim.x) {
+      a = max(a, p[2 * s * nblk + k]);
+      c = min(c, p[(2 * s + 1) * nblk + k]);
+    }
+  for (int o = 16; o > 0; o >>= 1) {
+    a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
+    c = min(c, __shfl_xor_sync(0xffffffffu, c, o));
+  }
+  __shared__ int wa[32], wc[32];
+  if ((threadIdx.x & 31) == 0) {
+    wa[threadIdx.x >> 5] = a;
+    wc[threadIdx.x >> 5] = c;
   }
   __syncthreads();
-  return s_shift;
+  if (threadIdx.x == 0) {
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) {
+      a = max(a, wa[k]);
+      c = min(c, wc[k]);
+    }
+    emax = a;
+    emin = c;
+  }
 }
 
-// out (planar, slot order) = 2^-shift x (FP64, rank order) for rows r0 .. r1 - 1, shift from
-// emax (0 when emax is null); one row per block and step
+__device__ __forceinline__ bool out_of_window(int emax, int emin) {
+  return emax != 0 && (emax < kExpLo || emax > kExpHi || emin < emax - kExpSpan);
+}
+
+// One block: scale[0] = shift (max |x| 2^-shift in [1, 2); 0 for a zero vector), scale[1] =
+// 1 if the vector lies outside the fast path's window (see kExpSpan).
+__global__ void k_scale(const int *__restrict__ partials, int nblk, int *__restrict__ scale) {
+  int emax = 0, emin = 2048;
+  range_of(partials, nblk, 1, emax, emin);
+  if (threadIdx.x == 0) {
+    scale[0] = emax == 0 ? 0 : emax - 1023;
+    scale[1] = out_of_window(emax, emin) ? 1 : 0;
+  }
+}
+
+// Host-buffer product, after all chunks: n_sets exponent partial sets (one per chunk, the
+// first one gave the scale used so far).  scale[2] = shift of the whole vector, scale[3] =
+// its window flag; flag[0] = 2 if the whole vector lies outside the window, 1 if its
+// largest exponent exceeds the first chunk's (convert again with scale[2]), else 0.
+__global__ void k_scale_all(const int *__restrict__ partials, int nblk, int n_sets, int *__restrict__ scale,
+                            int *__restrict__ flag) {
+  int emax = 0, emin = 2048;
+  range_of(partials, nblk, n_sets, emax, emin);
+  if (threadIdx.x == 0) {
+    const int shift = emax == 0 ? 0 : emax - 1023;
+    const bool out = out_of_window(emax, emin);
+    scale[2] = shift;
+    scale[3] = out ? 1 : 0;
+    flag[0] = out ? 2 : (shift != scale[0] ? 1 : 0);
+  }
+}
+
+// out (planar, slot order) = 2^-shift x (FP64, rank order) for rows r0 .. r1 - 1, shift =
+// scale[0] (0 when scale is null); one row per block and step
 __global__ void k_f64_to_df(int64_t r0, int64_t r1, int64_t n_up, int64_t ld, const double *__restrict__ x,
-                            const int *__restrict__ emax, int nblk, const int32_t *__restrict__ slot_row,
+                            const int *__restrict__ scale, const int32_t *__restrict__ slot_row,
                             float *__restrict__ out) {
-  const int shift = emax ? block_shift(emax, nblk) : 0;
+  const int shift = scale ? scale[0] : 0;
   for (int64_t d = r0 + blockIdx.x; d < r1; d += gridDim.x) {
     float *__restrict__ row = out + d * 2 * ld;
     const double *__restrict__ xr = x + d * n_up;
@@ -207,47 +277,22 @@ __global__ void k_f64_to_df(int64_t r0, int64_t r1, int64_t n_up, int64_t ld, co
   }
 }
 
-// y[d][u] (FP64, rank order) = 2^shift * v[d][slot_of[u]] (planar double-float, slot
-// order) for rows r0 .. r1 - 1, one row per block and step so that the gathers of a row are
-// served from L1.
+// y[d][u] (FP64, rank order) = tabs 2^shift v[d][slot_of[u]] (planar double-float, slot
+// order) for rows r0 .. r1 - 1, shift = scale[0]; one row per block and step so that the
+// gathers of a row are served from L1.  Nothing is written when scale[1] is set (the FP64
+// kernel writes y instead).  tabs = |t|: the kernels applied H / |t|.
 __global__ void k_unpermute(int64_t r0, int64_t r1, int64_t n_up, int64_t ld, const float *__restrict__ v,
-                            const int32_t *__restrict__ slot_of, const int *__restrict__ emax, int nblk,
+                            const int32_t *__restrict__ slot_of, const int *__restrict__ scale, double tabs,
                             double *__restrict__ y) {
-  const int shift = block_shift(emax, nblk);
+  if (scale[1]) return;
+  const int shift = scale[0];
   for (int64_t d = r0 + blockIdx.x; d < r1; d += gridDim.x) {
     const float *__restrict__ row = v + d * 2 * ld;
     for (int64_t u = threadIdx.x; u < n_up; u += blockDim.x) {
       const int32_t s = slot_of[u];
-      y[d * n_up + u] = df_to_f64(make_float2(row[s], row[ld + s]), shift);
+      const double val = df_to_f64(make_float2(row[s], row[ld + s]), shift);
+      y[d * n_up + u] = tabs == 1.0 ? val : val * tabs;
     }
-  }
-}
-
-// flag = 1 if the largest exponent among emax[0 .. n_all) exceeds that of emax[0 .. n_first)
-__global__ void k_shift_check(const int *__restrict__ emax, int n_all, int n_first, int *__restrict__ flag) {
-  int a = 0, f = 0;
-  for (int k = threadIdx.x; k < n_all; k += blockDim.x) {
-    a = max(a, emax[k]);
-    if (k < n_first) f = max(f, emax[k]);
-  }
-  for (int o = 16; o > 0; o >>= 1) {
-    a = max(a, __shfl_xor_sync(0xffffffffu, a, o));
-    f = max(f, __shfl_xor_sync(0xffffffffu, f, o));
-  }
-  __shared__ int wa[32], wf[32];
-  if ((threadIdx.x & 31) == 0) {
-    wa[threadIdx.x >> 5] = a;
-    wf[threadIdx.x >> 5] = f;
-  }
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    for (int k = 1; k < (int)(blockDim.x >> 5); ++k) {
-      a = max(a, wa[k]);
-      f = max(f, wf[k]);
-    }
-    a = max(a, wa[0]);
-    f = max(f, wf[0]);
-    flag[0] = a > f ? 1 : 0;
   }
 }
 
@@ -268,9 +313,34 @@ __device__ __forceinline__ void prefetch_l2(const void *p, uint32_t bytes) {
 // and serve as the column of idle schedule steps (adding zero is exact).
 constexpr int kUpPlane = 14080;
 
-template <typename Col, bool kEps>
-__global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *__restrict__ x,
-                                                float *__restrict__ z, int64_t p_begin, int64_t p_end) {
+// FP64 value of lane a + lane b of a packed (hi, lo) pair
+__device__ __forceinline__ double df2_lanes_to_f64(f2x h, f2x l) {
+  const float2 hh = upk2(h), ll = upk2(l);
+  return df_to_f64(make_float2(hh.x, ll.x), 0) + df_to_f64(make_float2(hh.y, ll.y), 0);
+}
+
+// The Lanczos recurrence fused into pass 1 (kUpd): the staged rows are those of w (the
+// previous step's pass-2 output); before the gathers each CTA forms r_j = w + c r_{j-1}
+// (c = -alpha_{j-1} / |r_{j-1}|, the update of Sec. IV's recurrence) in shared memory, writes
+// it back over w in HBM for pass 2 and the next steps, and accumulates |r_j|^2.
+#ifndef HUB_UPD_Q
+#define HUB_UPD_Q 1   // column quads per thread whose loads the fused update issues together
+#endif
+#ifndef HUB_FUSED_UPDATE
+#define HUB_FUSED_UPDATE 1   // 0: the Lanczos update as a separate vector pass before pass 1
+#endif
+constexpr int kUpdQ = HUB_UPD_Q;
+constexpr bool kFusedUpdate = HUB_FUSED_UPDATE != 0;
+
+struct UpdArgs {
+  const float *r_prev;               // r_{j-1} (planar rows)
+  const float2 *coef;                // coef[2] = c (double-float)
+  double *partials;                  // |r_j|^2 per CTA
+};
+
+template <typename Col, bool kUpd>
+__global__ void __launch_bounds__(1024, 1) k_up(const FastView F, float *x, float *__restrict__ z,
+                                                int64_t p_begin, int64_t p_end, UpdArgs U) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *xs = reinterpret_cast<float *>(smem_raw);
   __shared__ __align__(8) uint64_t bar;
@@ -280,6 +350,8 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
   const uint32_t pbytes = (uint32_t)(ld * sizeof(float));
   if (tid < 32) utab[tid] = F.Utab[tid];
   if (tid < 8) xs[(tid >> 1) * kUpPlane + ld + (tid & 1)] = 0.f;
+  __shared__ double wnorm[32];              // |r_j|^2 per warp, summed in a fixed order (kUpd)
+  if (kUpd && tid < 32) wnorm[tid] = 0.0;
   if (tid == 0) {
     mbar_init(&bar, 1);
     fence_mbar_init();
@@ -300,6 +372,10 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
       if (pn < p_end) {
         prefetch_l2(x + 2 * pn * 2 * ld, 2 * pbytes);
         if (2 * pn + 1 < F.n_dn) prefetch_l2(x + (2 * pn + 1) * 2 * ld, 2 * pbytes);
+        if (kUpd) {
+          prefetch_l2(U.r_prev + 2 * pn * 2 * ld, 2 * pbytes);
+          if (2 * pn + 1 < F.n_dn) prefetch_l2(U.r_prev + (2 * pn + 1) * 2 * ld, 2 * pbytes);
+        }
       }
     }
     if (!mbar_wait_bounded(&bar, phase)) {
@@ -307,13 +383,91 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
       mbar_wait_bounded(&bar, phase);      // give a late copy one more bounded chance to land
       return;
     }
-    phase ^= 1u;
-    const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
-    float2 e0 = make_float2(0.f, 0.f), e1 = e0;
-    if (kEps) {
-      e0 = F.eps_dn[d0];
-      e1 = F.eps_dn[d1];
+    if (F.fail_waits) {                    // test hook: the same exit, after the copies landed
+      if (tid == 0) atomicExch(F.err, 1);
+      return;
     }
+    phase ^= 1u;
+    if (kUpd) {
+      // r_j = w + c r_{j-1} for both rows, four columns per thread step: in shared memory,
+      // in HBM over w, and into |r_j|^2 (lane b counted only when the rows differ)
+      const float *pr0 = U.r_prev + d0 * 2 * ld, *pr1 = U.r_prev + d1 * 2 * ld;
+      float *x0 = x + d0 * 2 * ld, *x1 = x + d1 * 2 * ld;
+      const float2 cf = U.coef[2];
+      const f2x cph = bcast2(cf.x), cpl = bcast2(cf.y);
+      DfAcc2 nacc{0ull, 0ull};
+      // kUpdQ quads per thread and batch, their global loads issued before any arithmetic
+      const int64_t stride = 4 * (int64_t)blockDim.x;
+      for (int64_t q0 = 4 * (int64_t)tid; q0 < ld; q0 += kUpdQ * stride) {
+        float4 ph0[kUpdQ], pl0[kUpdQ], ph1[kUpdQ], pl1[kUpdQ];
+#pragma unroll
+        for (int i = 0; i < kUpdQ; ++i) {
+          const int64_t q = q0 + i * stride;
+          if (q < ld) {
+            ph0[i] = *reinterpret_cast<const float4 *>(pr0 + q);
+            pl0[i] = *reinterpret_cast<const float4 *>(pr0 + ld + q);
+            ph1[i] = *reinterpret_cast<const float4 *>(pr1 + q);
+            pl1[i] = *reinterpret_cast<const float4 *>(pr1 + ld + q);
+          }
+        }
+#pragma unroll
+        for (int i = 0; i < kUpdQ; ++i) {
+          const int64_t q = q0 + i * stride;
+          if (q >= ld) break;
+          float4 *s0 = reinterpret_cast<float4 *>(xs + q), *s1 = reinterpret_cast<float4 *>(xs + kUpPlane + q);
+          float4 *s2 = reinterpret_cast<float4 *>(xs + 2 * kUpPlane + q);
+          float4 *s3 = reinterpret_cast<float4 *>(xs + 3 * kUpPlane + q);
+          const float4 wh0 = *s0, wl0 = *s1, wh1 = *s2, wl1 = *s3;
+          const float a_wh0[4] = {wh0.x, wh0.y, wh0.z, wh0.w}, a_wl0[4] = {wl0.x, wl0.y, wl0.z, wl0.w};
+          const float a_wh1[4] = {wh1.x, wh1.y, wh1.z, wh1.w}, a_wl1[4] = {wl1.x, wl1.y, wl1.z, wl1.w};
+          const float a_ph0[4] = {ph0[i].x, ph0[i].y, ph0[i].z, ph0[i].w};
+          const float a_pl0[4] = {pl0[i].x, pl0[i].y, pl0[i].z, pl0[i].w};
+          const float a_ph1[4] = {ph1[i].x, ph1[i].y, ph1[i].z, ph1[i].w};
+          const float a_pl1[4] = {pl1[i].x, pl1[i].y, pl1[i].z, pl1[i].w};
+          float rh0[4], rl0[4], rh1[4], rl1[4];
+#pragma unroll
+          for (int k = 0; k < 4; ++k) {
+            f2x mh, ml, rh, rl, sh, sl;
+            df2_mul(cph, cpl, pk2(a_ph0[k], a_ph1[k]), pk2(a_pl0[k], a_pl1[k]), mh, ml);
+            df2_add(mh, ml, pk2(a_wh0[k], a_wh1[k]), pk2(a_wl0[k], a_wl1[k]), rh, rl);
+            df2_mul(rh, rl, rh, rl, sh, sl);
+            if (d1 == d0) {
+              sh &= 0xffffffffull;
+              sl &= 0xffffffffull;
+            }
+            acc2_add(nacc, sh, sl);
+            const float2 h2 = upk2(rh), l2 = upk2(rl);
+            rh0[k] = h2.x;
+            rh1[k] = h2.y;
+            rl0[k] = l2.x;
+            rl1[k] = l2.y;
+          }
+          const float4 oh0 = make_float4(rh0[0], rh0[1], rh0[2], rh0[3]);
+          const float4 ol0 = make_float4(rl0[0], rl0[1], rl0[2], rl0[3]);
+          const float4 oh1 = make_float4(rh1[0], rh1[1], rh1[2], rh1[3]);
+          const float4 ol1 = make_float4(rl1[0], rl1[1], rl1[2], rl1[3]);
+          *s0 = oh0;
+          *s1 = ol0;
+          *s2 = oh1;
+          *s3 = ol1;
+          *reinterpret_cast<float4 *>(x0 + q) = oh0;
+          *reinterpret_cast<float4 *>(x0 + ld + q) = ol0;
+          if (d1 != d0) {
+            *reinterpret_cast<float4 *>(x1 + q) = oh1;
+            *reinterpret_cast<float4 *>(x1 + ld + q) = ol1;
+          }
+        }
+      }
+      {
+        f2x h, l;
+        acc2_norm(nacc, h, l);
+        double v = df2_lanes_to_f64(h, l);
+        for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+        if ((tid & 31) == 0) wnorm[tid >> 5] += v;
+      }
+      __syncthreads();
+    }
+    const uint32_t I0 = F.basis_dn[d0], I1 = F.basis_dn[d1];
     float *__restrict__ z0 = z + d0 * 2 * ld;
     float *__restrict__ z1 = z + d1 * 2 * ld;
     for (int64_t slot = tid; slot < ld; slot += blockDim.x) {
@@ -324,24 +478,25 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
         z1[ld + slot] = 0.f;
         continue;
       }
-      DfAcc2 acc{0ull, 0ull};
+      DfSum4 acc{0ull, 0ull, 0ull, {0ull, 0ull, 0ull, 0ull}};
       const int64_t sl = slot >> 5, lane = slot & 31;
       const uint4 *__restrict__ wa = reinterpret_cast<const uint4 *>(F.sl_add + F.sl_off_add[sl]) + lane;
       const uint4 *__restrict__ wsb = reinterpret_cast<const uint4 *>(F.sl_sub + F.sl_off_sub[sl]) + lane;
       const int na = F.steps_add[sl], ns = F.steps_sub[sl];
-      // one scheduled entry (idle steps read the zero column): (hi d0, hi d1), (lo d0, lo d1)
-#define HUB_TERM(OP, C)                                                                  \
+      // one scheduled entry (idle steps read the zero column): (hi d0, hi d1), (lo d0, lo d1);
+      // J: the low-part accumulator, by the entry's position in its batch
+#define HUB_TERM(OP, J, C)                                                               \
   do {                                                                                   \
     const float *p_ = xs + (C);                                                          \
-    OP(acc, pk2(p_[0], p_[2 * kUpPlane]), pk2(p_[kUpPlane], p_[3 * kUpPlane]));          \
+    OP(acc, pk2(p_[0], p_[2 * kUpPlane]), pk2(p_[kUpPlane], p_[3 * kUpPlane]), (J));     \
   } while (0)
-#define HUB_WORD(OP, WD)                                                                 \
+#define HUB_WORD(OP, J, WD)                                                              \
   do {                                                                                   \
     if (sizeof(Col) == 2) {                                                              \
-      HUB_TERM(OP, (WD) & 0xffffu);                                                      \
-      HUB_TERM(OP, (WD) >> 16);                                                          \
+      HUB_TERM(OP, (J), (WD) & 0xffffu);                                                 \
+      HUB_TERM(OP, (J) + 1, (WD) >> 16);                                                 \
     } else {                                                                             \
-      HUB_TERM(OP, (WD));                                                                \
+      HUB_TERM(OP, (J), (WD));                                                           \
     }                                                                                    \
   } while (0)
       // Full batches of four words run unguarded; the last batch is taken word by word
@@ -350,40 +505,33 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
   do {                                                                                   \
     constexpr int kPer = sizeof(Col) == 2 ? 8 : 4;       /* steps per batch */           \
     constexpr int kPerWord = sizeof(Col) == 2 ? 2 : 1;                                   \
-    const int nst = (N);                                                                 \
-    int b = 0;                                                                           \
-    for (; kPer * (b + 1) <= nst; ++b) {                                                 \
-      const uint4 q = W[b * 32];                                                         \
-      HUB_WORD(OP, q.x);                                                                 \
-      HUB_WORD(OP, q.y);                                                                 \
-      HUB_WORD(OP, q.z);                                                                 \
-      HUB_WORD(OP, q.w);                                                                 \
-    }                                                                                    \
-    const int rem = nst - kPer * b;                                                      \
-    if (rem > 0) {                                                                       \
-      const uint4 q = W[b * 32];                                                         \
-      HUB_WORD(OP, q.x);                                                                 \
-      if (rem > kPerWord) HUB_WORD(OP, q.y);                                             \
-      if (rem > 2 * kPerWord) HUB_WORD(OP, q.z);                                         \
-      if (rem > 3 * kPerWord) HUB_WORD(OP, q.w);                                         \
+    constexpr int kJ1 = kPerWord, kJ2 = (2 * kPerWord) & 3, kJ3 = (3 * kPerWord) & 3;   \
+    const int nst = (N), nb = (nst + kPer - 1) / kPer;                                   \
+    uint4 qn = nb > 0 ? W[0] : make_uint4(0u, 0u, 0u, 0u);                               \
+    for (int b = 0; b < nb; ++b) {                                                       \
+      const uint4 q = qn;                                                                \
+      if (b + 1 < nb) qn = W[(b + 1) * 32];     /* next batch's columns in flight */     \
+      const int rem = nst - kPer * b;                                                    \
+      HUB_WORD(OP, 0, q.x);                                                              \
+      if (rem > kPerWord) HUB_WORD(OP, kJ1, q.y);                                        \
+      if (rem > 2 * kPerWord) HUB_WORD(OP, kJ2, q.z);                                    \
+      if (rem > 3 * kPerWord) HUB_WORD(OP, kJ3, q.w);                                    \
     }                                                                                    \
   } while (0)
-      HUB_GROUP(acc2_add, wa, na);
-      HUB_GROUP(acc2_sub, wsb, ns);
+      HUB_GROUP(sum4_add, wa, na);
+      HUB_GROUP(sum4_sub, wsb, ns);
 #undef HUB_GROUP
 #undef HUB_WORD
 #undef HUB_TERM
-      // Z = diag x + t S for both rows (packed)
+      // Z = diag x + t' S for both rows (packed), t' = +-1
       f2x Sh, Sl;
-      acc2_norm(acc, Sh, Sl);
-      if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
-      const uint32_t Iu = F.basis_up_slot[slot];
-      float2 dg0 = utab[__popc(Iu & I0)], dg1 = utab[__popc(Iu & I1)];
-      if (kEps) {
-        const float2 ep = F.eps_up[slot];
-        dg0 = df_add(df_add(dg0, ep), e0);
-        dg1 = df_add(df_add(dg1, ep), e1);
+      sum4_norm(acc, Sh, Sl);
+      if (F.t_neg) {
+        Sh ^= kSign2;
+        Sl ^= kSign2;
       }
+      const uint32_t Iu = F.basis_up_slot[slot];
+      const float2 dg0 = utab[__popc(Iu & I0)], dg1 = utab[__popc(Iu & I1)];
       f2x ph, pl, zh, zl;
       df2_mul(pk2(dg0.x, dg1.x), pk2(dg0.y, dg1.y), pk2(xs[slot], xs[slot + 2 * kUpPlane]),
               pk2(xs[slot + kUpPlane], xs[slot + 3 * kUpPlane]), ph, pl);
@@ -397,6 +545,11 @@ __global__ void __launch_bounds__(1024, 1) k_up(const FastView F, const float *_
       }
     }
     __syncthreads();
+  }
+  if (kUpd && tid == 0) {                  // wnorm was last written before the loop's final barrier
+    double t = 0.0;
+    for (int k = 0; k < (int)(blockDim.x >> 5); ++k) t += wnorm[k];
+    U.partials[blockIdx.x] = t;
   }
 }
 
@@ -499,11 +652,6 @@ __global__ void k_set_scal(double *__restrict__ scal, int i0, double v0, int i1,
 __device__ __forceinline__ f2x ld2(const float *p) { return *reinterpret_cast<const f2x *>(p); }
 __device__ __forceinline__ void st2(float *p, f2x v) { *reinterpret_cast<f2x *>(p) = v; }
 
-// FP64 value of lane a + lane b of a packed (hi, lo) pair
-__device__ __forceinline__ double df2_lanes_to_f64(f2x h, f2x l) {
-  const float2 hh = upk2(h), ll = upk2(l);
-  return df_to_f64(make_float2(hh.x, ll.x), 0) + df_to_f64(make_float2(hh.y, ll.y), 0);
-}
 
 // kLane packed pairs per lane: columns u .. u + 2 kLane - 1 (16-byte loads for even kLane)
 template <int kLane>
@@ -538,6 +686,62 @@ __device__ __forceinline__ void stv(float *p, const Vec<kLane> &a) {
   }
 }
 
+// Strip rows k, k + 1 of one sign group (loads issued together) into the lane's accumulators
+// as a pair whose low parts go to accumulator J.
+template <int kLane, int J, bool kAdd, typename Col>
+__device__ __forceinline__ void dn_pair(DfSumP (&acc)[kLane], const Side &S, const char *__restrict__ xh,
+                                        const char *__restrict__ xl, int32_t k, uint32_t row_bytes) {
+  Vec<kLane> vh[2], vl[2];
+#pragma unroll
+  for (int q = 0; q < 2; ++q) {
+    const uint64_t o = (uint64_t)colat<Col>(S.col, k + q) * row_bytes;
+    vh[q] = ldv<kLane>(reinterpret_cast<const float *>(xh + o));
+    vl[q] = ldv<kLane>(reinterpret_cast<const float *>(xl + o));
+  }
+#pragma unroll
+  for (int i = 0; i < kLane; ++i) sump_pair(acc[i], vh[0].v[i], vl[0].v[i], vh[1].v[i], vl[1].v[i], kAdd, J);
+}
+
+// The strip rows ka .. kb - 1 of one sign group (bounds warp-uniform): pairs of rows with
+// their low parts into the two accumulators in turn (HUB_DN_BATCH = 4: two pairs' loads in
+// flight together), a last single row into accumulator 1.
+template <int kLane, bool kAdd, typename Col>
+__device__ __forceinline__ void dn_group(DfSumP (&acc)[kLane], const Side &S, const char *__restrict__ xh,
+                                         const char *__restrict__ xl, int32_t ka, int32_t kb, uint32_t row_bytes) {
+  static_assert(HUB_DN_BATCH == 2 || HUB_DN_BATCH == 4, "HUB_DN_BATCH must be 2 or 4");
+  int32_t k = ka;
+  for (; k + 4 <= kb; k += 4) {
+    if (HUB_DN_BATCH == 4) {
+      Vec<kLane> vh[4], vl[4];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const uint64_t o = (uint64_t)colat<Col>(S.col, k + q) * row_bytes;
+        vh[q] = ldv<kLane>(reinterpret_cast<const float *>(xh + o));
+        vl[q] = ldv<kLane>(reinterpret_cast<const float *>(xl + o));
+      }
+#pragma unroll
+      for (int i = 0; i < kLane; ++i) {
+        sump_pair(acc[i], vh[0].v[i], vl[0].v[i], vh[1].v[i], vl[1].v[i], kAdd, 0);
+        sump_pair(acc[i], vh[2].v[i], vl[2].v[i], vh[3].v[i], vl[3].v[i], kAdd, 1);
+      }
+    } else {
+      dn_pair<kLane, 0, kAdd, Col>(acc, S, xh, xl, k, row_bytes);
+      dn_pair<kLane, 1, kAdd, Col>(acc, S, xh, xl, k + 2, row_bytes);
+    }
+  }
+  if (k + 2 <= kb) {
+    dn_pair<kLane, 0, kAdd, Col>(acc, S, xh, xl, k, row_bytes);
+    k += 2;
+  }
+  if (k < kb) {
+    const uint64_t o = (uint64_t)colat<Col>(S.col, k) * row_bytes;
+    const Vec<kLane> vh = ldv<kLane>(reinterpret_cast<const float *>(xh + o));
+    const Vec<kLane> vl = ldv<kLane>(reinterpret_cast<const float *>(xl + o));
+#pragma unroll
+    for (int i = 0; i < kLane; ++i) sump_one(acc[i], vh.v[i], vl.v[i], kAdd, 1);
+  }
+}
+
 // kMode 0: w (planar double-float, slot order; may alias z) = Z + t S_dn, for hub_apply
 //          (the FP64 output in rank order is written afterwards by k_unpermute).
 // kMode 1: w = (Z + t S_dn)/beta_cur - (beta_cur/beta_prev) r_prev, partials <- <q_j, w>
@@ -558,14 +762,6 @@ __global__ void __launch_bounds__(kDnThreads, HUB_DN_MINB) k_dn(const FastView F
   const int64_t u = (int64_t)blockIdx.y * kDnCols + kDnLaneCols * lane;
   const int64_t r0 = (int64_t)blockIdx.x * kDnRows;
   const uint32_t row_bytes = (uint32_t)(2 * ld * sizeof(float));
-  f2x ibh = 0ull, ibl = 0ull, cph = 0ull, cpl = 0ull;
-  if (kMode == 1) {
-    const float2 ib = L.coef[0], cp = L.coef[1];
-    ibh = bcast2(ib.x);
-    ibl = bcast2(ib.y);
-    cph = bcast2(cp.x);
-    cpl = bcast2(cp.y);
-  }
   DfAcc2 dacc{0ull, 0ull};
   const bool active = u < S.n_cols;                    // u + kDnLaneCols <= ld (see fast_build)
   const char *__restrict__ xh = reinterpret_cast<const char *>(x + u);
@@ -582,55 +778,31 @@ __global__ void __launch_bounds__(kDnThreads, HUB_DN_MINB) k_dn(const FastView F
       }
       continue;
     }
-    DfAcc2 acc[kLane];
+    DfSumP acc[kLane];
 #pragma unroll
-    for (int i = 0; i < kLane; ++i) acc[i] = DfAcc2{0ull, 0ull};
-    // strip rows of each group, HUB_DN_BATCH loads in flight; the bounds are warp-uniform
-#define HUB_DN_GROUP(OP, KA, KB)                                                           \
-  do {                                                                                     \
-    int32_t k = (KA);                                                                      \
-    for (; k + HUB_DN_BATCH <= (KB); k += HUB_DN_BATCH) {                                  \
-      Vec<kLane> vh[HUB_DN_BATCH], vl[HUB_DN_BATCH];                                       \
-      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q) {                           \
-        const uint64_t o = (uint64_t)colat<Col>(S.col, k + q) * row_bytes;                 \
-        vh[q] = ldv<kLane>(reinterpret_cast<const float *>(xh + o));                       \
-        vl[q] = ldv<kLane>(reinterpret_cast<const float *>(xl + o));                       \
-      }                                                                                    \
-      _Pragma("unroll") for (int q = 0; q < HUB_DN_BATCH; ++q)                             \
-        _Pragma("unroll") for (int i = 0; i < kLane; ++i) OP(acc[i], vh[q].v[i], vl[q].v[i]); \
-    }                                                                                      \
-    for (; k < (KB); ++k) {                                                                \
-      const uint64_t o = (uint64_t)colat<Col>(S.col, k) * row_bytes;                       \
-      const Vec<kLane> vh = ldv<kLane>(reinterpret_cast<const float *>(xh + o));           \
-      const Vec<kLane> vl = ldv<kLane>(reinterpret_cast<const float *>(xl + o));           \
-      _Pragma("unroll") for (int i = 0; i < kLane; ++i) OP(acc[i], vh.v[i], vl.v[i]);      \
-    }                                                                                      \
-  } while (0)
-    HUB_DN_GROUP(acc2_add, k0, ks);
-    HUB_DN_GROUP(acc2_sub, ks, k1);
-#undef HUB_DN_GROUP
+    for (int i = 0; i < kLane; ++i) acc[i] = DfSumP{0ull, 0ull, 0ull, {0ull, 0ull}};
+    dn_group<kLane, true, Col>(acc, S, xh, xl, k0, ks, row_bytes);
+    dn_group<kLane, false, Col>(acc, S, xh, xl, ks, k1, row_bytes);
     Vec<kLane> yh, yl;
     if (kMode == 2) {
       // diag x for the columns (spin-down states) u .. u + kDnLaneCols - 1 of spin-up row d
       const float *xr = x + d * 2 * ld;
       const Vec<kLane> xvh = ldv<kLane>(xr + u), xvl = ldv<kLane>(xr + ld + u);
       const uint32_t Iu = F.basis_up[d];
-      const float2 ep = F.eps_up ? F.eps_up[d] : make_float2(0.f, 0.f);
 #pragma unroll
       for (int i = 0; i < kLane; ++i) {
         float2 dg[2];
 #pragma unroll
         for (int b = 0; b < 2; ++b) {
           const int64_t c = u + 2 * i + b;
-          dg[b] = make_float2(0.f, 0.f);
-          if (c < S.n_cols) {
-            dg[b] = utab[__popc(Iu & F.basis_dn[c])];
-            if (F.eps_up) dg[b] = df_add(df_add(dg[b], ep), F.eps_dn[c]);
-          }
+          dg[b] = c < S.n_cols ? utab[__popc(Iu & F.basis_dn[c])] : make_float2(0.f, 0.f);
         }
         f2x Sh, Sl, ph, pl;
-        acc2_norm(acc[i], Sh, Sl);
-        if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+        sump_norm(acc[i], Sh, Sl);
+        if (F.t_neg) {
+          Sh ^= kSign2;
+          Sl ^= kSign2;
+        }
         df2_mul(pk2(dg[0].x, dg[1].x), pk2(dg[0].y, dg[1].y), xvh.v[i], xvl.v[i], ph, pl);
         df2_add(ph, pl, Sh, Sl, yh.v[i], yl.v[i]);
       }
@@ -640,8 +812,11 @@ __global__ void __launch_bounds__(kDnThreads, HUB_DN_MINB) k_dn(const FastView F
 #pragma unroll
       for (int i = 0; i < kLane; ++i) {
         f2x Sh, Sl;
-        acc2_norm(acc[i], Sh, Sl);
-        if (!F.t_is_one) df2_mul(Sh, Sl, bcast2(F.t.x), bcast2(F.t.y), Sh, Sl);
+        sump_norm(acc[i], Sh, Sl);
+        if (F.t_neg) {
+          Sh ^= kSign2;
+          Sl ^= kSign2;
+        }
         df2_add(zh.v[i], zl.v[i], Sh, Sl, yh.v[i], yl.v[i]);
       }
     }
@@ -652,6 +827,10 @@ __global__ void __launch_bounds__(kDnThreads, HUB_DN_MINB) k_dn(const FastView F
       const float *rc = L.r_cur + d * 2 * ld, *rp = L.r_prev + d * 2 * ld;
       const Vec<kLane> rph = ldv<kLane>(rp + u), rpl = ldv<kLane>(rp + ld + u);
       const Vec<kLane> rch = ldv<kLane>(rc + u), rcl = ldv<kLane>(rc + ld + u);
+      // recurrence coefficients, read per row (L1-resident) rather than held across the
+      // hopping loop in registers
+      const float2 ib = L.coef[0], cp = L.coef[1];
+      const f2x ibh = bcast2(ib.x), ibl = bcast2(ib.y), cph = bcast2(cp.x), cpl = bcast2(cp.y);
       Vec<kLane> wh, wl;
 #pragma unroll
       for (int i = 0; i < kLane; ++i) {
@@ -841,22 +1020,21 @@ struct FastState {
   uint32_t idle_word = 0xffffffffu;
   int32_t *slot_row = nullptr, *slot_of = nullptr;
   uint32_t *basis_slot = nullptr;
-  float2 *eps_up_slot = nullptr;
   void *col[2] = {nullptr, nullptr};
-  float2 *eps_df[2] = {nullptr, nullptr};
   float *xdf = nullptr, *zdf = nullptr;      // hub_apply scratch (planar double-float)
   bool staged = true;                        // pass 1 stages rows; else it runs on X^T
+  int acc_terms = 0;                         // most terms one low-part accumulator sums (error bound)
   int64_t ld_t = 0;                          // plane length of X^T rows (count_dn padded)
   float *xt = nullptr, *zt = nullptr;        // X^T and Z^T (rows too long to stage)
   float *lz[3] = {nullptr, nullptr, nullptr};
   float *psi = nullptr;
-  int *d_emax = nullptr;
+  int *d_range = nullptr;                    // exponent partials [2 G], then scale[4] (k_scale)
   int *d_err = nullptr;
   int64_t ld = 0;
   // pipelined host-buffer apply: copy stream, per-chunk events, exponent partials, flag
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> events;
-  int *d_emax_chunks = nullptr, *d_flag = nullptr, *h_flag = nullptr;
+  int *d_range_chunks = nullptr, *d_flag = nullptr, *h_flag = nullptr;
   // CUDA graphs of one Lanczos iteration (first pass), one per rotation of the three
   // vectors, captured on graph_stream and replayed on the caller's stream; lz_graph_key holds
   // the operands they were captured with
@@ -874,7 +1052,6 @@ void fast_release(hub_ctx *h) {
   for (int s = 0; s < 2; ++s) {
     dev_free(f->sp[s]);
     dev_free(f->col[s]);
-    dev_free(f->eps_df[s]);
   }
   dev_free(f->xdf);
   dev_free(f->zdf);
@@ -882,9 +1059,9 @@ void fast_release(hub_ctx *h) {
   dev_free(f->zt);
   for (int k = 0; k < 3; ++k) dev_free(f->lz[k]);
   dev_free(f->psi);
-  dev_free(f->d_emax);
+  dev_free(f->d_range);
   dev_free(f->d_err);
-  dev_free(f->d_emax_chunks);
+  dev_free(f->d_range_chunks);
   dev_free(f->d_flag);
   if (f->h_flag) cudaFreeHost(f->h_flag);
   for (cudaEvent_t e : f->events) cudaEventDestroy(e);
@@ -902,7 +1079,6 @@ void fast_release(hub_ctx *h) {
   dev_free(f->slot_row);
   dev_free(f->slot_of);
   dev_free(f->basis_slot);
-  dev_free(f->eps_up_slot);
   delete f;
   h->fast = nullptr;
 }
@@ -914,11 +1090,29 @@ static int64_t padded_ld(int64_t n_up) {
   return (n_up + a - 1) / a * a;
 }
 
+// Parameter magnitudes the double-float window allows (0, or 2^-16 .. 2^16; see kExpSpan).
+static bool in_param_range(double v) {
+  const double a = std::fabs(v);
+  return a == 0.0 || (a >= 0x1p-16 && a <= 0x1p16);
+}
+
+// Most terms (pass 2: pair sums) one low-part accumulator of a hopping sum may take: with
+// N such additions the product's error is at most max(N + 10.1, 16) u^2 (|H||x|)_n,
+// u = 2^-24, so N <= 15 keeps it, with the oracle's own FP64 rounding (2 u^2), below
+// 1e-13 (|H||x|)_n = 28.1 u^2.  A row with F_add adding and F_sub subtracting entries gives
+// N <= ceil(F_add/4) + ceil(F_sub/4) (9 for the 32-entry rows of the 4x4 lattice).
+constexpr int kMaxAccTerms = 15;
+
+// The fast path: uniform t != 0 and U, no site energies (the diagonal is then U k exactly),
+// |t| and U / |t| in the parameter range, hopping rows short enough for kMaxAccTerms.
 bool fast_eligible(const hub_ctx *h) {
-  if (!h->have_hop || !h->have_U || !h->uniform_U) return false;
+  if (!h->have_hop || !h->have_U || !h->uniform_U || h->has_eps) return false;
   for (double tb : h->t)
     if (tb != h->t[0]) return false;
+  if (h->t.empty() || h->t[0] == 0.0 || !in_param_range(h->t[0])) return false;
+  if (!in_param_range(h->U0 / std::fabs(h->t[0]))) return false;
   if (h->count[0] <= 0 || h->count[1] <= 0) return false;
+  if (h->fast && h->fast->acc_terms > kMaxAccTerms) return false;
   // element quads of a vector are indexed with 32-bit integers
   return h->count[1] * (padded_ld(h->count[0]) / 4) < ((int64_t)1 << 32);
 }
@@ -947,11 +1141,6 @@ int fast_build(hub_ctx *h) {
     else
       k_split_csr<uint32_t><<<std::max(g, 1), 256>>>(n, c.rowptr, c.scol, f->sp[s], (uint32_t *)f->col[s]);
     HUB_LAUNCH_CHECK();
-    if (h->has_eps) {
-      if (!dev_alloc((void **)&f->eps_df[s], sizeof(float2) * n, "site energies (double-float)")) return HUB_ERR_OOM;
-      k_eps_df<<<std::max(g, 1), 256>>>(n, h->eps_state[s], f->eps_df[s]);
-      HUB_LAUNCH_CHECK();
-    }
   }
   // sliced, bank-scheduled H_up for pass 1 (built on the host from the sign-split CSR)
   {
@@ -980,6 +1169,22 @@ int fast_build(hub_ctx *h) {
     });
     std::vector<int32_t> slot_of(n);
     for (int64_t k = 0; k < n; ++k) slot_of[slot_row[k]] = (int32_t)k;
+    // terms per low-part accumulator: whole rows of a CSR (pass 2; pass 1 on X^T), or the
+    // scheduled steps of a slice (staged pass 1, below)
+    auto acc_of_rows = [](const std::vector<int32_t> &r, const std::vector<int32_t> &sp) {
+      int m = 0;
+      for (size_t k = 0; k + 1 < r.size(); ++k)
+        m = std::max(m, (sp[k] - r[k] + 3) / 4 + (r[k + 1] - sp[k] + 3) / 4);
+      return m;
+    };
+    {
+      const int sd = h->shared ? 0 : 1;
+      std::vector<int32_t> rpd(h->count[sd] + 1), spd(h->count[sd]);
+      HUB_CUDA(cudaMemcpy(rpd.data(), h->csr[sd].rowptr, sizeof(int32_t) * rpd.size(), cudaMemcpyDeviceToHost));
+      HUB_CUDA(cudaMemcpy(spd.data(), f->sp[sd], sizeof(int32_t) * spd.size(), cudaMemcpyDeviceToHost));
+      f->acc_terms = acc_of_rows(rpd, spd);
+      if (!f->staged) f->acc_terms = std::max(f->acc_terms, acc_of_rows(rp, spv));
+    }
     const int g = (int)std::max<int64_t>(1, std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 16));
     if (!dev_alloc((void **)&f->slot_row, sizeof(int32_t) * n, "slot order") ||
         !dev_alloc((void **)&f->slot_of, sizeof(int32_t) * n, "slot order") ||
@@ -987,10 +1192,7 @@ int fast_build(hub_ctx *h) {
       return HUB_ERR_OOM;
     HUB_CUDA(cudaMemcpy(f->slot_row, slot_row.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
     HUB_CUDA(cudaMemcpy(f->slot_of, slot_of.data(), sizeof(int32_t) * n, cudaMemcpyHostToDevice));
-    if (h->has_eps && !dev_alloc((void **)&f->eps_up_slot, sizeof(float2) * n, "site energies in slot order"))
-      return HUB_ERR_OOM;
-    k_to_slots<<<g, 256>>>(n, f->slot_row, h->basis[0], f->basis_slot, h->has_eps ? f->eps_df[0] : nullptr,
-                           f->eps_up_slot);
+    k_to_slots<<<g, 256>>>(n, f->slot_row, h->basis[0], f->basis_slot);
     HUB_LAUNCH_CHECK();
     if (f->staged) {
       // Per slice and group, the lanes' entries are scheduled into steps; the 32-bit loads of
@@ -1085,6 +1287,7 @@ int fast_build(hub_ctx *h) {
           const int S = (int)warp_steps.size();
           if (S > 65535) return fail(HUB_ERR_ARG, "fast path: hopping row schedule too long");
           st[grp][sl] = (uint16_t)S;
+          if (grp == 1) f->acc_terms = std::max(f->acc_terms, (st[0][sl] + 3) / 4 + (S + 3) / 4);
           const int nw = (S + pack - 1) / pack, nb = (nw + 3) / 4;
           off[grp][sl + 1] = off[grp][sl] + 32 * 4 * nb;
           for (int bt = 0; bt < nb; ++bt)
@@ -1152,18 +1355,19 @@ static FastView fast_view(const hub_ctx *h, const FastState *f) {
   v.slot_row = f->slot_row;
   v.idle_word = f->idle_word;
   v.basis_up_slot = f->basis_slot;
-  v.eps_up = f->eps_up_slot;
-  v.eps_dn = f->eps_df[sd];
-  const double t = h->t.empty() ? 0.0 : h->t[0];
-  v.t_is_one = (t == 1.0);
-  // host double -> double-float: hi = float(t), lo = float(t - hi)
+  // The kernels apply H / |t| (hopping elements -sign(t) esign, exact), the caller's results
+  // are scaled by |t| in FP64 (hub_apply) or through alpha, beta (Lanczos).
+  const double t = h->t.empty() ? 1.0 : h->t[0];
+  v.t_neg = t < 0.0;
+  // host double -> double-float: hi = float(a), lo = float(a - hi)
   auto hdf = [](double a) {
     float hi = (float)a;
     return make_float2(hi, (float)(a - (double)hi));
   };
-  v.t = hdf(t);
-  for (int k = 0; k < 32; ++k) v.Utab[k] = hdf(h->U0 * (double)k);
+  const double u_scaled = h->U0 / std::fabs(t);
+  for (int k = 0; k < 32; ++k) v.Utab[k] = hdf(u_scaled * (double)k);
   v.err = f->d_err;
+  v.fail_waits = h->fail_waits ? 1 : 0;
   return v;
 }
 
@@ -1222,29 +1426,42 @@ static int transpose(int64_t n_r, int64_t n_c, int64_t ld_s, int64_t ld_d, const
 static int ensure_vec(float **p, int64_t n, const char *what);
 
 // z <- pass 1 (x planar double-float); with staged rows, only the row pairs p0 .. p1 - 1
-// (p1 < 0: all pairs)
-static int run_up(hub_ctx *h, FastState *f, const float *x, float *z, cudaStream_t s, int64_t p0 = 0,
-                  int64_t p1 = -1) {
+// (p1 < 0: all pairs).  With upd: first x <- x + c r_prev (the Lanczos update, fused into the
+// staging of pass 1 when rows are staged, else a separate vector pass), |x|^2 partials into
+// upd->partials, their number in *n_part.
+static int run_up(hub_ctx *h, FastState *f, float *x, float *z, cudaStream_t s, int64_t p0 = 0, int64_t p1 = -1,
+                  const UpdArgs *upd = nullptr, int *n_part = nullptr) {
   const FastView v = fast_view(h, f);
   if (p1 < 0) p1 = (v.n_dn + 1) / 2;
-  if (!f->staged && (p0 != 0 || p1 != (v.n_dn + 1) / 2)) return fail(HUB_ERR_STATE, "pass 1: partial range");
+  if ((!f->staged || upd) && (p0 != 0 || p1 != (v.n_dn + 1) / 2))
+    return fail(HUB_ERR_STATE, "pass 1: partial range");
   if (p1 <= p0) return HUB_OK;
   int rc = prof_mark(h, HUB_PROF_UP, true, s);
   if (rc) return rc;
+  const bool fused = upd && f->staged && kFusedUpdate;
+  if (upd && !fused) {
+    const int G = grid_vec();
+    count_launch(h);
+    k_df_update<<<G, 256, 0, s>>>(quads(h, f), x, upd->r_prev, upd->coef, upd->partials);
+    HUB_LAUNCH_CHECK();
+    if (n_part) *n_part = G;
+  }
   if (f->staged) {
     count_launch(h);
     const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
     const int grid = (int)std::min<int64_t>(p1 - p0, (int64_t)num_sms());
     const size_t smem = up_smem(f);
-#define HUB_UP(C, E)                                                                                      \
+    const UpdArgs U = fused ? *upd : UpdArgs{};
+    if (fused && n_part) *n_part = grid;
+#define HUB_UP(C, K)                                                                                      \
   do {                                                                                                    \
-    HUB_CUDA(cudaFuncSetAttribute(k_up<C, E>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage)); \
-    k_up<C, E><<<grid, threads, smem, s>>>(v, x, z, p0, p1);                                             \
+    HUB_CUDA(cudaFuncSetAttribute(k_up<C, K>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMaxStage)); \
+    k_up<C, K><<<grid, threads, smem, s>>>(v, x, z, p0, p1, U);                                          \
   } while (0)
     if (f->col16) {
-      if (h->has_eps) HUB_UP(uint16_t, true); else HUB_UP(uint16_t, false);
+      if (fused) HUB_UP(uint16_t, true); else HUB_UP(uint16_t, false);
     } else {
-      if (h->has_eps) HUB_UP(uint32_t, true); else HUB_UP(uint32_t, false);
+      if (fused) HUB_UP(uint32_t, true); else HUB_UP(uint32_t, false);
     }
 #undef HUB_UP
     HUB_LAUNCH_CHECK();
@@ -1278,7 +1495,16 @@ static int ensure_vec(float **p, int64_t n, const char *what) {
 
 static int row_grid(const hub_ctx *h) { return (int)std::min<int64_t>(h->count[1], (int64_t)num_sms() * 8); }
 
-// hub_apply on the fast path: FP64 in, FP64 out.
+// Exponent partials and scale words of the handle: [2 G] partials, then scale[0..3].
+static int *range_buf(FastState *f) {
+  if (!f->d_range && !dev_alloc((void **)&f->d_range, sizeof(int) * (2 * grid_vec() + 4), "exponent partials"))
+    return nullptr;
+  return f->d_range;
+}
+
+// hub_apply on the fast path: FP64 in, FP64 out.  A vector outside the double-float window
+// (kExpSpan) is multiplied by the FP64 kernel instead: both are launched, the device-side
+// flag scale[1] decides which one writes y, so the call stays asynchronous.
 int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   FastState *f = fast_of(h);
   if (!f || !f->built) return fail(HUB_ERR_STATE, "fast apply: not built");
@@ -1287,19 +1513,21 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   if ((rc = ensure_vec(&f->xdf, Dp, "apply scratch x")) || (rc = ensure_vec(&f->zdf, Dp, "apply scratch z")))
     return rc;
   const int G = grid_vec();
-  if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
-  count_launch(h, 2);
-  k_max_exp<<<G, 256, 0, s>>>(D, x, f->d_emax);
-  k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, h->count[1], h->count[0], f->ld, x, f->d_emax, G, f->slot_row,
-                                          f->xdf);
+  int *part = range_buf(f);
+  if (!part) return HUB_ERR_OOM;
+  int *scale = part + 2 * G;
+  count_launch(h, 3);
+  k_exp_range<<<G, 256, 0, s>>>(D, x, part);
+  k_scale<<<1, 256, 0, s>>>(part, G, scale);
+  k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, h->count[1], h->count[0], f->ld, x, scale, f->slot_row, f->xdf);
   HUB_LAUNCH_CHECK();
   if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
   if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s))) return rc;
   count_launch(h);
-  k_unpermute<<<row_grid(h), 512, 0, s>>>(0, h->count[1], h->count[0], f->ld, f->zdf, f->slot_of, f->d_emax, G,
-                                          y);
+  k_unpermute<<<row_grid(h), 512, 0, s>>>(0, h->count[1], h->count[0], f->ld, f->zdf, f->slot_of, scale,
+                                          std::fabs(h->t[0]), y);
   HUB_LAUNCH_CHECK();
-  return HUB_OK;
+  return f64_apply(h, x, y, scale + 1, s);
 }
 
 // hub_apply_host on the fast path with staged rows.  The input arrives in row chunks on a copy
@@ -1330,8 +1558,10 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
   if ((rc = ensure_vec(&f->xdf, Dp, "apply scratch x")) || (rc = ensure_vec(&f->zdf, Dp, "apply scratch z")))
     return rc;
   const int G = grid_vec();
-  if (!f->d_emax_chunks && !dev_alloc((void **)&f->d_emax_chunks, sizeof(int) * G * kHostChunks, "exponent partials"))
+  if (!f->d_range_chunks &&
+      !dev_alloc((void **)&f->d_range_chunks, sizeof(int) * 2 * G * kHostChunks, "exponent partials"))
     return HUB_ERR_OOM;
+  if (!range_buf(f)) return HUB_ERR_OOM;
   if (!f->d_flag && !dev_alloc((void **)&f->d_flag, sizeof(int), "scale flag")) return HUB_ERR_OOM;
   if (!f->h_flag) HUB_CUDA(cudaMallocHost((void **)&f->h_flag, sizeof(int)));
   if (!f->copy_stream) HUB_CUDA(cudaStreamCreateWithFlags(&f->copy_stream, cudaStreamNonBlocking));
@@ -1371,33 +1601,40 @@ static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double 
                              cudaMemcpyHostToDevice, sc));
     HUB_CUDA(cudaEventRecord(ev_in[c], sc));
   }
-  int *emax = f->d_emax_chunks;
+  int *part = f->d_range_chunks;                 // 2 G exponent partials per chunk
+  int *scale = f->d_range + 2 * G;                // [0, 1] first chunk's scale, [2, 3] the whole vector's
   const int rg = (int)std::min<int64_t>(per, (int64_t)num_sms() * 8);
   for (int c = 0; c < nc; ++c) {
     HUB_CUDA(cudaStreamWaitEvent(s, ev_in[c], 0));
-    count_launch(h, 2);
-    k_max_exp<<<G, 256, 0, s>>>((b[c + 1] - b[c]) * n_up, xd + b[c] * n_up, emax + c * G);
-    k_f64_to_df<<<rg, 256, 0, s>>>(b[c], b[c + 1], n_up, f->ld, xd, emax, G, f->slot_row, f->xdf);
+    count_launch(h, c == 0 ? 3 : 2);
+    k_exp_range<<<G, 256, 0, s>>>((b[c + 1] - b[c]) * n_up, xd + b[c] * n_up, part + 2 * c * G);
+    if (c == 0) k_scale<<<1, 256, 0, s>>>(part, G, scale);
+    k_f64_to_df<<<rg, 256, 0, s>>>(b[c], b[c + 1], n_up, f->ld, xd, scale, f->slot_row, f->xdf);
     HUB_LAUNCH_CHECK();
     if ((rc = run_up(h, f, f->xdf, f->zdf, s, b[c] / 2, (b[c + 1] + 1) / 2))) return rc;
   }
   count_launch(h);
-  k_shift_check<<<1, 256, 0, s>>>(emax, nc * G, G, f->d_flag);
+  k_scale_all<<<1, 256, 0, s>>>(part, G, nc, scale, f->d_flag);
   HUB_LAUNCH_CHECK();
   HUB_CUDA(cudaMemcpyAsync(f->h_flag, f->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
   HUB_CUDA(cudaStreamSynchronize(s));
-  int nblk = G;
-  if (*f->h_flag) {   // the largest exponent lies outside the first chunk: redo with the global one
-    nblk = nc * G;
+  if (*f->h_flag == 2) {   // outside the double-float window: the FP64 kernel, one copy back
+    if ((rc = f64_apply(h, xd, yd, nullptr, s))) return rc;
+    HUB_CUDA(cudaMemcpyAsync(y_host, yd, sizeof(double) * n_dn * n_up, cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    return HUB_OK;
+  }
+  if (*f->h_flag == 1) {   // the largest exponent lies outside the first chunk: redo with the global one
     count_launch(h);
-    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, n_dn, n_up, f->ld, xd, emax, nblk, f->slot_row, f->xdf);
+    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, n_dn, n_up, f->ld, xd, scale + 2, f->slot_row, f->xdf);
     HUB_LAUNCH_CHECK();
     if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
   }
   if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s))) return rc;
   for (int c = 0; c < nc; ++c) {
     count_launch(h);
-    k_unpermute<<<rg, 512, 0, s>>>(b[c], b[c + 1], n_up, f->ld, f->zdf, f->slot_of, emax, nblk, yd);
+    k_unpermute<<<rg, 512, 0, s>>>(b[c], b[c + 1], n_up, f->ld, f->zdf, f->slot_of, scale + 2,
+                                   std::fabs(h->t[0]), yd);
     HUB_LAUNCH_CHECK();
     HUB_CUDA(cudaEventRecord(ev_out[c], s));
     HUB_CUDA(cudaStreamWaitEvent(sc, ev_out[c], 0));
@@ -1504,141 +1741,165 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   const int64_t n_dn_blocks = (int64_t)gd.x * gd.y;
   constexpr int kTmp = 2048;                      // first-stage slots of the alpha reduction
   if ((rc = ensure_partials(h, std::max<int64_t>(n_dn_blocks, G) + kTmp))) return rc;
-  if (!f->d_emax && !dev_alloc((void **)&f->d_emax, sizeof(int) * G, "exponent partials")) return HUB_ERR_OOM;
+  int *part = range_buf(f);
+  if (!part) return HUB_ERR_OOM;
+  int *scale = part + 2 * G;
   if (!h->d_scal && !dev_alloc((void **)&h->d_scal, sizeof(double) * 8, "Lanczos scalars")) return HUB_ERR_OOM;
   if (!h->h_scal) HUB_CUDA(cudaMallocHost((void **)&h->h_scal, sizeof(double) * 8));
   double *scal = h->d_scal, *P = h->partials;
   float2 *coef = f->coef;
 
-  // r_1 = x0 as double-float (no scaling), scal[1] = beta_0 = |x0|, scal[2] = 0
+  // r_1 = 2^-shift x0 as double-float (max |r_1| in [1, 2): the FP32 exponent range holds
+  // any scale of x0; entries below 2^-126 max |x0| lose bits, which E0 and psi do not
+  // notice), scal[1] = |r_1|, scal[0] = scal[2] = 0, coef[2] = 0 (no update before step 1)
+  const int64_t D = h->count[0] * h->count[1];
   auto start = [&](float *r) -> int {
-    count_launch(h, 3);
-    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, h->count[1], h->count[0], f->ld, x0, nullptr, 0, f->slot_row, r);
+    count_launch(h, 6);
+    k_exp_range<<<G, 256, 0, s>>>(D, x0, part);
+    k_scale<<<1, 256, 0, s>>>(part, G, scale);
+    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, h->count[1], h->count[0], f->ld, x0, scale, f->slot_row, r);
     k_df_norm2<<<G, 256, 0, s>>>(Q, r, P);
     HUB_LAUNCH_CHECK();
     int rc2 = reduce_partials(P, G, scal + 1, 1, s);
     if (rc2) return rc2;
-    HUB_CUDA(cudaMemsetAsync(scal + 2, 0, sizeof(double), s));
+    k_set_scal<<<1, 1, 0, s>>>(scal, 0, 0.0, 2, 0.0, -1, 0.0);
+    k_coeffs<<<1, 1, 0, s>>>(scal, coef);
+    HUB_LAUNCH_CHECK();
     return HUB_OK;
   };
-  // one step of the recurrence: w = H q_j - beta_prev q_{j-1}, alpha partials, then (with
-  // alpha in scal[0]) r_{j+1} = w - alpha q_j in place and |r_{j+1}|^2 partials
-  auto step_apply = [&](float *rp, float *rcur, float *w, cudaStream_t st) -> int {
-    count_launch(h);
-    k_coeffs<<<1, 1, 0, st>>>(scal, coef);
-    HUB_LAUNCH_CHECK();
+  // One step of the recurrence on (rp, wb, ot) = (r_{j-1}, w_{j-1}, free):
+  //   pass 1 forms r_j = w_{j-1} - (alpha_{j-1} / |r_{j-1}|) r_{j-1} over wb (fused update),
+  //   Z = (H_up + diag) r_j and |r_j|^2;  beta: scal[2] <- |r_{j-1}|, scal[1] <- |r_j|;
+  //   pass 2 writes w_j = H r_j / |r_j| - (|r_j| / |r_{j-1}|) r_{j-1} into ot and the alpha
+  //   partials <q_j, w_j>;  alpha_j -> scal[0], coef[2] <- -alpha_j / |r_j| for the next
+  //   step;  (alpha_j, |r_j|) to the pinned host scalars.  With full == false only pass 1
+  //   and the norm (the last step of the second pass).
+  auto iteration = [&](float *rp, float *wb, float *ot, cudaStream_t st, bool full) -> int {
     int rc2 = prof_mark(h, HUB_PROF_APPLY, true, st);
     if (rc2) return rc2;
-    if ((rc2 = run_up(h, f, rcur, f->zdf, st))) return rc2;
-    LzArgs L{rcur, rp, coef, scal + 6, P};
-    if ((rc2 = run_dn(h, f, 1, rcur, f->zdf, w, L, st))) return rc2;
-    return prof_mark(h, HUB_PROF_APPLY, false, st);
-  };
-  auto step_update = [&](float *rcur, float *w, cudaStream_t st) -> int {
+    const UpdArgs U{rp, coef, P};
+    int n_norm = 0;
+    if ((rc2 = run_up(h, f, wb, f->zdf, st, 0, -1, &U, &n_norm))) return rc2;
+    if ((rc2 = reduce_partials(P, n_norm, scal + 3, 1, st))) return rc2;
     count_launch(h, 2);
+    k_rotate_beta<<<1, 1, 0, st>>>(scal);
     k_coeffs<<<1, 1, 0, st>>>(scal, coef);
-    k_df_update<<<G, 256, 0, st>>>(Q, w, rcur, coef, P);
     HUB_LAUNCH_CHECK();
-    return HUB_OK;
-  };
-  // a whole first-pass iteration: alpha_j and beta_j into the pinned host scalars, then the
-  // device-side rotation of the betas
-  auto iteration = [&](float *rp, float *rcur, float *w, cudaStream_t st) -> int {
-    int rc2;
-    if ((rc2 = step_apply(rp, rcur, w, st))) return rc2;
+    if (!full) return prof_mark(h, HUB_PROF_APPLY, false, st);
+    LzArgs L{wb, rp, coef, scal + 6, P};
+    if ((rc2 = run_dn(h, f, 1, wb, f->zdf, ot, L, st))) return rc2;
+    if ((rc2 = prof_mark(h, HUB_PROF_APPLY, false, st))) return rc2;
     if ((rc2 = reduce_partials_2stage(P, (int)n_dn_blocks, P + std::max<int64_t>(n_dn_blocks, G), kTmp, scal + 0, 0,
                                       st)))
       return rc2;
-    if ((rc2 = step_update(rcur, w, st))) return rc2;
-    if ((rc2 = reduce_partials(P, G, scal + 3, 1, st))) return rc2;      // beta_j
-    HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     count_launch(h);
-    k_rotate_beta<<<1, 1, 0, st>>>(scal);
+    k_coeffs<<<1, 1, 0, st>>>(scal, coef);
     HUB_LAUNCH_CHECK();
+    HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     return HUB_OK;
   };
+  auto full_step = [&](float *rp, float *wb, float *ot, cudaStream_t st) -> int {
+    return iteration(rp, wb, ot, st, true);
+  };
 
-  float *rp = f->lz[0], *rcur = f->lz[1], *w = f->lz[2];
+  float *rp = f->lz[0], *wb = f->lz[1], *ot = f->lz[2];
   // Replay captured iterations unless profiling (event pairs per launch) is on; rows that
   // take the transposed pass 1 allocate on first use and are not captured.
-  const bool graphs = !h->prof && f->staged && lz_graphs(h, f, rp, rcur, w, iteration);
-  if ((rc = start(rcur))) return rc;
+  const bool graphs = !h->prof && f->staged && lz_graphs(h, f, rp, wb, ot, full_step);
+  if ((rc = start(wb))) return rc;
   HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float) * Dp, s));
   HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
+  int shift = 0;
+  HUB_CUDA(cudaMemcpyAsync(&shift, scale, sizeof(int), cudaMemcpyDeviceToHost, s));
   HUB_CUDA(cudaStreamSynchronize(s));
-  h->start_norm = h->h_scal[1];
+  h->start_norm = std::ldexp(h->h_scal[1], shift);   // |x0|
   if (!(h->h_scal[1] > 0.0) || !std::isfinite(h->h_scal[1]))
     return fail(HUB_ERR_ARG, "hub_lanczos_ground: start vector is zero or not finite");
 
   h->alpha.clear();
   h->beta.clear();
+  // the device recurrence runs on H / |t|: its alpha and beta times |t| are those of H
+  const double tabs = std::fabs(h->t[0]);
   double E = 0.0, E_prev = 0.0;
   int status = HUB_ERR_NOCONV;
+  float *last_r = nullptr, *last_w = nullptr;     // r_k and w_k of the last completed step
   for (int j = 0; j < maxit; ++j) {
     if (graphs) {
       HUB_CUDA(cudaGraphLaunch(f->lz_graph[j % 3], s));
-    } else if ((rc = iteration(rp, rcur, w, s))) {
+    } else if ((rc = full_step(rp, wb, ot, s))) {
       return rc;
     }
     HUB_CUDA(cudaStreamSynchronize(s));
-    const double a = h->h_scal[0], b = h->h_scal[3];
-    if (!std::isfinite(a) || !std::isfinite(b)) return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha/beta");
-    h->alpha.push_back(a);
-    h->beta.push_back(b);
+    const double a_dev = h->h_scal[0], r_dev = h->h_scal[1];   // alpha_{j+1}, |r_{j+1}| (1-based)
+    if (!std::isfinite(r_dev)) {
+      if ((rc = fast_check_error(h))) return rc;         // a given-up wait left the step incomplete
+      return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite beta");
+    }
+    if (j > 0) {
+      // |r_{j+1}| is beta_j, the coupling of q_j and q_{j+1}: on breakdown T_j is final and
+      // this step's alpha (formed with 1/beta_j) is dropped
+      h->beta.push_back(tabs * r_dev);
+      if (tabs * r_dev <= 1e-14 * std::fmax(1.0, std::fabs(h->alpha.back()))) {
+        status = HUB_CONVERGED_BREAKDOWN;
+        break;
+      }
+    }
+    if (!std::isfinite(a_dev)) {
+      if ((rc = fast_check_error(h))) return rc;
+      return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha");
+    }
+    h->alpha.push_back(tabs * a_dev);
+    last_r = wb;
+    last_w = ot;
     E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
     if (tol > 0 && j > 0 && std::fabs(E - E_prev) < tol) {
       status = HUB_OK;
       break;
     }
     E_prev = E;
-    if (b <= 1e-14 * std::fmax(1.0, std::fabs(a))) {
-      status = HUB_CONVERGED_BREAKDOWN;
-      break;
-    }
-    // r_{j-1} <- r_j <- r_{j+1} (the betas rotated on the device)
+    // r_{j-1} <- r_j <- w_j (the betas rotated on the device)
     float *t0 = rp;
-    rp = rcur;
-    rcur = w;
-    w = t0;
+    rp = wb;
+    wb = ot;
+    ot = t0;
   }
   if (tol <= 0 && status == HUB_ERR_NOCONV) status = HUB_OK;
   if ((rc = fast_check_error(h))) return rc;
+  if (status != HUB_CONVERGED_BREAKDOWN && last_r) {
+    // beta_k = |w_k - (alpha_k / |r_k|) r_k| (the next step's update, coef[2] already set), so
+    // that the coefficients returned are those of k full steps
+    count_launch(h);
+    k_df_update<<<G, 256, 0, s>>>(Q, last_w, last_r, coef, P);
+    HUB_LAUNCH_CHECK();
+    if ((rc = reduce_partials(P, G, scal + 3, 1, s))) return rc;
+    HUB_CUDA(cudaMemcpyAsync(h->h_scal + 3, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    h->beta.push_back(tabs * h->h_scal[3]);
+  }
   *E0 = E;
   const int k = (int)h->alpha.size();
   if (iters) *iters = k;
 
   if (psi_out) {
-    // second pass with the stored coefficients: psi = sum_j v_j q_j = sum_j v_j r_j / beta_{j-1}
+    // second pass, the same deterministic steps again: psi = sum_j v_j q_j = sum_j v_j r_j / |r_j|
     std::vector<double> vv = tridiag_vector(h->alpha.data(), h->beta.data(), k, psi_eigenvalue(h, E));
     if ((rc = ensure_vec(&f->psi, Dp, "ground-state vector"))) return rc;
     rp = f->lz[0];
-    rcur = f->lz[1];
-    w = f->lz[2];
-    if ((rc = start(rcur))) return rc;
+    wb = f->lz[1];
+    ot = f->lz[2];
+    if ((rc = start(wb))) return rc;
     HUB_CUDA(cudaMemsetAsync(rp, 0, sizeof(float) * Dp, s));
     HUB_CUDA(cudaMemsetAsync(f->psi, 0, sizeof(float) * Dp, s));
-    HUB_CUDA(cudaMemcpyAsync(h->h_scal + 1, scal + 1, sizeof(double), cudaMemcpyDeviceToHost, s));
-    HUB_CUDA(cudaStreamSynchronize(s));
-    double bc = h->h_scal[1];
     for (int j = 0; j < k; ++j) {
+      if ((rc = iteration(rp, wb, ot, s, j + 1 < k))) return rc;
       count_launch(h, 2);
       k_psi_coef<<<1, 1, 0, s>>>(scal, vv[j], coef);
-      k_df_axpy<<<G, 256, 0, s>>>(Q, coef, 3, rcur, f->psi);
+      k_df_axpy<<<G, 256, 0, s>>>(Q, coef, 3, wb, f->psi);
       HUB_LAUNCH_CHECK();
-      if (j + 1 == k) break;
-      if ((rc = step_apply(rp, rcur, w, s))) return rc;
-      count_launch(h);
-      k_set_scal<<<1, 1, 0, s>>>(scal, 0, h->alpha[j], -1, 0.0, -1, 0.0);
-      HUB_LAUNCH_CHECK();
-      if ((rc = step_update(rcur, w, s))) return rc;
-      count_launch(h);
-      k_set_scal<<<1, 1, 0, s>>>(scal, 1, h->beta[j], 2, bc, -1, 0.0);
-      HUB_LAUNCH_CHECK();
-      bc = h->beta[j];
       float *t0 = rp;
-      rp = rcur;
-      rcur = w;
-      w = t0;
+      rp = wb;
+      wb = ot;
+      ot = t0;
     }
     count_launch(h, 3);
     k_df_norm2<<<G, 256, 0, s>>>(Q, f->psi, P);

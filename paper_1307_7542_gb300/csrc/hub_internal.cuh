@@ -121,6 +121,7 @@ struct hub_ctx {
   // fast path (double-float, two-pass apply) for uniform hopping and interaction
   hub::FastState *fast = nullptr;
   int mode = 0;                        // HUB_MODE_AUTO or HUB_MODE_FP64
+  bool fail_waits = false;             // test hook: pass 1 reports a given-up wait (hub_test_fail_waits)
 
   // k = 0 sector of the translation i -> i-1 mod M (hub_set_symmetry); vectors are then in
   // row form, rows x cols (hub_k0.cu)
@@ -148,6 +149,9 @@ int reduce_partials_2stage(const double *partials, int n, double *tmp, int ntmp,
 
 // Apply entry used by Lanczos and the VJP (no argument checks).
 int apply_launch(hub_ctx *h, const double *x, double *y, cudaStream_t s);
+// The FP64 product kernel of the full sector; with a gate it does nothing unless gate[0] != 0
+// when it runs (a device flag written earlier on the stream).
+int f64_apply(hub_ctx *h, const double *x, double *y, const int *gate, cudaStream_t s);
 
 // Fast path (hub_fast.cu).
 bool fast_eligible(const hub_ctx *h);
