@@ -178,20 +178,15 @@ constexpr int64_t kNoAllocDoubles = (int64_t)kNoAllocMaxBlocks * kNoAllocMaxPara
 // 608 * 160 + 160 doubles = 779,520 bytes, held by every GPU that loads the library.
 static __device__ __align__(256) double g_grad_scratch[kNoAllocDoubles];
 
-// Device address of g_grad_scratch, looked up once per device with that device current.
-// In host code the symbol g_grad_scratch is only a host-side stand-in; kernels must be
-// given this address.
-constexpr int kMaxDevices = 64;
-static double *g_scratch_addr[kMaxDevices] = {nullptr};
-
-static int noalloc_scratch(int dev, double **out) {
-  if (dev < 0 || dev >= kMaxDevices) return fail(HUB_ERR_ARG, "hub_grad_noalloc: device ordinal out of range");
-  if (!g_scratch_addr[dev]) {
-    void *p = nullptr;
-    HUB_CUDA(cudaGetSymbolAddress(&p, g_grad_scratch));
-    g_scratch_addr[dev] = static_cast<double *>(p);
-  }
-  *out = g_scratch_addr[dev];
+// Device address of g_grad_scratch on the current device.  In host code the symbol
+// g_grad_scratch is only a host-side stand-in; kernels must be given this address.  It is
+// looked up on every call (a host-side lookup once the library's device code is loaded on
+// the device), so a context that was torn down and created again never sees a stale
+// address; the first call on a device may load that code, which places the array there.
+static int noalloc_scratch(double **out) {
+  void *p = nullptr;
+  HUB_CUDA(cudaGetSymbolAddress(&p, g_grad_scratch));
+  *out = static_cast<double *>(p);
   return HUB_OK;
 }
 
@@ -212,7 +207,7 @@ extern "C" int hub_grad_noalloc(hub_t h, const double *psi_dev, double *dE_dt_ho
   HUB_CUDA(cudaGetDevice(&dev));
   if (dev != h->device) return fail(HUB_ERR_ARG, "hub_grad_noalloc: the handle's device is not the current device");
   double *scratch = nullptr;
-  if ((rc = noalloc_scratch(dev, &scratch))) return rc;
+  if ((rc = noalloc_scratch(&scratch))) return rc;
 
   const Ham H = h->view();
   GradArgs G;

@@ -41,6 +41,31 @@ def test_noalloc_matches_hub_grad_twice(hub):
         m.close()
 
 
+def test_noalloc_allocates_no_device_memory(hub):
+    """Free device memory (cudaMemGetInfo) is unchanged across several calls on a fresh handle
+    that has run neither Lanczos nor hub_grad, so no lazily allocated scratch of the handle
+    exists; a first call on another handle has already loaded the library's device code."""
+    w = dict(W.disordered3x4(), n_up=5, n_dn=6)
+    warm = hub.Hubbard(w["M"], w["n_up"], w["n_dn"], w["bonds"], w["t"], w["U"], w["eps"])
+    m = hub.Hubbard(w["M"], w["n_up"], w["n_dn"], w["bonds"], w["t"], w["U"], w["eps"])
+    try:
+        v = torch.from_numpy(W.normal(9, m.D)).cuda()
+        hub.hub_grad_noalloc(warm.h, v, warm.n_bonds, warm.M)
+        torch.cuda.synchronize()
+        free0, _ = torch.cuda.mem_get_info()
+        got = [hub.hub_grad_noalloc(m.h, v, m.n_bonds, m.M) for _ in range(3)]
+        torch.cuda.synchronize()
+        free1, _ = torch.cuda.mem_get_info()
+        assert free1 == free0, (free0, free1)
+        ref = hub.hub_grad(m.h, v, m.n_bonds, m.M)
+        for g in got:
+            for a, b in zip(g, ref):
+                np.testing.assert_allclose(a, b, rtol=0, atol=1e-12 * max(1.0, np.abs(b).max()))
+    finally:
+        m.close()
+        warm.close()
+
+
 def test_noalloc_rejects_models_beyond_its_capacity(hub):
     """n_bonds + 2M above the fixed capacity (160) is refused with HUB_ERR_ARG."""
     M = 30
