@@ -64,6 +64,7 @@ SIGNATURES = {
     "hub_k_project": (_i, [_p, _p, _p, _p]),
     "hub_set_mode": (_i, [_p, _i]),
     "hub_check": (_i, [_p]),
+    "hub_test_fail_waits": (_i, [_p, _i]),
     "hub_profile": (_i, [_p, _i]),
     "hub_profile_read": (_i, [_p, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "hub_free": (None, [_p]),
@@ -328,6 +329,11 @@ def hub_check(h):
     _check(lib().hub_check(h))
 
 
+def hub_test_fail_waits(h, enable):
+    """Test hook: pass 1 takes its given-up-wait exit (see include/hub.h)."""
+    _check(lib().hub_test_fail_waits(h, 1 if enable else 0))
+
+
 def hub_free(h):
     if h:
         lib().hub_free(h)
@@ -360,6 +366,22 @@ class Hubbard:
         hub_hopping(self.h, self.bonds, self.t, self.eps if np.any(self.eps) else None)
         hub_set_U(self.h, self.U if np.any(self.U != self.U[0]) else self.U[:1])
         self.D = self.count_up * self.count_dn      # new parameters leave the k = 0 sector
+
+    def ensure_params(self, t, U, eps=None):
+        """set_params unless (t, U, eps) equal the current parameters and the model is in its
+        full sector: the hopping tables (and the captured Lanczos iterations that depend on
+        them) are then kept."""
+        nb = self.bonds.shape[0]
+        t = np.asarray(t, dtype=np.float64)
+        t = np.full(nb, float(t)) if t.ndim == 0 else t.reshape(nb)
+        U = np.asarray(U, dtype=np.float64)
+        U = np.full(self.M, float(U)) if U.ndim == 0 else U.reshape(self.M)
+        e = np.zeros(self.M) if eps is None else np.asarray(eps, dtype=np.float64).reshape(self.M)
+        same = (hasattr(self, "t") and np.array_equal(t, self.t) and np.array_equal(U, self.U)
+                and np.array_equal(e, self.eps) and self.D == self.count_up * self.count_dn)
+        if not same:
+            self.set_params(t, U, e)
+        return not same
 
     def set_symmetry(self, sym):
         """HUB_SYM_K0 / HUB_SYM_KPI: work in the k = 0 / k = pi sector of the translation
@@ -447,7 +469,7 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, model, x, t, U, eps):
-            model.set_params(t.detach().cpu().numpy(), U.detach().cpu().numpy(), eps.detach().cpu().numpy())
+            model.ensure_params(t.detach().cpu().numpy(), U.detach().cpu().numpy(), eps.detach().cpu().numpy())
             y = model.apply(x.detach().contiguous())
             ctx.model = model
             ctx.param_devices = (t.device, U.device, eps.device)
@@ -468,7 +490,7 @@ def _autograd():
 
         @staticmethod
         def forward(ctx, model, t, U, eps, x0, maxit, tol):
-            model.set_params(t.detach().cpu().numpy(), U.detach().cpu().numpy(), eps.detach().cpu().numpy())
+            model.ensure_params(t.detach().cpu().numpy(), U.detach().cpu().numpy(), eps.detach().cpu().numpy())
             r = model.ground(x0, maxit=maxit, tol=tol, want_psi=True)
             ctx.model = model
             ctx.psi = r["psi"]
