@@ -31,11 +31,18 @@ FALLBACK_HBM_GBS = 6800.0
 # flops, i.e. 152 SMs x 2 FP64 instructions/clock x 2.07 GHz = 0.629e12 instructions/s.
 FP64_INSTR_PEAK = 152 * 2 * 2.07e9
 SMEM_PEAK_TBS = 28.7          # shared-memory load bandwidth, conflict-free, all SMs (probe)
+# FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (a packed f32x2 instruction occupies two lanes)
+FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
+FP32_OPS_PER_TERM = 14        # compensated double-float sum: TwoSum, TwoSum of its error, two adds
 # DRAM bytes (read + write) per element of X from one ncu capture of the same kernels on the
-# 4x4 (6,6) sector (profiles/k_up_k_dn_4x4_sector66.md); the per-element traffic does not depend
-# on the sector, so a launch's traffic is this times D
-NCU_DRAM_BYTES_PER_ELEMENT = {"k_up": 0.981464e9 / 64128064, "k_dn": 2.136734e9 / 64128064}
+# 4x4 (6,6) sector (profiles/k_up_4x4_sector66.md, profiles/k_dn_4x4_sector66.md); the
+# per-element traffic does not depend on the sector, so a launch's traffic is this times D.
+# Empty until a capture of the current kernels exists (traffic is then reported as null).
+NCU_DRAM_BYTES_PER_ELEMENT = {}
 STAGE_MAX_COLS = 14076        # rows up to this length are staged in shared memory by pass 1
+# arithmetic of the timed fast path: vectors as pairs of FP32 numbers (48-bit significands),
+# compensated sums; FP64 at the interface
+DTYPE_FAST = "df32 (FP32 pairs, compensated sums; FP64 in/out)"
 
 
 def parse():
@@ -46,6 +53,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--U", type=float, default=4.0)
     p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--fp64-steps", type=int, default=10, help="Lanczos steps timed with HUB_MODE_FP64")
     p.add_argument("--lanczos-iters", type=int, default=200, help="iterations of the E0 wall-time run")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
     p.add_argument("--no-cpu-baseline", action="store_true")
@@ -485,11 +493,20 @@ def run_gpu(a):
              "fp64_equiv_rate_T": nnz_H / (apply_avg_ms / 1000.0) / 1e12,
              "fp64_alu_frac": nnz_H / (apply_avg_ms / 1000.0) / FP64_INSTR_PEAK}
     if n_up_l and n_dn_l:
-        # fast path: pass 1 reads X and writes Z (16 B/element); pass 2 (Lanczos epilogue)
-        # reads X by strips, Z, r_j, r_{j-1} and writes w (40 B/element)
+        # fast path.  HBM bytes per element: pass 1 with the fused Lanczos update reads w and
+        # r_{j-1} rows and writes r_j and Z (32 B); pass 2 (Lanczos epilogue) reads X by strips,
+        # Z, r_j, r_{j-1} and writes w (40 B).  FP32 pipe: each hopping term costs 14 FP32
+        # operations in the compensated double-float sum (both passes).
         up_avg, dn_avg = up_ms / n_up_l, dn_ms / n_dn_l
-        passes = {"k_up": {"ms": up_avg, "algorithmic_bytes": 16 * D, "gbs": gb(16 * D, up_avg)},
+        terms = {"k_up": nnz_u * m.count_dn, "k_dn": nnz_d * m.count_up}
+        passes = {"k_up": {"ms": up_avg, "algorithmic_bytes": 32 * D, "gbs": gb(32 * D, up_avg)},
                   "k_dn": {"ms": dn_avg, "algorithmic_bytes": 40 * D, "gbs": gb(40 * D, dn_avg)}}
+        for k_, v_ in passes.items():
+            ops = FP32_OPS_PER_TERM * terms[k_]
+            v_["hbm_frac"] = v_["gbs"] / hbm_gbs
+            v_["fp32_ops"] = ops
+            v_["fp32_tops"] = ops / (v_["ms"] / 1000.0) / 1e12
+            v_["fp32_frac"] = v_["fp32_tops"] / FP32_PEAK_TOPS
         if m.count_up <= STAGE_MAX_COLS:
             # pass 1 gathers from shared memory: 8 B (high and low word) per spin-up hop and
             # for the diagonal's own element, per element of X
@@ -500,12 +517,21 @@ def run_gpu(a):
                 "peak_source": "probe: conflict-free 64-bit shared loads, all SMs (GB300)"}
         dom = max(passes, key=lambda k: passes[k]["ms"])
         staged_4x4 = a.workload.startswith("4x4") and m.count_up <= STAGE_MAX_COLS
-        traffic = NCU_DRAM_BYTES_PER_ELEMENT[dom] * D if staged_4x4 else None
-        roofline = {"bound": "hbm", "kernel": dom, "achieved": passes[dom]["gbs"], "peak": hbm_gbs,
-                    "unit": "GB/s", "frac": passes[dom]["gbs"] / hbm_gbs, "traffic": traffic,
-                    "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel on "
-                                       "the 4x4 (6,6) sector, scaled by elements" if traffic else None),
-                    "peak_source": peak_src, "passes": passes, "apply": apply}
+        traffic = NCU_DRAM_BYTES_PER_ELEMENT[dom] * D if staged_4x4 and dom in NCU_DRAM_BYTES_PER_ELEMENT else None
+        pd = passes[dom]
+        if pd["fp32_frac"] >= pd["hbm_frac"]:
+            roofline = {"bound": "alu", "kernel": dom, "achieved": pd["fp32_tops"], "peak": FP32_PEAK_TOPS,
+                        "unit": "T FP32 op/s", "frac": pd["fp32_frac"],
+                        "peak_source": "derived: 152 SMs x 128 FP32 lanes x 2.07 GHz",
+                        "hbm": {"achieved": pd["gbs"], "peak": hbm_gbs, "unit": "GB/s", "frac": pd["hbm_frac"],
+                                "peak_source": peak_src}}
+        else:
+            roofline = {"bound": "hbm", "kernel": dom, "achieved": pd["gbs"], "peak": hbm_gbs, "unit": "GB/s",
+                        "frac": pd["hbm_frac"], "peak_source": peak_src}
+        roofline.update({"traffic": traffic,
+                         "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel "
+                                            "on the 4x4 (6,6) sector, scaled by elements" if traffic else None),
+                         "passes": passes, "apply": apply})
     else:
         # native FP64 kernel: bound by the FP64 pipe
         roofline = {"bound": "alu", "kernel": "k_apply_f64", "achieved": apply["fp64_equiv_rate_T"],
@@ -538,6 +564,32 @@ def run_gpu(a):
                 mc.close()
             lanczos["to_tol_1e-12"] = conv
 
+    # the same step with the native FP64 kernels (HUB_MODE_FP64): the path whose arithmetic is
+    # FP64 throughout, bound by the FP64 pipe
+    fp64_mode = None
+    if a.fp64_steps > 0:
+        hub.hub_set_mode(m.h, hub.HUB_MODE_FP64)
+        m.ground(x0, maxit=2, tol=0.0)
+        hub.hub_profile(m.h, True)
+        torch.cuda.synchronize()
+        f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        f0.record(stream)
+        rf = m.ground(x0, maxit=a.fp64_steps, tol=0.0)
+        f1.record(stream)
+        torch.cuda.synchronize()
+        f_ms = f0.elapsed_time(f1) / a.fp64_steps
+        fa_ms, fa_n, _ = hub.hub_profile_read(m.h, hub.HUB_PROF_APPLY)
+        hub.hub_profile(m.h, False)
+        hub.hub_set_mode(m.h, hub.HUB_MODE_AUTO)
+        fa = fa_ms / max(fa_n, 1)
+        fp64_mode = {"dtype": "f64", "kernel": "k_apply_f64", "steps": a.fp64_steps, "ms_per_step": f_ms,
+                     "applies_per_s": 1000.0 / f_ms, "apply_ms": fa,
+                     "apply_hbm_frac_16B_per_element": gb(16 * D, fa) / hbm_gbs,
+                     "fp64_instr_per_s_T": nnz_H / (fa / 1000.0) / 1e12,
+                     "fp64_pipe_frac": nnz_H / (fa / 1000.0) / FP64_INSTR_PEAK,
+                     "fp64_peak_source": "derived: 152 SMs x 2 FP64 instr/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
+                     "E0_after_steps": rf["E0"]}
+
     # end-to-end: the host-buffer apply through the C ABI (H2D + apply + D2H each step)
     e2e = None
     if a.e2e_steps > 0:
@@ -549,17 +601,36 @@ def run_gpu(a):
         for _ in range(a.e2e_steps):
             hub.hub_apply_host(m.h, xh, yh)
         e2e_s = time.perf_counter() - t0
+        # what the call is made of: one copy each way alone, and the device product alone
+        xd_ = torch.empty(D, dtype=torch.float64, device="cuda")
+        yd_ = torch.empty(D, dtype=torch.float64, device="cuda")
+        c0, c1, c2, c3 = (torch.cuda.Event(enable_timing=True) for _ in range(4))
+        xd_.copy_(xh, non_blocking=True)
+        torch.cuda.synchronize()
+        c0.record(stream)
+        xd_.copy_(xh, non_blocking=True)
+        c1.record(stream)
+        yh.copy_(yd_, non_blocking=True)
+        c2.record(stream)
+        hub.hub_apply(m.h, xd_, yd_)
+        c3.record(stream)
+        torch.cuda.synchronize()
+        h2d_ms, d2h_ms, dev_ms = c0.elapsed_time(c1), c1.elapsed_time(c2), c2.elapsed_time(c3)
+        call_ms = 1000 * e2e_s / a.e2e_steps
         e2e = {"value": world * a.e2e_steps / e2e_s, "unit": "applies/s",
                "h2d_bytes_per_step": 8 * D, "d2h_bytes_per_step": 8 * D,
-               "call": "hub_apply_host (pinned host x in, host y out)"}
-        del xh, yh
+               "call": "hub_apply_host (pinned host x in, host y out)", "ms_per_call": call_ms,
+               "h2d_gbs": gb(8 * D, h2d_ms), "d2h_gbs": gb(8 * D, d2h_ms), "hub_apply_device_ms": dev_ms,
+               "serial_ms": h2d_ms + dev_ms + d2h_ms,
+               "overlap_saved_ms": h2d_ms + dev_ms + d2h_ms - call_ms}
+        del xh, yh, xd_, yd_
 
     line = {"metric": "H.x applies/s (4x4 PBC half filling, U=4)",
             "value": value, "unit": "applies/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": config_json(w, D, world), "roofline": roofline, "lanczos_e0": lanczos,
-            "setup_s": setup_s, "e2e": e2e, "gpu_launches": n_kern, "clocks": clk}
+            "vs_baseline": None, "dtype": DTYPE_FAST if n_up_l else "f64", "data": "synthetic",
+            "config": config_json(w, D, world), "roofline": roofline, "fp64_mode": fp64_mode,
+            "lanczos_e0": lanczos, "setup_s": setup_s, "e2e": e2e, "gpu_launches": n_kern, "clocks": clk}
 
     if rank == 0 and world == 1 and not a.no_cpu_baseline and a.e2e_steps >= 0:
         aps, R, el, thr, _, _ = oracle_sample(w, x_host, a.cpu_seconds)
