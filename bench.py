@@ -34,11 +34,10 @@ SMEM_PEAK_TBS = 28.7          # shared-memory load bandwidth, conflict-free, all
 # FP32 pipe: 152 SMs x 128 lanes x 2.07 GHz (a packed f32x2 instruction occupies two lanes)
 FP32_PEAK_TOPS = 152 * 128 * 2.07e9 / 1e12
 FP32_OPS_PER_TERM = 14        # compensated double-float sum: TwoSum, TwoSum of its error, two adds
-# DRAM bytes (read + write) per element of X from one ncu capture of the same kernels on the
-# 4x4 (6,6) sector (profiles/k_up_4x4_sector66.md, profiles/k_dn_4x4_sector66.md); the
+# DRAM bytes (read + write) per element of X from one ncu capture of each kernel on the 4x4
+# (6,6) sector (profiles/k_up_4x4_sector66.md, profiles/k_dn_4x4_sector66.md); the
 # per-element traffic does not depend on the sector, so a launch's traffic is this times D.
-# Empty until a capture of the current kernels exists (traffic is then reported as null).
-NCU_DRAM_BYTES_PER_ELEMENT = {}
+NCU_DRAM_BYTES_PER_ELEMENT = {"k_up": 0.981968e9 / 64128064, "k_dn": 2.078456e9 / 64128064}
 STAGE_MAX_COLS = 14076        # rows up to this length are staged in shared memory by pass 1
 # arithmetic of the timed fast path: vectors as pairs of FP32 numbers (48-bit significands),
 # compensated sums; FP64 at the interface
@@ -52,7 +51,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--U", type=float, default=4.0)
-    p.add_argument("--e2e-steps", type=int, default=5)
+    p.add_argument("--e2e-steps", type=int, default=8)
     p.add_argument("--fp64-steps", type=int, default=10, help="Lanczos steps timed with HUB_MODE_FP64")
     p.add_argument("--lanczos-iters", type=int, default=200, help="iterations of the E0 wall-time run")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -597,10 +596,12 @@ def run_gpu(a):
         yh = torch.empty(D, dtype=torch.float64).pin_memory()
         hub.hub_apply_host(m.h, xh, yh)
         torch.cuda.synchronize()
-        t0 = time.perf_counter()
+        calls = []
         for _ in range(a.e2e_steps):
+            t0 = time.perf_counter()
             hub.hub_apply_host(m.h, xh, yh)
-        e2e_s = time.perf_counter() - t0
+            calls.append(time.perf_counter() - t0)
+        e2e_s = sum(calls)
         # what the call is made of: one copy each way alone, and the device product alone
         xd_ = torch.empty(D, dtype=torch.float64, device="cuda")
         yd_ = torch.empty(D, dtype=torch.float64, device="cuda")
@@ -622,7 +623,9 @@ def run_gpu(a):
                "call": "hub_apply_host (pinned host x in, host y out)", "ms_per_call": call_ms,
                "h2d_gbs": gb(8 * D, h2d_ms), "d2h_gbs": gb(8 * D, d2h_ms), "hub_apply_device_ms": dev_ms,
                "serial_ms": h2d_ms + dev_ms + d2h_ms,
-               "overlap_saved_ms": h2d_ms + dev_ms + d2h_ms - call_ms}
+               "overlap_saved_ms": h2d_ms + dev_ms + d2h_ms - call_ms,
+               "call_ms_min_median_max": [1000 * min(calls), 1000 * sorted(calls)[len(calls) // 2],
+                                          1000 * max(calls)]}
         del xh, yh, xd_, yd_
 
     line = {"metric": "H.x applies/s (4x4 PBC half filling, U=4)",
