@@ -175,6 +175,25 @@ int hub_lanczos_spectrum(hub_t h, const double *x0_dev, int maxit, int n_eig, do
                          int *n_found, void *stream);
 
 /*
+ * Low-lying levels with their multiplicities by block Lanczos (Sec. IV's recurrence on a block
+ * of k start vectors; a single start vector finds each degenerate level once).  X0_dev: k
+ * vectors of the handle's vector length, contiguous (vector c at c * length), linearly
+ * independent; NULL: SplitMix64 uniform [-1, 1) vectors (counter offset c * length, so the
+ * first equals hub_lanczos_ground's default).  steps block steps of
+ *   W = H Q_j - Q_{j-1} B_{j-1}^T, A_j = Q_j^T W, W -= Q_j A_j, full re-orthogonalisation
+ *   against all earlier blocks (twice), Q_{j+1} B_j = W (Cholesky QR, twice),
+ * then the eigenvalues of the block-tridiagonal matrix of the A_j and B_j (dense, on the host):
+ * the lowest min(n_eig, k * steps) into eig_host, ascending, a level of multiplicity g <= k
+ * appearing g times, and, if resid_host != NULL, the residual norms |H y - theta y| of their
+ * Ritz vectors (|B_m s_m|; 0 when the space became invariant, which ends the steps early).
+ * 1 <= k <= 8, k * steps <= 512.  Device memory: (steps + 2) * k vectors, allocated and freed
+ * by the call.  Products as hub_apply (fast or FP64 path); works inside a momentum sector.
+ * Blocks until done; *n_found = number of values written.
+ */
+int hub_lanczos_block(hub_t h, int k, const double *X0_dev, int steps, int n_eig, double *eig_host,
+                      double *resid_host, int *n_found, void *stream);
+
+/*
  * Eigenvector of a low-lying excited state (Sec. IV): maxit steps of the plain recurrence
  * from x0_dev (NULL: the seeded start vector), then the second pass of hub_lanczos_ground
  * forms the normalised Ritz vector psi_dev (device, count_up * count_dn) for the eigenvalue

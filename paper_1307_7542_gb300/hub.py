@@ -49,6 +49,7 @@ SIGNATURES = {
     "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
     "hub_lanczos_spectrum": (_i, [_p, _p, _i, _i, _p, _p, ctypes.POINTER(_i), _p]),
     "hub_lanczos_ritz": (_i, [_p, _p, _i, _d, _p, ctypes.POINTER(_d), _p]),
+    "hub_lanczos_block": (_i, [_p, _i, _p, _i, _i, _p, _p, ctypes.POINTER(_i), _p]),
     "hub_ladder": (_i, [_p, _p, _i, _i, _i, _p, _p, _p]),
     "hub_green_coeffs": (_i, [_p, _p, _i, _p, _p, ctypes.POINTER(_d), ctypes.POINTER(_i), _p]),
     "hub_green_eval": (_i, [_i, _p, _p, _d, _d, _i, _i, _p, _p, _p, _p]),
@@ -200,6 +201,16 @@ def hub_lanczos_spectrum(h, x0, maxit, n_eig, stream=None):
     n = _i()
     _check(lib().hub_lanczos_spectrum(h, _ptr(x0), maxit, n_eig, _ptr(e), _ptr(r), ctypes.byref(n),
                                       _stream(stream)))
+    return e[: n.value], r[: n.value]
+
+
+def hub_lanczos_block(h, k, X0, steps, n_eig, stream=None):
+    """Lowest n_eig eigenvalues with multiplicity (block Lanczos, block size k) and the
+    residual norms of their Ritz vectors."""
+    e, r = np.empty(n_eig), np.empty(n_eig)
+    n = _i()
+    _check(lib().hub_lanczos_block(h, k, _ptr(X0), steps, n_eig, _ptr(e), _ptr(r), ctypes.byref(n),
+                                   _stream(stream)))
     return e[: n.value], r[: n.value]
 
 

@@ -85,6 +85,7 @@ def test_null_handles_are_refused(libpath):
         "hub_lanczos_coeffs": lambda: L.hub_lanczos_coeffs(None, None, None, 0, ctypes.byref(n)),
         "hub_lanczos_spectrum": lambda: L.hub_lanczos_spectrum(None, None, 10, 1, None, None, ctypes.byref(n), None),
         "hub_lanczos_ritz": lambda: L.hub_lanczos_ritz(None, None, 10, 0.0, None, ctypes.byref(d), None),
+        "hub_lanczos_block": lambda: L.hub_lanczos_block(None, 2, None, 10, 1, buf, None, ctypes.byref(n), None),
         "hub_green_coeffs": lambda: L.hub_green_coeffs(None, None, 1, None, None, ctypes.byref(d), ctypes.byref(n), None),
         "hub_ladder": lambda: L.hub_ladder(None, None, 0, 0, 1, None, None, None),
         "hub_grad": lambda: L.hub_grad(None, None, None, None, None, None),
