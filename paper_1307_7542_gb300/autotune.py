@@ -11,6 +11,7 @@ shapes from compile-time knobs:
 * ``HUB_FUSED_UPDATE`` -- 1: the Lanczos update r_j = w - c r_{j-1} is formed by pass 1 while
   it stages the rows; 0: a separate vector pass before pass 1;
 * ``HUB_UPD_Q``        -- column quads per thread whose loads the fused update issues together;
+* ``HUB_UP_THREADS``   -- threads of the pass-1 CTA (1024, 768 or 512; fewer leave more registers);
 * ``HUB_BATCH_THREADS`` -- threads per CTA of the batched persistent solver.
 
 For each candidate setting this module builds one copy of the library, times on the GPU what
@@ -43,10 +44,11 @@ APPLY_SPACE = {
     "HUB_BANK_CAP": [2, 3, 0, -2],
     "HUB_FUSED_UPDATE": [1, 0],
     "HUB_UPD_Q": [1, 2],
+    "HUB_UP_THREADS": [1024, 768, 512],
 }
 BATCH_SPACE = {"HUB_BATCH_THREADS": [256, 512, 1024]}
 DEFAULTS = {"HUB_DN_LANE_COLS": 4, "HUB_DN_BATCH": 2, "HUB_DN_MINB": 4, "HUB_BANK_CAP": 2,
-            "HUB_FUSED_UPDATE": 1, "HUB_UPD_Q": 1, "HUB_BATCH_THREADS": 256}
+            "HUB_FUSED_UPDATE": 0, "HUB_UPD_Q": 1, "HUB_UP_THREADS": 1024, "HUB_BATCH_THREADS": 256}
 MARGIN = 0.01
 
 

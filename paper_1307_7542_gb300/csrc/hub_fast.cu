@@ -329,7 +329,15 @@ __device__ __forceinline__ double df2_lanes_to_f64(f2x h, f2x l) {
 #ifndef HUB_FUSED_UPDATE
 #define HUB_FUSED_UPDATE 1   // 0: the Lanczos update as a separate vector pass before pass 1
 #endif
+#ifndef HUB_UP_THREADS
+#define HUB_UP_THREADS 1024   // threads of the pass-1 CTA (one CTA per SM; fewer leave more registers)
+#endif
+constexpr int kUpThreads = HUB_UP_THREADS;
+static_assert(kUpThreads % 32 == 0 && kUpThreads >= 512 && kUpThreads <= 1024, "pass-1 CTA size");
 constexpr int kUpdQ = HUB_UPD_Q;
+// Lanczos steps per host read-back for sectors of at most kBatchStepsMaxDim states
+constexpr int kMaxBatchSteps = 8;
+constexpr int64_t kBatchStepsMaxDim = 1 << 21;
 constexpr bool kFusedUpdate = HUB_FUSED_UPDATE != 0;
 
 struct UpdArgs {
@@ -339,7 +347,7 @@ struct UpdArgs {
 };
 
 template <typename Col, bool kUpd>
-__global__ void __launch_bounds__(1024, 1) k_up(const FastView F, float *x, float *__restrict__ z,
+__global__ void __launch_bounds__(kUpThreads, 1) k_up(const FastView F, float *x, float *__restrict__ z,
                                                 int64_t p_begin, int64_t p_end, UpdArgs U) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   float *xs = reinterpret_cast<float *>(smem_raw);
@@ -647,6 +655,17 @@ __global__ void k_set_scal(double *__restrict__ scal, int i0, double v0, int i1,
   if (i0 >= 0) scal[i0] = v0;
   if (i1 >= 0) scal[i1] = v1;
   if (i2 >= 0) scal[i2] = v2;
+}
+
+// Appends (alpha, |r|) = (scal[0], scal[1]) to hist (room for cap pairs) at the count kept
+// in scal[7], so that several steps can run between two host read-backs.
+__global__ void k_record(double *__restrict__ scal, double *__restrict__ hist, int cap) {
+  const int i = (int)scal[7];
+  if (i >= 0 && i < cap) {
+    hist[2 * i] = scal[0];
+    hist[2 * i + 1] = scal[1];
+  }
+  scal[7] = (double)(i + 1);
 }
 
 __device__ __forceinline__ f2x ld2(const float *p) { return *reinterpret_cast<const f2x *>(p); }
@@ -1029,6 +1048,7 @@ struct FastState {
   float *lz[3] = {nullptr, nullptr, nullptr};
   float *psi = nullptr;
   int *d_range = nullptr;                    // exponent partials [2 G], then scale[4] (k_scale)
+  double *d_hist = nullptr, *h_hist = nullptr;  // (alpha, |r|) of the steps since the last read-back
   int *d_err = nullptr;
   int64_t ld = 0;
   // pipelined host-buffer apply: copy stream, per-chunk events, exponent partials, flag
@@ -1060,6 +1080,8 @@ void fast_release(hub_ctx *h) {
   for (int k = 0; k < 3; ++k) dev_free(f->lz[k]);
   dev_free(f->psi);
   dev_free(f->d_range);
+  dev_free(f->d_hist);
+  if (f->h_hist) cudaFreeHost(f->h_hist);
   dev_free(f->d_err);
   dev_free(f->d_range_chunks);
   dev_free(f->d_flag);
@@ -1448,7 +1470,7 @@ static int run_up(hub_ctx *h, FastState *f, float *x, float *z, cudaStream_t s, 
   }
   if (f->staged) {
     count_launch(h);
-    const int threads = v.n_up >= 4096 ? 1024 : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
+    const int threads = v.n_up >= 4096 ? kUpThreads : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));
     const int grid = (int)std::min<int64_t>(p1 - p0, (int64_t)num_sms());
     const size_t smem = up_smem(f);
     const UpdArgs U = fused ? *upd : UpdArgs{};
@@ -1772,7 +1794,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   //   Z = (H_up + diag) r_j and |r_j|^2;  beta: scal[2] <- |r_{j-1}|, scal[1] <- |r_j|;
   //   pass 2 writes w_j = H r_j / |r_j| - (|r_j| / |r_{j-1}|) r_{j-1} into ot and the alpha
   //   partials <q_j, w_j>;  alpha_j -> scal[0], coef[2] <- -alpha_j / |r_j| for the next
-  //   step;  (alpha_j, |r_j|) to the pinned host scalars.  With full == false only pass 1
+  //   step;  (alpha_j, |r_j|) appended to the step record.  With full == false only pass 1
   //   and the norm (the last step of the second pass).
   auto iteration = [&](float *rp, float *wb, float *ot, cudaStream_t st, bool full) -> int {
     int rc2 = prof_mark(h, HUB_PROF_APPLY, true, st);
@@ -1792,10 +1814,10 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
     if ((rc2 = reduce_partials_2stage(P, (int)n_dn_blocks, P + std::max<int64_t>(n_dn_blocks, G), kTmp, scal + 0, 0,
                                       st)))
       return rc2;
-    count_launch(h);
+    count_launch(h, 2);
     k_coeffs<<<1, 1, 0, st>>>(scal, coef);
+    k_record<<<1, 1, 0, st>>>(scal, f->d_hist, kMaxBatchSteps);
     HUB_LAUNCH_CHECK();
-    HUB_CUDA(cudaMemcpyAsync(h->h_scal, scal, 4 * sizeof(double), cudaMemcpyDeviceToHost, st));
     return HUB_OK;
   };
   auto full_step = [&](float *rp, float *wb, float *ot, cudaStream_t st) -> int {
@@ -1803,6 +1825,10 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   };
 
   float *rp = f->lz[0], *wb = f->lz[1], *ot = f->lz[2];
+  float *const vecs[3] = {f->lz[0], f->lz[1], f->lz[2]};   // step j works on (vecs[j%3], [j+1], [j+2])
+  if (!f->d_hist && !dev_alloc((void **)&f->d_hist, sizeof(double) * 2 * kMaxBatchSteps, "step record"))
+    return HUB_ERR_OOM;
+  if (!f->h_hist) HUB_CUDA(cudaMallocHost((void **)&f->h_hist, sizeof(double) * 2 * kMaxBatchSteps));
   // Replay captured iterations unless profiling (event pairs per launch) is on; rows that
   // take the transposed pass 1 allocate on first use and are not captured.
   const bool graphs = !h->prof && f->staged && lz_graphs(h, f, rp, wb, ot, full_step);
@@ -1820,61 +1846,79 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   h->beta.clear();
   // the device recurrence runs on H / |t|: its alpha and beta times |t| are those of H
   const double tabs = std::fabs(h->t[0]);
+  // Small sectors run several steps per host read-back (a step costs less than the read-back's
+  // latency); the steps after the stopping one are discarded, so E0, the iteration count and
+  // the coefficients are those of one step per read-back.
+  const int batch = D <= kBatchStepsMaxDim ? kMaxBatchSteps : 1;
   double E = 0.0, E_prev = 0.0;
   int status = HUB_ERR_NOCONV;
-  float *last_r = nullptr, *last_w = nullptr;     // r_k and w_k of the last completed step
-  for (int j = 0; j < maxit; ++j) {
-    if (graphs) {
-      HUB_CUDA(cudaGraphLaunch(f->lz_graph[j % 3], s));
-    } else if ((rc = full_step(rp, wb, ot, s))) {
-      return rc;
-    }
-    HUB_CUDA(cudaStreamSynchronize(s));
-    const double a_dev = h->h_scal[0], r_dev = h->h_scal[1];   // alpha_{j+1}, |r_{j+1}| (1-based)
-    if (!std::isfinite(r_dev)) {
-      if ((rc = fast_check_error(h))) return rc;         // a given-up wait left the step incomplete
-      return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite beta");
-    }
-    if (j > 0) {
-      // |r_{j+1}| is beta_j, the coupling of q_j and q_{j+1}: on breakdown T_j is final and
-      // this step's alpha (formed with 1/beta_j) is dropped
-      h->beta.push_back(tabs * r_dev);
-      if (tabs * r_dev <= 1e-14 * std::fmax(1.0, std::fabs(h->alpha.back()))) {
-        status = HUB_CONVERGED_BREAKDOWN;
-        break;
+  int computed = 0;                                // steps run on the device
+  bool done = false;
+  for (int j = 0; j < maxit && !done;) {
+    const int nb = std::min(batch, maxit - j);
+    count_launch(h);
+    k_set_scal<<<1, 1, 0, s>>>(scal, 7, 0.0, -1, 0.0, -1, 0.0);
+    HUB_LAUNCH_CHECK();
+    for (int b = 0; b < nb; ++b) {
+      const int jj = j + b;
+      if (graphs) {
+        HUB_CUDA(cudaGraphLaunch(f->lz_graph[jj % 3], s));
+      } else if ((rc = full_step(vecs[jj % 3], vecs[(jj + 1) % 3], vecs[(jj + 2) % 3], s))) {
+        return rc;
       }
     }
-    if (!std::isfinite(a_dev)) {
-      if ((rc = fast_check_error(h))) return rc;
-      return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha");
+    HUB_CUDA(cudaMemcpyAsync(f->h_hist, f->d_hist, sizeof(double) * 2 * nb, cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    computed = j + nb;
+    for (int b = 0; b < nb && !done; ++b) {
+      const int jj = j + b;
+      const double a_dev = f->h_hist[2 * b], r_dev = f->h_hist[2 * b + 1];   // alpha_{jj+1}, |r_{jj+1}|
+      if (!std::isfinite(r_dev)) {
+        if ((rc = fast_check_error(h))) return rc;       // a given-up wait left the step incomplete
+        return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite beta");
+      }
+      if (jj > 0) {
+        // |r_{jj+1}| is beta_jj, the coupling of q_jj and q_{jj+1}: on breakdown T_jj is final
+        // and this step's alpha (formed with 1/beta_jj) is dropped
+        h->beta.push_back(tabs * r_dev);
+        if (tabs * r_dev <= 1e-14 * std::fmax(1.0, std::fabs(h->alpha.back()))) {
+          status = HUB_CONVERGED_BREAKDOWN;
+          done = true;
+          break;
+        }
+      }
+      if (!std::isfinite(a_dev)) {
+        if ((rc = fast_check_error(h))) return rc;
+        return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha");
+      }
+      h->alpha.push_back(tabs * a_dev);
+      E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
+      if (tol > 0 && jj > 0 && std::fabs(E - E_prev) < tol) {
+        status = HUB_OK;
+        done = true;
+        break;
+      }
+      E_prev = E;
     }
-    h->alpha.push_back(tabs * a_dev);
-    last_r = wb;
-    last_w = ot;
-    E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
-    if (tol > 0 && j > 0 && std::fabs(E - E_prev) < tol) {
-      status = HUB_OK;
-      break;
-    }
-    E_prev = E;
-    // r_{j-1} <- r_j <- w_j (the betas rotated on the device)
-    float *t0 = rp;
-    rp = wb;
-    wb = ot;
-    ot = t0;
+    j += nb;
   }
   if (tol <= 0 && status == HUB_ERR_NOCONV) status = HUB_OK;
   if ((rc = fast_check_error(h))) return rc;
-  if (status != HUB_CONVERGED_BREAKDOWN && last_r) {
-    // beta_k = |w_k - (alpha_k / |r_k|) r_k| (the next step's update, coef[2] already set), so
-    // that the coefficients returned are those of k full steps
-    count_launch(h);
-    k_df_update<<<G, 256, 0, s>>>(Q, last_w, last_r, coef, P);
-    HUB_LAUNCH_CHECK();
-    if ((rc = reduce_partials(P, G, scal + 3, 1, s))) return rc;
-    HUB_CUDA(cudaMemcpyAsync(h->h_scal + 3, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
-    HUB_CUDA(cudaStreamSynchronize(s));
-    h->beta.push_back(tabs * h->h_scal[3]);
+  const int last = (int)h->alpha.size() - 1;        // 0-based index of the last kept step
+  if (status != HUB_CONVERGED_BREAKDOWN && last >= 0) {
+    // beta_k = |w_k - (alpha_k / |r_k|) r_k|: recorded by the following step if it ran in the
+    // same batch, else formed now by that step's update (coef[2] is still the last step's)
+    if (last + 1 < computed && (last + 1) / batch == last / batch) {
+      h->beta.push_back(tabs * f->h_hist[2 * ((last + 1) % batch) + 1]);
+    } else {
+      count_launch(h);
+      k_df_update<<<G, 256, 0, s>>>(Q, vecs[(last + 2) % 3], vecs[(last + 1) % 3], coef, P);
+      HUB_LAUNCH_CHECK();
+      if ((rc = reduce_partials(P, G, scal + 3, 1, s))) return rc;
+      HUB_CUDA(cudaMemcpyAsync(h->h_scal + 3, scal + 3, sizeof(double), cudaMemcpyDeviceToHost, s));
+      HUB_CUDA(cudaStreamSynchronize(s));
+      h->beta.push_back(tabs * h->h_scal[3]);
+    }
   }
   *E0 = E;
   const int k = (int)h->alpha.size();
