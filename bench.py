@@ -404,6 +404,50 @@ def extras(hub, W, torch):
                     "E0": r8["E0"], "iterations": r8["iters"], "lanczos_ground_ms": 1000 * min(reps8),
                     "batched_single_job_E0": float(Eb[0]), "batched_single_job_iterations": int(itb[0]),
                     "batched_single_job_ms": 1000 * min(reps_b)}
+    # (7b) block Lanczos at 4x4 (8,8): a block step applies H to k vectors with the same product
+    # kernels (k products, FP64 in and out) plus the FP64 block Gram/QR work and the full
+    # re-orthogonalisation; timed against k single Lanczos steps of hub_lanczos_ground on the
+    # same handle, with the products inside the block step timed separately
+    w = W.square4x4(4.0)
+    mb = hub.Hubbard(16, 8, 8, w["bonds"], w["t"], w["U"], w["eps"])
+    x0b = torch.from_numpy(W.normal(0, mb.D)).cuda()
+    mb.ground(x0b, maxit=3, tol=0.0)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    mb.ground(x0b, maxit=6, tol=0.0)
+    torch.cuda.synchronize()
+    single_ms = 1000 * (time.perf_counter() - t0) / 6
+    del x0b
+    blk = {"workload": "4x4 PBC (8,8), U=4", "single_step_ms": single_ms}
+    # one product alone (FP64 in and out, as the block solver calls it)
+    xa = torch.from_numpy(W.normal(1, mb.D)).cuda()
+    ya = torch.empty_like(xa)
+    hub.hub_apply(mb.h, xa, ya)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for _ in range(4):
+        hub.hub_apply(mb.h, xa, ya)
+    torch.cuda.synchronize()
+    apply_ms = 1000 * (time.perf_counter() - t0) / 4
+    del xa, ya
+    blk["single_product_ms"] = apply_ms
+    for kb in (2, 4):
+        hub.hub_profile(mb.h, True)
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        evb, rsb = hub.hub_lanczos_block(mb.h, kb, None, 3, kb)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        pa_ms, pa_n, _ = hub.hub_profile_read(mb.h, hub.HUB_PROF_APPLY)
+        hub.hub_profile(mb.h, False)
+        blk[f"k={kb}"] = {"steps": 3, "ms_per_block_step": 1000 * el / 3,
+                          "products_per_block_step": pa_n / 3, "product_ms_in_block": pa_ms / max(pa_n, 1),
+                          "products_ms_per_block_step": pa_ms / 3,
+                          "block_work_ms_per_block_step": 1000 * el / 3 - pa_ms / 3,
+                          "vs_k_single_steps": (1000 * el / 3) / (kb * single_ms)}
+    mb.close()
+    torch.cuda.empty_cache()
+    out["block_lanczos_4x4"] = blk
     # (7) the 4x4 torus (the benchmark lattice) in its four real-momentum sectors of the two
     # translations, U = 4, each to |dE0| < 1e-12; the lowest is the full sector's ground state
     tor = {}
