@@ -620,6 +620,7 @@ struct Side {
   int64_t n_rows, n_cols, ld;
   const int32_t *rp, *sp;            // sign-split CSR of this side's hopping matrix
   const void *col;
+  int64_t r_begin = 0;               // first row a launch covers (rows r_begin .. n_rows - 1)
 };
 
 struct LzArgs {                      // Lanczos epilogue operands
@@ -779,7 +780,7 @@ __global__ void __launch_bounds__(kDnThreads, HUB_DN_MINB) k_dn(const FastView F
     __syncthreads();
   }
   const int64_t u = (int64_t)blockIdx.y * kDnCols + kDnLaneCols * lane;
-  const int64_t r0 = (int64_t)blockIdx.x * kDnRows;
+  const int64_t r0 = S.r_begin + (int64_t)blockIdx.x * kDnRows;
   const uint32_t row_bytes = (uint32_t)(2 * ld * sizeof(float));
   DfAcc2 dacc{0ull, 0ull};
   const bool active = u < S.n_cols;                    // u + kDnLaneCols <= ld (see fast_build)
@@ -1415,7 +1416,7 @@ static Side side_up(const hub_ctx *h, const FastState *f) {
 }
 
 static dim3 dn_grid(const Side &S) {
-  return dim3((unsigned)((S.n_rows + kDnRows - 1) / kDnRows), (unsigned)((S.n_cols + kDnCols - 1) / kDnCols));
+  return dim3((unsigned)((S.n_rows - S.r_begin + kDnRows - 1) / kDnRows), (unsigned)((S.n_cols + kDnCols - 1) / kDnCols));
 }
 
 template <typename Col, int kMode>
@@ -1498,13 +1499,17 @@ static int run_up(hub_ctx *h, FastState *f, float *x, float *z, cudaStream_t s, 
   return prof_mark(h, HUB_PROF_UP, false, s);
 }
 
+// pass 2 on the rows r0 .. r1 - 1 of X (r1 < 0: all rows)
 static int run_dn(hub_ctx *h, FastState *f, int mode, const float *x, const float *z, float *w, LzArgs L,
-                  cudaStream_t s) {
+                  cudaStream_t s, int64_t r0 = 0, int64_t r1 = -1) {
   const FastView v = fast_view(h, f);
   count_launch(h);
   int rc = prof_mark(h, HUB_PROF_DN, true, s);
   if (rc) return rc;
-  const Side S = side_dn(h, f);
+  Side S = side_dn(h, f);
+  S.r_begin = r0;
+  if (r1 >= 0) S.n_rows = r1;
+  if (S.n_rows <= S.r_begin) return prof_mark(h, HUB_PROF_DN, false, s);
   rc = mode == 0 ? launch_dn<0>(f, v, S, x, z, w, L, s) : launch_dn<1>(f, v, S, x, z, w, L, s);
   if (rc) return rc;
   return prof_mark(h, HUB_PROF_DN, false, s);
@@ -1652,8 +1657,10 @@ static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double 
     HUB_LAUNCH_CHECK();
     if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
   }
-  if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s))) return rc;
+  // pass 2 in the same row chunks, so that each chunk's result goes back while the next is
+  // computed (every chunk reads the whole of X by strips; X is read from HBM once per chunk)
   for (int c = 0; c < nc; ++c) {
+    if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s, b[c], b[c + 1]))) return rc;
     count_launch(h);
     k_unpermute<<<rg, 512, 0, s>>>(b[c], b[c + 1], n_up, f->ld, f->zdf, f->slot_of, scale + 2,
                                    std::fabs(h->t[0]), yd);
