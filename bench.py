@@ -375,20 +375,27 @@ def extras(hub, W, torch):
         r["terms_per_s"] = terms * r["vector_len"] / (r["apply_ms"] / 1000)
         r["as_fp64_fma_frac_of_fp64_issue"] = r["terms_per_s"] / FP64_INSTR_PEAK
     # (6) the 8-site ring at half filling (D = 4900), E0 to |dE0| < 1e-12 from a seed-0 normal
-    # start vector: latency-bound; through hub_lanczos_ground (one host read-back of alpha and
-    # beta per iteration) and as a single job of the persistent batched solver (one launch; it
-    # draws its own start vector)
+    # start vector: latency-bound; through hub_lanczos_ground (the single-launch small-sector
+    # solver: one cooperative kernel per batch of eight iterations; and, with it turned off, the
+    # multi-kernel driver with its per-iteration launches and read-backs) and as a single job of
+    # the persistent batched solver (one launch; it draws its own start vector)
     bonds8 = np.array([(i, (i + 1) % 8) for i in range(8)], dtype=np.int32)
     m8 = hub.Hubbard(8, 4, 4, bonds8, 1.0, 4.0)
     x8 = torch.from_numpy(W.normal(0, m8.D)).cuda()
-    m8.ground(x8, maxit=300, tol=1e-12)
-    reps8 = []
-    for _ in range(5):
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        r8 = m8.ground(x8, maxit=300, tol=1e-12)
-        torch.cuda.synchronize()
-        reps8.append(time.perf_counter() - t0)
+
+    def time_ground(reps=5):
+        m8.ground(x8, maxit=300, tol=1e-12)
+        ts = []
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            r_ = m8.ground(x8, maxit=300, tol=1e-12)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        return r_, ts
+    r8, reps8 = time_ground()
+    hub.hub_set_small_dim(m8.h, 0)
+    r8m, reps8m = time_ground()
     m8.close()
     one = lambda a: np.asarray(a, dtype=np.float64).reshape(1, -1)
     hub.hub_batch_ground(8, bonds8, one(np.ones(8)), one(np.full(8, 4.0)), one(np.zeros(8)),
@@ -402,6 +409,9 @@ def extras(hub, W, torch):
         reps_b.append(time.perf_counter() - t0)
     out["ring8"] = {"workload": "ring M=8, (4,4), D=4900, t=1, U=4, to |dE0| < 1e-12",
                     "E0": r8["E0"], "iterations": r8["iters"], "lanczos_ground_ms": 1000 * min(reps8),
+                    "lanczos_ground_path": "single-launch small-sector solver (FP64, cooperative kernel)",
+                    "multi_kernel_driver_E0": r8m["E0"], "multi_kernel_driver_iterations": r8m["iters"],
+                    "multi_kernel_driver_ms": 1000 * min(reps8m),
                     "batched_single_job_E0": float(Eb[0]), "batched_single_job_iterations": int(itb[0]),
                     "batched_single_job_ms": 1000 * min(reps_b)}
     # (7b) block Lanczos at 4x4 (8,8): a block step applies H to k vectors with the same product

@@ -147,7 +147,10 @@ int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream);
  * the Lanczos vectors are held in double-float form: x0 is scaled by a power of two so
  * that its largest entry lies in [1, 2), and components smaller than about 2^-126 times
  * the largest entry of a Lanczos vector are flushed.  Neither changes E0 at the 1e-10
- * level; HUB_MODE_FP64 keeps every vector in FP64.
+ * level; HUB_MODE_FP64 keeps every vector in FP64.  Sectors of at most hub_set_small_dim's
+ * bound (default 262144 states; not in a momentum sector) run instead in one cooperative
+ * kernel per batch of iterations, FP64 throughout, in either mode: the same recurrence and
+ * stopping rule, alpha_j and beta_j equal to the other drivers' up to rounding.
  */
 int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, double tol, double *E0,
                        double *psi_dev, int *iters, void *stream);
@@ -392,6 +395,17 @@ int hub_k_project(hub_t h, const double *x_dev, double *y_dev, void *stream);
 int hub_set_mode(hub_t h, int mode);
 
 /*
+ * Small-sector Lanczos (no counterpart in the paper): hub_lanczos_ground (and the calls built
+ * on it: spectra, Ritz vectors, Green's-function coefficients) runs sectors of at most max_dim
+ * states as one cooperative kernel per batch of iterations, whose CTAs meet at grid barriers
+ * between the phases of an iteration (bounded waits: a wait that gives up sets the handle's
+ * error flag and hub_lanczos_ground returns HUB_ERR_TIMEOUT).  This removes the per-iteration
+ * launches and host round trips that bound small sectors.  max_dim = 0 turns it off; the
+ * default is 262144.  HUB_ERR_ARG for a NULL handle or max_dim < 0.
+ */
+int hub_set_small_dim(hub_t h, int64_t max_dim);
+
+/*
  * Waits for the handle's queued work and reports a device-side failure: HUB_ERR_TIMEOUT
  * if a bounded wait inside a kernel gave up since the last check (the flag is cleared),
  * HUB_ERR_CUDA on a CUDA error, else HUB_OK.  hub_lanczos_ground checks this itself.
@@ -400,9 +414,9 @@ int hub_check(hub_t h);
 
 /*
  * Test hook (no counterpart in the paper; off by default).  While enabled, every CTA of the
- * fast path's first pass, once the bulk copies of its first row pair have landed, takes the
- * exit a given-up bounded wait takes: it sets the handle's device error flag and returns
- * without computing.  No wait runs out and no copy is left in flight; the hook exists so
+ * fast path's first pass, once the bulk copies of its first row pair have landed, and every
+ * CTA of the small-sector Lanczos, before its first grid barrier, takes the exit a given-up
+ * bounded wait takes: it sets the handle's device error flag and returns without computing.  No wait runs out and no copy is left in flight; the hook exists so
  * that the error path (hub_check and hub_lanczos_ground returning HUB_ERR_TIMEOUT) can be
  * exercised.  Results computed while it is enabled are meaningless.
  */

@@ -12,16 +12,21 @@ shapes from compile-time knobs:
   it stages the rows; 0: a separate vector pass before pass 1;
 * ``HUB_UPD_Q``        -- column quads per thread whose loads the fused update issues together;
 * ``HUB_UP_THREADS``   -- threads of the pass-1 CTA (1024, 768 or 512; fewer leave more registers);
-* ``HUB_BATCH_THREADS`` -- threads per CTA of the batched persistent solver.
+* ``HUB_BATCH_THREADS`` -- threads per CTA of the batched persistent solver;
+* ``HUB_SMALL_CLUSTER_MAX``, ``HUB_SMALL_THREADS``, ``HUB_SMALL_PER_THREAD``,
+  ``HUB_SMALL_BATCH`` -- the largest sector the single-launch small-sector Lanczos
+  (csrc/hub_small.cu) runs as one thread-block cluster (0: always the cooperative grid), its
+  threads per CTA, states per thread the grid is sized for, and iterations per launch.
 
 For each candidate setting this module builds one copy of the library, times on the GPU what
 the knob affects (one Lanczos step at 4x4 half filling for the apply knobs; the 5184-job
-impurity batch of 81 sectors x 64 parameter sets for the batched knob), each in a fresh
-process, and keeps the fastest by coordinate descent from the current setting (a change is
-kept only if it is at least 1 % faster).  ``--write`` stores the result in tuned.json, which
-``build()`` compiles in.
+impurity batch of 81 sectors x 64 parameter sets for the batched knob; the 8-site ring's ground
+state to |dE0| < 1e-12 for the small-sector knobs), each in a fresh process, and keeps the
+fastest by coordinate descent from the current setting (a change is kept only if it is at least
+1 % faster).  ``--only`` tunes some of the three groups and keeps the others' stored values;
+``--write`` stores the result in tuned.json, which ``build()`` compiles in.
 
-    python -m paper_1307_7542_gb300.autotune [--write] [--steps 20]
+    python -m paper_1307_7542_gb300.autotune [--write] [--steps 20] [--only apply,batch,small]
 """
 from __future__ import annotations
 
@@ -47,8 +52,14 @@ APPLY_SPACE = {
     "HUB_UP_THREADS": [1024, 768, 512],
 }
 BATCH_SPACE = {"HUB_BATCH_THREADS": [256, 512, 1024]}
+SMALL_SPACE = {"HUB_SMALL_CLUSTER_MAX": [16384, 0], "HUB_SMALL_THREADS": [128, 256, 320, 384, 512],
+               "HUB_SMALL_PER_THREAD": [1, 2, 4], "HUB_SMALL_BATCH": [8, 4, 16]}
 DEFAULTS = {"HUB_DN_LANE_COLS": 4, "HUB_DN_BATCH": 2, "HUB_DN_MINB": 4, "HUB_BANK_CAP": 2,
-            "HUB_FUSED_UPDATE": 0, "HUB_UPD_Q": 1, "HUB_UP_THREADS": 1024, "HUB_BATCH_THREADS": 256}
+            "HUB_FUSED_UPDATE": 0, "HUB_UPD_Q": 1, "HUB_UP_THREADS": 1024, "HUB_BATCH_THREADS": 256,
+            "HUB_SMALL_CLUSTER_MAX": 16384, "HUB_SMALL_THREADS": 320, "HUB_SMALL_PER_THREAD": 1,
+            "HUB_SMALL_BATCH": 8}
+# tuned.json key of each group's timing
+RESULT_KEYS = {"apply": "lanczos_step_ms_4x4", "batch": "aim_batch_ms", "small": "ring8_ground_ms"}
 MARGIN = 0.01
 
 
@@ -101,6 +112,31 @@ def _child_batch(lib_path: str, steps: int) -> float:
     return best
 
 
+def _child_small(lib_path: str, steps: int) -> float:
+    """ms for the 8-site ring's ground state (D = 4900) to |dE0| < 1e-12 from the seed-0 normal
+    vector (best of `steps` // 2 runs), with the library at lib_path."""
+    import torch
+    from paper_1307_7542_gb300 import hub, workloads as W
+    hub.LIB_PATH = lib_path
+    hub._lib = None
+    m = hub.Hubbard(8, 4, 4, W.ring_bonds(8), 1.0, 4.0)
+    x0 = torch.from_numpy(W.normal(0, m.D)).cuda()
+    m.ground(x0, maxit=300, tol=1e-12)
+    best = float("inf")
+    for _ in range(max(3, steps // 2)):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        m.ground(x0, maxit=300, tol=1e-12)
+        torch.cuda.synchronize()
+        best = min(best, 1000 * (time.perf_counter() - t0))
+    m.close()
+    return best
+
+
+CHILDREN = {"apply": _child_apply, "batch": _child_batch, "small": _child_small}
+SPACES = {"apply": APPLY_SPACE, "batch": BATCH_SPACE, "small": SMALL_SPACE}
+
+
 def measure(knobs: dict, what: str, steps: int) -> float:
     """Build the library with these knobs and time `what` ("apply" or "batch") in a child process."""
     from paper_1307_7542_gb300 import build
@@ -138,30 +174,44 @@ def coordinate_descent(space: dict, start: dict, what: str, steps: int, log: lis
     return best, t_best
 
 
+def _gpu_name() -> str:
+    try:
+        import torch
+        return torch.cuda.get_device_name(0)
+    except Exception:
+        return "unknown"
+
+
 def main(argv=None) -> int:
     p = argparse.ArgumentParser(description=__doc__.split("\n\n")[0])
     p.add_argument("--write", action="store_true", help="store the result in tuned.json")
     p.add_argument("--steps", type=int, default=20, help="Lanczos steps timed per candidate")
-    p.add_argument("--child", choices=["apply", "batch"], help=argparse.SUPPRESS)
+    p.add_argument("--only", default="apply,batch,small", help="groups to tune (comma-separated)")
+    p.add_argument("--child", choices=sorted(CHILDREN), help=argparse.SUPPRESS)
     p.add_argument("--lib", help=argparse.SUPPRESS)
     a = p.parse_args(argv)
     if a.child:
-        fn = _child_apply if a.child == "apply" else _child_batch
-        print(json.dumps({"ms": fn(a.lib, a.steps)}))
+        print(json.dumps({"ms": CHILDREN[a.child](a.lib, a.steps)}))
         return 0
+    groups = [g for g in a.only.split(",") if g]
+    if any(g not in SPACES for g in groups):
+        p.error(f"--only takes groups from {sorted(SPACES)}")
     start = dict(DEFAULTS)
+    stored = {}
     if os.path.exists(TUNED):
         with open(TUNED) as f:
-            start.update(json.load(f).get("defines", {}))
+            stored = json.load(f)
+        start.update(stored.get("defines", {}))
     log = []
-    apply_start = {k: start[k] for k in APPLY_SPACE}
-    best_apply, t_apply = coordinate_descent(APPLY_SPACE, apply_start, "apply", a.steps, log)
-    batch_start = {k: start[k] for k in BATCH_SPACE}
-    best_batch, t_batch = coordinate_descent(BATCH_SPACE, batch_start, "batch", a.steps, log)
-    import torch
-    result = {"gpu": torch.cuda.get_device_name(0), "defines": {**best_apply, **best_batch},
-              "lanczos_step_ms_4x4": t_apply, "aim_batch_ms": t_batch, "trials": log}
-    print(json.dumps({k: result[k] for k in ("gpu", "defines", "lanczos_step_ms_4x4", "aim_batch_ms")}))
+    defines = dict(start)
+    timings = {RESULT_KEYS[g]: stored[RESULT_KEYS[g]] for g in SPACES if g not in groups and RESULT_KEYS[g] in stored}
+    for g in groups:
+        best, t = coordinate_descent(SPACES[g], {k: start[k] for k in SPACES[g]}, g, a.steps, log)
+        defines.update(best)
+        timings[RESULT_KEYS[g]] = t
+    result = {"gpu": _gpu_name(), "defines": defines, **timings,
+              "trials": [t for t in stored.get("trials", []) if t.get("what") not in groups] + log}
+    print(json.dumps({k: v for k, v in result.items() if k != "trials"}))
     if a.write:
         with open(TUNED, "w") as f:
             json.dump(result, f, indent=1)

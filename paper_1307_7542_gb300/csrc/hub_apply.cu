@@ -16,18 +16,6 @@
 
 namespace hub {
 
-__device__ __forceinline__ double diag_of(const Ham &H, uint32_t Iu, uint32_t Id, int64_t u, int64_t d) {
-  double v;
-  if (H.uniform_U) {
-    v = H.U0 * (double)__popc(Iu & Id);
-  } else {
-    v = 0.0;
-    for (uint32_t m = Iu & Id; m; m &= m - 1) v += H.U[__ffs(m) - 1];
-  }
-  if (H.has_eps) v += H.eps_up[u] + H.eps_dn[d];
-  return v;
-}
-
 // gate: null, or a device flag; the kernel does nothing while gate[0] is 0 (the fast path
 // passes its out-of-window flag, so that this kernel multiplies exactly the vectors the
 // double-float kernels cannot).
@@ -207,5 +195,6 @@ extern "C" int hub_test_fail_waits(hub_t h, int enable) {
 extern "C" int hub_check(hub_t h) {
   if (!h) return fail(HUB_ERR_ARG, "hub_check: NULL handle");
   HUB_CUDA(cudaDeviceSynchronize());
-  return fast_check_error(h);
+  const int rc = fast_check_error(h);
+  return rc ? rc : small_check_error(h);
 }

@@ -42,7 +42,6 @@
 namespace hub {
 
 int ready(const hub_ctx *h, const char *who);
-double tridiag_lowest(const double *a, const double *b, int k);
 std::vector<double> tridiag_vector(const double *a, const double *b, int k, double lam);
 
 // ---------------------------------------------------------------------------------------
@@ -1858,6 +1857,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
   // the coefficients are those of one step per read-back.
   const int batch = D <= kBatchStepsMaxDim ? kMaxBatchSteps : 1;
   double E = 0.0, E_prev = 0.0;
+  LowestTracker lowest;
   int status = HUB_ERR_NOCONV;
   int computed = 0;                                // steps run on the device
   bool done = false;
@@ -1899,7 +1899,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
         return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha");
       }
       h->alpha.push_back(tabs * a_dev);
-      E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
+      if (tol > 0) E = lowest.next(h->alpha.data(), h->beta.data(), (int)h->alpha.size());   // else at the end
       if (tol > 0 && jj > 0 && std::fabs(E - E_prev) < tol) {
         status = HUB_OK;
         done = true;
@@ -1910,6 +1910,7 @@ int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0
     j += nb;
   }
   if (tol <= 0 && status == HUB_ERR_NOCONV) status = HUB_OK;
+  if (tol <= 0 && !h->alpha.empty()) E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
   if ((rc = fast_check_error(h))) return rc;
   const int last = (int)h->alpha.size() - 1;        // 0-based index of the last kept step
   if (status != HUB_CONVERGED_BREAKDOWN && last >= 0) {

@@ -45,6 +45,7 @@ struct SpinCSR {
 
 struct FastState;   // fast-path tables and scratch (hub_fast.cu)
 struct K0State;     // k = 0 translation-sector tables (hub_k0.cu)
+struct SmallState;  // single-launch Lanczos of small sectors (hub_small.cu)
 
 // Read-only view of everything a kernel needs, passed by value.
 struct Ham {
@@ -127,6 +128,11 @@ struct hub_ctx {
   // row form, rows x cols (hub_k0.cu)
   hub::K0State *k0 = nullptr;
 
+  // sectors of at most small_max_dim states run hub_lanczos_ground as one cooperative
+  // kernel per batch of iterations (hub_small.cu); 0 turns that off
+  int64_t small_max_dim = int64_t(1) << 18;
+  hub::SmallState *small = nullptr;
+
   hub::Ham view() const;
 };
 
@@ -162,12 +168,31 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
 int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out, int *iters,
                  cudaStream_t s);
 int fast_check_error(hub_ctx *h);
+// Lowest eigenvalues of the successive tridiagonals T_1, T_2, ... of one Lanczos run (host),
+// each by bisection on the Sturm count like tridiag_lowest, but started from a bracket around
+// the previous value (by Cauchy interlacing the new one lies at or below it), widened until the
+// count is 0 at its lower end and at least 1 at its upper end; both bisections end on the two
+// adjacent doubles where the count steps from 0 to 1, so they return the same value.
+struct LowestTracker {
+  double last = 0.0, step = 0.0;
+  int n = 0;
+  double next(const double *a, const double *b, int k);
+};
+double tridiag_lowest(const double *a, const double *b, int k);
+
 // Eigenvalue of the last run's T whose eigenvector the second Lanczos pass expands (E0, or the
 // one nearest h->psi_target); also stored in h->psi_value.
 double psi_eigenvalue(hub_ctx *h, double E0);
 inline bool use_fast(const hub_ctx *h) {
   return h->mode == HUB_MODE_AUTO && h->fast && !h->k0 && fast_eligible(h);
 }
+
+// Single-launch Lanczos of small sectors (hub_small.cu).
+bool small_eligible(const hub_ctx *h);
+int small_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out, int *iters,
+                  cudaStream_t s);
+int small_check_error(hub_ctx *h);
+void small_release(hub_ctx *h);
 
 // k = 0 sector (hub_k0.cu).
 int64_t vec_len(const hub_ctx *h);   // length of a state vector in the handle's current layout
@@ -200,6 +225,19 @@ __device__ __forceinline__ uint32_t rank_of(uint32_t s, const uint64_t *__restri
     s &= s - 1;
   }
   return r;
+}
+
+// Diagonal of H at (u, d) (Sec. III.B): sum_i U_i bit_i(I_up & I_dn) + eps(I_up) + eps(I_dn).
+__device__ __forceinline__ double diag_of(const Ham &H, uint32_t Iu, uint32_t Id, int64_t u, int64_t d) {
+  double v;
+  if (H.uniform_U) {
+    v = H.U0 * (double)__popc(Iu & Id);
+  } else {
+    v = 0.0;
+    for (uint32_t m = Iu & Id; m; m &= m - 1) v += H.U[__ffs(m) - 1];
+  }
+  if (H.has_eps) v += H.eps_up[u] + H.eps_dn[d];
+  return v;
 }
 
 __host__ __device__ inline int popc32(uint32_t v) {

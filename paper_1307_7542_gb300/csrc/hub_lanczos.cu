@@ -142,6 +142,16 @@ static int sturm_count(const double *a, const double *b, int k, double x) {
   return cnt;
 }
 
+// Bisection of [lo, hi] (count 0 at lo, >= 1 at hi) down to adjacent doubles.
+static double bisect_lowest(const double *a, const double *b, int k, double lo, double hi) {
+  for (int it = 0; it < 200; ++it) {
+    double mid = 0.5 * (lo + hi);
+    if (mid <= lo || mid >= hi) break;
+    if (sturm_count(a, b, k, mid) >= 1) hi = mid; else lo = mid;
+  }
+  return 0.5 * (lo + hi);
+}
+
 double tridiag_lowest(const double *a, const double *b, int k) {
   if (k == 1) return a[0];
   double lo = INFINITY, hi = -INFINITY;
@@ -150,12 +160,33 @@ double tridiag_lowest(const double *a, const double *b, int k) {
     lo = fmin(lo, a[i] - r);
     hi = fmax(hi, a[i] + r);
   }
-  for (int it = 0; it < 200; ++it) {
-    double mid = 0.5 * (lo + hi);
-    if (mid <= lo || mid >= hi) break;
-    if (sturm_count(a, b, k, mid) >= 1) hi = mid; else lo = mid;
+  return bisect_lowest(a, b, k, lo, hi);
+}
+
+double LowestTracker::next(const double *a, const double *b, int k) {
+  double e;
+  if (n < 2 || k == 1 || !std::isfinite(last) || !std::isfinite(step)) {
+    e = tridiag_lowest(a, b, k);
+  } else {
+    double d = fmax(2.0 * step, 4e-16 * fmax(1.0, fabs(last)));
+    double lo = last - d, hi = last + d;
+    bool ok = true;
+    for (int t = 0; ok && sturm_count(a, b, k, hi) < 1; ++t) {
+      hi += d;
+      d *= 4.0;
+      ok = t < 40;
+    }
+    for (int t = 0; ok && sturm_count(a, b, k, lo) >= 1; ++t) {
+      lo -= d;
+      d *= 4.0;
+      ok = t < 40;
+    }
+    e = ok ? bisect_lowest(a, b, k, lo, hi) : tridiag_lowest(a, b, k);
   }
-  return 0.5 * (lo + hi);
+  if (n > 0) step = fabs(e - last);
+  last = e;
+  ++n;
+  return e;
 }
 
 // Eigenvector of T for eigenvalue lam by inverse iteration (tridiagonal LU with partial
@@ -287,6 +318,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
   if (maxit < 1) return fail(HUB_ERR_ARG, "hub_lanczos_ground: maxit < 1");
   const int64_t D = vec_len(h);
   if (D == 0) return fail(HUB_ERR_ARG, "hub_lanczos_ground: empty sector");
+  if (small_eligible(h)) return small_lanczos(h, x0_dev, maxit, tol, E0, psi_dev, iters, (cudaStream_t)stream);
   if (use_fast(h)) {
     if (!x0_dev) {
       // the fast driver converts an FP64 start vector: draw it into the FP64 workspace
@@ -328,6 +360,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
   h->alpha.clear();
   h->beta.clear();
   double E = 0.0, E_prev = 0.0;
+  LowestTracker lowest;
   int status = HUB_ERR_NOCONV;
   for (int j = 0; j < maxit; ++j) {
     if ((rc = apply_launch(h, q, w, s))) return rc;
@@ -344,7 +377,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
     if (!std::isfinite(a) || !std::isfinite(b)) return fail(HUB_ERR_CUDA, "hub_lanczos_ground: non-finite alpha/beta");
     h->alpha.push_back(a);
     h->beta.push_back(b);
-    E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
+    if (tol > 0) E = lowest.next(h->alpha.data(), h->beta.data(), (int)h->alpha.size());   // else at the end
     if (tol > 0 && j > 0 && fabs(E - E_prev) < tol) {
       status = HUB_OK;
       break;
@@ -364,6 +397,7 @@ extern "C" int hub_lanczos_ground(hub_t h, const double *x0_dev, int maxit, doub
     }
   }
   if (tol <= 0 && status == HUB_ERR_NOCONV) status = HUB_OK;
+  if (tol <= 0) E = tridiag_lowest(h->alpha.data(), h->beta.data(), (int)h->alpha.size());
   *E0 = E;
   const int k = (int)h->alpha.size();
   if (iters) *iters = k;

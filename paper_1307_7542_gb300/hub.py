@@ -69,6 +69,7 @@ SIGNATURES = {
     "hub_profile": (_i, [_p, _i]),
     "hub_profile_read": (_i, [_p, _i, ctypes.POINTER(_d), ctypes.POINTER(_i64), ctypes.POINTER(_i64)]),
     "hub_free": (None, [_p]),
+    "hub_set_small_dim": (_i, [_p, _i64]),
 }
 
 _lib = None
@@ -338,6 +339,11 @@ def hub_set_mode(h, mode):
 
 def hub_check(h):
     _check(lib().hub_check(h))
+
+
+def hub_set_small_dim(h, max_dim):
+    """Largest sector hub_lanczos_ground runs as the single-launch small-sector solver (0: off)."""
+    _check(lib().hub_set_small_dim(h, int(max_dim)))
 
 
 def hub_test_fail_waits(h, enable):

@@ -100,6 +100,7 @@ def test_null_handles_are_refused(libpath):
         "hub_set_mode": lambda: L.hub_set_mode(None, 0),
         "hub_check": lambda: L.hub_check(None),
         "hub_test_fail_waits": lambda: L.hub_test_fail_waits(None, 1),
+        "hub_set_small_dim": lambda: L.hub_set_small_dim(None, 0),
         "hub_profile": lambda: L.hub_profile(None, 1),
         "hub_profile_read": lambda: L.hub_profile_read(None, 0, None, None, None),
         "hub_csr_info": lambda: L.hub_csr_info(None, 0, None, None),

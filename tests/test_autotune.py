@@ -32,3 +32,23 @@ def test_tags_are_distinct_and_filesystem_safe():
     a = A._tag({"HUB_BANK_CAP": -2, "HUB_DN_BATCH": 2})
     b = A._tag({"HUB_BANK_CAP": 2, "HUB_DN_BATCH": 2})
     assert a != b and "-" not in a and "/" not in a
+
+
+def test_only_one_group_keeps_the_stored_others(monkeypatch, tmp_path):
+    """--only small tunes the small-sector knobs and keeps the stored defines, timings and
+    trials of the other groups in tuned.json."""
+    import json
+    tuned = tmp_path / "tuned.json"
+    stored = {"gpu": "x", "defines": dict(A.DEFAULTS, HUB_DN_BATCH=4, HUB_BATCH_THREADS=512),
+              "lanczos_step_ms_4x4": 4.9, "aim_batch_ms": 62.0,
+              "trials": [{"what": "apply", "knobs": {}, "ms": 4.9}, {"what": "small", "knobs": {}, "ms": 9.0}]}
+    tuned.write_text(json.dumps(stored))
+    monkeypatch.setattr(A, "TUNED", str(tuned))
+    monkeypatch.setattr(A, "measure", lambda knobs, what, steps: 1.0 if knobs["HUB_SMALL_THREADS"] != 128 else 0.5)
+    assert A.main(["--only", "small", "--write", "--steps", "3"]) == 0
+    out = json.loads(tuned.read_text())
+    assert out["defines"]["HUB_SMALL_THREADS"] == 128
+    assert out["defines"]["HUB_DN_BATCH"] == 4 and out["defines"]["HUB_BATCH_THREADS"] == 512
+    assert out["lanczos_step_ms_4x4"] == 4.9 and out["aim_batch_ms"] == 62.0 and out["ring8_ground_ms"] == 0.5
+    whats = [t["what"] for t in out["trials"]]
+    assert whats[0] == "apply" and all(w == "small" for w in whats[1:]) and len(whats) > 2

@@ -1,7 +1,7 @@
 """The bounded-wait error path of the fast product, driven by the test hook
 hub_test_fail_waits: pass 1 takes the exit a given-up mbarrier wait takes (device error flag
 set, kernel returns) after its bulk copies have landed, so no wait runs out and no copy is in
-flight.  The flag must surface as HUB_ERR_TIMEOUT from hub_check and hub_lanczos_ground, be
+flight; the small-sector Lanczos takes its given-up-barrier exit before any barrier.  The flag must surface as HUB_ERR_TIMEOUT from hub_check and hub_lanczos_ground, be
 cleared once reported, and leave the handle usable."""
 import numpy as np
 import pytest
@@ -21,9 +21,14 @@ def hub(cuda_ok):
     return H
 
 
-def test_timeout_flag_reaches_the_caller(hub):
+@pytest.mark.parametrize("small", [False, True])
+def test_timeout_flag_reaches_the_caller(hub, small):
+    """small: hub_lanczos_ground runs the single-launch small-sector solver, whose CTAs take
+    the same exit before their first grid barrier; else the double-float driver."""
     w = W.ring8()
     m = hub.Hubbard(8, 4, 4, w["bonds"], w["t"], w["U"], w["eps"])
+    if not small:
+        hub.hub_set_small_dim(m.h, 0)
     try:
         x = torch.from_numpy(W.normal(5, m.D)).cuda()
         y_ref = m.apply(x)

@@ -577,6 +577,7 @@ def test_fast_lanczos_matches_fp64_lanczos(hub):
     and the same psi, on a sector with unequal spins."""
     w = dict(M=10, n_up=4, n_dn=5, bonds=W.ring_bonds(10), t=np.ones(10), U=np.full(10, 4.0), eps=np.zeros(10))
     m = _gpu_model(hub, w)
+    hub.hub_set_small_dim(m.h, 0)          # the multi-kernel drivers, not the small-sector solver
     try:
         x0 = torch.from_numpy(W.normal(2, m.D)).cuda()
         r1 = m.ground(x0, maxit=400, tol=1e-13, want_psi=True)
@@ -648,6 +649,7 @@ def test_lanczos_graph_replay_matches_direct_launches(hub):
     M = 8
     bonds = W.ring_bonds(M)
     m = hub.Hubbard(M, 4, 4, bonds, 1.0, 4.0)
+    hub.hub_set_small_dim(m.h, 0)          # the multi-kernel driver, not the small-sector solver
     x0 = torch.from_numpy(W.normal(0, m.D)).cuda()
     runs = []
     for prof in (False, False, True):
@@ -663,6 +665,7 @@ def test_lanczos_graph_replay_matches_direct_launches(hub):
     a6 = hub.hub_lanczos_coeffs(m.h)[0]
     m.close()
     fresh = hub.Hubbard(M, 4, 4, bonds, 1.0, 6.0)
+    hub.hub_set_small_dim(fresh.h, 0)
     hub.hub_profile(fresh.h, True)
     ef = fresh.ground(x0, maxit=40, tol=0.0)["E0"]
     af = hub.hub_lanczos_coeffs(fresh.h)[0]

@@ -28,10 +28,12 @@ def _distinct(w, tol=1e-8):
     return np.array(out)
 
 
-def test_spectrum_ring8_fast_path(hub):
-    """Ring M = 8, (4,4), U = 4 (double-float path): the five lowest distinct eigenvalues
-    agree with ARPACK on the oracle's apply to 1e-9; their residual estimates are small (an
-    eigenvalue converges as the square of its residual, so 1e-4 suffices for 1e-9)."""
+@pytest.mark.parametrize("small", [False, True])
+def test_spectrum_ring8_fast_path(hub, small):
+    """Ring M = 8, (4,4), U = 4 (double-float driver, or the single-launch small-sector
+    solver): the five lowest distinct eigenvalues agree with ARPACK on the oracle's apply to
+    1e-9; their residual estimates are small (an eigenvalue converges as the square of its
+    residual, so 1e-4 suffices for 1e-9)."""
     from scipy.sparse.linalg import LinearOperator, eigsh
     M = 8
     bonds = W.ring_bonds(M)
@@ -41,6 +43,8 @@ def test_spectrum_ring8_fast_path(hub):
                         dtype=np.float64)
     ref = _distinct(eigsh(op, k=24, which="SA", tol=1e-13, v0=W.normal(3, B.size))[0])[:5]
     m = hub.Hubbard(M, 4, 4, bonds, 1.0, 4.0)
+    if not small:
+        hub.hub_set_small_dim(m.h, 0)
     e, r = hub.hub_lanczos_spectrum(m.h, torch.from_numpy(W.normal(2, m.D)).cuda(), 400, 5)
     m.close()
     assert e.size == 5
@@ -48,9 +52,11 @@ def test_spectrum_ring8_fast_path(hub):
     assert np.all(r < 1e-4)          # eigenvalue error ~ residual^2 / gap
 
 
-def test_spectrum_disordered_fp64_path(hub):
-    """Disordered open chain M = 7, (3,2), per-bond t, per-site U and eps (FP64 path): the six
-    lowest distinct eigenvalues equal those of the dense Hamiltonian."""
+@pytest.mark.parametrize("small", [False, True])
+def test_spectrum_disordered_fp64_path(hub, small):
+    """Disordered open chain M = 7, (3,2), per-bond t, per-site U and eps (FP64 driver, or the
+    single-launch small-sector solver): the six lowest distinct eigenvalues equal those of the
+    dense Hamiltonian."""
     M, nu, nd = 7, 3, 2
     bonds = W.chain_bonds(M)
     r = W.uniform(31, 3 * M)
@@ -59,6 +65,8 @@ def test_spectrum_disordered_fp64_path(hub):
     om = O.Model(M, bonds, t, U, eps)
     ref = _distinct(np.linalg.eigvalsh(O.dense_fock(om, nu, nd)))[:6]
     m = hub.Hubbard(M, nu, nd, bonds, t, U, eps)
+    if not small:
+        hub.hub_set_small_dim(m.h, 0)
     e, res = hub.hub_lanczos_spectrum(m.h, None, 2 * m.D, 6)
     m.close()
     assert np.max(np.abs(e - ref)) < 1e-9 * max(1.0, np.max(np.abs(ref)))
@@ -91,9 +99,11 @@ def _ritz_checks(hub, m, x0, maxit, levels, ref_vals, ref_vecs):
         assert r < 1e-6, (i, r)
 
 
-def test_ritz_vectors_disordered_fp64_path(hub):
-    """Excited-state eigenvectors (Sec. IV) on the FP64 path: the Ritz vectors of the second
-    and third levels of a disordered 7-site chain, (3,2), match the dense eigenvectors."""
+@pytest.mark.parametrize("small", [False, True])
+def test_ritz_vectors_disordered_fp64_path(hub, small):
+    """Excited-state eigenvectors (Sec. IV) on the FP64 driver (or the single-launch
+    small-sector solver): the Ritz vectors of the second and third levels of a disordered
+    7-site chain, (3,2), match the dense eigenvectors."""
     M, nu, nd = 7, 3, 2
     bonds = W.chain_bonds(M)
     r = W.uniform(31, 3 * M)
@@ -103,14 +113,18 @@ def test_ritz_vectors_disordered_fp64_path(hub):
     w, V = np.linalg.eigh(O.dense_fock(om, nu, nd))
     assert min(w[2] - w[1], w[1] - w[0], w[3] - w[2]) > 1e-3
     m = hub.Hubbard(M, nu, nd, bonds, t, U, eps)
+    if not small:
+        hub.hub_set_small_dim(m.h, 0)
     x0 = torch.from_numpy(W.normal(4, m.D)).cuda()
     _ritz_checks(hub, m, x0, 150, [0, 1, 2], w, V)
     m.close()
 
 
-def test_ritz_vectors_chain8_fast_path(hub):
-    """Excited-state eigenvectors on the double-float path: open chain M = 8, (4,4), U = 4;
-    the two lowest levels against ARPACK eigenvectors of the oracle's apply."""
+@pytest.mark.parametrize("small", [False, True])
+def test_ritz_vectors_chain8_fast_path(hub, small):
+    """Excited-state eigenvectors on the double-float driver (or the single-launch
+    small-sector solver): open chain M = 8, (4,4), U = 4; the two lowest levels against ARPACK
+    eigenvectors of the oracle's apply."""
     from scipy.sparse.linalg import LinearOperator, eigsh
     M = 8
     bonds = W.chain_bonds(M)
@@ -124,6 +138,8 @@ def test_ritz_vectors_chain8_fast_path(hub):
     levels = [i for i in range(2) if min(abs(w[i] - w[j]) for j in range(len(w)) if j != i) > 1e-3]
     assert levels
     m = hub.Hubbard(M, 4, 4, bonds, 1.0, 4.0)
+    if not small:
+        hub.hub_set_small_dim(m.h, 0)
     x0 = torch.from_numpy(W.normal(2, m.D)).cuda()
     _ritz_checks(hub, m, x0, 200, levels, w, V)
     m.close()
