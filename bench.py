@@ -135,23 +135,26 @@ def smi_index(local_rank):
 
 
 WORKLOADS = {
-    "4x4": ("4x4 periodic square lattice, half filling (8,8), t=1", 8, 8),
-    "4x4-sector66": ("4x4 periodic square lattice, sector (6,6), t=1 (profiling case)", 6, 6),
+    "4x4": ("4x4 periodic square lattice, half filling (8,8), t=1", "4x4", 8, 8),
+    "4x4-sector66": ("4x4 periodic square lattice, sector (6,6), t=1 (profiling case)", "4x4", 6, 6),
+    # rows of C(18, 9) = 48620 spin-up states, too long to stage: pass 1 runs on the transposed
+    # matrix (profiling case of the 3x6 (9,9) path at 1/60 of its size, vectors still > L2)
+    "3x6-sector93": ("3x6 periodic square lattice, sector (9,3), t=1 (profiling case)", "3x6", 9, 3),
 }
 
 
 def workload(U, name="4x4"):
     from paper_1307_7542_gb300 import workloads as W
-    w = W.square4x4(U)
-    _, nu, nd = WORKLOADS[name]
+    label, lattice, nu, nd = WORKLOADS[name]
+    w = W.square4x4(U) if lattice == "4x4" else W.square3x6(U)
     w["n_up"], w["n_dn"] = nu, nd
-    w["label"] = WORKLOADS[name][0]
+    w["label"] = label
     return w
 
 
 def config_json(w, D, n_gpus):
     return {"workload": f"{w['label']}, U={w['U'][0]:g}",
-            "M": 16, "n_up": w["n_up"], "n_dn": w["n_dn"], "dim": D,
+            "M": w["M"], "n_up": w["n_up"], "n_dn": w["n_dn"], "dim": D,
             "step": "one Lanczos iteration (apply + recurrence)",
             "vector_bytes": 8 * D, "l2": f"inputs larger than L2 ({8 * D / 1e9:.2f} GB per FP64 vector); no flush needed",
             "parallelism": f"replicas x{n_gpus}" if n_gpus > 1 else "single GPU"}
@@ -682,7 +685,9 @@ def run_gpu(a):
                                           1000 * max(calls)]}
         del xh, yh, xd_, yd_
 
-    line = {"metric": "H.x applies/s (4x4 PBC half filling, U=4)",
+    metric = ("H.x applies/s (4x4 PBC half filling, U=4)" if a.workload == "4x4"
+              else f"H.x applies/s ({w['label']}, U={w['U'][0]:g})")
+    line = {"metric": metric,
             "value": value, "unit": "applies/s", "n_gpus": world, "steps": a.steps, "warmup": a.warmup,
             "ms_per_step": elapsed_ms / a.steps, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": DTYPE_FAST if n_up_l else "f64", "data": "synthetic",
