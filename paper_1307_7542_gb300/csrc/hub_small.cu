@@ -5,10 +5,13 @@
 // small that the multi-kernel drivers are bound by launch and synchronisation latency, not by
 // the product: the 8-site ring at half filling has 4,900 states and a product of about 45,000
 // multiply-adds, while a Lanczos iteration of the multi-kernel drivers is about ten launches
-// and a host round trip.  Here every CTA of one cooperative launch runs several iterations
-// and the CTAs meet at a grid barrier between the phases of an iteration (an arrival counter
-// and a generation word in global memory; every wait is bounded).  With the Lanczos vectors
-// kept unnormalised, q_j = c_j S_j (c_0 = 1/|x0|, c_j = 1/beta_{j-1}), iteration j is
+// and a host round trip.  Here one launch runs several iterations and its CTAs meet at a
+// barrier between the phases of an iteration: for sectors of at most kSmallClusterMax states
+// the launch is one thread-block cluster (k_small_cluster, below: hardware cluster barriers,
+// vectors exchanged through distributed shared memory), for larger ones a cooperative grid
+// (k_small_lanczos: an arrival counter in global memory, every wait bounded).  In the grid
+// form, with the Lanczos vectors kept unnormalised, q_j = c_j S_j (c_0 = 1/|x0|,
+// c_j = 1/beta_{j-1}), iteration j is
 //   phase 1  w = c_j (H S_j) - beta_{j-1} c_{j-1} S_{j-1};  CTA partials of <q_j, w>
 //   barrier  alpha_j = the sum of the partials, in one fixed order in every CTA
 //   phase 2  w -= alpha_j q_j, stored as S_{j+1};  CTA partials of |w|^2
@@ -57,10 +60,12 @@ static_assert(kSmallThreads % 32 == 0 && kSmallThreads <= 1024 && kSmallPerThrea
               "small-sector launch shape");
 constexpr int64_t kSmallStageMax = 25600;      // S_j staged in shared memory up to 200 KB
 #ifndef HUB_SMALL_CLUSTER_MAX
-#define HUB_SMALL_CLUSTER_MAX 16384            // sectors up to this size run as one CTA cluster
+#define HUB_SMALL_CLUSTER_MAX 12800            // sectors up to this size run as one CTA cluster
 #endif
 constexpr int64_t kSmallClusterMax = HUB_SMALL_CLUSTER_MAX;
 constexpr int kSmallClusterCtas = 16;          // CTAs of that cluster at most (non-portable size)
+static_assert(kSmallClusterMax >= 0 && 2 * sizeof(double) * kSmallClusterMax <= 200 * 1024,
+              "two copies of a cluster-size vector fit in shared memory");
 constexpr uint32_t kSmallSpin = 1u << 21;      // polls of a barrier wait before it gives up (about 1 s)
 
 struct SmallState {
@@ -202,7 +207,7 @@ __device__ __forceinline__ double splitmix_uniform(int64_t k) {
   return (double)(z >> 11) * (2.0 / 9007199254740992.0) - 1.0;
 }
 
-template <bool kStage, bool kCluster>
+template <bool kStage>
 __global__ void __launch_bounds__(kSmallThreads, 1) k_small_lanczos(const SmallArgs A) {
   extern __shared__ double xs[];
   __shared__ double red[kSmallThreads / 32];
@@ -210,7 +215,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_lanczos(const SmallA
   __shared__ double s_part[2];
   __shared__ double s_diag[kMaxSites + 1];   // uniform U: U * k for k doubly occupied sites
   __shared__ int s_ok;
-  GridSync<kCluster> gs{A.bar, A.err, A.part, s_part, &s_ok, red, &s_tot, 0u, 0};
+  GridSync<false> gs{A.bar, A.err, A.part, s_part, &s_ok, red, &s_tot, 0u, 0};
   const Ham &H = A.H;
   const int64_t D = A.D, nu = H.n_up;
   const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -340,6 +345,182 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_lanczos(const SmallA
 }
 
 // ---------------------------------------------------------------------------------------
+// Sectors of at most kSmallClusterMax states: one thread-block cluster (at most 16 CTAs, one
+// GPC).  Here the Lanczos vectors are normalised explicitly (q_j); each thread keeps its states'
+// q_j, q_{j-1} and w in registers, and every CTA holds the whole of q_j in shared memory: once
+// beta_j is known each CTA writes its slice of q_{j+1} into the shared memory of every CTA of
+// the cluster (distributed shared memory), so inside a launch no vector passes through L2.
+// Per iteration three cluster barriers: after the <q_j, w> partials, after the |w|^2 partials,
+// after the broadcast of q_{j+1} (shared-memory copies alternate, so a broadcast never
+// overwrites the copy a slower CTA is still reading).  q_j also goes to global memory (slot
+// j % 3), where the next launch of the run finds q_{j0} and q_{j0-1}; the psi pass repeats the
+// same operations with the recorded alpha_j, beta_j.
+// ---------------------------------------------------------------------------------------
+constexpr int kClusterE = 3;        // states per thread at most
+
+__global__ void __launch_bounds__(kSmallThreads, 1) k_small_cluster(const SmallArgs A) {
+  extern __shared__ double xs[];      // [2][D]: q_j and q_{j+1}
+  __shared__ double red[kSmallThreads / 32];
+  __shared__ double s_tot;
+  __shared__ double s_part[2];
+  __shared__ double s_diag[kMaxSites + 1];
+  __shared__ int s_ok;
+  GridSync<true> gs{nullptr, nullptr, nullptr, s_part, &s_ok, red, &s_tot, 0u, 0};
+  cg::cluster_group cl = cg::this_cluster();
+  const Ham &H = A.H;
+  const int64_t D = A.D, nu = H.n_up;
+  const int G = (int)gridDim.x;
+  const int64_t chunk = (D + G - 1) / G;
+  const int64_t lo = (int64_t)blockIdx.x * chunk, hi = min(D, lo + chunk);
+  const bool lead = blockIdx.x == 0 && threadIdx.x == 0;
+  auto V = [&](int k) { return k == 0 ? A.V0 : (k == 1 ? A.V1 : A.V2); };
+  if (threadIdx.x <= kMaxSites) s_diag[threadIdx.x] = H.U0 * (double)threadIdx.x;
+  __syncthreads();
+  // the two exits below come before any access to another CTA's shared memory
+  if (A.mode == 0 && __ldcg(A.stat + 1) != 0) return;   // stopped in an earlier launch (all CTAs)
+  if (A.fail_waits) {                 // test hook: every CTA takes a given-up wait's exit at once
+    if (threadIdx.x == 0) atomicExch(A.err, 1);
+    return;
+  }
+  int64_t nid[kClusterE];
+  double q[kClusterE], qp[kClusterE], w[kClusterE], psi[kClusterE];
+#pragma unroll
+  for (int e = 0; e < kClusterE; ++e) {
+    nid[e] = lo + threadIdx.x + (int64_t)e * blockDim.x;
+    q[e] = qp[e] = w[e] = psi[e] = 0.0;
+  }
+  auto own = [&](int e) { return nid[e] < hi; };
+  double *cur = xs, *nxt = xs + D;
+  // q_{j+1} (in q) into global slot k and into every CTA's copy dst
+  auto publish = [&](double *dst, int k) {
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e)
+      if (own(e)) {
+        V(k)[nid[e]] = q[e];
+        for (int r = 0; r < G; ++r) cl.map_shared_rank(dst, (unsigned)r)[nid[e]] = q[e];
+      }
+  };
+  double bp = 0.0;
+  if (A.j0 == 0) {                    // q_0 = x0 / |x0|
+    double nn = 0.0;
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e)
+      if (own(e)) {
+        q[e] = A.x0 ? A.x0[nid[e]] : splitmix_uniform(nid[e]);
+        nn = fma(q[e], q[e], nn);
+      }
+    double s2;
+    gs.total(nn, &s2);
+    const double s = sqrt(s2);
+    const bool good = s > 0.0 && isfinite(s);
+    if (A.mode == 0 && lead) {
+      A.start[0] = s;
+      if (!good) A.stat[1] = 2;
+    }
+    if (!good) {
+      gs.leave();
+      return;
+    }
+    const double inv = 1.0 / s;
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e) q[e] *= inv;
+    publish(cur, 0);
+    cl.sync();
+  } else {                            // q_{j0}, q_{j0-1} and beta_{j0-1} from the earlier launches
+    bp = __ldcg(A.hist + 2 * (A.j0 - 1) + 1);
+    const double *Q = V(A.j0 % 3), *Qp = V((A.j0 + 2) % 3);
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e)
+      if (own(e)) {
+        q[e] = __ldcg(Q + nid[e]);
+        qp[e] = __ldcg(Qp + nid[e]);
+      }
+    for (int64_t k = threadIdx.x; k < D; k += blockDim.x) cur[k] = __ldcg(Q + k);
+    __syncthreads();
+  }
+  for (int j = A.j0; j < A.j1; ++j) {
+    if (A.mode == 1) {                // psi += y_j q_j
+      const double y = A.coef[j];
+#pragma unroll
+      for (int e = 0; e < kClusterE; ++e) psi[e] = j == 0 ? y * q[e] : fma(y, q[e], psi[e]);
+      if (j + 1 == A.j1) break;
+    }
+    // w = H q_j - beta_{j-1} q_{j-1}
+    double dot = 0.0;
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e)
+      if (own(e)) {
+        const int64_t n = nid[e], d = n / nu, u = n - d * nu;
+        const uint32_t Iu = __ldg(H.basis_up + u), Id = __ldg(H.basis_dn + d);
+        const double dg = (H.uniform_U && !H.has_eps) ? s_diag[__popc(Iu & Id)] : diag_of(H, Iu, Id, u, d);
+        double acc_up = 0.0, acc_dn = 0.0;
+        const double *row = cur + d * nu;
+        for (int32_t k = __ldg(H.rp_up + u), k1 = __ldg(H.rp_up + u + 1); k < k1; ++k)
+          acc_up = fma(__ldg(H.val_up + k), row[__ldg(H.col_up + k)], acc_up);
+        for (int32_t k = __ldg(H.rp_dn + d), k1 = __ldg(H.rp_dn + d + 1); k < k1; ++k)
+          acc_dn = fma(__ldg(H.val_dn + k), cur[(int64_t)__ldg(H.col_dn + k) * nu + u], acc_dn);
+        double v = fma(dg, q[e], acc_up + acc_dn);
+        if (j) v = fma(-bp, qp[e], v);
+        w[e] = v;
+        dot = fma(q[e], v, dot);
+      }
+    double b;
+    if (A.mode == 0) {
+      double a, b2;
+      gs.total(dot, &a);
+      double nn = 0.0;
+#pragma unroll
+      for (int e = 0; e < kClusterE; ++e)
+        if (own(e)) {
+          w[e] = fma(-a, q[e], w[e]);
+          nn = fma(w[e], w[e], nn);
+        }
+      gs.total(nn, &b2);
+      b = sqrt(b2);
+      if (lead) {
+        A.hist[2 * j] = a;
+        A.hist[2 * j + 1] = b;
+        A.stat[0] = j + 1;
+      }
+      if (b <= 1e-14 * fmax(1.0, fabs(a))) {   // breakdown: the same decision in every CTA
+        if (lead) A.stat[1] = 1;
+        gs.leave();
+        return;
+      }
+    } else {                          // psi pass: the recorded coefficients
+      const double a = __ldcg(A.hist + 2 * j);
+#pragma unroll
+      for (int e = 0; e < kClusterE; ++e) w[e] = fma(-a, q[e], w[e]);
+      b = __ldcg(A.hist + 2 * j + 1);
+    }
+    const double inv = 1.0 / b;       // q_{j+1} = w / beta_j
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e) {
+      qp[e] = q[e];
+      q[e] = w[e] * inv;
+    }
+    publish(nxt, (j + 1) % 3);
+    cl.sync();
+    double *t = cur;
+    cur = nxt;
+    nxt = t;
+    bp = b;
+  }
+  if (A.mode == 1) {                  // psi /= |psi|
+    double nn = 0.0, p2;
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e)
+      if (own(e)) nn = fma(psi[e], psi[e], nn);
+    gs.total(nn, &p2);
+    const double inv = 1.0 / sqrt(p2);
+#pragma unroll
+    for (int e = 0; e < kClusterE; ++e)
+      if (own(e)) A.psi[nid[e]] = psi[e] * inv;
+  }
+  gs.leave();
+}
+
+// ---------------------------------------------------------------------------------------
 // Host side
 // ---------------------------------------------------------------------------------------
 
@@ -424,52 +605,57 @@ static int small_setup(hub_ctx *h, int64_t D, int maxit, SmallShape *shape) {
   for (int k = 0; k < 3; ++k)
     if (!h->work[k] && !dev_alloc((void **)&h->work[k], sizeof(double) * D, "Lanczos vector")) return HUB_ERR_OOM;
   if (!S->attr_set) {
-    const int smax = (int)(sizeof(double) * kSmallStageMax);
-    HUB_CUDA(cudaFuncSetAttribute(k_small_lanczos<true, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    HUB_CUDA(cudaFuncSetAttribute(k_small_lanczos<true, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, smax));
-    HUB_CUDA(cudaFuncSetAttribute(k_small_lanczos<true, true>, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
+    HUB_CUDA(cudaFuncSetAttribute(k_small_lanczos<true>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(sizeof(double) * kSmallStageMax)));
+    HUB_CUDA(cudaFuncSetAttribute(k_small_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                  (int)(2 * sizeof(double) * kSmallClusterMax)));
+    HUB_CUDA(cudaFuncSetAttribute(k_small_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1));
     S->attr_set = true;
   }
   const int64_t per_cta = (int64_t)kSmallThreads * kSmallPerThread;
   const int64_t want = (D + per_cta - 1) / per_cta;
+  // one cluster of up to 16 CTAs when the sector is small enough, each CTA's slice holds at most
+  // kClusterE states per thread, and such a cluster fits on this GPU
+  shape->cluster = false;
+  if (D <= kSmallClusterMax) {
+    int ctas = (int)std::min<int64_t>(want, kSmallClusterCtas);
+    if ((D + ctas - 1) / ctas > (int64_t)kClusterE * kSmallThreads) ctas = kSmallClusterCtas;
+    if ((D + ctas - 1) / ctas <= (int64_t)kClusterE * kSmallThreads) {
+      cudaLaunchAttribute attr;
+      cudaLaunchConfig_t cfg = cluster_config(ctas, 2 * sizeof(double) * (size_t)D, nullptr, &attr);
+      int n_clusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&n_clusters, k_small_cluster, &cfg) == cudaSuccess && n_clusters >= 1) {
+        shape->cluster = true;
+        shape->stage = true;
+        shape->grid = ctas;
+        return HUB_OK;
+      }
+      (void)cudaGetLastError();      // no such cluster here: the cooperative form
+    }
+  }
   shape->stage = D <= kSmallStageMax;
   const size_t smem = shape->stage ? sizeof(double) * (size_t)D : 0;
-  // one cluster of up to 16 CTAs when the sector is small enough and such a cluster fits
-  shape->cluster = false;
-  if (shape->stage && D <= kSmallClusterMax) {
-    const int ctas = (int)std::min<int64_t>(want, kSmallClusterCtas);
-    cudaLaunchAttribute attr;
-    cudaLaunchConfig_t cfg = cluster_config(ctas, smem, nullptr, &attr);
-    int n_clusters = 0;
-    if (cudaOccupancyMaxActiveClusters(&n_clusters, k_small_lanczos<true, true>, &cfg) == cudaSuccess &&
-        n_clusters >= 1) {
-      shape->cluster = true;
-      shape->grid = ctas;
-      return HUB_OK;
-    }
-    (void)cudaGetLastError();        // no such cluster here: the cooperative form
-  }
   int per_sm = 0;
   if (shape->stage)
-    HUB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_lanczos<true, false>, kSmallThreads, smem));
+    HUB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_lanczos<true>, kSmallThreads, smem));
   else
-    HUB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_lanczos<false, false>, kSmallThreads, 0));
+    HUB_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_small_lanczos<false>, kSmallThreads, 0));
   if (per_sm < 1) return fail(HUB_ERR_CUDA, "small-sector Lanczos: kernel cannot be resident");
   shape->grid = (int)std::min<int64_t>(want, std::min<int64_t>(sms, (int64_t)per_sm * sms));
   return HUB_OK;
 }
 
 static int small_launch(hub_ctx *h, const SmallArgs &A, const SmallShape &shape, cudaStream_t s) {
-  const size_t smem = shape.stage ? sizeof(double) * (size_t)A.D : 0;
   if (shape.cluster) {
     cudaLaunchAttribute attr;
-    cudaLaunchConfig_t cfg = cluster_config(shape.grid, smem, s, &attr);
-    HUB_CUDA(cudaLaunchKernelEx(&cfg, k_small_lanczos<true, true>, A));
+    cudaLaunchConfig_t cfg = cluster_config(shape.grid, 2 * sizeof(double) * (size_t)A.D, s, &attr);
+    HUB_CUDA(cudaLaunchKernelEx(&cfg, k_small_cluster, A));
   } else {
+    const size_t smem = shape.stage ? sizeof(double) * (size_t)A.D : 0;
     // the arrival counter starts every launch at zero
     HUB_CUDA(cudaMemsetAsync(A.bar, 0, sizeof(unsigned), s));
     void *args[] = {(void *)&A};
-    const void *fn = shape.stage ? (const void *)k_small_lanczos<true, false> : (const void *)k_small_lanczos<false, false>;
+    const void *fn = shape.stage ? (const void *)k_small_lanczos<true> : (const void *)k_small_lanczos<false>;
     HUB_CUDA(cudaLaunchCooperativeKernel(fn, dim3(shape.grid), dim3(kSmallThreads), args, smem, s));
   }
   count_launch(h);

@@ -50,11 +50,13 @@ def _launches(hub, m, x0, **kw):
     return r, n
 
 
-# ring 8 (uniform: the double-float driver otherwise), a disordered 9-site ring (FP64 driver
-# otherwise), both staged in shared memory; 10 and 11 sites: vectors beyond the staging size
+# ring 8 (uniform: the double-float driver otherwise) and a disordered 9-site ring (FP64 driver
+# otherwise) run as one thread-block cluster; 9 sites (5,4) as a cooperative grid with the
+# vector staged in shared memory; 10 and 11 sites: vectors beyond the staging size
 CASES = {
-    "ring8": lambda: _uniform(8, 4, 4),
-    "disordered9": lambda: _disordered(9, 4, 3, 40),
+    "ring8_cluster": lambda: _uniform(8, 4, 4),
+    "disordered9_cluster": lambda: _disordered(9, 4, 3, 40),
+    "disordered9_staged": lambda: _disordered(9, 5, 4, 45),
     "ring10_unstaged": lambda: _uniform(10, 5, 5),
     "disordered11_unstaged": lambda: _disordered(11, 5, 4, 50),
 }
@@ -165,9 +167,11 @@ def test_small_refusals_and_reuse(hub):
         m.close()
 
 
-def test_small_deterministic(hub):
-    """Fixed-order reductions: two runs give bit-identical coefficients, E0 and psi."""
-    w = _disordered(10, 5, 4, 80)
+@pytest.mark.parametrize("M,nu,nd", [(10, 5, 4), (8, 4, 3)])
+def test_small_deterministic(hub, M, nu, nd):
+    """Fixed-order reductions: two runs give bit-identical coefficients, E0 and psi (a
+    cooperative grid and a cluster)."""
+    w = _disordered(M, nu, nd, 80)
     m = _model(hub, w)
     try:
         x0 = torch.from_numpy(W.normal(9, m.D)).cuda()
