@@ -50,6 +50,7 @@
 // throughout (also used when t is not uniform).
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <map>
 #include <new>
 #include <utility>
@@ -97,6 +98,7 @@ struct K0State {
   int fix = 0;                  // integer accumulation of the +-t hops (uniform t)
   int s0 = 0;                   // guard bits of the fixed-point terms
   double mt = 0.0;              // -t
+  int *d_clean = nullptr;       // k_k0_clean's flag
 };
 
 constexpr int kDiagTab = 32;   // U n + eps (N_up + N_dn) for n = 0 .. 31 doubly occupied sites
@@ -161,8 +163,9 @@ __device__ __forceinline__ uint32_t k0_move(const K0View &K, uint32_t c, uint32_
 }
 
 // Row value of the product at (i, c) before the projection of short rows, FP64 throughout.
-__device__ __forceinline__ double k0_row_value(const K0View &K, int64_t i, int64_t c, const double *__restrict__ x) {
-  const double *xi = x + i * K.cols;
+// xi: row i of x (in global memory, or staged in shared memory)
+__device__ __forceinline__ double k0_row_value(const K0View &K, int64_t i, int64_t c, const double *__restrict__ x,
+                                               const double *xi) {
   double acc = K.diag_tab[__popc(__ldg(K.rep + i) & __ldg(K.cbits + c))] * xi[c];
   const int k0 = __ldg(K.krp + c), k1 = __ldg(K.krp + c + 1);
   int k = k0;
@@ -196,6 +199,9 @@ struct FixSum {
 };
 
 // Four terms at once: one rescale to the largest of their exponents, then four aligned adds.
+// kClean: the vector holds only zeros and normal numbers (checked before the launch), so an
+// exponent field of 0 marks a zero term and no term is Inf or NaN.
+template <bool kClean>
 __device__ __forceinline__ void fix_add4(FixSum &f, const double (&x)[4], const bool (&neg)[4], int s0) {
   int ek[4];
   unsigned long long m[4];
@@ -205,7 +211,9 @@ __device__ __forceinline__ void fix_add4(FixSum &f, const double (&x)[4], const 
     const unsigned long long b = (unsigned long long)__double_as_longlong(x[j]);
     ek[j] = (int)((b >> 52) & 0x7ff);
     m[j] = b & 0x000fffffffffffffull;
-    if (ek[j] == 0x7ff) {
+    if (kClean) {
+      if (ek[j]) m[j] |= 0x0010000000000000ull;
+    } else if (ek[j] == 0x7ff) {
       f.bad = 1;
       ek[j] = 0;
       m[j] = 0;
@@ -230,10 +238,11 @@ __device__ __forceinline__ void fix_add4(FixSum &f, const double (&x)[4], const 
   }
 }
 
+template <bool kClean>
 __device__ __forceinline__ void fix_add(FixSum &f, double x, bool neg, int s0) {
   const double xs[4] = {x, 0.0, 0.0, 0.0};
   const bool ns[4] = {neg, false, false, false};
-  fix_add4(f, xs, ns, s0);
+  fix_add4<kClean>(f, xs, ns, s0);
 }
 
 // acc * 2^(e - 1075 - s0): the power of two is built from its exponent bits, in two factors
@@ -248,9 +257,9 @@ __device__ __forceinline__ double fix_value(const FixSum &f, int s0) {
 }
 
 // Row value on the integer path: diag x + (-t) S + (hops with other coefficients, FP64).
+template <bool kClean>
 __device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, int64_t c,
-                                                    const double *__restrict__ x) {
-  const double *xi = x + i * K.cols;
+                                                    const double *__restrict__ x, const double *xi) {
   FixSum f{0ll, 0, 0};
   double side = 0.0;
   const int k0 = __ldg(K.krp + c), k1 = __ldg(K.krp + c + 1);
@@ -266,11 +275,11 @@ __device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, i
       v[j] = xi[w[j] & 0x7fffffffu];
       ng[j] = (w[j] >> 31) != 0;
     }
-    fix_add4(f, v, ng, K.s0);
+    fix_add4<kClean>(f, v, ng, K.s0);
   }
   for (; k < k1; ++k) {
     const uint32_t w = __ldg(K.kscol + k);
-    fix_add(f, xi[w & 0x7fffffffu], (w >> 31) != 0, K.s0);
+    fix_add<kClean>(f, xi[w & 0x7fffffffu], (w >> 31) != 0, K.s0);
   }
   const uint32_t ci = __ldg(K.cinfo + c);
   const int h0 = __ldg(K.uh_ptr + i), h1 = __ldg(K.uh_ptr + i + 1);
@@ -293,7 +302,7 @@ __device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, i
         v[j] = 0.0;
       }
     }
-    fix_add4(f, v, ng, K.s0);
+    fix_add4<kClean>(f, v, ng, K.s0);
   }
   for (; k < h1; ++k) {
     const int tw = __ldg(K.uh_t + k);
@@ -301,20 +310,29 @@ __device__ __forceinline__ double k0_row_value_fix(const K0View &K, int64_t i, i
     const uint32_t c2 = k0_move(K, (uint32_t)c, ci, tw & 0xff, &flip);
     const double v = x[(int64_t)__ldg(K.uh_row + k) * K.cols + c2];
     if (tw & kHopUnit) {
-      fix_add(f, v, flip != ((tw & kHopNeg) != 0), K.s0);
+      fix_add<kClean>(f, v, flip != ((tw & kHopNeg) != 0), K.s0);
     } else {
       const double cf = __ldg(K.uh_val + k);
       side = fma(flip ? -cf : cf, v, side);
     }
   }
   const double diag = K.diag_tab[__popc(__ldg(K.rep + i) & __ldg(K.cbits + c))];
+  if (kClean) {
+    // (-t) 2^(e - 1075 - s0) formed exactly in the exponent field of -t (a normal number for
+    // every exponent of the checked vector), so one FMA gives the same rounding as
+    // (-t) (acc 2^(e - 1075 - s0)); e = 0: every term was zero
+    const double sc =
+        f.e ? __longlong_as_double(__double_as_longlong(K.mt) + ((long long)(f.e - 1075 - K.s0) << 52)) : 0.0;
+    return fma(diag, xi[c], fma(sc, (double)f.acc, side));
+  }
   return fma(diag, xi[c], fma(K.mt, fix_value(f, K.s0), side));
 }
 
-template <bool kFix>
-__device__ __forceinline__ double k0_value(const K0View &K, int64_t i, int64_t c, const double *__restrict__ x) {
-  if (kFix) return k0_row_value_fix(K, i, c, x);
-  return k0_row_value(K, i, c, x);
+template <bool kFix, bool kClean>
+__device__ __forceinline__ double k0_value(const K0View &K, int64_t i, int64_t c, const double *__restrict__ x,
+                                           const double *xi) {
+  if (kFix) return k0_row_value_fix<kClean>(K, i, c, x, xi);
+  return k0_row_value(K, i, c, x, xi);
 }
 
 // Member of the orbit of column c under the stabiliser entry s of row i: its column and the
@@ -356,9 +374,12 @@ __device__ __forceinline__ double k0_projected(const K0View &K, int64_t i, int64
   return ls < 0 ? -avg : avg;
 }
 
-template <bool kFix>
-__global__ void __launch_bounds__(kK0Threads) k_k0_apply(K0View K, const double *__restrict__ x,
-                                                         double *__restrict__ y) {
+// gate: null, or the flag of k_k0_clean (0: the vector is clean); the kClean kernel then runs
+// only on a clean vector and the other one only on a vector that is not.
+template <bool kFix, bool kClean>
+__global__ void __launch_bounds__(kK0Threads, 4) k_k0_apply(K0View K, const double *__restrict__ x,
+                                                         double *__restrict__ y, const int *__restrict__ gate) {
+  if (gate && ((__ldg(gate) == 0) != kClean)) return;
   const int64_t chunks = (K.cols + kK0Threads - 1) / kK0Threads;
   const int64_t tiles = K.rows * chunks;
   for (int64_t tile = blockIdx.x; tile < tiles; tile += gridDim.x) {
@@ -367,11 +388,23 @@ __global__ void __launch_bounds__(kK0Threads) k_k0_apply(K0View K, const double 
     if (c >= K.cols) continue;
     double v;
     if (__ldg(K.st_ptr + i) == __ldg(K.st_ptr + i + 1))
-      v = k0_value<kFix>(K, i, c, x);
+      v = k0_value<kFix, kClean>(K, i, c, x, x + i * K.cols);
     else
-      v = k0_projected(K, i, c, [&](int64_t col) { return k0_value<kFix>(K, i, col, x); });
+      v = k0_projected(K, i, c, [&](int64_t col) { return k0_value<kFix, kClean>(K, i, col, x, x + i * K.cols); });
     y[i * K.cols + c] = v;
   }
+}
+
+// *flag |= 1 unless every entry of x is zero or a normal number whose exponent field lies in
+// [lo, hi] (*flag zeroed before the launch)
+__global__ void k_k0_clean(int64_t n, const double *__restrict__ x, int lo, int hi, int *__restrict__ flag) {
+  int bad = 0;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < n; k += (int64_t)gridDim.x * blockDim.x) {
+    const unsigned long long b = (unsigned long long)__double_as_longlong(x[k]);
+    const int e = (int)((b >> 52) & 0x7ff);
+    if ((b << 1) != 0ull && (e < lo || e > hi)) bad = 1;
+  }
+  if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(flag, 1);
 }
 
 // scratch[s, c] = x[short_rows[s], c]
@@ -443,6 +476,7 @@ void k0_release(hub_ctx *h) {
   dev_free(k->short_rows);
   dev_free(k->scratch);
   dev_free(k->d_count);
+  dev_free(k->d_clean);
   delete k;
   h->k0 = nullptr;
 }
@@ -647,18 +681,40 @@ static int k0_build(hub_ctx *h, const Group &G) {
   return HUB_OK;
 }
 
+// Launch one product kernel: CTAs of 256 columns of one row, grid-stride over rows x chunks.
+template <bool kFix, bool kClean>
+static int k0_launch(const hub_ctx *h, const double *x, double *y, const int *gate, cudaStream_t s) {
+  const K0State *k = h->k0;
+  const int64_t tiles = k->rows * ((k->cols + kK0Threads - 1) / kK0Threads);
+  const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 16);
+  k_k0_apply<kFix, kClean><<<grid, kK0Threads, 0, s>>>(k0_view(h), x, y, gate);
+  HUB_LAUNCH_CHECK();
+  return HUB_OK;
+}
+
 int k0_apply(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   const K0State *k = h->k0;
   if (k->rows == 0 || k->cols == 0) return HUB_OK;
-  const int64_t tiles = k->rows * ((k->cols + kK0Threads - 1) / kK0Threads);
-  const int grid = (int)std::min<int64_t>(tiles, (int64_t)num_sms() * 16);
+  int rc;
+  if (k->fix && h->mode == HUB_MODE_AUTO) {
+    // the integer path without the Inf / NaN / subnormal handling when x holds none and every
+    // scale (-t) 2^(e - 1075 - s0) of an entry exponent e is a normal number
+    unsigned long long mt_bits;
+    std::memcpy(&mt_bits, &k->mt, sizeof mt_bits);
+    const int et = (int)((mt_bits >> 52) & 0x7ff);
+    const int lo = std::max(1, 1076 + k->s0 - et), hi = std::min(2046, 2046 + 1075 + k->s0 - et);
+    if (!k->d_clean && !dev_alloc((void **)&k->d_clean, sizeof(int), "momentum-sector flag")) return HUB_ERR_OOM;
+    const int64_t n = k->rows * k->cols;
+    count_launch(h, 3);
+    HUB_CUDA(cudaMemsetAsync(k->d_clean, 0, sizeof(int), s));
+    k_k0_clean<<<(int)std::min<int64_t>((n + 255) / 256, (int64_t)num_sms() * 8), 256, 0, s>>>(n, x, lo, hi,
+                                                                                               k->d_clean);
+    HUB_LAUNCH_CHECK();
+    if ((rc = k0_launch<true, true>(h, x, y, k->d_clean, s))) return rc;
+    return k0_launch<true, false>(h, x, y, k->d_clean, s);
+  }
   count_launch(h);
-  if (k->fix && h->mode == HUB_MODE_AUTO)
-    k_k0_apply<true><<<grid, kK0Threads, 0, s>>>(k0_view(h), x, y);
-  else
-    k_k0_apply<false><<<grid, kK0Threads, 0, s>>>(k0_view(h), x, y);
-  HUB_LAUNCH_CHECK();
-  return HUB_OK;
+  return k0_launch<false, false>(h, x, y, nullptr, s);
 }
 
 int k0_project_inplace(hub_ctx *h, double *x, cudaStream_t s) {

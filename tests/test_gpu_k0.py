@@ -147,6 +147,28 @@ def test_k0_apply_wide_range(hub, M, nu, nd, nnn, omega):
     assert_entrywise(y, Yref.ravel(), np.abs(bound).ravel())
 
 
+@pytest.mark.parametrize("M,omega", [(12, 1), (14, -1)])
+def test_k0_clean_and_general_integer_kernels_agree(hub, M, omega):
+    """The integer-pipe product has two kernels: one for vectors of zeros and normal numbers
+    (checked on the device before each product), one that also handles subnormal, Inf and NaN
+    entries.  Putting a subnormal (1e-310) where the vector had a zero sends the product to the
+    second kernel; every entry the subnormal cannot reach at the 1e-300 level is bit-identical
+    to the first kernel's product of the vector with the zero."""
+    m = hub.Hubbard(M, M // 2, M // 2, ring(M), 1.0, 4.0)
+    m.set_symmetry(hub.HUB_SYM_K0 if omega == 1 else hub.HUB_SYM_KPI)
+    x = m.k_project(torch.from_numpy(W.normal(5, m.D)).cuda())
+    p = int(torch.argmax(x.abs()).item())
+    x[p] = 0.0
+    y_clean = m.apply(x)
+    x2 = x.clone()
+    x2[p] = 1e-310
+    y_gen = m.apply(x2)
+    m.close()
+    keep = y_clean.abs() > 1e-200
+    assert bool(keep.float().mean() > 0.99)
+    assert torch.equal(y_clean[keep], y_gen[keep])
+
+
 @pytest.mark.parametrize("M,omega", [(14, 1), (16, -1)])
 def test_k0_integer_path_matches_fp64_kernel(hub, M, omega):
     """Full-size rings: the integer-pipe product (default) against the FP64 kernel
