@@ -651,7 +651,8 @@ def run_gpu(a):
     if a.e2e_steps > 0:
         xh = torch.from_numpy(x_host).pin_memory()
         yh = torch.empty(D, dtype=torch.float64).pin_memory()
-        hub.hub_apply_host(m.h, xh, yh)
+        for _ in range(2):
+            hub.hub_apply_host(m.h, xh, yh)
         torch.cuda.synchronize()
         calls = []
         for _ in range(a.e2e_steps):
@@ -682,7 +683,8 @@ def run_gpu(a):
                "serial_ms": h2d_ms + dev_ms + d2h_ms,
                "overlap_saved_ms": h2d_ms + dev_ms + d2h_ms - call_ms,
                "call_ms_min_median_max": [1000 * min(calls), 1000 * sorted(calls)[len(calls) // 2],
-                                          1000 * max(calls)]}
+                                          1000 * max(calls)],
+               "call_ms": [1000 * c for c in calls]}
         del xh, yh, xd_, yd_
 
     metric = ("H.x applies/s (4x4 PBC half filling, U=4)" if a.workload == "4x4"

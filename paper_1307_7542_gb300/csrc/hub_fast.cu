@@ -1565,7 +1565,22 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
 constexpr int kHostChunks = 8;
 
 static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double *y_host, double *xd, double *yd,
-                         cudaStream_t s, const int64_t *b, int nc, int64_t per);
+                         cudaStream_t s, const int64_t *bi, int nci, const int64_t *bo, int nco, int64_t per);
+
+// Row chunk bounds b[0..n] of n_dn rows with relative sizes w (boundaries even, so that no
+// pass-1 row pair straddles two chunks; empty chunks dropped); returns n.
+static int chunk_bounds(int64_t n_dn, const int (&w)[kHostChunks], int64_t *b) {
+  int total = 0;
+  for (int c = 0; c < kHostChunks; ++c) total += w[c];
+  int n = 0, acc = 0;
+  b[0] = 0;
+  for (int c = 0; c < kHostChunks; ++c) {
+    acc += w[c];
+    const int64_t e = c + 1 == kHostChunks ? n_dn : std::min<int64_t>(n_dn, (n_dn * acc / total) & ~(int64_t)1);
+    if (e > b[n]) b[++n] = e;
+  }
+  return n;
+}
 
 int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd, double *yd, cudaStream_t s) {
   FastState *f = fast_of(h);
@@ -1598,15 +1613,18 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
   }
   cudaStream_t sc = f->copy_stream;
   const cudaEvent_t ev_start = f->events[2 * kHostChunks];
-  // row chunks with even boundaries, so that no pass-1 row pair straddles two chunks
-  const int64_t per = ((n_dn + kHostChunks - 1) / kHostChunks + 1) & ~(int64_t)1;
-  int nc = 0;
-  int64_t b[kHostChunks + 1];
-  for (int c = 0; c <= kHostChunks; ++c) b[c] = std::min<int64_t>((int64_t)c * per, n_dn);
-  while (nc < kHostChunks && b[nc + 1] > b[nc]) ++nc;
+  // the input's last chunk and the output's first chunk are a quarter of the others: little
+  // pass-1 work is left once the last input chunk has landed, and the first output chunk is
+  // ready to go back early
+  static const int w_in[kHostChunks] = {4, 4, 4, 4, 4, 4, 4, 1}, w_out[kHostChunks] = {1, 4, 4, 4, 4, 4, 4, 4};
+  int64_t bi[kHostChunks + 1], bo[kHostChunks + 1];
+  const int nci = chunk_bounds(n_dn, w_in, bi), nco = chunk_bounds(n_dn, w_out, bo);
+  int64_t per = 0;
+  for (int c = 0; c < nci; ++c) per = std::max(per, bi[c + 1] - bi[c]);
+  for (int c = 0; c < nco; ++c) per = std::max(per, bo[c + 1] - bo[c]);
   HUB_CUDA(cudaEventRecord(ev_start, s));
   HUB_CUDA(cudaStreamWaitEvent(sc, ev_start, 0));
-  rc = pipeline_host(h, f, x_host, y_host, xd, yd, s, b, nc, per);
+  rc = pipeline_host(h, f, x_host, y_host, xd, yd, s, bi, nci, bo, nco, per);
   if (rc) {   // no copy into or out of the caller's buffers may outlive the call
     cudaStreamSynchronize(sc);
     cudaStreamSynchronize(s);
@@ -1614,14 +1632,17 @@ int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd
   return rc;
 }
 
-// The chunked copies and passes of fast_apply_host (b: chunk row bounds, nc chunks).
+// The chunked copies and passes of fast_apply_host (bi: input chunk row bounds, nci chunks;
+// bo: output chunk row bounds, nco chunks; per: the largest chunk).
 static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double *y_host, double *xd, double *yd,
-                         cudaStream_t s, const int64_t *b, int nc, int64_t per) {
+                         cudaStream_t s, const int64_t *bi, int nci, const int64_t *bo, int nco, int64_t per) {
   const int64_t n_up = h->count[0], n_dn = h->count[1];
   const int G = grid_vec();
   int rc;
   cudaStream_t sc = f->copy_stream;
   cudaEvent_t *ev_in = f->events.data(), *ev_out = ev_in + kHostChunks, ev_end = ev_in[2 * kHostChunks + 1];
+  const int64_t *b = bi;
+  int nc = nci;
   for (int c = 0; c < nc; ++c) {
     HUB_CUDA(cudaMemcpyAsync(xd + b[c] * n_up, x_host + b[c] * n_up, sizeof(double) * (b[c + 1] - b[c]) * n_up,
                              cudaMemcpyHostToDevice, sc));
@@ -1656,8 +1677,10 @@ static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double 
     HUB_LAUNCH_CHECK();
     if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
   }
-  // pass 2 in the same row chunks, so that each chunk's result goes back while the next is
+  // pass 2 in the output's row chunks, so that each chunk's result goes back while the next is
   // computed (every chunk reads the whole of X by strips; X is read from HBM once per chunk)
+  b = bo;
+  nc = nco;
   for (int c = 0; c < nc; ++c) {
     if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s, b[c], b[c + 1]))) return rc;
     count_launch(h);

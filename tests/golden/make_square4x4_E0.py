@@ -4,8 +4,8 @@ Hubbard lattice at half filling, (N_up, N_dn) = (8, 8), t = 1, from the CPU orac
 The oracle's plain Lanczos (Sec. IV, Sec. V: no re-orthogonalisation, E0 the lowest
 eigenvalue of the tridiagonal matrix) runs in the two-spin basis of dimension
 12870^2 = 165,636,900 from the seed-0 normal start vector until |E0_j - E0_{j-1}| < 1e-12.
-Nothing here touches the CUDA library.  One U takes one to two hours on eight cores
-(about 45 s per oracle product there).
+Nothing here touches the CUDA library.  One U takes two to four hours on eight cores
+(45 to 90 s per oracle product there, 105 to 140 products).
 
     python tests/golden/make_square4x4_E0.py 4 2 8
 
