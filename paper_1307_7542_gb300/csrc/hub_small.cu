@@ -352,9 +352,9 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_lanczos(const SmallA
 // the cluster (distributed shared memory), so inside a launch no vector passes through L2.
 // Per iteration three cluster barriers: after the <q_j, w> partials, after the |w|^2 partials,
 // after the broadcast of q_{j+1} (shared-memory copies alternate, so a broadcast never
-// overwrites the copy a slower CTA is still reading).  q_j also goes to global memory (slot
-// j % 3), where the next launch of the run finds q_{j0} and q_{j0-1}; the psi pass repeats the
-// same operations with the recorded alpha_j, beta_j.
+// overwrites the copy a slower CTA is still reading).  The last two vectors of a launch also go
+// to global memory (slot j % 3), where the next launch of the run finds q_{j0} and q_{j0-1}; the
+// psi pass repeats the same operations with the recorded alpha_j, beta_j.
 // ---------------------------------------------------------------------------------------
 constexpr int kClusterE = 3;        // states per thread at most
 
@@ -391,12 +391,14 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_cluster(const SmallA
   }
   auto own = [&](int e) { return nid[e] < hi; };
   double *cur = xs, *nxt = xs + D;
-  // q_{j+1} (in q) into global slot k and into every CTA's copy dst
-  auto publish = [&](double *dst, int k) {
+  // q (q_{j+1}) into every CTA's copy dst and, when `global`, into global slot k: the next launch
+  // of the run reads only the last two vectors of this one, so only those are stored (fewer
+  // stores for the cluster barrier's release to wait for)
+  auto publish = [&](double *dst, int k, bool global) {
 #pragma unroll
     for (int e = 0; e < kClusterE; ++e)
       if (own(e)) {
-        V(k)[nid[e]] = q[e];
+        if (global) V(k)[nid[e]] = q[e];
         for (int r = 0; r < G; ++r) cl.map_shared_rank(dst, (unsigned)r)[nid[e]] = q[e];
       }
   };
@@ -424,7 +426,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_cluster(const SmallA
     const double inv = 1.0 / s;
 #pragma unroll
     for (int e = 0; e < kClusterE; ++e) q[e] *= inv;
-    publish(cur, 0);
+    publish(cur, 0, A.mode == 0);
     cl.sync();
   } else {                            // q_{j0}, q_{j0-1} and beta_{j0-1} from the earlier launches
     bp = __ldcg(A.hist + 2 * (A.j0 - 1) + 1);
@@ -499,7 +501,7 @@ __global__ void __launch_bounds__(kSmallThreads, 1) k_small_cluster(const SmallA
       qp[e] = q[e];
       q[e] = w[e] * inv;
     }
-    publish(nxt, (j + 1) % 3);
+    publish(nxt, (j + 1) % 3, A.mode == 0 && j + 2 >= A.j1);
     cl.sync();
     double *t = cur;
     cur = nxt;
