@@ -527,6 +527,7 @@ def run_gpu(a):
     apply_ms, n_apply, n_kern = hub.hub_profile_read(m.h, hub.HUB_PROF_APPLY)
     up_ms, n_up_l, _ = hub.hub_profile_read(m.h, hub.HUB_PROF_UP)
     dn_ms, n_dn_l, _ = hub.hub_profile_read(m.h, hub.HUB_PROF_DN)
+    ud_ms, n_ud_l, _ = hub.hub_profile_read(m.h, hub.HUB_PROF_UPDATE)
     hub.hub_profile(m.h, False)
     clk = clocks.stop() if clocks else None
     assert r["iters"] == a.steps, r
@@ -549,14 +550,20 @@ def run_gpu(a):
              "fp64_equiv_rate_T": nnz_H / (apply_avg_ms / 1000.0) / 1e12,
              "fp64_alu_frac": nnz_H / (apply_avg_ms / 1000.0) / FP64_INSTR_PEAK}
     if n_up_l and n_dn_l:
-        # fast path.  HBM bytes per element: pass 1 with the fused Lanczos update reads w and
-        # r_{j-1} rows and writes r_j and Z (32 B); pass 2 (Lanczos epilogue) reads X by strips,
-        # Z, r_j, r_{j-1} and writes w (40 B).  FP32 pipe: each hopping term costs 14 FP32
-        # operations in the compensated double-float sum (both passes).
+        # fast path, each pass timed by its own event pair.  HBM bytes per element (double-float
+        # vectors, 8 B): pass 1 reads X and writes Z (16 B); pass 2 (Lanczos epilogue) reads X by
+        # strips, Z, r_j, r_{j-1} and writes w (40 B); the update reads w and r_{j-1} and writes
+        # r_j (24 B).  FP32 pipe: each hopping term costs 14 FP32 operations in the compensated
+        # double-float sum (both passes).
         up_avg, dn_avg = up_ms / n_up_l, dn_ms / n_dn_l
         terms = {"k_up": nnz_u * m.count_dn, "k_dn": nnz_d * m.count_up}
-        passes = {"k_up": {"ms": up_avg, "algorithmic_bytes": 32 * D, "gbs": gb(32 * D, up_avg)},
+        passes = {"k_up": {"ms": up_avg, "algorithmic_bytes": 16 * D, "gbs": gb(16 * D, up_avg)},
                   "k_dn": {"ms": dn_avg, "algorithmic_bytes": 40 * D, "gbs": gb(40 * D, dn_avg)}}
+        update = None
+        if n_ud_l:
+            ud_avg = ud_ms / n_ud_l
+            update = {"kernel": "k_df_update", "ms": ud_avg, "launches": n_ud_l, "algorithmic_bytes": 24 * D,
+                      "gbs": gb(24 * D, ud_avg), "hbm_frac": gb(24 * D, ud_avg) / hbm_gbs}
         for k_, v_ in passes.items():
             ops = FP32_OPS_PER_TERM * terms[k_]
             v_["hbm_frac"] = v_["gbs"] / hbm_gbs
@@ -587,7 +594,7 @@ def run_gpu(a):
         roofline.update({"traffic": traffic,
                          "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the same kernel "
                                             "on the 4x4 (6,6) sector, scaled by elements" if traffic else None),
-                         "passes": passes, "apply": apply})
+                         "passes": passes, "update": update, "apply": apply})
     else:
         # native FP64 kernel: bound by the FP64 pipe
         roofline = {"bound": "alu", "kernel": "k_apply_f64", "achieved": apply["fp64_equiv_rate_T"],

@@ -65,6 +65,7 @@ extern "C" {
 #define HUB_PROF_APPLY 0  /* a whole product H x (both passes on the fast path)       */
 #define HUB_PROF_UP 1     /* fast path pass 1: spin-up hops + diagonal                 */
 #define HUB_PROF_DN 2     /* fast path pass 2: spin-down hops + epilogue               */
+#define HUB_PROF_UPDATE 3 /* fast Lanczos: the update r_j = w - c r_{j-1} (its own pass) */
 
 typedef struct hub_ctx *hub_t;
 
@@ -425,8 +426,9 @@ int hub_test_fail_waits(hub_t h, int enable);
 /*
  * Measurement hooks (no counterpart in the paper).  hub_profile(h, 1) resets the counters
  * and starts recording a CUDA event pair on the launching stream around every product
- * (HUB_PROF_APPLY) and every fast-path pass (HUB_PROF_UP, HUB_PROF_DN); up to 65536
- * launches per kind are timed, later ones only counted.  hub_profile(h, 0) stops.
+ * (HUB_PROF_APPLY), every fast-path pass (HUB_PROF_UP, HUB_PROF_DN) and every separate
+ * Lanczos update pass of the fast driver (HUB_PROF_UPDATE); up to 65536 launches per kind are
+ * timed, later ones only counted.  hub_profile(h, 0) stops.
  * hub_profile_read waits for the events and returns, for one kind, the summed time in
  * milliseconds and the number of launches, plus the number of kernels the handle launched
  * since profiling started.  Any output pointer may be NULL.

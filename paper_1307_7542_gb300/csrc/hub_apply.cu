@@ -158,14 +158,14 @@ extern "C" int hub_profile(hub_t h, int enable) {
   if (!h) return fail(HUB_ERR_ARG, "hub_profile: NULL handle");
   h->prof = enable != 0;
   if (h->prof) {
-    for (int k = 0; k < 3; ++k) h->n_launch[k] = h->n_timed[k] = 0;
+    for (int k = 0; k < hub_ctx::kProfKinds; ++k) h->n_launch[k] = h->n_timed[k] = 0;
     h->n_kernels = 0;
   }
   return HUB_OK;
 }
 
 extern "C" int hub_profile_read(hub_t h, int kind, double *ms, int64_t *launches, int64_t *kernel_launches) {
-  if (!h || kind < 0 || kind > 2) return fail(HUB_ERR_ARG, "hub_profile_read: bad argument");
+  if (!h || kind < 0 || kind >= hub_ctx::kProfKinds) return fail(HUB_ERR_ARG, "hub_profile_read: bad argument");
   double total = 0.0;
   for (int64_t k = 0; k < h->n_timed[kind]; ++k) {
     HUB_CUDA(cudaEventSynchronize(h->ev_end[kind][k]));

@@ -1458,16 +1458,18 @@ static int run_up(hub_ctx *h, FastState *f, float *x, float *z, cudaStream_t s, 
   if ((!f->staged || upd) && (p0 != 0 || p1 != (v.n_dn + 1) / 2))
     return fail(HUB_ERR_STATE, "pass 1: partial range");
   if (p1 <= p0) return HUB_OK;
-  int rc = prof_mark(h, HUB_PROF_UP, true, s);
-  if (rc) return rc;
+  int rc;
   const bool fused = upd && f->staged && kFusedUpdate;
-  if (upd && !fused) {
+  if (upd && !fused) {                 // the update as its own pass, timed on its own
+    if ((rc = prof_mark(h, HUB_PROF_UPDATE, true, s))) return rc;
     const int G = grid_vec();
     count_launch(h);
     k_df_update<<<G, 256, 0, s>>>(quads(h, f), x, upd->r_prev, upd->coef, upd->partials);
     HUB_LAUNCH_CHECK();
     if (n_part) *n_part = G;
+    if ((rc = prof_mark(h, HUB_PROF_UPDATE, false, s))) return rc;
   }
+  if ((rc = prof_mark(h, HUB_PROF_UP, true, s))) return rc;
   if (f->staged) {
     count_launch(h);
     const int threads = v.n_up >= 4096 ? kUpThreads : (v.n_up >= 1024 ? 512 : (v.n_up >= 256 ? 256 : 128));

@@ -114,9 +114,10 @@ struct hub_ctx {
 
   // measurement: event pairs per kind (HUB_PROF_*), launch counters
   bool prof = false;
-  std::vector<cudaEvent_t> ev_start[3], ev_end[3];
-  int64_t n_launch[3] = {0, 0, 0};     // launches per kind since hub_profile(h, 1)
-  int64_t n_timed[3] = {0, 0, 0};      // of which timed with an event pair
+  static constexpr int kProfKinds = 4; // HUB_PROF_APPLY .. HUB_PROF_UPDATE
+  std::vector<cudaEvent_t> ev_start[kProfKinds], ev_end[kProfKinds];
+  int64_t n_launch[kProfKinds] = {0, 0, 0, 0};   // launches per kind since hub_profile(h, 1)
+  int64_t n_timed[kProfKinds] = {0, 0, 0, 0};    // of which timed with an event pair
   int64_t n_kernels = 0;               // all kernels launched since hub_profile(h, 1)
 
   // fast path (double-float, two-pass apply) for uniform hopping and interaction

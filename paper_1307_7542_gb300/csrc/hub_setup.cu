@@ -556,7 +556,7 @@ extern "C" void hub_free(hub_t h) {
   fast_release(h);
   k0_release(h);
   small_release(h);
-  for (int k = 0; k < 3; ++k) {
+  for (int k = 0; k < hub_ctx::kProfKinds; ++k) {
     for (cudaEvent_t e : h->ev_start[k]) cudaEventDestroy(e);
     for (cudaEvent_t e : h->ev_end[k]) cudaEventDestroy(e);
   }

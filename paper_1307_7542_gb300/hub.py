@@ -288,7 +288,7 @@ def hub_profile(h, enable):
 
 
 HUB_MODE_AUTO, HUB_MODE_FP64 = 0, 1
-HUB_PROF_APPLY, HUB_PROF_UP, HUB_PROF_DN = 0, 1, 2
+HUB_PROF_APPLY, HUB_PROF_UP, HUB_PROF_DN, HUB_PROF_UPDATE = 0, 1, 2, 3
 
 
 def hub_profile_read(h, kind=HUB_PROF_APPLY):
