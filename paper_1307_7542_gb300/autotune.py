@@ -46,7 +46,7 @@ APPLY_SPACE = {
     "HUB_DN_LANE_COLS": [2, 4],
     "HUB_DN_BATCH": [2, 4],
     "HUB_DN_MINB": [3, 4, 5, 6],
-    "HUB_BANK_CAP": [2, 3, 0, -2],
+    "HUB_BANK_CAP": [2, 1, 3, 0, -2],
     "HUB_FUSED_UPDATE": [1, 0],
     "HUB_UPD_Q": [1, 2],
     "HUB_UP_THREADS": [1024, 768, 512],
