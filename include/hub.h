@@ -117,11 +117,12 @@ int hub_get_csr(hub_t h, int spin, int32_t *rowptr_host, int32_t *cols_host, dou
  * absolute matrix.  The native FP64 kernel (HUB_MODE_FP64; non-uniform t or U) does
  * this with FP64 multiply-adds.  In HUB_MODE_AUTO with uniform t and U the product runs
  * in double-float arithmetic (pairs of FP32 numbers, 48 significant bits; compensated
- * sums) with a worst-case error of about 12 * 2^-48 (|H||x|)_n = 4.3e-14 (|H||x|)_n.
+ * sums) with a derived worst-case error of max(N + 10.1, 16) * 2^-48 (|H||x|)_n, N <= 15 the
+ * most terms one low-part accumulator takes (N = 9 on the 4x4 lattice: 6.8e-14 (|H||x|)_n).
  * That bound needs a window, checked on the device for every call: the largest |x_n| in
  * [2^-823, 2^877], every nonzero |x_n| at least 2^-80 times the largest (no FP64
- * subnormals, infinities or NaN), and |t|, |U| and every |eps_i| either 0 or in
- * [2^-16, 2^16] (t != 0).  A vector or model outside it is multiplied by the FP64 kernel
+ * subnormals, infinities or NaN); and a model with uniform t != 0 and U, no site energies,
+ * |t| and U/|t| either 0 or in [2^-16, 2^16].  A vector or model outside it is multiplied by the FP64 kernel
  * instead, on the same stream and with no host synchronisation, so every call meets the
  * bound.
  */
@@ -389,7 +390,7 @@ int hub_k_project(hub_t h, const double *x_dev, double *y_dev, void *stream);
  * with uniform t and U on the fast path: vectors held as pairs of FP32 numbers (about 48
  * significant bits), sums by error-free transformations on the FP32 pipe, because the
  * FP64 unit of this GPU issues about 1/70 of the FP32 rate.  Its per-entry error is at
- * most about 4.3e-14 (|H||x|)_n inside the window stated at hub_apply, and inputs outside
+ * most 6.8e-14 (|H||x|)_n at 4x4 inside the window stated at hub_apply, and inputs outside
  * the window go to the FP64 kernel, so both modes meet 1e-13 (|H||x|)_n.  Inputs and
  * outputs of every entry point stay FP64.  HUB_MODE_FP64 forces the native FP64 kernels.
  */

@@ -12,6 +12,8 @@ shapes from compile-time knobs:
   it stages the rows; 0: a separate vector pass before pass 1;
 * ``HUB_UPD_Q``        -- column quads per thread whose loads the fused update issues together;
 * ``HUB_UP_THREADS``   -- threads of the pass-1 CTA (1024, 768 or 512; fewer leave more registers);
+* ``HUB_UP_PAIRED``    -- 1: pass 1 adds the low parts of a column word's two entries together
+  before accumulating them (two accumulators, as pass 2); 0: four accumulators of single terms;
 * ``HUB_BATCH_THREADS`` -- threads per CTA of the batched persistent solver;
 * ``HUB_SMALL_CLUSTER_MAX``, ``HUB_SMALL_THREADS``, ``HUB_SMALL_PER_THREAD``,
   ``HUB_SMALL_BATCH`` -- the largest sector the single-launch small-sector Lanczos
@@ -50,12 +52,14 @@ APPLY_SPACE = {
     "HUB_FUSED_UPDATE": [1, 0],
     "HUB_UPD_Q": [1, 2],
     "HUB_UP_THREADS": [1024, 768, 512],
+    "HUB_UP_PAIRED": [1, 0],
 }
 BATCH_SPACE = {"HUB_BATCH_THREADS": [256, 512, 1024]}
 SMALL_SPACE = {"HUB_SMALL_CLUSTER_MAX": [12800, 0], "HUB_SMALL_THREADS": [128, 256, 320, 384, 512],
                "HUB_SMALL_PER_THREAD": [1, 2, 4], "HUB_SMALL_BATCH": [8, 4, 16]}
 DEFAULTS = {"HUB_DN_LANE_COLS": 4, "HUB_DN_BATCH": 2, "HUB_DN_MINB": 4, "HUB_BANK_CAP": 2,
-            "HUB_FUSED_UPDATE": 0, "HUB_UPD_Q": 1, "HUB_UP_THREADS": 1024, "HUB_BATCH_THREADS": 256,
+            "HUB_FUSED_UPDATE": 0, "HUB_UPD_Q": 1, "HUB_UP_THREADS": 1024, "HUB_UP_PAIRED": 1,
+            "HUB_BATCH_THREADS": 256,
             "HUB_SMALL_CLUSTER_MAX": 12800, "HUB_SMALL_THREADS": 320, "HUB_SMALL_PER_THREAD": 1,
             "HUB_SMALL_BATCH": 8}
 # tuned.json key of each group's timing

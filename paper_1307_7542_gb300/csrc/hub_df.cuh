@@ -31,7 +31,7 @@ __device__ __forceinline__ void fast_two_sum(float a, float b, float &s, float &
 
 // Accumulator: the exact sum of the high parts is kept as H plus the rounding errors,
 // which go to L together with the low parts (used for the long dot products of Lanczos;
-// the hopping sums of the product use the compensated DfSum4 below).
+// the hopping sums of the product use the compensated DfSumP or DfSum4 below).
 struct DfAcc {
   float H, L;
 };

@@ -328,6 +328,9 @@ __device__ __forceinline__ double df2_lanes_to_f64(f2x h, f2x l) {
 #ifndef HUB_FUSED_UPDATE
 #define HUB_FUSED_UPDATE 1   // 0: the Lanczos update as a separate vector pass before pass 1
 #endif
+#ifndef HUB_UP_PAIRED
+#define HUB_UP_PAIRED 1   // 1: pass 1 sums with DfSumP (low parts of a word's two entries paired); 0: DfSum4
+#endif
 #ifndef HUB_UP_THREADS
 #define HUB_UP_THREADS 1024   // threads of the pass-1 CTA (one CTA per SM; fewer leave more registers)
 #endif
@@ -485,54 +488,85 @@ __global__ void __launch_bounds__(kUpThreads, 1) k_up(const FastView F, float *x
         z1[ld + slot] = 0.f;
         continue;
       }
+#if HUB_UP_PAIRED
+      DfSumP acc{0ull, 0ull, 0ull, {0ull, 0ull}};
+#else
       DfSum4 acc{0ull, 0ull, 0ull, {0ull, 0ull, 0ull, 0ull}};
+#endif
       const int64_t sl = slot >> 5, lane = slot & 31;
       const uint4 *__restrict__ wa = reinterpret_cast<const uint4 *>(F.sl_add + F.sl_off_add[sl]) + lane;
       const uint4 *__restrict__ wsb = reinterpret_cast<const uint4 *>(F.sl_sub + F.sl_off_sub[sl]) + lane;
       const int na = F.steps_add[sl], ns = F.steps_sub[sl];
-      // one scheduled entry (idle steps read the zero column): (hi d0, hi d1), (lo d0, lo d1);
-      // J: the low-part accumulator, by the entry's position in its batch
-#define HUB_TERM(OP, J, C)                                                               \
-  do {                                                                                   \
-    const float *p_ = xs + (C);                                                          \
-    OP(acc, pk2(p_[0], p_[2 * kUpPlane]), pk2(p_[kUpPlane], p_[3 * kUpPlane]), (J));     \
-  } while (0)
-#define HUB_WORD(OP, J, WD)                                                              \
+      // the (hi d0, hi d1) and (lo d0, lo d1) pairs of staged column C (idle steps read the zero
+      // column)
+#define HUB_HI(C) pk2(xs[(C)], xs[(C) + 2 * kUpPlane])
+#define HUB_LO(C) pk2(xs[(C) + kUpPlane], xs[(C) + 3 * kUpPlane])
+#if HUB_UP_PAIRED
+      // one word: both of its scheduled entries as a pair (uint16) or one entry (uint32), the
+      // low parts to accumulator J (alternating by the word's position in its batch)
+#define HUB_WORD(ADD, J, WD)                                                             \
   do {                                                                                   \
     if (sizeof(Col) == 2) {                                                              \
-      HUB_TERM(OP, (J), (WD) & 0xffffu);                                                 \
-      HUB_TERM(OP, (J) + 1, (WD) >> 16);                                                 \
+      const uint32_t ca_ = (WD) & 0xffffu, cb_ = (WD) >> 16;                             \
+      sump_pair(acc, HUB_HI(ca_), HUB_LO(ca_), HUB_HI(cb_), HUB_LO(cb_), (ADD), (J));    \
     } else {                                                                             \
-      HUB_TERM(OP, (J), (WD));                                                           \
+      sump_one(acc, HUB_HI(WD), HUB_LO(WD), (ADD), (J));                                 \
     }                                                                                    \
   } while (0)
+#define HUB_J(w) (w)
+#else
+      // one scheduled entry: J, the low-part accumulator, by the entry's position in its batch
+#define HUB_TERM(ADD, J, C)                                                              \
+  do {                                                                                   \
+    if (ADD)                                                                             \
+      sum4_add(acc, HUB_HI(C), HUB_LO(C), (J));                                          \
+    else                                                                                 \
+      sum4_sub(acc, HUB_HI(C), HUB_LO(C), (J));                                          \
+  } while (0)
+#define HUB_WORD(ADD, J, WD)                                                             \
+  do {                                                                                   \
+    if (sizeof(Col) == 2) {                                                              \
+      HUB_TERM(ADD, (J), (WD) & 0xffffu);                                                \
+      HUB_TERM(ADD, (J) + 1, (WD) >> 16);                                                \
+    } else {                                                                             \
+      HUB_TERM(ADD, (J), (WD));                                                          \
+    }                                                                                    \
+  } while (0)
+#define HUB_J(w) (((w) * (sizeof(Col) == 2 ? 2 : 1)) & 3)
+#endif
       // Full batches of four words run unguarded; the last batch is taken word by word
       // (a word's padding step reads the zero column).  N is uniform over the warp.
-#define HUB_GROUP(OP, W, N)                                                              \
+#define HUB_GROUP(ADD, W, N)                                                             \
   do {                                                                                   \
     constexpr int kPer = sizeof(Col) == 2 ? 8 : 4;       /* steps per batch */           \
     constexpr int kPerWord = sizeof(Col) == 2 ? 2 : 1;                                   \
-    constexpr int kJ1 = kPerWord, kJ2 = (2 * kPerWord) & 3, kJ3 = (3 * kPerWord) & 3;   \
     const int nst = (N), nb = (nst + kPer - 1) / kPer;                                   \
     uint4 qn = nb > 0 ? W[0] : make_uint4(0u, 0u, 0u, 0u);                               \
     for (int b = 0; b < nb; ++b) {                                                       \
       const uint4 q = qn;                                                                \
       if (b + 1 < nb) qn = W[(b + 1) * 32];     /* next batch's columns in flight */     \
       const int rem = nst - kPer * b;                                                    \
-      HUB_WORD(OP, 0, q.x);                                                              \
-      if (rem > kPerWord) HUB_WORD(OP, kJ1, q.y);                                        \
-      if (rem > 2 * kPerWord) HUB_WORD(OP, kJ2, q.z);                                    \
-      if (rem > 3 * kPerWord) HUB_WORD(OP, kJ3, q.w);                                    \
+      HUB_WORD(ADD, HUB_J(0), q.x);                                                      \
+      if (rem > kPerWord) HUB_WORD(ADD, HUB_J(1), q.y);                                  \
+      if (rem > 2 * kPerWord) HUB_WORD(ADD, HUB_J(2), q.z);                              \
+      if (rem > 3 * kPerWord) HUB_WORD(ADD, HUB_J(3), q.w);                              \
     }                                                                                    \
   } while (0)
-      HUB_GROUP(sum4_add, wa, na);
-      HUB_GROUP(sum4_sub, wsb, ns);
+      HUB_GROUP(true, wa, na);
+      HUB_GROUP(false, wsb, ns);
 #undef HUB_GROUP
 #undef HUB_WORD
+#undef HUB_J
 #undef HUB_TERM
+#undef HUB_HI
+#undef HUB_LO
       // Z = diag x + t' S for both rows (packed), t' = +-1
       f2x Sh, Sl;
+#if HUB_UP_PAIRED
+      sump_norm(acc, Sh, Sl);
+#else
       sum4_norm(acc, Sh, Sl);
+#endif
       if (F.t_neg) {
         Sh ^= kSign2;
         Sl ^= kSign2;
