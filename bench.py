@@ -37,7 +37,7 @@ FP32_OPS_PER_TERM = 14        # compensated double-float sum: TwoSum, TwoSum of 
 # DRAM bytes (read + write) per element of X from one ncu capture of each kernel on the 4x4
 # (6,6) sector (profiles/k_up_4x4_sector66.md, profiles/k_dn_4x4_sector66.md); the
 # per-element traffic does not depend on the sector, so a launch's traffic is this times D.
-NCU_DRAM_BYTES_PER_ELEMENT = {"k_up": 0.98187776e9 / 64128064, "k_dn": 2.0847303e9 / 64128064}
+NCU_DRAM_BYTES_PER_ELEMENT = {"k_up": 0.98165581e9 / 64128064, "k_dn": 2.0847303e9 / 64128064}
 STAGE_MAX_COLS = 14076        # rows up to this length are staged in shared memory by pass 1
 # arithmetic of the timed fast path: vectors as pairs of FP32 numbers (48-bit significands),
 # compensated sums; FP64 at the interface
