@@ -502,16 +502,14 @@ __global__ void __launch_bounds__(kUpThreads, 1) k_up(const FastView F, float *x
 #define HUB_HI(C) pk2(xs[(C)], xs[(C) + 2 * kUpPlane])
 #define HUB_LO(C) pk2(xs[(C) + kUpPlane], xs[(C) + 3 * kUpPlane])
 #if HUB_UP_PAIRED
-      // one word: both of its scheduled entries as a pair (uint16) or one entry (uint32), the
-      // low parts to accumulator J (alternating by the word's position in its batch)
+      // uint16: one word, both of its scheduled entries as a pair, the low parts to accumulator
+      // J (alternating by the word's position in its batch); uint32 (one entry per word): the
+      // batch's words x, y as one pair (accumulator 0) and z, w as another (accumulator 1), so
+      // that either way an accumulator takes one pair sum per four scheduled entries
 #define HUB_WORD(ADD, J, WD)                                                             \
   do {                                                                                   \
-    if (sizeof(Col) == 2) {                                                              \
-      const uint32_t ca_ = (WD) & 0xffffu, cb_ = (WD) >> 16;                             \
-      sump_pair(acc, HUB_HI(ca_), HUB_LO(ca_), HUB_HI(cb_), HUB_LO(cb_), (ADD), (J));    \
-    } else {                                                                             \
-      sump_one(acc, HUB_HI(WD), HUB_LO(WD), (ADD), (J));                                 \
-    }                                                                                    \
+    const uint32_t ca_ = (WD) & 0xffffu, cb_ = (WD) >> 16;                               \
+    sump_pair(acc, HUB_HI(ca_), HUB_LO(ca_), HUB_HI(cb_), HUB_LO(cb_), (ADD), (J));      \
   } while (0)
 #define HUB_J(w) (w)
 #else
@@ -546,15 +544,35 @@ __global__ void __launch_bounds__(kUpThreads, 1) k_up(const FastView F, float *x
       const uint4 q = qn;                                                                \
       if (b + 1 < nb) qn = W[(b + 1) * 32];     /* next batch's columns in flight */     \
       const int rem = nst - kPer * b;                                                    \
-      HUB_WORD(ADD, HUB_J(0), q.x);                                                      \
-      if (rem > kPerWord) HUB_WORD(ADD, HUB_J(1), q.y);                                  \
-      if (rem > 2 * kPerWord) HUB_WORD(ADD, HUB_J(2), q.z);                              \
-      if (rem > 3 * kPerWord) HUB_WORD(ADD, HUB_J(3), q.w);                              \
+      if (HUB_UP_PAIRED && sizeof(Col) == 4) {                                           \
+        HUB_PAIR32(ADD, 0, q.x, q.y, rem > 1);                                           \
+        if (rem > 2) HUB_PAIR32(ADD, 1, q.z, q.w, rem > 3);                              \
+      } else {                                                                           \
+        HUB_WORD(ADD, HUB_J(0), q.x);                                                    \
+        if (rem > kPerWord) HUB_WORD(ADD, HUB_J(1), q.y);                                \
+        if (rem > 2 * kPerWord) HUB_WORD(ADD, HUB_J(2), q.z);                            \
+        if (rem > 3 * kPerWord) HUB_WORD(ADD, HUB_J(3), q.w);                            \
+      }                                                                                  \
     }                                                                                    \
   } while (0)
+#if HUB_UP_PAIRED
+      // two 32-bit words as one pair, or the first alone when the batch ends after it
+#define HUB_PAIR32(ADD, J, WA, WB, BOTH)                                                 \
+  do {                                                                                   \
+    if (BOTH)                                                                            \
+      sump_pair(acc, HUB_HI(WA), HUB_LO(WA), HUB_HI(WB), HUB_LO(WB), (ADD), (J));        \
+    else                                                                                 \
+      sump_one(acc, HUB_HI(WA), HUB_LO(WA), (ADD), (J));                                 \
+  } while (0)
+#else
+#define HUB_PAIR32(ADD, J, WA, WB, BOTH) \
+  do {                                   \
+  } while (0)
+#endif
       HUB_GROUP(true, wa, na);
       HUB_GROUP(false, wsb, ns);
 #undef HUB_GROUP
+#undef HUB_PAIR32
 #undef HUB_WORD
 #undef HUB_J
 #undef HUB_TERM
