@@ -700,8 +700,8 @@ int small_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E
     int j0, j1, slot;
   } queue[2];
   int head = 0, n_q = 0, next = 0;
-  auto enqueue = [&](int slot) -> int {
-    const int j0 = next, j1 = std::min(maxit, next + B);
+  auto enqueue = [&](int slot, int size) -> int {
+    const int j0 = next, j1 = std::min(maxit, next + size);
     A.mode = 0;
     A.j0 = j0;
     A.j1 = j1;
@@ -724,9 +724,9 @@ int small_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E
 
   h->alpha.clear();
   h->beta.clear();
-  if ((rc = enqueue(0))) return rc;
-  if (next < maxit && (rc = enqueue(1))) return rc;
-  double E = 0.0, E_prev = 0.0;
+  if ((rc = enqueue(0, B))) return rc;
+  if (next < maxit && (rc = enqueue(1, B))) return rc;
+  double E = 0.0, E_prev = 0.0, dE_prev = -1.0, dE_last = -1.0;
   LowestTracker lowest;
   int status = HUB_ERR_NOCONV;
   bool stop = false;
@@ -761,6 +761,10 @@ int small_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E
         stop = true;
         break;
       }
+      if (tol > 0 && j > 0) {
+        dE_prev = dE_last;
+        dE_last = std::fabs(E - E_prev);
+      }
       E_prev = E;
       if (bb <= 1e-14 * std::fmax(1.0, std::fabs(a))) {
         status = HUB_CONVERGED_BREAKDOWN;
@@ -772,7 +776,24 @@ int small_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E
       status = HUB_CONVERGED_BREAKDOWN;
       stop = true;
     }
-    if (!stop && next < maxit && (rc = enqueue(b.slot))) return rc;
+    if (!stop && next < maxit) {
+      // Batch size: once |dE0| falls geometrically, the iterations still needed are about
+      // log(tol / dE) / log(rate); a batch that would run past the predicted stop is cut
+      // short, and none is started while the one in flight is predicted to reach it (the
+      // stopping rule itself is unchanged: the predictions only move launch boundaries)
+      int size = B;
+      bool wait = false;
+      if (tol > 0 && dE_prev > 0.0 && dE_last > 0.0 && dE_last < 0.95 * dE_prev) {
+        const double need = std::log(tol / dE_last) / std::log(dE_last / dE_prev);
+        const int ahead = next - (int)h->alpha.size();    // launched, not yet seen
+        const int more = (int)std::ceil(need) - ahead;
+        if (more <= 0 && n_q > 0)
+          wait = true;
+        else
+          size = std::max(1, std::min(B, more + 1));
+      }
+      if (!wait && (rc = enqueue(b.slot, size))) return rc;
+    }
   }
   if ((rc = drain())) return rc;
   if (tol <= 0 && status == HUB_ERR_NOCONV) status = HUB_OK;
