@@ -72,7 +72,7 @@ struct SmallState {
   int64_t cap = 0;             // iterations the history holds
   int grid_cap = 0;            // CTAs the partial sums hold
   double *dev = nullptr;       // part [2 grid_cap] | hist [2 cap] | start [1] | coef [cap]
-  int *dint = nullptr;         // stat [4] (iterations done, stop flag) | err | pad | barrier [2]
+  int *dint = nullptr;         // stat [4] (iterations done, stop flag) | err | pad | arrival counter | pad
   double *host = nullptr;      // pinned: hist [2 cap] | start
   int *hstat = nullptr;        // pinned: stat copies, [2][4] (one per batch in flight)
   cudaEvent_t ev[2] = {nullptr, nullptr};
@@ -82,7 +82,7 @@ struct SmallState {
 struct SmallArgs {
   Ham H;
   int64_t D;
-  double *V0, *V1, *V2;        // S_j in slot j % 3
+  double *V0, *V1, *V2;        // Lanczos vectors in slot j % 3 (S_j in the grid form, q_j in the cluster form)
   const double *x0;            // start vector (nullptr: SplitMix64 uniform [-1, 1), seed 0)
   double *part, *hist, *start;
   const double *coef;          // mode 1: y
