@@ -400,7 +400,7 @@ int hub_set_mode(hub_t h, int mode);
  * Small-sector Lanczos (no counterpart in the paper): hub_lanczos_ground (and the calls built
  * on it: spectra, Ritz vectors, Green's-function coefficients) runs sectors of at most max_dim
  * states as one kernel per batch of iterations whose CTAs meet at barriers between the phases
- * of an iteration: up to 12800 states one thread-block cluster (hardware cluster barriers),
+ * of an iteration: up to 8192 states one thread-block cluster (hardware cluster barriers),
  * above that a cooperative grid (bounded waits: a wait that gives up sets the handle's error
  * flag and hub_lanczos_ground returns HUB_ERR_TIMEOUT).  This removes the per-iteration
  * launches and host round trips that bound small sectors.  max_dim = 0 turns it off; the

@@ -55,12 +55,12 @@ APPLY_SPACE = {
     "HUB_UP_PAIRED": [1, 0],
 }
 BATCH_SPACE = {"HUB_BATCH_THREADS": [256, 512, 1024]}
-SMALL_SPACE = {"HUB_SMALL_CLUSTER_MAX": [12800, 0], "HUB_SMALL_THREADS": [128, 256, 320, 384, 512],
+SMALL_SPACE = {"HUB_SMALL_CLUSTER_MAX": [8192, 12800, 0], "HUB_SMALL_THREADS": [128, 256, 320, 384, 512],
                "HUB_SMALL_PER_THREAD": [1, 2, 4], "HUB_SMALL_BATCH": [8, 4, 16]}
 DEFAULTS = {"HUB_DN_LANE_COLS": 4, "HUB_DN_BATCH": 2, "HUB_DN_MINB": 4, "HUB_BANK_CAP": 2,
             "HUB_FUSED_UPDATE": 0, "HUB_UPD_Q": 1, "HUB_UP_THREADS": 1024, "HUB_UP_PAIRED": 1,
             "HUB_BATCH_THREADS": 256,
-            "HUB_SMALL_CLUSTER_MAX": 12800, "HUB_SMALL_THREADS": 320, "HUB_SMALL_PER_THREAD": 1,
+            "HUB_SMALL_CLUSTER_MAX": 8192, "HUB_SMALL_THREADS": 320, "HUB_SMALL_PER_THREAD": 1,
             "HUB_SMALL_BATCH": 8}
 # tuned.json key of each group's timing
 RESULT_KEYS = {"apply": "lanczos_step_ms_4x4", "batch": "aim_batch_ms", "small": "ring8_ground_ms"}

@@ -60,7 +60,7 @@ static_assert(kSmallThreads % 32 == 0 && kSmallThreads <= 1024 && kSmallPerThrea
               "small-sector launch shape");
 constexpr int64_t kSmallStageMax = 25600;      // S_j staged in shared memory up to 200 KB
 #ifndef HUB_SMALL_CLUSTER_MAX
-#define HUB_SMALL_CLUSTER_MAX 12800            // sectors up to this size run as one CTA cluster
+#define HUB_SMALL_CLUSTER_MAX 8192             // sectors up to this size run as one CTA cluster (<= 12800)
 #endif
 constexpr int64_t kSmallClusterMax = HUB_SMALL_CLUSTER_MAX;
 constexpr int kSmallClusterCtas = 16;          // CTAs of that cluster at most (non-portable size)

@@ -50,13 +50,14 @@ def _launches(hub, m, x0, **kw):
     return r, n
 
 
-# ring 8 (uniform: the double-float driver otherwise) and a disordered 9-site ring (FP64 driver
-# otherwise) run as one thread-block cluster; 9 sites (5,4) as a cooperative grid with the
-# vector staged in shared memory; 10 and 11 sites: vectors beyond the staging size
+# ring 8 (uniform: the double-float driver otherwise) and a disordered 8-site ring (FP64 driver
+# otherwise) run as one thread-block cluster; 9 sites, (4,3) and (5,4), as a cooperative grid
+# with the vector staged in shared memory; 10 and 11 sites: vectors beyond the staging size
 CASES = {
     "ring8_cluster": lambda: _uniform(8, 4, 4),
-    "disordered9_cluster": lambda: _disordered(9, 4, 3, 40),
-    "disordered9_staged": lambda: _disordered(9, 5, 4, 45),
+    "disordered8_cluster": lambda: _disordered(8, 4, 3, 40),
+    "disordered9_staged": lambda: _disordered(9, 4, 3, 40),
+    "disordered9_54_staged": lambda: _disordered(9, 5, 4, 45),
     "ring10_unstaged": lambda: _uniform(10, 5, 5),
     "disordered11_unstaged": lambda: _disordered(11, 5, 4, 50),
 }
