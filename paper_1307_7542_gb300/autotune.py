@@ -15,6 +15,8 @@ shapes from compile-time knobs:
 * ``HUB_UP_PAIRED``    -- 1: pass 1 adds the low parts of a column word's two entries together
   before accumulating them (two accumulators, as pass 2); 0: four accumulators of single terms;
 * ``HUB_BATCH_THREADS`` -- threads per CTA of the batched persistent solver;
+* ``HUB_BATCH_SPLIT``  -- jobs of at most this many states run in a second launch of the batched
+  solver, its shared memory sized for them (0: one launch);
 * ``HUB_SMALL_CLUSTER_MAX``, ``HUB_SMALL_THREADS``, ``HUB_SMALL_PER_THREAD``,
   ``HUB_SMALL_BATCH`` -- the largest sector the single-launch small-sector Lanczos
   (csrc/hub_small.cu) runs as one thread-block cluster (0: always the cooperative grid), its
@@ -54,12 +56,12 @@ APPLY_SPACE = {
     "HUB_UP_THREADS": [1024, 768, 512],
     "HUB_UP_PAIRED": [1, 0],
 }
-BATCH_SPACE = {"HUB_BATCH_THREADS": [256, 512, 1024]}
+BATCH_SPACE = {"HUB_BATCH_THREADS": [256, 512, 1024], "HUB_BATCH_SPLIT": [2048, 1024, 4096, 0]}
 SMALL_SPACE = {"HUB_SMALL_CLUSTER_MAX": [8192, 12800, 0], "HUB_SMALL_THREADS": [128, 256, 320, 384, 512],
                "HUB_SMALL_PER_THREAD": [1, 2, 4], "HUB_SMALL_BATCH": [8, 4, 16]}
 DEFAULTS = {"HUB_DN_LANE_COLS": 4, "HUB_DN_BATCH": 2, "HUB_DN_MINB": 4, "HUB_BANK_CAP": 2,
             "HUB_FUSED_UPDATE": 0, "HUB_UPD_Q": 1, "HUB_UP_THREADS": 1024, "HUB_UP_PAIRED": 1,
-            "HUB_BATCH_THREADS": 256,
+            "HUB_BATCH_THREADS": 256, "HUB_BATCH_SPLIT": 2048,
             "HUB_SMALL_CLUSTER_MAX": 8192, "HUB_SMALL_THREADS": 320, "HUB_SMALL_PER_THREAD": 1,
             "HUB_SMALL_BATCH": 8}
 # tuned.json key of each group's timing

@@ -28,6 +28,10 @@ constexpr int kBatchMaxDim = 8192;      // three FP64 vectors of this length in 
 #endif
 constexpr int kBatchThreads = HUB_BATCH_THREADS;
 constexpr int kBatchCheckEvery = 8;     // E0 of T_j is evaluated every this many iterations
+#ifndef HUB_BATCH_SPLIT
+#define HUB_BATCH_SPLIT 2048              // jobs of at most this many states run in a second launch
+#endif
+constexpr int kBatchSplit = HUB_BATCH_SPLIT;
 
 struct BatchTables {
   const uint32_t *basis;     // all one-spin bases, N = 0..M, concatenated
@@ -335,7 +339,7 @@ extern "C" int hub_batch_ground(int M, int n_bonds, const int32_t *bonds_host, i
   A.job_ndn = (const int32_t *)up(job_ndn, sizeof(int32_t) * n_jobs, "batch jobs");
   A.job_param = (const int32_t *)up(job_param, sizeof(int32_t) * n_jobs, "batch jobs");
   A.order = (const int32_t *)up(order.data(), sizeof(int32_t) * n_jobs, "batch order");
-  A.counter = (int *)up(nullptr, sizeof(int), "batch queue");
+  A.counter = (int *)up(nullptr, 2 * sizeof(int), "batch queues");
   A.E0 = (double *)up(nullptr, sizeof(double) * n_jobs, "batch E0");
   A.iters = (int32_t *)up(nullptr, sizeof(int32_t) * n_jobs, "batch iterations");
   A.status = (int32_t *)up(nullptr, sizeof(int32_t) * n_jobs, "batch status");
@@ -344,24 +348,63 @@ extern "C" int hub_batch_ground(int M, int n_bonds, const int32_t *bonds_host, i
     release();
     return fail(HUB_ERR_OOM, "hub_batch_ground: device allocation or upload failed");
   }
+  // The shared memory of a CTA holds three vectors of the largest job it may take, so one
+  // launch for every job would give the small ones the large ones' footprint (one CTA per SM
+  // at the impurity star's 4900 states).  Jobs of at most kBatchSplit states (a suffix of
+  // the largest-first order) therefore run in a second launch on a second stream, sized for
+  // them, whose CTAs fill the SMs beside the large jobs' (two independent queues, no waits
+  // between the launches).
   cudaStream_t s = (cudaStream_t)stream;
-  const size_t smem = sizeof(double) * (3 * (size_t)Dmax + 2 * (size_t)maxit);
+  auto dim_of = [&](int32_t j) { return (int64_t)cnt[job_nup[j]] * cnt[job_ndn[j]]; };
+  int n_large = 0;
+  while (n_large < n_jobs && dim_of(order[n_large]) > kBatchSplit) ++n_large;
+  if (n_large == 0 || n_large == n_jobs) n_large = n_jobs;        // one size class: one launch
+  struct Part {
+    int first, count, dmax;
+  } parts[2] = {{0, n_large, Dmax}, {n_large, n_jobs - n_large, n_large < n_jobs ? (int)dim_of(order[n_large]) : 0}};
+  const int n_parts = n_large < n_jobs ? 2 : 1;
+  cudaStream_t s2 = nullptr;
+  cudaEvent_t ev_ready = nullptr, ev_done = nullptr;
   int rc = HUB_OK;
-  cudaError_t e = cudaMemsetAsync(A.counter, 0, sizeof(int), s);
+  cudaError_t e = cudaMemsetAsync(A.counter, 0, 2 * sizeof(int), s);
+  if (e == cudaSuccess && n_parts == 2) {
+    e = cudaStreamCreateWithFlags(&s2, cudaStreamNonBlocking);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_ready, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventCreateWithFlags(&ev_done, cudaEventDisableTiming);
+    if (e == cudaSuccess) e = cudaEventRecord(ev_ready, s);
+    if (e == cudaSuccess) e = cudaStreamWaitEvent(s2, ev_ready, 0);
+  }
+  size_t smem_max = 0;
+  for (int p = 0; p < n_parts; ++p)
+    smem_max = std::max(smem_max, sizeof(double) * (3 * (size_t)parts[p].dmax + 2 * (size_t)maxit));
   if (e == cudaSuccess)
-    e = cudaFuncSetAttribute(k_batch_lanczos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  int per_sm = 1;
-  if (e == cudaSuccess) e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_lanczos, kBatchThreads, smem);
-  if (e == cudaSuccess) {
-    const int grid = std::max(1, std::min(n_jobs, num_sms() * std::max(per_sm, 1)));
-    k_batch_lanczos<<<grid, kBatchThreads, smem, s>>>(T, A);
+    e = cudaFuncSetAttribute(k_batch_lanczos, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem_max);
+  for (int p = 0; p < n_parts && e == cudaSuccess; ++p) {
+    const size_t smem = sizeof(double) * (3 * (size_t)parts[p].dmax + 2 * (size_t)maxit);
+    int per_sm = 1;
+    e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_batch_lanczos, kBatchThreads, smem);
+    if (e != cudaSuccess) break;
+    BatchArgs Ap = A;
+    Ap.n_jobs = parts[p].count;
+    Ap.order = A.order + parts[p].first;
+    Ap.counter = A.counter + p;
+    const int grid = std::max(1, std::min(parts[p].count, num_sms() * std::max(per_sm, 1)));
+    k_batch_lanczos<<<grid, kBatchThreads, smem, p == 0 ? s : s2>>>(T, Ap);
     e = cudaGetLastError();
   }
+  if (e == cudaSuccess && n_parts == 2) e = cudaEventRecord(ev_done, s2);
+  if (e == cudaSuccess && n_parts == 2) e = cudaStreamWaitEvent(s, ev_done, 0);
   if (e == cudaSuccess) e = cudaMemcpyAsync(E0_host, A.E0, sizeof(double) * n_jobs, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(iters_host, A.iters, sizeof(int32_t) * n_jobs, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaMemcpyAsync(status_host, A.status, sizeof(int32_t) * n_jobs, cudaMemcpyDeviceToHost, s);
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) rc = cuda_fail(e, "hub_batch_ground", __FILE__, __LINE__);
+  if (s2) {
+    cudaStreamSynchronize(s2);         // nothing of this call may outlive it
+    cudaStreamDestroy(s2);
+  }
+  if (ev_ready) cudaEventDestroy(ev_ready);
+  if (ev_done) cudaEventDestroy(ev_done);
   release();
   if (rc) return rc;
   for (int k = 0; k < n_jobs; ++k)
