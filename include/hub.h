@@ -297,12 +297,12 @@ int hub_grad(hub_t h, const double *psi_dev, double *dE_dt_host, double *dE_dU_h
  *   - Limit: n_bonds + 2*M <= 160; larger models return HUB_ERR_ARG (use hub_grad).
  *   - The handle's device must be the current device.  Every call looks up the array's
  *     device address there (cudaGetSymbolAddress); the first call on a device may also
- *     load the library's device code on it, which places the array.  Make that first call
- *     before any stream capture.
+ *     load the library's device code on it, which places the array.
  *   - All calls share the one array: calls that overlap on the GPU (two streams, two
  *     threads, two handles) race and give wrong results.  Every value a call reads from
  *     the array is written earlier in the same call, so nothing needs clearing.
- *   - Blocks until the results are in the host arrays.
+ *   - Blocks: every call synchronises its stream and returns after the results are in the
+ *     host arrays.
  */
 int hub_grad_noalloc(hub_t h, const double *psi_dev, double *dE_dt_host, double *dE_dU_host,
                      double *dE_deps_host, void *stream);
