@@ -51,7 +51,7 @@ def parse():
     p.add_argument("--warmup", type=int, default=5)
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--U", type=float, default=4.0)
-    p.add_argument("--e2e-steps", type=int, default=8)
+    p.add_argument("--e2e-steps", type=int, default=16)
     p.add_argument("--fp64-steps", type=int, default=10, help="Lanczos steps timed with HUB_MODE_FP64")
     p.add_argument("--lanczos-iters", type=int, default=200, help="iterations of the E0 wall-time run")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -658,14 +658,25 @@ def run_gpu(a):
     if a.e2e_steps > 0:
         xh = torch.from_numpy(x_host).pin_memory()
         yh = torch.empty(D, dtype=torch.float64).pin_memory()
-        for _ in range(2):
-            hub.hub_apply_host(m.h, xh, yh)
-        torch.cuda.synchronize()
-        calls = []
-        for _ in range(a.e2e_steps):
+        warm = []
+        for _ in range(3):
             t0 = time.perf_counter()
             hub.hub_apply_host(m.h, xh, yh)
+            warm.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        # per call: the host wall time, and the stream time between events recorded just before
+        # and just after the call (the copies and passes the call enqueues, as the GPU ran them)
+        calls, dev_calls = [], []
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+              for _ in range(a.e2e_steps)]
+        for k in range(a.e2e_steps):
+            t0 = time.perf_counter()
+            ev[k][0].record(stream)
+            hub.hub_apply_host(m.h, xh, yh)
+            ev[k][1].record(stream)
             calls.append(time.perf_counter() - t0)
+        torch.cuda.synchronize()
+        dev_calls = [e0_.elapsed_time(e1_) for e0_, e1_ in ev]
         e2e_s = sum(calls)
         # what the call is made of: one copy each way alone, and the device product alone
         xd_ = torch.empty(D, dtype=torch.float64, device="cuda")
@@ -691,7 +702,8 @@ def run_gpu(a):
                "overlap_saved_ms": h2d_ms + dev_ms + d2h_ms - call_ms,
                "call_ms_min_median_max": [1000 * min(calls), 1000 * sorted(calls)[len(calls) // 2],
                                           1000 * max(calls)],
-               "call_ms": [1000 * c for c in calls]}
+               "call_ms": [1000 * c for c in calls], "call_stream_ms": dev_calls,
+               "warmup_call_ms": [1000 * c for c in warm]}
         del xh, yh, xd_, yd_
 
     metric = ("H.x applies/s (4x4 PBC half filling, U=4)" if a.workload == "4x4"
