@@ -52,6 +52,7 @@ def parse():
     p.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     p.add_argument("--U", type=float, default=4.0)
     p.add_argument("--e2e-steps", type=int, default=16)
+    p.add_argument("--e2e-vectors", type=int, default=4)
     p.add_argument("--fp64-steps", type=int, default=10, help="Lanczos steps timed with HUB_MODE_FP64")
     p.add_argument("--lanczos-iters", type=int, default=200, help="iterations of the E0 wall-time run")
     p.add_argument("--cpu-seconds", type=float, default=12.0, help="target CPU time of the oracle sample")
@@ -653,31 +654,39 @@ def run_gpu(a):
                      "fp64_peak_source": "derived: 152 SMs x 2 FP64 instr/clk x 2.07 GHz (nominal 1.25 TFLOP/s)",
                      "E0_after_steps": rf["E0"]}
 
-    # end-to-end: the host-buffer apply through the C ABI (H2D + apply + D2H each step)
+    # end-to-end through the C ABI with host buffers, host<->device copies inside the timed
+    # region: hub_apply_host_many (several vectors per call, one vector's copies overlapping its
+    # neighbours') gives `value`; the one-vector blocking call hub_apply_host is reported beside it
     e2e = None
     if a.e2e_steps > 0:
+        def timed_calls(fn, n_calls, n_warm):
+            """Host wall time and stream time (events recorded on the call's stream just before
+            and after it: the copies and passes the call enqueues, as the GPU ran them) per call."""
+            warm = []
+            for _ in range(n_warm):
+                t0 = time.perf_counter()
+                fn()
+                warm.append(time.perf_counter() - t0)
+            torch.cuda.synchronize()
+            ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+                  for _ in range(n_calls)]
+            calls = []
+            for k in range(n_calls):
+                t0 = time.perf_counter()
+                ev[k][0].record(stream)
+                fn()
+                ev[k][1].record(stream)
+                calls.append(time.perf_counter() - t0)
+            torch.cuda.synchronize()
+            return calls, [e0_.elapsed_time(e1_) for e0_, e1_ in ev], warm
+
+        def spread(calls):
+            return [1000 * min(calls), 1000 * sorted(calls)[len(calls) // 2], 1000 * max(calls)]
+
         xh = torch.from_numpy(x_host).pin_memory()
         yh = torch.empty(D, dtype=torch.float64).pin_memory()
-        warm = []
-        for _ in range(3):
-            t0 = time.perf_counter()
-            hub.hub_apply_host(m.h, xh, yh)
-            warm.append(time.perf_counter() - t0)
-        torch.cuda.synchronize()
-        # per call: the host wall time, and the stream time between events recorded just before
-        # and just after the call (the copies and passes the call enqueues, as the GPU ran them)
-        calls, dev_calls = [], []
-        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
-              for _ in range(a.e2e_steps)]
-        for k in range(a.e2e_steps):
-            t0 = time.perf_counter()
-            ev[k][0].record(stream)
-            hub.hub_apply_host(m.h, xh, yh)
-            ev[k][1].record(stream)
-            calls.append(time.perf_counter() - t0)
-        torch.cuda.synchronize()
-        dev_calls = [e0_.elapsed_time(e1_) for e0_, e1_ in ev]
-        e2e_s = sum(calls)
+        calls, dev_calls, warm = timed_calls(lambda: hub.hub_apply_host(m.h, xh, yh), a.e2e_steps, 3)
+        single_s = sum(calls)
         # what the call is made of: one copy each way alone, and the device product alone
         xd_ = torch.empty(D, dtype=torch.float64, device="cuda")
         yd_ = torch.empty(D, dtype=torch.float64, device="cuda")
@@ -693,18 +702,31 @@ def run_gpu(a):
         c3.record(stream)
         torch.cuda.synchronize()
         h2d_ms, d2h_ms, dev_ms = c0.elapsed_time(c1), c1.elapsed_time(c2), c2.elapsed_time(c3)
-        call_ms = 1000 * e2e_s / a.e2e_steps
-        e2e = {"value": world * a.e2e_steps / e2e_s, "unit": "applies/s",
-               "h2d_bytes_per_step": 8 * D, "d2h_bytes_per_step": 8 * D,
-               "call": "hub_apply_host (pinned host x in, host y out)", "ms_per_call": call_ms,
-               "h2d_gbs": gb(8 * D, h2d_ms), "d2h_gbs": gb(8 * D, d2h_ms), "hub_apply_device_ms": dev_ms,
-               "serial_ms": h2d_ms + dev_ms + d2h_ms,
-               "overlap_saved_ms": h2d_ms + dev_ms + d2h_ms - call_ms,
-               "call_ms_min_median_max": [1000 * min(calls), 1000 * sorted(calls)[len(calls) // 2],
-                                          1000 * max(calls)],
-               "call_ms": [1000 * c for c in calls], "call_stream_ms": dev_calls,
-               "warmup_call_ms": [1000 * c for c in warm]}
+        single_ms = 1000 * single_s / a.e2e_steps
+        single = {"value": world * a.e2e_steps / single_s, "unit": "applies/s",
+                  "call": "hub_apply_host (one vector per call)", "ms_per_call": single_ms,
+                  "h2d_gbs": gb(8 * D, h2d_ms), "d2h_gbs": gb(8 * D, d2h_ms), "hub_apply_device_ms": dev_ms,
+                  "serial_ms": h2d_ms + dev_ms + d2h_ms,
+                  "overlap_saved_ms": h2d_ms + dev_ms + d2h_ms - single_ms,
+                  "call_ms_min_median_max": spread(calls), "call_ms": [1000 * c for c in calls],
+                  "call_stream_ms": dev_calls, "warmup_call_ms": [1000 * c for c in warm]}
         del xh, yh, xd_, yd_
+        # several vectors per call (the same input vector repeated: the contents do not change
+        # the work)
+        nv = max(1, a.e2e_vectors)
+        n_calls = max(1, a.e2e_steps // nv)
+        xs = torch.from_numpy(np.tile(x_host, nv)).pin_memory()
+        ys = torch.empty(nv * D, dtype=torch.float64).pin_memory()
+        calls, dev_calls, warm = timed_calls(lambda: hub.hub_apply_host_many(m.h, nv, xs, ys), n_calls, 1)
+        e2e_s = sum(calls)
+        e2e = {"value": world * nv * n_calls / e2e_s, "unit": "applies/s",
+               "h2d_bytes_per_step": 8 * D, "d2h_bytes_per_step": 8 * D,
+               "call": f"hub_apply_host_many ({nv} vectors per call, pinned host x in, host y out)",
+               "vectors_per_call": nv, "calls": n_calls, "ms_per_apply": 1000 * e2e_s / (nv * n_calls),
+               "call_ms_min_median_max": spread(calls), "call_ms": [1000 * c for c in calls],
+               "call_stream_ms": dev_calls, "warmup_call_ms": [1000 * c for c in warm],
+               "single_call": single}
+        del xs, ys
 
     metric = ("H.x applies/s (4x4 PBC half filling, U=4)" if a.workload == "4x4"
               else f"H.x applies/s ({w['label']}, U={w['U'][0]:g})")

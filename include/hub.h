@@ -136,6 +136,23 @@ int hub_apply(hub_t h, const double *x_dev, double *y_dev, void *stream);
 int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream);
 
 /*
+ * y_v = H x_v for n_vec host vectors (Sec. IV.A, Eq. 11, as hub_apply): x_host holds the
+ * vectors one after another (n_vec * D doubles, D the sector's vector length), y_host receives
+ * the results in the same layout; returns when all of y_host is complete.  x_host and y_host
+ * are either the same array (the product in place) or do not overlap at all; page-locked
+ * buffers let the copies run at the link's rate.  Each result is bit for bit that of
+ * hub_apply_host on the same vector (same kernels, window check and routing).  On the fast
+ * path with row-chunked copies (pass 1 staging rows, at least 16 rows) the copies of
+ * neighbouring vectors overlap: vector v + 1 comes in and vector v - 1 goes back while vector
+ * v is computed, on two copy streams of the handle; this takes a second pair of device
+ * vectors (2 D doubles more), allocated on first use.  Elsewhere it is one hub_apply_host
+ * per vector.
+ *   - n_vec = 0: nothing happens.  n_vec < 0, a NULL vector with n_vec > 0, partly
+ *     overlapping arrays, or n_vec * D * 8 bytes beyond size_t: HUB_ERR_ARG.
+ */
+int hub_apply_host_many(hub_t h, int64_t n_vec, const double *x_host, double *y_host, void *stream);
+
+/*
  * Ground state by plain Lanczos without re-orthogonalisation (Sec. IV; Sec. V).
  * q_1 = x0/|x0| (x0_dev == NULL: a uniform [-1, 1) vector from SplitMix64, seed 0).
  * Each iteration: w = H q_j - beta_{j-1} q_{j-1}; alpha_j = <q_j, w>; w -= alpha_j q_j;

@@ -131,19 +131,26 @@ extern "C" int hub_apply(hub_t h, const double *x_dev, double *y_dev, void *stre
   return apply_launch(h, x_dev, y_dev, (cudaStream_t)stream);
 }
 
+// The FP64 device input and output vector of a host-buffer apply (x, y: hx and hy, or the
+// second pair hx2 and hy2), allocated on first use.
+static int host_apply_buffers(hub_ctx *h, double **x, double **y) {
+  if (*x) return HUB_OK;
+  const int64_t D = vec_len(h);
+  if (!dev_alloc((void **)x, sizeof(double) * D, "host-apply input") ||
+      !dev_alloc((void **)y, sizeof(double) * D, "host-apply output")) {
+    dev_free(*x);
+    *x = nullptr;
+    return HUB_ERR_OOM;
+  }
+  return HUB_OK;
+}
+
 extern "C" int hub_apply_host(hub_t h, const double *x_host, double *y_host, void *stream) {
   int rc = check_ready(h, "hub_apply_host");
   if (rc) return rc;
   if (!x_host || !y_host) return fail(HUB_ERR_ARG, "hub_apply_host: NULL vector");
   const int64_t D = vec_len(h);
-  if (!h->hx) {
-    if (!dev_alloc((void **)&h->hx, sizeof(double) * D, "host-apply input") ||
-        !dev_alloc((void **)&h->hy, sizeof(double) * D, "host-apply output")) {
-      dev_free(h->hx);
-      h->hx = nullptr;
-      return HUB_ERR_OOM;
-    }
-  }
+  if ((rc = host_apply_buffers(h, &h->hx, &h->hy))) return rc;
   cudaStream_t s = (cudaStream_t)stream;
   if (use_fast(h)) return fast_apply_host(h, x_host, y_host, h->hx, h->hy, s);
   HUB_CUDA(cudaMemcpyAsync(h->hx, x_host, sizeof(double) * D, cudaMemcpyHostToDevice, s));
@@ -152,6 +159,27 @@ extern "C" int hub_apply_host(hub_t h, const double *x_host, double *y_host, voi
   HUB_CUDA(cudaMemcpyAsync(y_host, h->hy, sizeof(double) * D, cudaMemcpyDeviceToHost, s));
   HUB_CUDA(cudaStreamSynchronize(s));
   return HUB_OK;
+}
+
+extern "C" int hub_apply_host_many(hub_t h, int64_t n_vec, const double *x_host, double *y_host, void *stream) {
+  int rc = check_ready(h, "hub_apply_host_many");
+  if (rc) return rc;
+  if (n_vec < 0) return fail(HUB_ERR_ARG, "hub_apply_host_many: negative vector count");
+  if (n_vec == 0) return HUB_OK;
+  if (!x_host || !y_host) return fail(HUB_ERR_ARG, "hub_apply_host_many: NULL vector");
+  const int64_t D = vec_len(h);
+  if (D > 0 && n_vec > (int64_t)(SIZE_MAX / sizeof(double)) / D)
+    return fail(HUB_ERR_ARG, "hub_apply_host_many: vector count too large");
+  if (x_host != y_host && x_host < y_host + n_vec * D && y_host < x_host + n_vec * D)
+    return fail(HUB_ERR_ARG, "hub_apply_host_many: x and y overlap without being the same array");
+  if (n_vec == 1 || !use_fast(h) || !fast_host_pipelined(h)) {   // one call per vector
+    for (int64_t v = 0; v < n_vec; ++v)
+      if ((rc = hub_apply_host(h, x_host + v * D, y_host + v * D, stream))) return rc;
+    return HUB_OK;
+  }
+  if ((rc = host_apply_buffers(h, &h->hx, &h->hy)) || (rc = host_apply_buffers(h, &h->hx2, &h->hy2))) return rc;
+  double *const xd[2] = {h->hx, h->hx2}, *const yd[2] = {h->hy, h->hy2};
+  return fast_apply_host_many(h, n_vec, x_host, y_host, xd, yd, (cudaStream_t)stream);
 }
 
 extern "C" int hub_profile(hub_t h, int enable) {

@@ -1107,6 +1107,9 @@ struct FastState {
   cudaStream_t copy_stream = nullptr;
   std::vector<cudaEvent_t> events;
   int *d_range_chunks = nullptr, *d_flag = nullptr, *h_flag = nullptr;
+  // the multi-vector form: a second copy stream (outputs) and its own events
+  cudaStream_t copy_out_stream = nullptr;
+  std::vector<cudaEvent_t> many_events;
   // CUDA graphs of one Lanczos iteration (first pass), one per rotation of the three
   // vectors, captured on graph_stream and replayed on the caller's stream; lz_graph_key holds
   // the operands they were captured with
@@ -1140,6 +1143,8 @@ void fast_release(hub_ctx *h) {
   if (f->h_flag) cudaFreeHost(f->h_flag);
   for (cudaEvent_t e : f->events) cudaEventDestroy(e);
   if (f->copy_stream) cudaStreamDestroy(f->copy_stream);
+  for (cudaEvent_t e : f->many_events) cudaEventDestroy(e);
+  if (f->copy_out_stream) cudaStreamDestroy(f->copy_out_stream);
   for (int k = 0; k < 3; ++k)
     if (f->lz_graph[k]) cudaGraphExecDestroy(f->lz_graph[k]);
   if (f->graph_stream) cudaStreamDestroy(f->graph_stream);
@@ -1610,16 +1615,8 @@ int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s) {
   return f64_apply(h, x, y, scale + 1, s);
 }
 
-// hub_apply_host on the fast path with staged rows.  The input arrives in row chunks on a copy
-// stream while the compute stream converts each chunk and runs pass 1 on its row pairs; after
-// pass 2 the output goes back in row chunks while later chunks are un-permuted.  The
-// power-of-two scale of the conversion is taken from the first chunk's largest exponent; if
-// the whole vector's largest exponent is larger, conversion and pass 1 are redone with it, so
-// the result is bit for bit that of hub_apply.  xd, yd: the handle's FP64 device buffers.
+// Row chunks of the host-buffer apply.
 constexpr int kHostChunks = 8;
-
-static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double *y_host, double *xd, double *yd,
-                         cudaStream_t s, const int64_t *bi, int nci, const int64_t *bo, int nco, int64_t per);
 
 // Row chunk bounds b[0..n] of n_dn rows with relative sizes w (boundaries even, so that no
 // pass-1 row pair straddles two chunks; empty chunks dropped); returns n.
@@ -1636,75 +1633,65 @@ static int chunk_bounds(int64_t n_dn, const int (&w)[kHostChunks], int64_t *b) {
   return n;
 }
 
-int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd, double *yd, cudaStream_t s) {
-  FastState *f = fast_of(h);
-  if (!f || !f->built) return fail(HUB_ERR_STATE, "fast apply: not built");
-  const int64_t n_up = h->count[0], n_dn = h->count[1];
-  if (!f->staged || n_dn < 2 * kHostChunks) {   // one piece: copy in, apply, copy out
-    HUB_CUDA(cudaMemcpyAsync(xd, x_host, sizeof(double) * n_up * n_dn, cudaMemcpyHostToDevice, s));
-    int rc = fast_apply_f64(h, xd, yd, s);
-    if (rc) return rc;
-    HUB_CUDA(cudaMemcpyAsync(y_host, yd, sizeof(double) * n_up * n_dn, cudaMemcpyDeviceToHost, s));
-    HUB_CUDA(cudaStreamSynchronize(s));
-    return HUB_OK;
-  }
-  const int64_t Dp = n_dn * 2 * f->ld;
+// Row chunks of a host-buffer apply: the input's last chunk and the output's first chunk are a
+// quarter of the others (little pass-1 work is left once the last input chunk has landed, and
+// the first output chunk is ready to go back early); per is the largest chunk.
+struct HostChunks {
+  int64_t bi[kHostChunks + 1], bo[kHostChunks + 1];
+  int nci, nco;
+  int64_t per;
+};
+
+static HostChunks host_chunks(int64_t n_dn) {
+  static const int w_in[kHostChunks] = {4, 4, 4, 4, 4, 4, 4, 1}, w_out[kHostChunks] = {1, 4, 4, 4, 4, 4, 4, 4};
+  HostChunks C;
+  C.nci = chunk_bounds(n_dn, w_in, C.bi);
+  C.nco = chunk_bounds(n_dn, w_out, C.bo);
+  C.per = 0;
+  for (int c = 0; c < C.nci; ++c) C.per = std::max(C.per, C.bi[c + 1] - C.bi[c]);
+  for (int c = 0; c < C.nco; ++c) C.per = std::max(C.per, C.bo[c + 1] - C.bo[c]);
+  return C;
+}
+
+// Scratch of the chunked host-buffer apply: double-float x and z, per-chunk exponent
+// partials, the scale words, the route flag (device and pinned host) and the input copy stream.
+static int host_pipe_buffers(FastState *f, int64_t Dp) {
   int rc;
   if ((rc = ensure_vec(&f->xdf, Dp, "apply scratch x")) || (rc = ensure_vec(&f->zdf, Dp, "apply scratch z")))
     return rc;
-  const int G = grid_vec();
   if (!f->d_range_chunks &&
-      !dev_alloc((void **)&f->d_range_chunks, sizeof(int) * 2 * G * kHostChunks, "exponent partials"))
+      !dev_alloc((void **)&f->d_range_chunks, sizeof(int) * 2 * grid_vec() * kHostChunks, "exponent partials"))
     return HUB_ERR_OOM;
   if (!range_buf(f)) return HUB_ERR_OOM;
   if (!f->d_flag && !dev_alloc((void **)&f->d_flag, sizeof(int), "scale flag")) return HUB_ERR_OOM;
   if (!f->h_flag) HUB_CUDA(cudaMallocHost((void **)&f->h_flag, sizeof(int)));
   if (!f->copy_stream) HUB_CUDA(cudaStreamCreateWithFlags(&f->copy_stream, cudaStreamNonBlocking));
-  while ((int)f->events.size() < 2 * kHostChunks + 2) {
-    cudaEvent_t e;
-    HUB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    f->events.push_back(e);
-  }
-  cudaStream_t sc = f->copy_stream;
-  const cudaEvent_t ev_start = f->events[2 * kHostChunks];
-  // the input's last chunk and the output's first chunk are a quarter of the others: little
-  // pass-1 work is left once the last input chunk has landed, and the first output chunk is
-  // ready to go back early
-  static const int w_in[kHostChunks] = {4, 4, 4, 4, 4, 4, 4, 1}, w_out[kHostChunks] = {1, 4, 4, 4, 4, 4, 4, 4};
-  int64_t bi[kHostChunks + 1], bo[kHostChunks + 1];
-  const int nci = chunk_bounds(n_dn, w_in, bi), nco = chunk_bounds(n_dn, w_out, bo);
-  int64_t per = 0;
-  for (int c = 0; c < nci; ++c) per = std::max(per, bi[c + 1] - bi[c]);
-  for (int c = 0; c < nco; ++c) per = std::max(per, bo[c + 1] - bo[c]);
-  HUB_CUDA(cudaEventRecord(ev_start, s));
-  HUB_CUDA(cudaStreamWaitEvent(sc, ev_start, 0));
-  rc = pipeline_host(h, f, x_host, y_host, xd, yd, s, bi, nci, bo, nco, per);
-  if (rc) {   // no copy into or out of the caller's buffers may outlive the call
-    cudaStreamSynchronize(sc);
-    cudaStreamSynchronize(s);
-  }
-  return rc;
+  return HUB_OK;
 }
 
-// The chunked copies and passes of fast_apply_host (bi: input chunk row bounds, nci chunks;
-// bo: output chunk row bounds, nco chunks; per: the largest chunk).
-static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double *y_host, double *xd, double *yd,
-                         cudaStream_t s, const int64_t *bi, int nci, const int64_t *bo, int nco, int64_t per) {
-  const int64_t n_up = h->count[0], n_dn = h->count[1];
-  const int G = grid_vec();
-  int rc;
-  cudaStream_t sc = f->copy_stream;
-  cudaEvent_t *ev_in = f->events.data(), *ev_out = ev_in + kHostChunks, ev_end = ev_in[2 * kHostChunks + 1];
-  const int64_t *b = bi;
-  int nc = nci;
-  for (int c = 0; c < nc; ++c) {
-    HUB_CUDA(cudaMemcpyAsync(xd + b[c] * n_up, x_host + b[c] * n_up, sizeof(double) * (b[c + 1] - b[c]) * n_up,
-                             cudaMemcpyHostToDevice, sc));
-    HUB_CUDA(cudaEventRecord(ev_in[c], sc));
+static int ensure_events(std::vector<cudaEvent_t> &ev, int n) {
+  while ((int)ev.size() < n) {
+    cudaEvent_t e;
+    HUB_CUDA(cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    ev.push_back(e);
   }
+  return HUB_OK;
+}
+
+// Pass 1 of a host-buffer apply in the input's row chunks (bounds b[0..nc]): each chunk waits
+// for its copy (ev_in[c]), then takes its exponent partials (the first chunk also fixes the
+// conversion scale), its conversion to double-float and pass 1 on its row pairs.  Ends with
+// the whole vector's scale and the route flag, copied to f->h_flag on s (0: converted with the
+// right scale; 1: the largest exponent lies outside the first chunk, redo with the global
+// scale; 2: outside the double-float window, FP64 kernel).  xd: the FP64 device input.
+static int host_pass1(hub_ctx *h, FastState *f, const double *xd, const int64_t *b, int nc, int64_t per,
+                      const cudaEvent_t *ev_in, cudaStream_t s) {
+  const int64_t n_up = h->count[0];
+  const int G = grid_vec();
   int *part = f->d_range_chunks;                 // 2 G exponent partials per chunk
   int *scale = f->d_range + 2 * G;                // [0, 1] first chunk's scale, [2, 3] the whole vector's
   const int rg = (int)std::min<int64_t>(per, (int64_t)num_sms() * 8);
+  int rc;
   for (int c = 0; c < nc; ++c) {
     HUB_CUDA(cudaStreamWaitEvent(s, ev_in[c], 0));
     count_launch(h, c == 0 ? 3 : 2);
@@ -1718,23 +1705,28 @@ static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double 
   k_scale_all<<<1, 256, 0, s>>>(part, G, nc, scale, f->d_flag);
   HUB_LAUNCH_CHECK();
   HUB_CUDA(cudaMemcpyAsync(f->h_flag, f->d_flag, sizeof(int), cudaMemcpyDeviceToHost, s));
-  HUB_CUDA(cudaStreamSynchronize(s));
-  if (*f->h_flag == 2) {   // outside the double-float window: the FP64 kernel, one copy back
-    if ((rc = f64_apply(h, xd, yd, nullptr, s))) return rc;
-    HUB_CUDA(cudaMemcpyAsync(y_host, yd, sizeof(double) * n_dn * n_up, cudaMemcpyDeviceToHost, s));
-    HUB_CUDA(cudaStreamSynchronize(s));
-    return HUB_OK;
-  }
-  if (*f->h_flag == 1) {   // the largest exponent lies outside the first chunk: redo with the global one
-    count_launch(h);
-    k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, n_dn, n_up, f->ld, xd, scale + 2, f->slot_row, f->xdf);
-    HUB_LAUNCH_CHECK();
-    if ((rc = run_up(h, f, f->xdf, f->zdf, s))) return rc;
-  }
-  // pass 2 in the output's row chunks, so that each chunk's result goes back while the next is
-  // computed (every chunk reads the whole of X by strips; X is read from HBM once per chunk)
-  b = bo;
-  nc = nco;
+  return HUB_OK;
+}
+
+// Route flag 1: conversion and pass 1 again, with the whole vector's scale.
+static int host_redo(hub_ctx *h, FastState *f, const double *xd, cudaStream_t s) {
+  int *scale = f->d_range + 2 * grid_vec();
+  count_launch(h);
+  k_f64_to_df<<<row_grid(h), 256, 0, s>>>(0, h->count[1], h->count[0], f->ld, xd, scale + 2, f->slot_row, f->xdf);
+  HUB_LAUNCH_CHECK();
+  return run_up(h, f, f->xdf, f->zdf, s);
+}
+
+// Pass 2 in the output's row chunks (bounds b[0..nc]), so that each chunk's result goes back
+// while the next is computed (every chunk reads the whole of X by strips; X is read from HBM
+// once per chunk): run_dn and the un-permutation into the FP64 device output yd on s, then the
+// chunk's copy to y_host on sc (ev_out[c] hands the chunk from s to sc).
+static int host_pass2(hub_ctx *h, FastState *f, double *yd, double *y_host, const int64_t *b, int nc, int64_t per,
+                      const cudaEvent_t *ev_out, cudaStream_t s, cudaStream_t sc) {
+  const int64_t n_up = h->count[0];
+  int *scale = f->d_range + 2 * grid_vec();
+  const int rg = (int)std::min<int64_t>(per, (int64_t)num_sms() * 8);
+  int rc;
   for (int c = 0; c < nc; ++c) {
     if ((rc = run_dn(h, f, 0, f->xdf, f->zdf, f->zdf, LzArgs{}, s, b[c], b[c + 1]))) return rc;
     count_launch(h);
@@ -1746,10 +1738,154 @@ static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double 
     HUB_CUDA(cudaMemcpyAsync(y_host + b[c] * n_up, yd + b[c] * n_up, sizeof(double) * (b[c + 1] - b[c]) * n_up,
                              cudaMemcpyDeviceToHost, sc));
   }
+  return HUB_OK;
+}
+
+bool fast_host_pipelined(const hub_ctx *h) {
+  const FastState *f = fast_of(h);
+  return f && f->built && f->staged && h->count[1] >= 2 * kHostChunks;
+}
+
+// The chunked copies and passes of fast_apply_host: input chunks on the copy stream, pass 1
+// per chunk, the route flag read on the host, pass 2 and the output chunks back on the copy
+// stream.
+static int pipeline_host(hub_ctx *h, FastState *f, const double *x_host, double *y_host, double *xd, double *yd,
+                         cudaStream_t s, const HostChunks &C) {
+  const int64_t n_up = h->count[0], n_dn = h->count[1];
+  int rc;
+  cudaStream_t sc = f->copy_stream;
+  cudaEvent_t *ev_in = f->events.data(), *ev_out = ev_in + kHostChunks, ev_end = ev_in[2 * kHostChunks + 1];
+  for (int c = 0; c < C.nci; ++c) {
+    HUB_CUDA(cudaMemcpyAsync(xd + C.bi[c] * n_up, x_host + C.bi[c] * n_up,
+                             sizeof(double) * (C.bi[c + 1] - C.bi[c]) * n_up, cudaMemcpyHostToDevice, sc));
+    HUB_CUDA(cudaEventRecord(ev_in[c], sc));
+  }
+  if ((rc = host_pass1(h, f, xd, C.bi, C.nci, C.per, ev_in, s))) return rc;
+  HUB_CUDA(cudaStreamSynchronize(s));
+  if (*f->h_flag == 2) {   // outside the double-float window: the FP64 kernel, one copy back
+    if ((rc = f64_apply(h, xd, yd, nullptr, s))) return rc;
+    HUB_CUDA(cudaMemcpyAsync(y_host, yd, sizeof(double) * n_dn * n_up, cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    return HUB_OK;
+  }
+  if (*f->h_flag == 1 && (rc = host_redo(h, f, xd, s))) return rc;
+  if ((rc = host_pass2(h, f, yd, y_host, C.bo, C.nco, C.per, ev_out, s, sc))) return rc;
   HUB_CUDA(cudaEventRecord(ev_end, sc));
   HUB_CUDA(cudaStreamWaitEvent(s, ev_end, 0));
   HUB_CUDA(cudaStreamSynchronize(s));
   return HUB_OK;
+}
+
+// hub_apply_host on the fast path with staged rows.  The input arrives in row chunks on a copy
+// stream while the compute stream converts each chunk and runs pass 1 on its row pairs; after
+// pass 2 the output goes back in row chunks while later chunks are un-permuted.  The
+// power-of-two scale of the conversion is taken from the first chunk's largest exponent; if
+// the whole vector's largest exponent is larger, conversion and pass 1 are redone with it, so
+// the result is bit for bit that of hub_apply.  xd, yd: the handle's FP64 device buffers.
+int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd, double *yd, cudaStream_t s) {
+  FastState *f = fast_of(h);
+  if (!f || !f->built) return fail(HUB_ERR_STATE, "fast apply: not built");
+  const int64_t n_up = h->count[0], n_dn = h->count[1];
+  if (!fast_host_pipelined(h)) {   // one piece: copy in, apply, copy out
+    HUB_CUDA(cudaMemcpyAsync(xd, x_host, sizeof(double) * n_up * n_dn, cudaMemcpyHostToDevice, s));
+    int rc = fast_apply_f64(h, xd, yd, s);
+    if (rc) return rc;
+    HUB_CUDA(cudaMemcpyAsync(y_host, yd, sizeof(double) * n_up * n_dn, cudaMemcpyDeviceToHost, s));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    return HUB_OK;
+  }
+  int rc;
+  if ((rc = host_pipe_buffers(f, n_dn * 2 * f->ld))) return rc;
+  // events: [kHostChunks] input chunks, [kHostChunks] output chunks, start, end
+  if ((rc = ensure_events(f->events, 2 * kHostChunks + 2))) return rc;
+  cudaStream_t sc = f->copy_stream;
+  const cudaEvent_t ev_start = f->events[2 * kHostChunks];
+  const HostChunks C = host_chunks(n_dn);
+  HUB_CUDA(cudaEventRecord(ev_start, s));
+  HUB_CUDA(cudaStreamWaitEvent(sc, ev_start, 0));
+  rc = pipeline_host(h, f, x_host, y_host, xd, yd, s, C);
+  if (rc) {   // no copy into or out of the caller's buffers may outlive the call
+    cudaStreamSynchronize(sc);
+    cudaStreamSynchronize(s);
+  }
+  return rc;
+}
+
+
+// hub_apply_host_many on the fast path with staged rows.  While the compute stream works on
+// vector v, vector v + 1's rows come in on the input copy stream and vector v - 1's output goes
+// back on the output copy stream (the host link carries both directions at once).  The FP64
+// device buffers alternate between even and odd vectors (xd[v & 1], yd[v & 1]): an input
+// buffer is refilled only after the compute stream has finished reading it (x_free), an output
+// buffer is rewritten only after its copy to the host has ended (y_free).  Each vector takes
+// the same kernels, scale and route as in fast_apply_host, so every result is bit for bit that
+// of one hub_apply_host call.  The host waits once per vector, for its route flag after pass 1;
+// the next vector's input copies are queued before that wait.
+int fast_apply_host_many(hub_ctx *h, int64_t n_vec, const double *x_host, double *y_host, double *const xd[2],
+                         double *const yd[2], cudaStream_t s) {
+  FastState *f = fast_of(h);
+  if (!fast_host_pipelined(h)) return fail(HUB_ERR_STATE, "fast apply: no row-chunk pipeline for this sector");
+  const int64_t n_up = h->count[0], n_dn = h->count[1], D = n_up * n_dn;
+  int rc;
+  if ((rc = host_pipe_buffers(f, n_dn * 2 * f->ld))) return rc;
+  if (!f->copy_out_stream) HUB_CUDA(cudaStreamCreateWithFlags(&f->copy_out_stream, cudaStreamNonBlocking));
+  // events: [2][kHostChunks] input chunks (by buffer), [kHostChunks] output chunks,
+  // x_free[2], y_free[2], start, end
+  if ((rc = ensure_events(f->many_events, 3 * kHostChunks + 6))) return rc;
+  cudaEvent_t *ev_in = f->many_events.data(), *ev_out = ev_in + 2 * kHostChunks, *x_free = ev_out + kHostChunks,
+              *y_free = x_free + 2;
+  const cudaEvent_t ev_start = y_free[2], ev_end = y_free[3];
+  const HostChunks C = host_chunks(n_dn);
+  cudaStream_t si = f->copy_stream, so = f->copy_out_stream;
+
+  auto copy_in = [&](int64_t v) -> int {
+    const int p = (int)(v & 1);
+    if (v >= 2) HUB_CUDA(cudaStreamWaitEvent(si, x_free[p], 0));
+    for (int c = 0; c < C.nci; ++c) {
+      HUB_CUDA(cudaMemcpyAsync(xd[p] + C.bi[c] * n_up, x_host + v * D + C.bi[c] * n_up,
+                               sizeof(double) * (C.bi[c + 1] - C.bi[c]) * n_up, cudaMemcpyHostToDevice, si));
+      HUB_CUDA(cudaEventRecord(ev_in[p * kHostChunks + c], si));
+    }
+    return HUB_OK;
+  };
+  auto run = [&]() -> int {
+    int rc;
+    HUB_CUDA(cudaEventRecord(ev_start, s));
+    HUB_CUDA(cudaStreamWaitEvent(si, ev_start, 0));
+    HUB_CUDA(cudaStreamWaitEvent(so, ev_start, 0));
+    if ((rc = copy_in(0))) return rc;
+    for (int64_t v = 0; v < n_vec; ++v) {
+      const int p = (int)(v & 1);
+      if ((rc = host_pass1(h, f, xd[p], C.bi, C.nci, C.per, ev_in + p * kHostChunks, s))) return rc;
+      if (v + 1 < n_vec && (rc = copy_in(v + 1))) return rc;
+      HUB_CUDA(cudaStreamSynchronize(s));
+      const int route = *f->h_flag;
+      if (route == 1 && (rc = host_redo(h, f, xd[p], s))) return rc;
+      if (v >= 2) HUB_CUDA(cudaStreamWaitEvent(s, y_free[p], 0));
+      if (route == 2) {   // outside the double-float window: the FP64 kernel, one copy back
+        if ((rc = f64_apply(h, xd[p], yd[p], nullptr, s))) return rc;
+        HUB_CUDA(cudaEventRecord(x_free[p], s));
+        HUB_CUDA(cudaEventRecord(ev_out[0], s));
+        HUB_CUDA(cudaStreamWaitEvent(so, ev_out[0], 0));
+        HUB_CUDA(cudaMemcpyAsync(y_host + v * D, yd[p], sizeof(double) * D, cudaMemcpyDeviceToHost, so));
+      } else {
+        HUB_CUDA(cudaEventRecord(x_free[p], s));
+        if ((rc = host_pass2(h, f, yd[p], y_host + v * D, C.bo, C.nco, C.per, ev_out, s, so))) return rc;
+      }
+      HUB_CUDA(cudaEventRecord(y_free[p], so));
+    }
+    HUB_CUDA(cudaEventRecord(ev_end, so));
+    HUB_CUDA(cudaStreamWaitEvent(s, ev_end, 0));
+    HUB_CUDA(cudaStreamSynchronize(s));
+    return HUB_OK;
+  };
+  rc = run();
+  if (rc) {   // no copy into or out of the caller's buffers may outlive the call
+    cudaStreamSynchronize(si);
+    cudaStreamSynchronize(so);
+    cudaStreamSynchronize(s);
+  }
+  return rc;
 }
 
 int fast_check_error(hub_ctx *h) {

@@ -99,8 +99,9 @@ struct hub_ctx {
   int64_t partials_n = 0;
   std::vector<double> alpha, beta;
 
-  // host-buffer apply
+  // host-buffer apply; the second pair alternates with the first in hub_apply_host_many
   double *hx = nullptr, *hy = nullptr;
+  double *hx2 = nullptr, *hy2 = nullptr;
 
   // |x0| of the last Lanczos run (the continued fraction of the Green's function needs it)
   double start_norm = 0.0;
@@ -166,6 +167,11 @@ int fast_build(hub_ctx *h);
 void fast_release(hub_ctx *h);
 int fast_apply_f64(hub_ctx *h, const double *x, double *y, cudaStream_t s);
 int fast_apply_host(hub_ctx *h, const double *x_host, double *y_host, double *xd, double *yd, cudaStream_t s);
+// True when the fast path's host-buffer apply runs in row chunks (staged pass 1, enough rows),
+// the case fast_apply_host_many pipelines across vectors.
+bool fast_host_pipelined(const hub_ctx *h);
+int fast_apply_host_many(hub_ctx *h, int64_t n_vec, const double *x_host, double *y_host, double *const xd[2],
+                         double *const yd[2], cudaStream_t s);
 int fast_lanczos(hub_ctx *h, const double *x0, int maxit, double tol, double *E0, double *psi_out, int *iters,
                  cudaStream_t s);
 int fast_check_error(hub_ctx *h);

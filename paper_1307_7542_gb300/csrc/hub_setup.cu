@@ -553,6 +553,8 @@ extern "C" void hub_free(hub_t h) {
   if (h->h_scal) cudaFreeHost(h->h_scal);
   dev_free(h->hx);
   dev_free(h->hy);
+  dev_free(h->hx2);
+  dev_free(h->hy2);
   fast_release(h);
   k0_release(h);
   small_release(h);

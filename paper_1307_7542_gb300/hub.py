@@ -45,6 +45,7 @@ SIGNATURES = {
     "hub_get_csr": (_i, [_p, _i, _p, _p, _p]),
     "hub_apply": (_i, [_p, _p, _p, _p]),
     "hub_apply_host": (_i, [_p, _p, _p, _p]),
+    "hub_apply_host_many": (_i, [_p, _i64, _p, _p, _p]),
     "hub_lanczos_ground": (_i, [_p, _p, _i, _d, ctypes.POINTER(_d), _p, ctypes.POINTER(_i), _p]),
     "hub_lanczos_coeffs": (_i, [_p, _p, _p, _i, ctypes.POINTER(_i)]),
     "hub_lanczos_spectrum": (_i, [_p, _p, _i, _i, _p, _p, ctypes.POINTER(_i), _p]),
@@ -173,6 +174,11 @@ def hub_apply(h, x, y, stream=None):
 
 def hub_apply_host(h, x, y, stream=None):
     _check(lib().hub_apply_host(h, _ptr(x), _ptr(y), _stream(stream)))
+
+
+def hub_apply_host_many(h, n_vec, x, y, stream=None):
+    """x, y: host arrays holding n_vec vectors one after another (e.g. shape (n_vec, D))."""
+    _check(lib().hub_apply_host_many(h, n_vec, _ptr(x), _ptr(y), _stream(stream)))
 
 
 def hub_lanczos_ground(h, x0, maxit, tol, psi=None, stream=None):

@@ -80,6 +80,7 @@ def test_null_handles_are_refused(libpath):
         "hub_set_U": lambda: L.hub_set_U(None, 1, None),
         "hub_apply": lambda: L.hub_apply(None, None, None, None),
         "hub_apply_host": lambda: L.hub_apply_host(None, None, None, None),
+        "hub_apply_host_many": lambda: L.hub_apply_host_many(None, 2, None, None, None),
         "hub_lanczos_ground": lambda: L.hub_lanczos_ground(None, None, 10, 0.0, ctypes.byref(d), None,
                                                            ctypes.byref(n), None),
         "hub_lanczos_coeffs": lambda: L.hub_lanczos_coeffs(None, None, None, 0, ctypes.byref(n)),

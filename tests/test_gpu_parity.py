@@ -473,6 +473,85 @@ def test_apply_host_pipelined(hub, case):
         m.close()
 
 
+def _singles(hub, m, X):
+    """One hub_apply_host call per row of X (pinned buffers)."""
+    out = []
+    for v in range(X.shape[0]):
+        xh = torch.from_numpy(np.ascontiguousarray(X[v])).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        hub.hub_apply_host(m.h, xh, yh)
+        out.append(yh.numpy().copy())
+    return np.stack(out)
+
+
+def test_apply_host_many_pipelined(hub):
+    """hub_apply_host_many on the fast path, 12-site ring (6, 6), 924 rows: five vectors in one
+    call (both buffer pairs used twice; one vector whose largest exponent is in its last row
+    chunk, one outside the double-float window, routed to the FP64 kernel) equal one
+    hub_apply_host call per vector bit for bit, also in place; the first equals the oracle
+    within the per-entry bound."""
+    M, nu, nd = 12, 6, 6
+    bonds = W.ring_bonds(M)
+    m = hub.Hubbard(M, nu, nd, bonds, 1.0, 4.0)
+    om = O.Model(M, bonds, 1.0, 4.0)
+    try:
+        D, n_up = m.D, m.count_up
+        X = np.stack([W.normal(30 + v, D) for v in range(5)])
+        X[1, -2 * n_up:] *= 1e6                     # largest exponent in the last input chunk
+        X[2, D // 3] = 1e280                        # above the window's largest |x|: FP64 kernel
+        xh = torch.from_numpy(X).pin_memory()
+        yh = torch.empty_like(xh).pin_memory()
+        hub.hub_apply_host_many(m.h, 5, xh, yh)
+        ref = _singles(hub, m, X)
+        for v in range(5):
+            assert np.array_equal(yh[v].numpy(), ref[v]), v
+        B = O.basis(M, nu, nd)
+        assert_entrywise(yh[0].numpy(), O.apply(om, B, X[0]), abs_bound(om, B, X[0]))
+        # in place: the results overwrite the inputs
+        zh = xh.clone().pin_memory()
+        hub.hub_apply_host_many(m.h, 5, zh, zh)
+        assert torch.equal(zh, yh)
+        # two vectors, then three: buffers of an earlier call reused
+        hub.hub_apply_host_many(m.h, 2, xh[3:], yh[3:])
+        assert np.array_equal(yh[3:].numpy(), ref[3:])
+    finally:
+        m.close()
+
+
+def test_apply_host_many_other_paths_and_arguments(hub):
+    """Off the pipelined path (FP64 model; a sector with fewer than 16 rows) the call is one
+    hub_apply_host per vector: the same results bit for bit.  n_vec = 0 leaves y untouched;
+    a negative count, NULL arrays and partly overlapping arrays are refused."""
+    w = _random_workload(9, 4, 3, 61)
+    m = _gpu_model(hub, w)
+    try:
+        X = np.stack([W.normal(40 + v, m.D) for v in range(3)])
+        Y = np.empty_like(X)
+        hub.hub_apply_host_many(m.h, 3, X, Y)
+        assert np.array_equal(Y, _singles(hub, m, X))
+        Y0 = Y.copy()
+        hub.hub_apply_host_many(m.h, 0, X, Y)
+        assert np.array_equal(Y, Y0)
+        for args in [(-1, X, Y), (2, None, Y), (2, X, None)]:
+            with pytest.raises(hub.HubError) as e:
+                hub.hub_apply_host_many(m.h, *args)
+            assert e.value.code == hub.HUB_ERR_ARG
+        flat = np.zeros(4 * m.D)
+        with pytest.raises(hub.HubError) as e:
+            hub.hub_apply_host_many(m.h, 2, flat[: 2 * m.D], flat[m.D:])
+        assert e.value.code == hub.HUB_ERR_ARG
+    finally:
+        m.close()
+    m = hub.Hubbard(5, 2, 2, W.ring_bonds(5), 1.0, 4.0)      # C(5, 2) = 10 rows: one piece
+    try:
+        X = np.stack([W.normal(50 + v, m.D) for v in range(3)])
+        Y = np.empty_like(X)
+        hub.hub_apply_host_many(m.h, 3, X, Y)
+        assert np.array_equal(Y, _singles(hub, m, X))
+    finally:
+        m.close()
+
+
 # --------------------------------------------------------------------------- autograd
 
 def test_autograd_apply(hub):
