@@ -380,7 +380,8 @@ def extras(hub, W, torch):
         r["as_fp64_fma_frac_of_fp64_issue"] = r["terms_per_s"] / FP64_INSTR_PEAK
     # (6) the 8-site ring at half filling (D = 4900), E0 to |dE0| < 1e-12 from a seed-0 normal
     # start vector: latency-bound; through hub_lanczos_ground (the single-launch small-sector
-    # solver: one cooperative kernel per batch of eight iterations; and, with it turned off, the
+    # solver: one thread-block-cluster launch per batch of eight iterations at this size; and,
+    # with it turned off, the
     # multi-kernel driver with its per-iteration launches and read-backs) and as a single job of
     # the persistent batched solver (one launch; it draws its own start vector)
     bonds8 = np.array([(i, (i + 1) % 8) for i in range(8)], dtype=np.int32)
@@ -413,7 +414,7 @@ def extras(hub, W, torch):
         reps_b.append(time.perf_counter() - t0)
     out["ring8"] = {"workload": "ring M=8, (4,4), D=4900, t=1, U=4, to |dE0| < 1e-12",
                     "E0": r8["E0"], "iterations": r8["iters"], "lanczos_ground_ms": 1000 * min(reps8),
-                    "lanczos_ground_path": "single-launch small-sector solver (FP64, cooperative kernel)",
+                    "lanczos_ground_path": "single-launch small-sector solver (FP64, one 16-CTA cluster launch per 8 iterations)",
                     "multi_kernel_driver_E0": r8m["E0"], "multi_kernel_driver_iterations": r8m["iters"],
                     "multi_kernel_driver_ms": 1000 * min(reps8m),
                     "batched_single_job_E0": float(Eb[0]), "batched_single_job_iterations": int(itb[0]),
