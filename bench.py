@@ -381,9 +381,9 @@ def extras(hub, W, torch):
     # (6) the 8-site ring at half filling (D = 4900), E0 to |dE0| < 1e-12 from a seed-0 normal
     # start vector: latency-bound; through hub_lanczos_ground (the single-launch small-sector
     # solver: one thread-block-cluster launch per batch of eight iterations at this size; and,
-    # with it turned off, the
-    # multi-kernel driver with its per-iteration launches and read-backs) and as a single job of
-    # the persistent batched solver (one launch; it draws its own start vector)
+    # with it turned off, the multi-kernel driver with its per-iteration launches and
+    # read-backs) and as a single job of the persistent batched solver (one launch; it draws
+    # its own start vector)
     bonds8 = np.array([(i, (i + 1) % 8) for i in range(8)], dtype=np.int32)
     m8 = hub.Hubbard(8, 4, 4, bonds8, 1.0, 4.0)
     x8 = torch.from_numpy(W.normal(0, m8.D)).cuda()
