@@ -170,7 +170,8 @@ extern "C" int hub_apply_host_many(hub_t h, int64_t n_vec, const double *x_host,
   const int64_t D = vec_len(h);
   if (D > 0 && n_vec > (int64_t)(SIZE_MAX / sizeof(double)) / D)
     return fail(HUB_ERR_ARG, "hub_apply_host_many: vector count too large");
-  if (x_host != y_host && x_host < y_host + n_vec * D && y_host < x_host + n_vec * D)
+  const uintptr_t xa = (uintptr_t)x_host, ya = (uintptr_t)y_host, bytes = (uintptr_t)(n_vec * D) * sizeof(double);
+  if (xa != ya && xa < ya + bytes && ya < xa + bytes)
     return fail(HUB_ERR_ARG, "hub_apply_host_many: x and y overlap without being the same array");
   if (n_vec == 1 || !use_fast(h) || !fast_host_pipelined(h)) {   // one call per vector
     for (int64_t v = 0; v < n_vec; ++v)
