@@ -98,15 +98,30 @@ __device__ __forceinline__ float2 upk2(f2x r) {
   asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(r));
   return make_float2(a, b);
 }
+// HUB_F32X2 0 issues two scalar round-to-nearest FP32 operations instead of one packed
+// instruction: the same results bit for bit (each lane is one IEEE add either way).
+#ifndef HUB_F32X2
+#define HUB_F32X2 1
+#endif
 __device__ __forceinline__ f2x add2(f2x a, f2x b) {
+#if HUB_F32X2
   f2x r;
   asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
+#else
+  const float2 u = upk2(a), v = upk2(b);
+  return pk2(__fadd_rn(u.x, v.x), __fadd_rn(u.y, v.y));
+#endif
 }
 __device__ __forceinline__ f2x sub2(f2x a, f2x b) {
+#if HUB_F32X2
   f2x r;
   asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
   return r;
+#else
+  const float2 u = upk2(a), v = upk2(b);
+  return pk2(__fsub_rn(u.x, v.x), __fsub_rn(u.y, v.y));
+#endif
 }
 
 __device__ __forceinline__ f2x bcast2(float a) { return pk2(a, a); }
