@@ -454,6 +454,22 @@ class Hubbard:
         hub_apply(self.h, x, y, stream)
         return y
 
+    def apply_host(self, x, y=None, stream=None):
+        """y = H x on host arrays (numpy arrays or CPU tensors; page-locked memory copies
+        fastest): one vector of shape (D,) through hub_apply_host, or n vectors of shape
+        (n, D) in one hub_apply_host_many call.  y defaults to a new array like x."""
+        if y is None:
+            y = x.new_empty(tuple(x.shape)) if hasattr(x, "new_empty") else np.empty_like(x)
+        if tuple(y.shape) != tuple(x.shape):
+            raise ValueError(f"apply_host: x has shape {tuple(x.shape)}, y {tuple(y.shape)}")
+        if len(x.shape) == 1:
+            hub_apply_host(self.h, x, y, stream)
+        elif len(x.shape) == 2:
+            hub_apply_host_many(self.h, int(x.shape[0]), x, y, stream)
+        else:
+            raise ValueError("apply_host: x must have one or two dimensions")
+        return y
+
     def ground(self, x0=None, maxit=300, tol=1e-12, want_psi=False, stream=None):
         import torch
         psi = torch.empty(self.D, dtype=torch.float64, device="cuda") if want_psi else None

@@ -43,3 +43,29 @@ def test_ensure_params_leaves_a_momentum_sector():
     m.D = 10                                          # a momentum sector is active
     assert m.ensure_params(np.ones(4), np.full(4, 4.0), None) is True
     assert len(m.calls) == 2
+
+
+def test_apply_host_dispatch(monkeypatch):
+    """Hubbard.apply_host: a 1-D array goes to hub_apply_host, a 2-D array to
+    hub_apply_host_many with the row count; y is allocated like x; bad shapes are refused."""
+    import pytest
+    calls = []
+    monkeypatch.setattr(H, "hub_apply_host", lambda h, x, y, s=None: calls.append(("one", h, x.shape, y.shape)))
+    monkeypatch.setattr(H, "hub_apply_host_many",
+                        lambda h, n, x, y, s=None: calls.append(("many", h, n, x.shape, y.shape)))
+    m = _stub()
+    m.h = "handle"          # a marker only: cleared below so that close() frees nothing
+    try:
+        y = m.apply_host(np.zeros(36))
+        assert y.shape == (36,) and calls[-1] == ("one", "handle", (36,), (36,))
+        y = m.apply_host(np.zeros((3, 36)))
+        assert y.shape == (3, 36) and calls[-1] == ("many", "handle", 3, (3, 36), (3, 36))
+        out = np.empty((2, 36))
+        assert m.apply_host(np.zeros((2, 36)), out) is out
+        with pytest.raises(ValueError):
+            m.apply_host(np.zeros((2, 36)), np.empty((3, 36)))
+        with pytest.raises(ValueError):
+            m.apply_host(np.zeros((2, 3, 6)))
+        assert len(calls) == 3
+    finally:
+        m.h = None
